@@ -1,0 +1,540 @@
+/*
+ * FP64 CPU oracle of one Risk-Aware MPPI (RA-MPPI) control update.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA path; it is a plain,
+ * slow, obviously-correct restatement of the method for checking it.
+ *
+ * What it computes (RA-MPPI, Yin, Zhang, Tsiotras; arXiv 2209.12842):
+ *   Algorithm 1, one pass of the while-loop body:
+ *     - sample K control sequences U^k = V + eps^k (or eps^k for the last
+ *       eta fraction), eps ~ N(0, Sigma)                      (Sec. II, Alg. 1)
+ *     - roll out each one on the nominal dynamics F (Eq. 1) and form
+ *       S_k = phi(x_T) + sum_t q(x_t) + gamma v_t' Sigma^-1 u_t      (Eq. 3)
+ *     - roll out M disturbed trajectories per sample on
+ *       x~_{t+1} = F(x~_t, u_t) + w_t and form L = sum_t l(x~_t)  (Eqs. 6, 9)
+ *     - scale the risk costs L_a = B (L - mean) + mean        (Eqs. 18, 19)
+ *     - CVaR_alpha of the M scaled costs                     (Eqs. 10-13)
+ *     - S~_k = S_k + A CVaR 1{CVaR > C_u}                    (Eqs. 14-16)
+ *   then the softmin-weighted update
+ *     w_k = exp(-(S~_k - min S~)/lambda), V+ = sum w U / sum w (Eqs. 4, 5, 17)
+ *
+ * Letters follow the implementation: K samples (the paper's M), M disturbed
+ * rollouts per sample (the paper's N), T horizon steps (the paper's K).
+ *
+ * Readings of points the paper leaves open (each is listed with its reason
+ * in the design notes):
+ *   - CVaR estimator: the fractional sorted-tail (Rockafellar-Uryasev) form
+ *       CVaR = [(j - alpha M) L_(j) + sum_{i>j} L_(i)] / ((1 - alpha) M),
+ *     j = ceil(alpha M), is the default; the literal tail mean over
+ *     {L >= VaR} (Eqs. 12, 13) is the alternative mode.  VaR = L_(j) (Eq. 11)
+ *   - the mean in Eq. 19 divides by M (the text calls it the mean)
+ *   - q and l are charged on x_0 .. x_{T-1}; phi on x_T
+ *   - controls are clipped to the box after the noise is added
+ *   - the control-cost weight uses 1/sigma^2 and is 0 where sigma = 0
+ *   - the random numbers come from Philox4x32-10 (Salmon, Moraes, Dror,
+ *     Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11), keyed by
+ *     (seed, iteration) with counter (t | draw << 16, m, k, instance);
+ *     m = 0xFFFFFFFF marks control noise, (m, k) = (0xFFFFFFFE, 0xFFFFFFFF)
+ *     the simulated plant's noise
+ *
+ * Parity status: every function below is pinned by the CPU tests against
+ * closed forms, invariants, brute force or an independent library routine;
+ * none is unpinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+enum { ORC_KIN = 0, ORC_DYN = 1, ORC_LIN = 2 };
+enum { ORC_GAUSS = 0, ORC_LAPLACE_MIX = 1 };
+enum { ORC_OBS_INDICATOR = 0, ORC_OBS_SOFTPLUS = 1 };
+enum { ORC_CVAR_RU = 0, ORC_CVAR_TCE = 1 };
+enum { ORC_R_DEV = 1, ORC_R_SPEED = 2, ORC_R_OBS = 4, ORC_R_BDRY = 8, ORC_R_LIN = 16 };
+
+typedef struct {
+  int32_t model, K, M, T, substeps;
+  int32_t noise_type, obs_mode, cvar_mode;
+  uint32_t risk_mask;
+  int32_t n_threads;
+  double dt;
+  double model_params[8];
+  double sigma_u[2], u_lo[2], u_hi[2];
+  double w_scale[4];
+  double mix_p, mix_scale;
+  double w_dev, w_speed, v_target, gamma, w_obs, w_bdry, c4, c5, c_lin;
+  double kappa;
+  double track_straight, track_radius, track_half_width;
+  double lam, alpha, A, B, C_u, eta;
+  double band_delta;
+  uint64_t seed;
+  uint64_t iteration;
+  uint32_t instance_id;
+  uint32_t pad_;
+} orc_problem;
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (SC'11): 10 rounds of the 4x32 Philox S-box with the   */
+/* multipliers 0xD2511F53, 0xCD9E8D57 and the Weyl key increments       */
+/* 0x9E3779B9, 0xBB67AE85.                                               */
+/* ------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void make_key(const orc_problem* p, uint64_t iteration, uint32_t key[2]) {
+  key[0] = (uint32_t)(p->seed & 0xFFFFFFFFu);
+  key[1] = (uint32_t)(p->seed >> 32) ^ (uint32_t)(iteration & 0xFFFFFFFFu);
+}
+
+/* uniform in (0, 1): (x + 1/2) 2^-32, exact in double */
+double orc_uniform(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+/* Box-Muller: two independent standard normals from two words */
+void orc_box_muller(uint32_t a, uint32_t b, double out[2]) {
+  double u1 = orc_uniform(a), u2 = orc_uniform(b);
+  double rad = sqrt(-2.0 * log(u1));
+  out[0] = rad * cos(2.0 * ORC_PI * u2);
+  out[1] = rad * sin(2.0 * ORC_PI * u2);
+}
+
+/* inverse of erfc on (0, 1]: the y >= 0 with erfc(y) = v.  Newton steps
+ * safeguarded by a bisection bracket; stops at double-precision resolution. */
+double orc_erfcinv(double v) {
+  if (!(v > 0.0)) return INFINITY;
+  if (v >= 1.0) return 0.0;
+  double lo = 0.0, hi = 27.0; /* erfc(27) < 1e-300 */
+  double y = sqrt(-log(v));   /* start inside the bracket */
+  if (y > hi) y = hi;
+  for (int it = 0; it < 200; ++it) {
+    double f = erfc(y) - v; /* decreasing in y */
+    if (f > 0.0) lo = y; else hi = y;
+    double dfdy = -2.0 / sqrt(ORC_PI) * exp(-y * y);
+    double ny = (dfdy != 0.0) ? y - f / dfdy : 0.5 * (lo + hi);
+    if (!(ny > lo && ny < hi)) ny = 0.5 * (lo + hi);
+    if (fabs(ny - y) <= 1e-16 * (1.0 + y) || hi - lo <= 1e-16 * (1.0 + y)) return ny;
+    y = ny;
+  }
+  return y;
+}
+
+/* Heavy-tailed slot value: Laplace(0, b) by its inverse CDF, replaced with
+ * probability p by N(0, (mix_scale b)^2) by the Gaussian inverse CDF.  Both
+ * use the same uniform a = (x + 1/2) 2^-32 through the tail mass
+ * v = 2 min(a, 1 - a) and the sign of a - 1/2; the branch is taken when the
+ * selector word is below floor(p 2^32). */
+double orc_mix_value(uint32_t sel, uint32_t word, double b, double p, double mix_scale) {
+  uint32_t hi = word >> 31;
+  uint32_t r = hi ? ~word : word;                 /* in [0, 2^31) */
+  double v = ((double)r + 0.5) * (1.0 / 2147483648.0);
+  double sgn = hi ? 1.0 : -1.0;
+  uint32_t thresh = (uint32_t)floor(p * 4294967296.0 > 4294967295.0 ? 4294967295.0 : p * 4294967296.0);
+  if (sel < thresh) return sgn * (mix_scale * b) * sqrt(2.0) * orc_erfcinv(v);
+  return sgn * (-b * log(v));
+}
+
+static int nx_of(int model) { return model == ORC_KIN ? 4 : model == ORC_DYN ? 6 : 1; }
+static int nu_of(int model) { return model == ORC_LIN ? 1 : 2; }
+static int nslots_of(int model) { return model == ORC_KIN ? 4 : model == ORC_DYN ? 3 : 1; }
+/* which state component noise slot s perturbs */
+static int slot_dim(int model, int s) { return model == ORC_DYN ? 3 + s : s; }
+
+/* control noise eps^k_t (Alg. 1: "Sample eps^m"), Sigma = diag(sigma_u^2) */
+void orc_control_noise(const orc_problem* p, int32_t k, int32_t t, double eps[2]) {
+  uint32_t key[2], ctr[4], w[4];
+  make_key(p, p->iteration, key);
+  ctr[0] = (uint32_t)t; ctr[1] = 0xFFFFFFFFu; ctr[2] = (uint32_t)k; ctr[3] = p->instance_id;
+  orc_philox(ctr, key, w);
+  double z[2];
+  orc_box_muller(w[0], w[1], z);
+  eps[0] = p->sigma_u[0] * z[0];
+  eps[1] = p->sigma_u[1] * z[1];
+}
+
+/* process noise w_t added to the state (Eq. 6 with F~ = F + w, so Eq. 7 holds) */
+static void noise_words(const orc_problem* p, uint64_t iteration, uint32_t c1, uint32_t c2,
+                        int32_t t, uint32_t draw, uint32_t w[4]) {
+  uint32_t key[2], ctr[4];
+  make_key(p, iteration, key);
+  ctr[0] = (uint32_t)t | (draw << 16); ctr[1] = c1; ctr[2] = c2; ctr[3] = p->instance_id;
+  orc_philox(ctr, key, w);
+}
+
+static void process_noise_at(const orc_problem* p, uint64_t iteration, uint32_t c1, uint32_t c2,
+                             int32_t t, double out[4]) {
+  int ns = nslots_of(p->model);
+  for (int s = 0; s < 4; ++s) out[s] = 0.0;
+  if (p->noise_type == ORC_GAUSS) {
+    uint32_t w[4];
+    noise_words(p, iteration, c1, c2, t, 0, w);
+    double z[4];
+    orc_box_muller(w[0], w[1], z);
+    orc_box_muller(w[2], w[3], z + 2);
+    for (int s = 0; s < ns; ++s) out[s] = p->w_scale[s] * z[s];
+  } else {
+    uint32_t sel[4], val[4];
+    noise_words(p, iteration, c1, c2, t, 0, sel);
+    noise_words(p, iteration, c1, c2, t, 1, val);
+    for (int s = 0; s < ns; ++s)
+      out[s] = (p->w_scale[s] == 0.0) ? 0.0
+                                      : orc_mix_value(sel[s], val[s], p->w_scale[s], p->mix_p, p->mix_scale);
+  }
+}
+
+void orc_process_noise(const orc_problem* p, int32_t k, int32_t m, int32_t t, double out[4]) {
+  process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Dynamics F (Eq. 1)                                                   */
+/* ------------------------------------------------------------------ */
+static void dyn_deriv(const double* mp, const double* x, const double* u, double* f) {
+  const double m = mp[0], Iz = mp[1], lf = mp[2], lr = mp[3];
+  const double Bt = mp[4], Ct = mp[5], Dt = mp[6], vfloor = mp[7];
+  const double g = 9.81;
+  double psi = x[2], vx = x[3], vy = x[4], r = x[5];
+  double delta = u[0], a = u[1];
+  double Fzf = m * g * lr / (lf + lr);
+  double Fzr = m * g * lf / (lf + lr);
+  double vxs = vx > vfloor ? vx : vfloor;
+  double alpha_f = delta - atan2(vy + lf * r, vxs);
+  double alpha_r = -atan2(vy - lr * r, vxs);
+  double Fyf = Dt * Fzf * sin(Ct * atan(Bt * alpha_f));
+  double Fyr = Dt * Fzr * sin(Ct * atan(Bt * alpha_r));
+  f[0] = vx * cos(psi) - vy * sin(psi);
+  f[1] = vx * sin(psi) + vy * cos(psi);
+  f[2] = r;
+  f[3] = a - Fyf * sin(delta) / m + r * vy;
+  f[4] = (Fyf * cos(delta) + Fyr) / m - r * vx;
+  f[5] = (lf * Fyf * cos(delta) - lr * Fyr) / Iz;
+}
+
+/* one control period of F: `substeps` explicit-Euler (kinematic, linear) or
+ * Heun/RK2 (dynamic) steps of dt / substeps */
+void orc_dynamics(const orc_problem* p, const double* x, const double* u, double* xn) {
+  int nx = nx_of(p->model);
+  double s[6];
+  for (int i = 0; i < nx; ++i) s[i] = x[i];
+  int n = p->substeps > 0 ? p->substeps : 1;
+  double h = p->dt / n;
+  for (int it = 0; it < n; ++it) {
+    if (p->model == ORC_KIN) {
+      double L = p->model_params[0];
+      double px = s[0], py = s[1], psi = s[2], v = s[3];
+      s[0] = px + h * v * cos(psi);
+      s[1] = py + h * v * sin(psi);
+      s[2] = psi + h * v * tan(u[0]) / L;
+      s[3] = v + h * u[1];
+    } else if (p->model == ORC_DYN) {
+      double k1[6], k2[6], xp[6];
+      dyn_deriv(p->model_params, s, u, k1);
+      for (int i = 0; i < 6; ++i) xp[i] = s[i] + h * k1[i];
+      dyn_deriv(p->model_params, xp, u, k2);
+      for (int i = 0; i < 6; ++i) s[i] = s[i] + 0.5 * h * (k1[i] + k2[i]);
+    } else {
+      s[0] = s[0] + h * u[0];
+    }
+  }
+  for (int i = 0; i < nx; ++i) xn[i] = s[i];
+}
+
+/* ------------------------------------------------------------------ */
+/* Track geometry (stadium): e lateral deviation (outward +), s arc     */
+/* length counter-clockwise from (0, -R), d distance to the boundary.   */
+/* ------------------------------------------------------------------ */
+void orc_track(const orc_problem* p, double px, double py, double out[3]) {
+  double S = p->track_straight, R = p->track_radius, hw = p->track_half_width;
+  double half = 0.5 * S;
+  double total = 2.0 * S + 2.0 * ORC_PI * R;
+  double e, s;
+  if (fabs(px) <= half) {
+    if (py < 0.0) {
+      e = -py - R;
+      s = px >= 0.0 ? px : total + px;
+    } else {
+      e = py - R;
+      s = half + ORC_PI * R + (half - px);
+    }
+  } else if (px > half) {
+    double dx = px - half;
+    e = sqrt(dx * dx + py * py) - R;
+    s = half + R * (atan2(py, dx) + 0.5 * ORC_PI);
+  } else {
+    double dx = px + half;
+    e = sqrt(dx * dx + py * py) - R;
+    double th = atan2(py, dx);
+    double phi = th > 0.0 ? th - 0.5 * ORC_PI : th + 1.5 * ORC_PI;
+    s = half + ORC_PI * R + S + R * phi;
+  }
+  out[0] = e;
+  out[1] = s;
+  out[2] = hw - fabs(e);
+}
+
+/* ------------------------------------------------------------------ */
+/* Running cost q (Eq. 20) and risk cost l (Eq. 9)                     */
+/* ------------------------------------------------------------------ */
+/* obstacle term: sum_i 1{d_i < r_i + shift} (Eq. 22) or the softplus
+ * barrier sum_i softplus(kappa (r_i - d_i)) / kappa */
+static double obstacle_term(const orc_problem* p, const double* x, const double* obs, int n_obs,
+                            double shift) {
+  double acc = 0.0;
+  for (int i = 0; i < n_obs; ++i) {
+    double dx = x[0] - obs[3 * i + 0], dy = x[1] - obs[3 * i + 1];
+    double d = sqrt(dx * dx + dy * dy);
+    double r = obs[3 * i + 2];
+    if (p->obs_mode == ORC_OBS_INDICATOR) {
+      if (d < r + shift) acc += 1.0;
+    } else {
+      double z = p->kappa * (r - d);
+      double sp = z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
+      acc += sp / p->kappa;
+    }
+  }
+  return acc;
+}
+
+/* cost of state x with the terms in `mask`; `shift` moves the obstacle
+ * indicator threshold (0 for the exact cost, -/+ delta for band bounds) */
+static double state_cost(const orc_problem* p, const double* x, const double* obs, int n_obs,
+                         uint32_t mask, double shift) {
+  double c = 0.0;
+  if (p->model == ORC_LIN) {
+    if (mask & ORC_R_LIN) c += p->c_lin * x[0];
+    return c;
+  }
+  double tr[3];
+  orc_track(p, x[0], x[1], tr);
+  if (mask & ORC_R_DEV) c += p->w_dev * tr[0] * tr[0];
+  if (mask & ORC_R_SPEED) c += p->w_speed * (x[3] - p->v_target) * (x[3] - p->v_target);
+  if (mask & ORC_R_OBS) c += p->w_obs * obstacle_term(p, x, obs, n_obs, shift);
+  if (mask & ORC_R_BDRY) {
+    double b = atan(-100.0 * tr[2]) / ORC_PI + 0.5;
+    c += p->w_bdry * (b > 0.0 ? b : 0.0);
+  }
+  if (mask & ORC_R_LIN) c += p->c_lin * x[0];
+  return c;
+}
+
+/* terminal cost phi(x) = c4 - c5 s(x) (Eq. 23) */
+static double terminal_cost(const orc_problem* p, const double* x) {
+  if (p->model == ORC_LIN) return 0.0;
+  double tr[3];
+  orc_track(p, x[0], x[1], tr);
+  return p->c4 - p->c5 * tr[1];
+}
+
+/* ------------------------------------------------------------------ */
+/* CVaR of a set of M risk costs: Scal, then Max(., 1 - alpha), then     */
+/* Average (Alg. 1; Eqs. 10-13, 18, 19)                                  */
+/* ------------------------------------------------------------------ */
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+double orc_cvar(const double* L, int32_t M, double alpha, double B, int32_t mode) {
+  /* a non-finite risk cost (NaN or inf) ranks as the worst outcome: the
+   * sample's CVaR is +inf, so it receives zero weight in the update */
+  for (int n = 0; n < M; ++n)
+    if (!isfinite(L[n])) return INFINITY;
+  double* La = (double*)malloc(sizeof(double) * (size_t)M);
+  double mean = 0.0;
+  for (int n = 0; n < M; ++n) mean += L[n];
+  mean /= (double)M;
+  for (int n = 0; n < M; ++n) La[n] = B * (L[n] - mean) + mean;
+  qsort(La, (size_t)M, sizeof(double), cmp_double);
+  double aM = alpha * (double)M; /* exact for float32 alpha and M < 2^29 */
+  int j = (int)ceil(aM);
+  if (j < 1) j = 1;
+  if (j > M) j = M;
+  double var = La[j - 1];
+  double out;
+  if (mode == ORC_CVAR_RU) {
+    double tail = ((double)j - aM) * var;
+    for (int i = j; i < M; ++i) tail += La[i];
+    out = tail / ((1.0 - alpha) * (double)M);
+  } else {
+    double s = 0.0;
+    int c = 0;
+    for (int n = 0; n < M; ++n)
+      if (La[n] >= var) { s += La[n]; ++c; }
+    out = s / (double)c;
+  }
+  free(La);
+  return out;
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-sample stage (Alg. 1 loop body for sample k)                     */
+/* ------------------------------------------------------------------ */
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static int n_warm_of(const orc_problem* p) {
+  /* Alg. 1: sample k keeps the mean control when k < (1 - eta) K */
+  return (int)ceil((1.0 - p->eta) * (double)p->K);
+}
+
+/* Outputs for sample index i of the list ks[] (all optional except none):
+ *   U[i][T][nu], S[i], L[i][M], cvar[i], S_tilde[i],
+ *   band bounds S_lo/S_hi, cvar_lo/cvar_hi (indicator threshold r -/+ delta) */
+int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, const double* obs,
+                    int32_t n_obs, const int32_t* ks, int32_t nk, double* U, double* S, double* L,
+                    double* cvar, double* S_tilde, double* S_lo, double* S_hi, double* cvar_lo,
+                    double* cvar_hi) {
+  const int nx = nx_of(p->model), nu = nu_of(p->model), T = p->T, M = p->M;
+  const int n_warm = n_warm_of(p);
+  double inv_sig2[2];
+  for (int j = 0; j < 2; ++j) inv_sig2[j] = p->sigma_u[j] > 0.0 ? 1.0 / (p->sigma_u[j] * p->sigma_u[j]) : 0.0;
+  int nthreads = p->n_threads > 0 ? p->n_threads : 1;
+  (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  for (int i = 0; i < nk; ++i) {
+    const int k = ks[i];
+    double* Uk = (double*)malloc(sizeof(double) * (size_t)T * nu);
+    double* Lm = (double*)malloc(sizeof(double) * (size_t)M * 3);
+    /* sample the control sequence */
+    for (int t = 0; t < T; ++t) {
+      double eps[2];
+      orc_control_noise(p, k, t, eps);
+      for (int j = 0; j < nu; ++j) {
+        double mean_part = (k < n_warm) ? V[t * nu + j] : 0.0;
+        Uk[t * nu + j] = clampd(mean_part + eps[j], p->u_lo[j], p->u_hi[j]);
+      }
+    }
+    /* nominal rollout and trajectory cost (Eq. 3) */
+    double x[6], xn[6];
+    for (int a = 0; a < nx; ++a) x[a] = x0[a];
+    double Sk = 0.0, Sk_lo = 0.0, Sk_hi = 0.0;
+    for (int t = 0; t < T; ++t) {
+      double ctrl = 0.0;
+      for (int j = 0; j < nu; ++j) ctrl += V[t * nu + j] * inv_sig2[j] * Uk[t * nu + j];
+      ctrl *= p->gamma;
+      uint32_t all = 0xFFFFFFFFu;
+      Sk += state_cost(p, x, obs, n_obs, all, 0.0) + ctrl;
+      Sk_lo += state_cost(p, x, obs, n_obs, all, -p->band_delta) + ctrl;
+      Sk_hi += state_cost(p, x, obs, n_obs, all, p->band_delta) + ctrl;
+      orc_dynamics(p, x, Uk + t * nu, xn);
+      for (int a = 0; a < nx; ++a) x[a] = xn[a];
+    }
+    double phi = terminal_cost(p, x);
+    Sk += phi; Sk_lo += phi; Sk_hi += phi;
+    /* disturbed rollouts and their risk costs (Eq. 9) */
+    for (int m = 0; m < M; ++m) {
+      double xt[6];
+      for (int a = 0; a < nx; ++a) xt[a] = x0[a];
+      double Lv = 0.0, Llo = 0.0, Lhi = 0.0;
+      for (int t = 0; t < T; ++t) {
+        Lv += state_cost(p, xt, obs, n_obs, p->risk_mask, 0.0);
+        Llo += state_cost(p, xt, obs, n_obs, p->risk_mask, -p->band_delta);
+        Lhi += state_cost(p, xt, obs, n_obs, p->risk_mask, p->band_delta);
+        double w[4];
+        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, w);
+        orc_dynamics(p, xt, Uk + t * nu, xn);
+        for (int a = 0; a < nx; ++a) xt[a] = xn[a];
+        for (int s = 0; s < nslots_of(p->model); ++s) xt[slot_dim(p->model, s)] += w[s];
+      }
+      Lm[m] = Lv; Lm[M + m] = Llo; Lm[2 * M + m] = Lhi;
+    }
+    double cv = orc_cvar(Lm, M, p->alpha, p->B, p->cvar_mode);
+    double cv_lo = orc_cvar(Lm + M, M, p->alpha, p->B, p->cvar_mode);
+    double cv_hi = orc_cvar(Lm + 2 * M, M, p->alpha, p->B, p->cvar_mode);
+    /* CVaR violation cost and modified trajectory cost (Eqs. 14-16) */
+    double st = Sk + ((cv > p->C_u) ? p->A * cv : 0.0);
+    if (U) memcpy(U + (size_t)i * T * nu, Uk, sizeof(double) * (size_t)T * nu);
+    if (S) S[i] = Sk;
+    if (L) memcpy(L + (size_t)i * M, Lm, sizeof(double) * (size_t)M);
+    if (cvar) cvar[i] = cv;
+    if (S_tilde) S_tilde[i] = st;
+    if (S_lo) S_lo[i] = Sk_lo + ((cv_lo > p->C_u) ? p->A * cv_lo : 0.0);
+    if (S_hi) S_hi[i] = Sk_hi + ((cv_hi > p->C_u) ? p->A * cv_hi : 0.0);
+    if (cvar_lo) cvar_lo[i] = cv_lo;
+    if (cvar_hi) cvar_hi[i] = cv_hi;
+    free(Uk);
+    free(Lm);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Softmin weights and the weighted update (Eqs. 4, 5, 17)              */
+/* ------------------------------------------------------------------ */
+int32_t orc_update(int32_t K, int32_t T, int32_t nu, double lam, const double* S_tilde, const double* U,
+                   double* V_plus, double* weights) {
+  double beta = INFINITY;
+  for (int k = 0; k < K; ++k)
+    if (isfinite(S_tilde[k]) && S_tilde[k] < beta) beta = S_tilde[k];
+  if (!isfinite(beta)) return -5;
+  double sum = 0.0;
+  for (int k = 0; k < K; ++k) {
+    double w = isfinite(S_tilde[k]) ? exp(-(S_tilde[k] - beta) / lam) : 0.0;
+    if (weights) weights[k] = w;
+    sum += w;
+  }
+  for (int t = 0; t < T; ++t)
+    for (int j = 0; j < nu; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < K; ++k) {
+        double w = isfinite(S_tilde[k]) ? exp(-(S_tilde[k] - beta) / lam) : 0.0;
+        acc += w * U[((size_t)k * T + t) * nu + j];
+      }
+      V_plus[t * nu + j] = acc / sum;
+    }
+  if (weights)
+    for (int k = 0; k < K; ++k) weights[k] /= sum;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Simulated plant for the receding-horizon loop (Alg. 1 outer loop)    */
+/* ------------------------------------------------------------------ */
+/* x_out = F(x, u) + w with the plant's own noise stream at `iteration`;
+ * returns 1 when x_out is a collision (inside an obstacle or off track) */
+int32_t orc_plant_step(const orc_problem* p, uint64_t iteration, const double* x, const double* u,
+                       const double* obs, int32_t n_obs, double* x_out) {
+  int nx = nx_of(p->model);
+  double xn[6], w[4];
+  orc_dynamics(p, x, u, xn);
+  process_noise_at(p, iteration, 0xFFFFFFFEu, 0xFFFFFFFFu, 0, w);
+  for (int s = 0; s < nslots_of(p->model); ++s) xn[slot_dim(p->model, s)] += w[s];
+  for (int a = 0; a < nx; ++a) x_out[a] = xn[a];
+  if (p->model == ORC_LIN) return 0;
+  double tr[3];
+  orc_track(p, xn[0], xn[1], tr);
+  int hit = fabs(tr[0]) > p->track_half_width;
+  for (int i = 0; i < n_obs; ++i) {
+    double dx = xn[0] - obs[3 * i], dy = xn[1] - obs[3 * i + 1];
+    if (sqrt(dx * dx + dy * dy) < obs[3 * i + 2]) hit = 1;
+  }
+  return hit;
+}
+
+/* scalar exports used by the pins */
+double orc_state_cost(const orc_problem* p, const double* x, const double* obs, int32_t n_obs, uint32_t mask) {
+  return state_cost(p, x, obs, n_obs, mask, 0.0);
+}
+double orc_terminal_cost(const orc_problem* p, const double* x) { return terminal_cost(p, x); }
+int32_t orc_sizeof_problem(void) { return (int32_t)sizeof(orc_problem); }
+int32_t orc_n_warm(const orc_problem* p) { return n_warm_of(p); }
