@@ -1,0 +1,359 @@
+"""Benchmark of the RA-MPPI control update on GB300.
+
+Metric: rollout-steps/s, one rollout-step being one disturbed step of one
+of the K x M rollouts (K M T per update); the K T nominal steps are extra
+work that is not counted.  A "step" of this benchmark is one complete
+update (sampling, nominal and disturbed rollouts, CVaR, softmin update) on
+the paper-scale closed-loop workload: dynamic single-track vehicle,
+K = 4096 samples, M = 128 disturbed rollouts, T = 40 steps, 50 obstacles.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own instance (seed + rank): weak scaling,
+no collective on the data path.  `--impl reference` times the FP64 CPU
+oracle on the host cores over bounded samples of the same workload.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ra_scenes as rs  # noqa: E402
+
+WORKLOADS = {
+    "c2": "c2_closed_loop",
+    "c1": "c1_plain",
+    "c5": "c5_stress",
+    "c4": "c4_gradient",
+}
+N_SMS = 152
+LANES_PER_SM = 128
+
+
+# ---------------------------------------------------------------- op counts
+def algorithmic_ops(p):
+    """Formula count of ALU lane-operations per disturbed step and per nominal
+    step: FP32 add/mul/FMA/min/max/compare/select and INT32 ops count 1 each,
+    every special-function evaluation (sin, cos, tan, atan, atan2, log, exp,
+    sqrt, erfcinv, division) counts 1."""
+    model, n_obs, sub = int(p["model"]), int(p["n_obs"]), int(p["substeps"])
+    philox = 100  # 10 rounds x (2 mullo + 2 mulhi + 4 xor + 2 key adds)
+    obs_ind = 6 * n_obs  # 2 sub, mul, fma, compare-select, add
+    obs_sp = 10 * n_obs  # 2 sub, mul, fma, sqrt, sub, mul, exp, log1p, add
+    obs = obs_ind if int(p["obs_mode"]) == 0 else obs_sp
+    if model == 1:
+        deriv = 38  # slip angles 7, two tyres 10, sincos 2, six derivatives 19
+        dyn = sub * (2 * deriv + 6 + 12)
+        noise = (2 * philox + 3 * 10) if int(p["noise_type"]) == 1 else (philox + 2 * 10 + 3)
+    elif model == 0:
+        dyn = sub * 7
+        noise = philox + 2 * 10 + 4
+    else:
+        dyn, noise = sub, philox + 10 + 1
+    risk = 1 + obs
+    disturbed = dyn + noise + risk
+    # nominal: control draw (Philox + Box-Muller + clip ~ 120), dynamics, full q
+    nominal = 120 + dyn + obs + 30
+    return disturbed, nominal
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_rate(p, x0, V, obs, target_s, threads, iteration=0):
+    """Oracle rollout-steps/s on a bounded sample of the workload's samples."""
+    import oracle
+
+    K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
+    n = max(threads, 8)
+    while True:
+        ks = np.arange(min(n, K), dtype=np.int32)
+        t0 = time.perf_counter()
+        out = oracle.samples(p, x0, V, obs, ks=ks, iteration=iteration, n_threads=threads)
+        oracle.update(out["S_tilde"], out["U"], float(np.float32(p["lam"])))
+        dt = time.perf_counter() - t0
+        if dt >= target_s or len(ks) >= K:
+            return len(ks) * M * T / dt, len(ks), dt
+        n = int(min(K, max(2 * n, n * target_s / max(dt, 1e-3) * 1.1)))
+
+
+def run_reference(args, p, x0, V, obs):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    # calibrate the per-step sample to about 1.5 s of CPU work
+    _, n_cal, dt_cal = oracle_rate(p, x0, V, obs, 0.3, threads)
+    per = n_cal / max(dt_cal, 1e-6)
+    ks_n = int(max(threads, min(int(p["K"]), per * 1.5)))
+    import oracle
+
+    K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
+    ks = np.arange(ks_n, dtype=np.int32)
+    for i in range(args.warmup):
+        oracle.samples(p, x0, V, obs, ks=ks[: max(1, ks_n // 4)], iteration=i, n_threads=threads)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        out = oracle.samples(p, x0, V, obs, ks=ks, iteration=args.warmup + i, n_threads=threads)
+        oracle.update(out["S_tilde"], out["U"], float(np.float32(p["lam"])))
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = ks_n * M * T / t
+    line = {
+        "impl": "reference", "metric": "rollout-steps/s (K*M*T)", "value": value,
+        "unit": "rollout-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": config_dict(p, args),
+        "cpu_baseline": {"value": value, "unit": "rollout-steps/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{ks_n} of {K} samples x M={M} x T={T} per step (FP64 C oracle, "
+                                   f"OpenMP over samples), then the softmin update over them"},
+        "e2e": {"value": value, "unit": "rollout-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(p, args):
+    return {"workload": f"{args.workload}: {p['K']} samples x {p['M']} rollouts x {p['T']} steps, "
+                        f"{['kinematic bicycle', 'dynamic single-track', 'linear'][int(p['model'])]}, "
+                        f"{p['n_obs']} obstacles",
+            "K": int(p["K"]), "M": int(p["M"]), "T": int(p["T"]), "model": int(p["model"]),
+            "substeps": int(p["substeps"]), "n_obs": int(p["n_obs"]), "alpha": float(p["alpha"]),
+            "l2": "flushed before every timed step (256 MB write, outside the step's events)"}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args, p, x0, V, obs):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2209_12842_gb300 import RaMppi
+    from paper_2209_12842_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = dict(p, seed=int(p["seed"]) + rank, instance_id=rank)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctl = RaMppi(p, obs)
+    x0_d = torch.from_numpy(x0).to(dev)
+    V_d = torch.from_numpy(V).to(dev)
+    V_out = torch.empty_like(V_d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kv_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kv_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    for i in range(args.warmup):
+        ctl.step(x0_d, V_d, V_out)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.4)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ctl.set_timing_events(kv_b[i], kv_e[i])
+        ev_b[i].record(stream)
+        ctl.step(x0_d, V_d, V_out)
+        ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    ctl.set_timing_events(None)
+    clk = clocks.stop() if rank == 0 else None
+    status = ctl.status()
+
+    step_ms = np.array([b.elapsed_time(e) for b, e in zip(ev_b, ev_e)])
+    kern_ms = np.array([b.elapsed_time(e) for b, e in zip(kv_b, kv_e)])
+    t_step = float(step_ms.sum()) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
+    units = K * M * T
+    value = world * units * args.steps / t_step
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    nx = x0.size
+    x0_h = torch.from_numpy(x0).pin_memory()
+    V_h = torch.from_numpy(V).pin_memory()
+    Vo_h = torch.empty_like(V_h).pin_memory()
+    for i in range(2):
+        B.ra_mppi_step_host(ctl.h, x0_h.data_ptr(), V_h.data_ptr(), Vo_h.data_ptr(), None, stream.cuda_stream)
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        B.ra_mppi_step_host(ctl.h, x0_h.data_ptr(), V_h.data_ptr(), Vo_h.data_ptr(), None, stream.cuda_stream)
+        e2e_ms.append(1e3 * (time.perf_counter() - t1))
+    e2e_t = float(np.mean(e2e_ms)) / 1e3
+    if world > 1:
+        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    ctl.close()
+
+    if rank == 0:
+        d_ops, n_ops = algorithmic_ops(p)
+        ops_per_launch = units * d_ops + K * T * n_ops
+        k_mean = float(kern_ms.mean()) / 1e3
+        achieved = ops_per_launch / k_mean / 1e9
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak = N_SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e9
+        traffic = load_traffic(args.workload)
+        line = {
+            "metric": "rollout-steps/s (K*M*T)", "value": value, "unit": "rollout-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(p, args),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "rollout_kernel_mean": 1e3 * k_mean},
+            "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
+            "gpu_launches": 2 * args.steps,
+            "status": B.STATUS_NAMES.get(status, status),
+            "clocks": clk,
+            "e2e": {"value": world * units / e2e_t, "unit": "rollout-steps/s",
+                    "h2d_bytes_per_step": 4 * (nx + V.size), "d2h_bytes_per_step": 4 * V.size,
+                    "ms_per_step": 1e3 * e2e_t},
+            "roofline": {"bound": "alu", "kernel": "rollout_cvar_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "Gop/s (ALU lane-ops, formula count)", "frac": achieved / peak,
+                         "ops_per_launch": ops_per_launch, "ops_per_disturbed_step": d_ops,
+                         "ops_per_nominal_step": n_ops,
+                         "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock {sm_mhz:.0f} MHz",
+                         "traffic": traffic},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            rate, n_s, dt = oracle_rate(p, x0, V, obs, args.cpu_seconds, threads)
+            line["cpu_baseline"] = {"value": rate, "unit": "rollout-steps/s", "cores": threads,
+                                    "kind": "oracle",
+                                    "sample": f"{n_s} of {K} samples x M={M} x T={T} "
+                                              f"({dt:.1f} s, FP64 C oracle, OpenMP over samples)"}
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def load_traffic(workload):
+    """DRAM bytes per rollout-kernel launch from the committed ncu summary,
+    or None when no summary matches the current kernel."""
+    path = os.path.join(ROOT, "profiles", f"rollout_cvar_{workload}.json")
+    try:
+        return json.load(open(path)).get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    p = rs.preset(WORKLOADS[args.workload])
+    obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
+    x0 = rs.initial_state(p["model"])
+    V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 3)
+    if args.impl == "reference":
+        run_reference(args, p, x0, V, obs)
+    else:
+        run_ours(args, p, x0, V, obs)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * ra_mppi.h — C ABI of the GB300 (sm_103a) Risk-Aware MPPI update library.
+ *
+ * One call of ra_mppi_step performs one control update of RA-MPPI
+ * (Yin, Zhang, Tsiotras, "Risk-Aware Model Predictive Path Integral Control
+ * Using Conditional Value-at-Risk", arXiv 2209.12842), i.e. one pass of the
+ * body of Algorithm 1 minus the state estimate and the actuation:
+ *
+ *   1. sample K control sequences U^k = clip(V + eps^k), eps ~ N(0, Sigma);
+ *      the last eta fraction of samples use U^k = clip(eps^k)   (Alg. 1)
+ *   2. roll each out on the nominal dynamics x_{t+1} = F(x_t, u_t) (Eq. 1)
+ *      and charge S_k = phi(x_T) + sum_t q(x_t) + gamma v_t' Sigma^-1 u_t
+ *                                                                 (Eq. 3)
+ *   3. roll out M disturbed trajectories x~_{t+1} = F(x~_t, u_t) + w_t per
+ *      sample (Eqs. 6, 7) with risk costs L = sum_t l(x~_t)        (Eq. 9)
+ *   4. CVaR_alpha of the M risk costs, after the sensitivity scaling
+ *      L_a = B (L - mean) + mean                       (Eqs. 10-13, 18, 19)
+ *   5. S~_k = S_k + A CVaR_k 1{CVaR_k > C_u}                 (Eqs. 14-16)
+ *   6. w_k = exp(-(S~_k - min S~) / lambda),
+ *      V+ = sum_k w_k U^k / sum_k w_k                      (Eqs. 4, 5, 17)
+ *
+ * Letters: K control samples (the paper's M), M disturbed rollouts per
+ * sample (the paper's N), T horizon steps (the paper's K).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status (ra_mppi_status); the library
+ *     never aborts the process.  Invalid arguments return RA_MPPI_EINVAL
+ *     before any work is enqueued.
+ *   - Arrays are float32, contiguous, row-major.  "device" pointers must be
+ *     CUDA device (or managed) memory on the handle's device; "host"
+ *     pointers are ordinary host memory (pinned memory gives faster copies).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream.  Device-pointer entry points only enqueue work: no
+ *     allocation, no synchronisation.  Results are valid once the stream
+ *     has reached the call.
+ *   - A handle owns its workspace (allocated at create, freed at destroy)
+ *     and is not thread-safe; distinct handles are independent.
+ *   - The random numbers come from Philox4x32-10 (Salmon et al., SC'11)
+ *     keyed by (seed, update iteration) and counted by (t, rollout m,
+ *     sample k, instance); the iteration counter lives in the handle and
+ *     advances by one per update, so a handle reproduces its sequence
+ *     exactly after ra_mppi_set_iteration.
+ */
+#ifndef RA_MPPI_H
+#define RA_MPPI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RA_MPPI_OK = 0,
+  RA_MPPI_EINVAL = -1,       /* invalid argument or size                    */
+  RA_MPPI_ENOMEM = -2,       /* device or host allocation failed            */
+  RA_MPPI_ECUDA = -3,        /* a CUDA runtime call or launch failed        */
+  RA_MPPI_ETIMEOUT = -4,     /* a bounded device wait gave up               */
+  RA_MPPI_ENONFINITE = -5,   /* a cost was NaN/inf or all weights vanished  */
+  RA_MPPI_EUNSUPPORTED = -6  /* valid request that this build does not do   */
+} ra_mppi_status;
+
+/* Dynamics F (Eq. 1).  The paper does not give its vehicle model; these are
+ * the three models of this library (state / control layout):
+ *   KIN_BICYCLE      x = (px, py, psi, v),           u = (steer, accel),
+ *                    explicit Euler; model_params[0] = wheelbase
+ *   DYN_SINGLE_TRACK x = (px, py, psi, vx, vy, r),   u = (steer, accel),
+ *                    Heun (RK2); model_params = m, Iz, lf, lr, Pacejka B,
+ *                    C, D, vx floor of the slip angles; lateral tyre force
+ *                    D Fz sin(C atan(B alpha)) with static axle loads Fz
+ *   LINEAR_TEST      x = (x),                         u = (u),
+ *                    x+ = x + dt u (closed-form checks)
+ * `substeps` integration steps of dt / substeps make one control period. */
+enum { RA_MPPI_KIN_BICYCLE = 0, RA_MPPI_DYN_SINGLE_TRACK = 1, RA_MPPI_LINEAR_TEST = 2 };
+
+/* Process noise w_t of the disturbed dynamics (Eq. 6), added to the state
+ * after each control period.  Slots: KIN (px, py, psi, v); DYN (vx, vy, r);
+ * LINEAR (x).  GAUSS: w_s ~ N(0, w_scale[s]^2).  LAPLACE_MIX: w_s ~
+ * Laplace(0, w_scale[s]), replaced with probability mix_p by
+ * N(0, (mix_scale w_scale[s])^2). */
+enum { RA_MPPI_NOISE_GAUSS = 0, RA_MPPI_NOISE_LAPLACE_MIX = 1 };
+
+/* Obstacle term of q and l: the indicator 1{d_i < r_i} of Eq. 22, or a
+ * smooth barrier softplus(kappa (r_i - d_i)) / kappa. */
+enum { RA_MPPI_OBS_INDICATOR = 0, RA_MPPI_OBS_SOFTPLUS = 1 };
+
+/* CVaR estimator over the M risk costs (Eqs. 10-13):
+ *   RU   fractional sorted tail [(j - alpha M) L_(j) + sum_{i>j} L_(i)] /
+ *        ((1 - alpha) M), j = ceil(alpha M)  (equals the Rockafellar-Uryasev
+ *        minimum; continuous in L and insensitive to ties)
+ *   TCE  the literal Monte-Carlo form of Eqs. 12-13: mean of {L >= VaR},
+ *        VaR = L_(j) (Eq. 11). */
+enum { RA_MPPI_CVAR_RU = 0, RA_MPPI_CVAR_TCE = 1 };
+
+/* Bits of risk_mask: the running-cost terms that form the risk cost l
+ * (Eq. 9).  The paper's experiments use l = q (all terms). */
+enum {
+  RA_MPPI_TERM_DEV = 1,   /* w_dev e(x)^2, lateral deviation from the centreline */
+  RA_MPPI_TERM_SPEED = 2, /* w_speed (v - v_target)^2 (v = speed, or vx)         */
+  RA_MPPI_TERM_OBS = 4,   /* w_obs sum_i obstacle term (Eq. 22)                   */
+  RA_MPPI_TERM_BDRY = 8,  /* w_bdry max{0, atan(-100 d(x))/pi + 1/2} (Eq. 21)     */
+  RA_MPPI_TERM_LIN = 16   /* c_lin x[0] (linear test cost)                        */
+};
+
+/* flags */
+enum { RA_MPPI_KEEP_RISK_COSTS = 1 /* keep the K x M risk costs L for inspection */ };
+
+#define RA_MPPI_MAX_M 256
+#define RA_MPPI_MAX_T 256
+#define RA_MPPI_MAX_OBSTACLES 1024
+
+/* Problem definition (the quantities of Sec. II-V).  All reals float32. */
+typedef struct ra_mppi_problem {
+  int32_t model;      /* RA_MPPI_KIN_BICYCLE, ...                            */
+  int32_t K;          /* control samples, 1 .. 2^24                          */
+  int32_t M;          /* disturbed rollouts per sample, 1 .. RA_MPPI_MAX_M   */
+  int32_t T;          /* horizon steps, 1 .. RA_MPPI_MAX_T                   */
+  int32_t substeps;   /* integration steps per control period, >= 1          */
+  int32_t noise_type; /* RA_MPPI_NOISE_*                                     */
+  int32_t obs_mode;   /* RA_MPPI_OBS_*                                       */
+  int32_t cvar_mode;  /* RA_MPPI_CVAR_*                                      */
+  uint32_t risk_mask; /* RA_MPPI_TERM_* bits forming l                       */
+  int32_t flags;      /* RA_MPPI_KEEP_RISK_COSTS                             */
+  float dt;           /* control period (s)                                  */
+  float model_params[8];
+  float sigma_u[2];   /* Sigma = diag(sigma_u^2); sigma 0 = no noise, no cost */
+  float u_lo[2], u_hi[2]; /* control box; samples are clipped after noise   */
+  float w_scale[4];   /* process-noise scale per slot                        */
+  float mix_p, mix_scale;
+  float w_dev, w_speed, v_target, gamma, w_obs, w_bdry, c4, c5, c_lin;
+  float kappa;        /* softplus barrier sharpness                          */
+  float track_straight, track_radius, track_half_width; /* stadium track    */
+  float lambda;       /* softmin temperature, > 0 (Eq. 5)                    */
+  float alpha;        /* CVaR level in (0, 1) (Eq. 8b)                        */
+  float A;            /* CVaR cost gain (Eq. 14)                              */
+  float B;            /* risk sensitivity scale, >= 0 (Eq. 18)                */
+  float C_u;          /* CVaR bound (Eq. 15)                                  */
+  float eta;          /* zero-mean sample fraction in [0, 1) (Alg. 1)         */
+  int32_t max_obstacles; /* capacity of the obstacle list, 0 .. RA_MPPI_MAX_OBSTACLES */
+  uint32_t instance_id;  /* fourth Philox counter word                        */
+  uint64_t seed;         /* Philox key                                        */
+} ra_mppi_problem;
+
+typedef struct ra_mppi ra_mppi_t;
+
+/* Size of ra_mppi_problem as compiled into the library (binding check). */
+int32_t ra_mppi_problem_size(void);
+
+/* Validate *p and allocate a handle with all workspace on the current CUDA
+ * device.  Returns EINVAL for out-of-range sizes or parameters (lambda <= 0,
+ * alpha outside (0, 1), B < 0, eta outside [0, 1), M > RA_MPPI_MAX_M, ...),
+ * ENOMEM if allocation fails.  *out is set only on success. */
+int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out);
+
+/* Release a handle and its workspace.  NULL is allowed. */
+void ra_mppi_destroy(ra_mppi_t* h);
+
+/* Set the obstacle circles used by q and l (Eq. 22): xyr[n_obs][3] =
+ * (centre x, centre y, radius), host or device pointer.  Synchronous: the
+ * copy has completed when the call returns.  EINVAL if n_obs >
+ * max_obstacles, a radius is negative or a centre is not finite. */
+int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* stream);
+
+/* One RA-MPPI update on device buffers (steps 1-6 above).
+ *   x0      [nx]      device, current state x(0)
+ *   V_in    [T][nu]   device, mean control sequence V
+ *   V_out   [T][nu]   device, receives V+ (may alias V_in)
+ *   S_tilde [K]       device, optional (NULL): receives S~_k
+ *   cvar    [K]       device, optional (NULL): receives CVaR_k
+ * Enqueues two kernels on `stream`; advances the iteration counter. */
+int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out, float* S_tilde,
+                 float* cvar, void* stream);
+
+/* The same update on HOST buffers: copies x0 and V_in to the device, runs
+ * ra_mppi_step, copies V+ (and S_tilde if non-NULL) back and waits for
+ * `stream`.  This is the end-to-end call of a controller loop (the paper
+ * keeps everything but the state and the command on the GPU, Sec. V-C). */
+int ra_mppi_step_host(ra_mppi_t* h, const float* x0_host, const float* V_in_host, float* V_out_host,
+                      float* S_tilde_host, void* stream);
+
+/* Device views of the last update's workspace, valid until destroy:
+ *   U [K][T][nu] sampled (clipped) controls, S [K] nominal costs (Eq. 3),
+ *   cvar [K] CVaR values, L [K][M] risk costs (NULL unless the problem had
+ *   RA_MPPI_KEEP_RISK_COSTS).  Any output pointer may be NULL. */
+int ra_mppi_workspace(ra_mppi_t* h, const float** U, const float** S, const float** cvar,
+                      const float** L);
+
+/* Copy the last update's workspace into caller buffers (host or device,
+ * any may be NULL): U [K][T][nu], S [K], cvar [K], L [K][M] (EINVAL if L is
+ * requested without RA_MPPI_KEEP_RISK_COSTS).  Enqueued on `stream`. */
+int ra_mppi_copy_workspace(ra_mppi_t* h, float* U, float* S, float* cvar, float* L, void* stream);
+
+/* Update counter that keys the noise.  get waits for the device. */
+int ra_mppi_get_iteration(ra_mppi_t* h, uint64_t* iteration);
+int ra_mppi_set_iteration(ra_mppi_t* h, uint64_t iteration);
+
+/* Device status word accumulated since the last call, then cleared: OK,
+ * or ENONFINITE when a cost was NaN/inf or every weight vanished.  Waits
+ * for the device. */
+int ra_mppi_get_status(ra_mppi_t* h);
+
+/* Human-readable reason of the last error on this handle ("" if none). */
+const char* ra_mppi_last_error(const ra_mppi_t* h);
+
+/* Kernel launch tuning: disturbed-rollout warps per block (1..16) and
+ * rollouts each lane interleaves (1, 2 or 4); 0 keeps the default. */
+int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp);
+
+/* Timing hook: when set, ra_mppi_step records the caller's CUDA events
+ * (cudaEvent_t passed as void*) immediately before and after the fused
+ * rollout kernel on the step's stream, so the caller can time that kernel
+ * alone.  NULL, NULL turns the hook off. */
+int ra_mppi_set_timing_events(ra_mppi_t* h, void* rollout_begin, void* rollout_end);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RA_MPPI_H */

@@ -89,7 +89,7 @@ def lib():
         L.orc_track.argtypes = [_P, ctypes.c_double, ctypes.c_double, _D]
         L.orc_cvar.argtypes = [_D, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32]
         L.orc_cvar.restype = ctypes.c_double
-        L.orc_samples.argtypes = [_P, _D, _D, _D, ctypes.c_int32, _I32, ctypes.c_int32] + [_D] * 9
+        L.orc_samples.argtypes = [_P, _D, _D, _D, ctypes.c_int32, _I32, ctypes.c_int32] + [_D] * 11
         L.orc_samples.restype = ctypes.c_int32
         L.orc_update.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                  _D, _D, _D, _D]
@@ -240,13 +240,15 @@ def samples(p, x0, V, obs, ks=None, iteration=0, band_delta=1e-4, n_threads=1, w
     x0 = _arr(np.asarray(x0, dtype=np.float32))
     V = _arr(np.asarray(V, dtype=np.float32).reshape(T, nu))
     o = _arr(np.asarray(obs, dtype=np.float32).reshape(-1, 3)) if len(obs) else np.zeros((0, 3))
-    out = {name: np.zeros(nk) for name in ("S", "cvar", "S_tilde", "S_lo", "S_hi", "cvar_lo", "cvar_hi")}
+    out = {name: np.zeros(nk) for name in ("S", "cvar", "S_tilde", "S_lo", "S_hi", "cvar_lo",
+                                          "cvar_hi", "St_lo", "St_hi")}
     out["U"] = np.zeros((nk, T, nu))
     Lbuf = np.zeros((nk, M)) if want_L else None
     rc = lib().orc_samples(ctypes.byref(prob), _ptr(x0), _ptr(V), _ptr(o), int(len(o)),
                            _ptr(ks, _I32), nk, _ptr(out["U"]), _ptr(out["S"]), _ptr(Lbuf),
                            _ptr(out["cvar"]), _ptr(out["S_tilde"]), _ptr(out["S_lo"]),
-                           _ptr(out["S_hi"]), _ptr(out["cvar_lo"]), _ptr(out["cvar_hi"]))
+                           _ptr(out["S_hi"]), _ptr(out["cvar_lo"]), _ptr(out["cvar_hi"]),
+                           _ptr(out["St_lo"]), _ptr(out["St_hi"]))
     if rc != 0:
         raise RuntimeError(f"orc_samples failed: {rc}")
     if want_L:

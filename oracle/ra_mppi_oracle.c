@@ -397,13 +397,14 @@ static int n_warm_of(const orc_problem* p) {
   return (int)ceil((1.0 - p->eta) * (double)p->K);
 }
 
-/* Outputs for sample index i of the list ks[] (all optional except none):
- *   U[i][T][nu], S[i], L[i][M], cvar[i], S_tilde[i],
- *   band bounds S_lo/S_hi, cvar_lo/cvar_hi (indicator threshold r -/+ delta) */
+/* Outputs for sample index i of the list ks[] (each may be NULL):
+ *   U[i][T][nu], S[i], L[i][M], cvar[i], S_tilde[i], and band bounds of S,
+ *   CVaR and S~ obtained with the obstacle indicator threshold at r - delta
+ *   (lo) and r + delta (hi) along the same trajectories */
 int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, const double* obs,
                     int32_t n_obs, const int32_t* ks, int32_t nk, double* U, double* S, double* L,
                     double* cvar, double* S_tilde, double* S_lo, double* S_hi, double* cvar_lo,
-                    double* cvar_hi) {
+                    double* cvar_hi, double* St_lo, double* St_hi) {
   const int nx = nx_of(p->model), nu = nu_of(p->model), T = p->T, M = p->M;
   const int n_warm = n_warm_of(p);
   double inv_sig2[2];
@@ -468,8 +469,10 @@ int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, con
     if (L) memcpy(L + (size_t)i * M, Lm, sizeof(double) * (size_t)M);
     if (cvar) cvar[i] = cv;
     if (S_tilde) S_tilde[i] = st;
-    if (S_lo) S_lo[i] = Sk_lo + ((cv_lo > p->C_u) ? p->A * cv_lo : 0.0);
-    if (S_hi) S_hi[i] = Sk_hi + ((cv_hi > p->C_u) ? p->A * cv_hi : 0.0);
+    if (S_lo) S_lo[i] = Sk_lo;
+    if (S_hi) S_hi[i] = Sk_hi;
+    if (St_lo) St_lo[i] = Sk_lo + ((cv_lo > p->C_u) ? p->A * cv_lo : 0.0);
+    if (St_hi) St_hi[i] = Sk_hi + ((cv_hi > p->C_u) ? p->A * cv_hi : 0.0);
     if (cvar_lo) cvar_lo[i] = cv_lo;
     if (cvar_hi) cvar_hi[i] = cv_hi;
     free(Uk);

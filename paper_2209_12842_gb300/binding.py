@@ -1,0 +1,209 @@
+"""ctypes binding of libramppi.so (include/ra_mppi.h), argument marshalling only.
+
+Every step of the RA-MPPI update runs in the library's CUDA kernels; this
+module fills the problem struct, passes device pointers (torch tensors'
+data_ptr()) and the CUDA stream, and turns status codes into exceptions.
+There is no fallback: if the library is missing or fails to load, every
+entry point raises.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libramppi.so")
+
+RA_MPPI_OK = 0
+RA_MPPI_EINVAL = -1
+RA_MPPI_ENOMEM = -2
+RA_MPPI_ECUDA = -3
+RA_MPPI_ETIMEOUT = -4
+RA_MPPI_ENONFINITE = -5
+RA_MPPI_EUNSUPPORTED = -6
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT",
+                -5: "ENONFINITE", -6: "EUNSUPPORTED"}
+
+RA_MPPI_KEEP_RISK_COSTS = 1
+
+
+class RaMppiError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} {detail}".strip())
+
+
+class ra_mppi_problem(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_int32), ("K", ctypes.c_int32), ("M", ctypes.c_int32),
+        ("T", ctypes.c_int32), ("substeps", ctypes.c_int32), ("noise_type", ctypes.c_int32),
+        ("obs_mode", ctypes.c_int32), ("cvar_mode", ctypes.c_int32),
+        ("risk_mask", ctypes.c_uint32), ("flags", ctypes.c_int32),
+        ("dt", ctypes.c_float), ("model_params", ctypes.c_float * 8),
+        ("sigma_u", ctypes.c_float * 2), ("u_lo", ctypes.c_float * 2), ("u_hi", ctypes.c_float * 2),
+        ("w_scale", ctypes.c_float * 4), ("mix_p", ctypes.c_float), ("mix_scale", ctypes.c_float),
+        ("w_dev", ctypes.c_float), ("w_speed", ctypes.c_float), ("v_target", ctypes.c_float),
+        ("gamma", ctypes.c_float), ("w_obs", ctypes.c_float), ("w_bdry", ctypes.c_float),
+        ("c4", ctypes.c_float), ("c5", ctypes.c_float), ("c_lin", ctypes.c_float),
+        ("kappa", ctypes.c_float), ("track_straight", ctypes.c_float),
+        ("track_radius", ctypes.c_float), ("track_half_width", ctypes.c_float),
+        ("lambda_", ctypes.c_float), ("alpha", ctypes.c_float), ("A", ctypes.c_float),
+        ("B", ctypes.c_float), ("C_u", ctypes.c_float), ("eta", ctypes.c_float),
+        ("max_obstacles", ctypes.c_int32), ("instance_id", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+_VP = ctypes.c_void_p
+_FP = ctypes.c_void_p  # float* passed as integer address
+_lib = None
+_load_error = None
+
+
+def _declare(L):
+    L.ra_mppi_problem_size.restype = ctypes.c_int32
+    L.ra_mppi_create.argtypes = [ctypes.POINTER(ra_mppi_problem), ctypes.POINTER(_VP)]
+    L.ra_mppi_destroy.argtypes = [_VP]
+    L.ra_mppi_destroy.restype = None
+    L.ra_mppi_set_obstacles.argtypes = [_VP, _FP, ctypes.c_int32, _VP]
+    L.ra_mppi_step.argtypes = [_VP, _FP, _FP, _FP, _FP, _FP, _VP]
+    L.ra_mppi_step_host.argtypes = [_VP, _FP, _FP, _FP, _FP, _VP]
+    L.ra_mppi_workspace.argtypes = [_VP] + [ctypes.POINTER(_VP)] * 4
+    L.ra_mppi_copy_workspace.argtypes = [_VP, _FP, _FP, _FP, _FP, _VP]
+    L.ra_mppi_get_iteration.argtypes = [_VP, ctypes.POINTER(ctypes.c_uint64)]
+    L.ra_mppi_set_iteration.argtypes = [_VP, ctypes.c_uint64]
+    L.ra_mppi_get_status.argtypes = [_VP]
+    L.ra_mppi_last_error.argtypes = [_VP]
+    L.ra_mppi_last_error.restype = ctypes.c_char_p
+    L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
+    L.ra_mppi_set_timing_events.argtypes = [_VP, _VP, _VP]
+    for name in ("ra_mppi_create", "ra_mppi_set_obstacles", "ra_mppi_step", "ra_mppi_step_host",
+                 "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_get_iteration", "ra_mppi_set_iteration",
+                 "ra_mppi_get_status", "ra_mppi_set_launch", "ra_mppi_set_timing_events"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+def lib():
+    """The loaded library; raises if it has not been built or cannot load."""
+    global _lib, _load_error
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_2209_12842_gb300.build` "
+            "(there is no CPU fallback)")
+    try:
+        L = ctypes.CDLL(LIB_PATH)
+    except OSError as e:  # pragma: no cover - depends on the host
+        _load_error = e
+        raise RuntimeError(f"cannot load {LIB_PATH}: {e}") from e
+    _declare(L)
+    if L.ra_mppi_problem_size() != ctypes.sizeof(ra_mppi_problem):
+        raise RuntimeError("ra_mppi_problem layout mismatch between binding and library")
+    _lib = L
+    return _lib
+
+
+def _f(v):
+    return float(v)
+
+
+def ra_mppi_problem_from(p, flags=0, max_obstacles=None):
+    """Fill the C problem struct from a preset dict (see ra_scenes.presets)."""
+    pr = ra_mppi_problem()
+    for name in ("model", "K", "M", "T", "substeps", "noise_type", "obs_mode", "cvar_mode"):
+        setattr(pr, name, int(p[name]))
+    pr.risk_mask = int(p["risk_mask"])
+    pr.flags = int(flags)
+    pr.dt = _f(p["dt"])
+    for i in range(8):
+        pr.model_params[i] = _f(p["model_params"][i])
+    for i in range(2):
+        pr.sigma_u[i] = _f(p["sigma_u"][i])
+        pr.u_lo[i] = _f(p["u_lo"][i])
+        pr.u_hi[i] = _f(p["u_hi"][i])
+    for i in range(4):
+        pr.w_scale[i] = _f(p["w_scale"][i])
+    for name in ("mix_p", "mix_scale", "w_dev", "w_speed", "v_target", "gamma", "w_obs", "w_bdry",
+                 "c4", "c5", "c_lin", "kappa", "track_straight", "track_radius", "track_half_width",
+                 "alpha", "A", "B", "C_u", "eta"):
+        setattr(pr, name, _f(p[name]))
+    pr.lambda_ = _f(p["lam"])
+    n_obs = int(p.get("n_obs", 0))
+    pr.max_obstacles = int(max_obstacles if max_obstacles is not None else max(n_obs, 1))
+    pr.instance_id = int(p["instance_id"]) & 0xFFFFFFFF
+    pr.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
+    return pr
+
+
+def _check(rc, where, handle=None):
+    if rc != RA_MPPI_OK:
+        detail = ""
+        if handle:
+            msg = lib().ra_mppi_last_error(handle)
+            detail = msg.decode() if msg else ""
+        raise RaMppiError(rc, where, detail)
+
+
+# ------------------------------------------------------------------ C names
+
+def ra_mppi_create(problem):
+    h = _VP()
+    _check(lib().ra_mppi_create(ctypes.byref(problem), ctypes.byref(h)), "ra_mppi_create")
+    return h
+
+
+def ra_mppi_destroy(h):
+    lib().ra_mppi_destroy(h)
+
+
+def ra_mppi_set_obstacles(h, xyr_ptr, n_obs, stream=0):
+    _check(lib().ra_mppi_set_obstacles(h, xyr_ptr, int(n_obs), stream), "ra_mppi_set_obstacles", h)
+
+
+def ra_mppi_step(h, x0_ptr, V_in_ptr, V_out_ptr, S_tilde_ptr=None, cvar_ptr=None, stream=0):
+    _check(lib().ra_mppi_step(h, x0_ptr, V_in_ptr, V_out_ptr, S_tilde_ptr, cvar_ptr, stream),
+           "ra_mppi_step", h)
+
+
+def ra_mppi_step_host(h, x0_ptr, V_in_ptr, V_out_ptr, S_tilde_ptr=None, stream=0):
+    _check(lib().ra_mppi_step_host(h, x0_ptr, V_in_ptr, V_out_ptr, S_tilde_ptr, stream),
+           "ra_mppi_step_host", h)
+
+
+def ra_mppi_workspace(h):
+    ptrs = [_VP() for _ in range(4)]
+    _check(lib().ra_mppi_workspace(h, *[ctypes.byref(p) for p in ptrs]), "ra_mppi_workspace", h)
+    return [p.value for p in ptrs]
+
+
+def ra_mppi_copy_workspace(h, U_ptr=None, S_ptr=None, cvar_ptr=None, L_ptr=None, stream=0):
+    _check(lib().ra_mppi_copy_workspace(h, U_ptr, S_ptr, cvar_ptr, L_ptr, stream),
+           "ra_mppi_copy_workspace", h)
+
+
+def ra_mppi_get_iteration(h):
+    it = ctypes.c_uint64()
+    _check(lib().ra_mppi_get_iteration(h, ctypes.byref(it)), "ra_mppi_get_iteration", h)
+    return it.value
+
+
+def ra_mppi_set_iteration(h, iteration):
+    _check(lib().ra_mppi_set_iteration(h, int(iteration)), "ra_mppi_set_iteration", h)
+
+
+def ra_mppi_get_status(h):
+    return lib().ra_mppi_get_status(h)
+
+
+def ra_mppi_last_error(h):
+    msg = lib().ra_mppi_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def ra_mppi_set_launch(h, warps_per_block=0, ilp=0):
+    _check(lib().ra_mppi_set_launch(h, int(warps_per_block), int(ilp)), "ra_mppi_set_launch", h)
+
+
+def ra_mppi_set_timing_events(h, begin_event_handle=None, end_event_handle=None):
+    _check(lib().ra_mppi_set_timing_events(h, begin_event_handle, end_event_handle),
+           "ra_mppi_set_timing_events", h)

@@ -1,0 +1,471 @@
+// C ABI of the RA-MPPI update library (declarations and contracts in
+// include/ra_mppi.h).  Host side only: validation, workspace, constants and
+// kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "ra_kernels.h"
+#include "ra_mppi.h"
+
+using ramppi::DevParams;
+using ramppi::DevState;
+
+struct ra_mppi {
+  ra_mppi_problem prob;
+  DevParams dp;
+  int device = 0;
+  int nx = 0, nu = 0;
+  int warps = 4, ilp = 1;
+  int nb_upd = 1;
+  int obs_cap = 0;
+  size_t smem = 0;
+  float* U = nullptr;
+  float* S = nullptr;
+  float* cvar = nullptr;
+  float* S_tilde = nullptr;
+  float* partials = nullptr;
+  float* L = nullptr;
+  float4* obs = nullptr;
+  DevState* st = nullptr;
+  float* x0_dev = nullptr;  // staging for ra_mppi_step_host
+  float* V_dev = nullptr;
+  cudaEvent_t ev_begin = nullptr;  // optional timing hook around the rollout kernel
+  cudaEvent_t ev_end = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(ra_mppi* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(ra_mppi* h, cudaError_t e, const char* where) {
+  return fail(h, RA_MPPI_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Host-side fault injection for tests of the error paths: RAMPPI_FAULT=alloc
+// makes create fail as if cudaMalloc had, RAMPPI_FAULT=launch makes step fail
+// before enqueueing anything.  Never touches the GPU.
+bool fault(const char* what) {
+  const char* f = std::getenv("RAMPPI_FAULT");
+  return f != nullptr && std::strcmp(f, what) == 0;
+}
+
+int model_nx(int model) { return model == RA_MPPI_KIN_BICYCLE ? 4 : model == RA_MPPI_DYN_SINGLE_TRACK ? 6 : 1; }
+int model_nu(int model) { return model == RA_MPPI_LINEAR_TEST ? 1 : 2; }
+
+bool finite_all(const float* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+// returns "" when valid, otherwise the reason
+std::string validate(const ra_mppi_problem& p) {
+  if (p.model < 0 || p.model > 2) return "model must be 0 (kinematic), 1 (dynamic) or 2 (linear)";
+  if (p.K < 1 || p.K > (1 << 24)) return "K must be in [1, 2^24]";
+  if (p.M < 1 || p.M > RA_MPPI_MAX_M) return "M must be in [1, 256]";
+  if (p.T < 1 || p.T > RA_MPPI_MAX_T) return "T must be in [1, 256]";
+  if (p.substeps < 1 || p.substeps > 64) return "substeps must be in [1, 64]";
+  if (p.noise_type != RA_MPPI_NOISE_GAUSS && p.noise_type != RA_MPPI_NOISE_LAPLACE_MIX) return "unknown noise_type";
+  if (p.obs_mode != RA_MPPI_OBS_INDICATOR && p.obs_mode != RA_MPPI_OBS_SOFTPLUS) return "unknown obs_mode";
+  if (p.cvar_mode != RA_MPPI_CVAR_RU && p.cvar_mode != RA_MPPI_CVAR_TCE) return "unknown cvar_mode";
+  if (p.max_obstacles < 0 || p.max_obstacles > RA_MPPI_MAX_OBSTACLES) return "max_obstacles must be in [0, 1024]";
+  if (!(p.dt > 0.0f) || !std::isfinite(p.dt)) return "dt must be finite and > 0";
+  if (!(p.lambda > 0.0f) || !std::isfinite(p.lambda)) return "lambda must be finite and > 0";
+  if (!(p.alpha > 0.0f && p.alpha < 1.0f)) return "alpha must be in (0, 1)";
+  if (!(p.B >= 0.0f) || !std::isfinite(p.B)) return "B must be finite and >= 0";
+  if (!(p.eta >= 0.0f && p.eta < 1.0f)) return "eta must be in [0, 1)";
+  if (!(p.mix_p >= 0.0f && p.mix_p <= 1.0f)) return "mix_p must be in [0, 1]";
+  if (!(p.kappa > 0.0f) && p.obs_mode == RA_MPPI_OBS_SOFTPLUS) return "kappa must be > 0";
+  for (int j = 0; j < 2; ++j) {
+    if (!(p.sigma_u[j] >= 0.0f) || !std::isfinite(p.sigma_u[j])) return "sigma_u must be finite and >= 0";
+    if (!(p.u_lo[j] <= p.u_hi[j])) return "u_lo must be <= u_hi";
+  }
+  for (int s = 0; s < 4; ++s)
+    if (!(p.w_scale[s] >= 0.0f) || !std::isfinite(p.w_scale[s])) return "w_scale must be finite and >= 0";
+  if (!finite_all(p.model_params, 8)) return "model_params must be finite";
+  if (p.model == RA_MPPI_KIN_BICYCLE && !(p.model_params[0] > 0.0f)) return "wheelbase must be > 0";
+  if (p.model == RA_MPPI_DYN_SINGLE_TRACK) {
+    const float* mp = p.model_params;
+    if (!(mp[0] > 0.0f && mp[1] > 0.0f && mp[2] > 0.0f && mp[3] > 0.0f && mp[7] > 0.0f))
+      return "dynamic model needs m, Iz, lf, lr and the vx floor > 0";
+  }
+  const float w[] = {p.w_dev, p.w_speed, p.v_target, p.gamma, p.w_obs, p.w_bdry, p.c4, p.c5, p.c_lin,
+                     p.track_straight, p.track_radius, p.track_half_width, p.A, p.C_u, p.mix_scale};
+  for (float v : w)
+    if (std::isnan(v)) return "cost and track parameters must not be NaN";
+  return "";
+}
+
+DevParams make_params(const ra_mppi_problem& p) {
+  DevParams d{};
+  d.K = p.K;
+  d.M = p.M;
+  d.T = p.T;
+  d.nu = model_nu(p.model);
+  d.substeps = p.substeps;
+  d.noise_type = p.noise_type;
+  d.obs_mode = p.obs_mode;
+  d.cvar_mode = p.cvar_mode;
+  d.risk_mask = p.risk_mask;
+  // Alg. 1: sample k keeps the mean control when k < (1 - eta) K; the
+  // products below are exact in double for float32 inputs
+  d.n_warm = (int)std::ceil((1.0 - (double)p.eta) * (double)p.K);
+  const double aM = (double)p.alpha * (double)p.M;
+  int j = (int)std::ceil(aM);
+  j = j < 1 ? 1 : (j > p.M ? p.M : j);
+  d.j_var = j;
+  d.frac_j = (float)((double)j - aM);
+  d.tail_denom = (float)((1.0 - (double)p.alpha) * (double)p.M);
+  d.h = p.dt / (float)p.substeps;
+  for (int i = 0; i < 8; ++i) d.mp[i] = p.model_params[i];
+  if (p.model == RA_MPPI_DYN_SINGLE_TRACK) {
+    const double m = p.model_params[0], Iz = p.model_params[1], lf = p.model_params[2], lr = p.model_params[3];
+    const double D = p.model_params[6], g = 9.81;
+    d.dfz_f = (float)(D * m * g * lr / (lf + lr));
+    d.dfz_r = (float)(D * m * g * lf / (lf + lr));
+    d.inv_m = (float)(1.0 / m);
+    d.inv_iz = (float)(1.0 / Iz);
+  }
+  for (int j2 = 0; j2 < 2; ++j2) {
+    d.sigma_u[j2] = p.sigma_u[j2];
+    d.inv_sig2[j2] = p.sigma_u[j2] > 0.0f ? (float)(1.0 / ((double)p.sigma_u[j2] * p.sigma_u[j2])) : 0.0f;
+    d.u_lo[j2] = p.u_lo[j2];
+    d.u_hi[j2] = p.u_hi[j2];
+  }
+  const double thr = std::floor(std::fmin((double)p.mix_p * 4294967296.0, 4294967295.0));
+  d.mix_thresh = (uint32_t)thr;
+  for (int s = 0; s < 4; ++s) {
+    d.w_scale[s] = p.w_scale[s];
+    d.mix_gauss[s] = (float)((double)p.mix_scale * (double)p.w_scale[s] * std::sqrt(2.0));
+  }
+  d.w_dev = p.w_dev;
+  d.w_speed = p.w_speed;
+  d.v_target = p.v_target;
+  d.gamma = p.gamma;
+  d.w_obs = p.w_obs;
+  d.w_bdry = p.w_bdry;
+  d.c4 = p.c4;
+  d.c5 = p.c5;
+  d.c_lin = p.c_lin;
+  d.kappa = p.kappa;
+  d.inv_kappa = p.kappa > 0.0f ? 1.0f / p.kappa : 0.0f;
+  d.track_S = p.track_straight;
+  d.track_R = p.track_radius;
+  d.track_hw = p.track_half_width;
+  d.inv_lambda = 1.0f / p.lambda;
+  d.A = p.A;
+  d.B = p.B;
+  d.C_u = p.C_u;
+  d.seed_lo = (uint32_t)(p.seed & 0xFFFFFFFFull);
+  d.seed_hi = (uint32_t)(p.seed >> 32);
+  d.instance = p.instance_id;
+  return d;
+}
+
+template <typename T>
+cudaError_t dalloc(T** ptr, size_t count) {
+  if (fault("alloc")) return cudaErrorMemoryAllocation;
+  return cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * (count > 0 ? count : 1));
+}
+
+void release(ra_mppi* h) {
+  cudaFree(h->U);
+  cudaFree(h->S);
+  cudaFree(h->cvar);
+  cudaFree(h->S_tilde);
+  cudaFree(h->partials);
+  cudaFree(h->L);
+  cudaFree(h->obs);
+  cudaFree(h->st);
+  cudaFree(h->x0_dev);
+  cudaFree(h->V_dev);
+}
+
+size_t rollout_smem(const ra_mppi* h) {
+  return (size_t)h->obs_cap * sizeof(float4) + (size_t)h->warps * h->prob.T * sizeof(float4) +
+         (size_t)h->warps * h->prob.M * sizeof(float);
+}
+
+cudaError_t prepare(ra_mppi* h) {
+  h->smem = rollout_smem(h);
+  switch (h->prob.model) {
+    case 0: return ramppi::prepare_rollout<0>(h->smem);
+    case 1: return ramppi::prepare_rollout<1>(h->smem);
+    default: return ramppi::prepare_rollout<2>(h->smem);
+  }
+}
+
+// largest interleave in {4, 2, 1} that divides the rollouts per lane
+int default_ilp(int M, int model) {
+  const int R = (M + 31) / 32;
+  const int cap = model == RA_MPPI_DYN_SINGLE_TRACK ? 2 : 4;
+  for (int ilp = cap; ilp > 1; ilp >>= 1)
+    if (R % ilp == 0) return ilp;
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ra_mppi_problem_size(void) { return (int32_t)sizeof(ra_mppi_problem); }
+
+int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
+  if (p == nullptr || out == nullptr) return RA_MPPI_EINVAL;
+  const std::string why = validate(*p);
+  if (!why.empty()) {
+    std::fprintf(stderr, "ra_mppi_create: %s\n", why.c_str());
+    return RA_MPPI_EINVAL;
+  }
+  ra_mppi* h = new (std::nothrow) ra_mppi();
+  if (h == nullptr) return RA_MPPI_ENOMEM;
+  h->prob = *p;
+  h->dp = make_params(*p);
+  h->nx = model_nx(p->model);
+  h->nu = model_nu(p->model);
+  h->obs_cap = p->max_obstacles;
+  h->ilp = default_ilp(p->M, p->model);
+  h->warps = 4;
+  cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaGetDevice(&h->device);
+  const size_t K = (size_t)p->K, TN = (size_t)p->T * h->nu;
+  h->nb_upd = (int)std::min<size_t>((K + ramppi::kUpdateThreads - 1) / ramppi::kUpdateThreads,
+                                    (size_t)ramppi::kMaxUpdateBlocks);
+  if (e == cudaSuccess) e = dalloc(&h->U, K * TN);
+  if (e == cudaSuccess) e = dalloc(&h->S, K);
+  if (e == cudaSuccess) e = dalloc(&h->cvar, K);
+  if (e == cudaSuccess) e = dalloc(&h->S_tilde, K);
+  if (e == cudaSuccess) e = dalloc(&h->partials, (size_t)h->nb_upd * (2 + TN));
+  if (e == cudaSuccess && (p->flags & RA_MPPI_KEEP_RISK_COSTS)) e = dalloc(&h->L, K * (size_t)p->M);
+  if (e == cudaSuccess) e = dalloc(&h->obs, (size_t)h->obs_cap);
+  if (e == cudaSuccess) e = dalloc(&h->st, 1);
+  if (e == cudaSuccess) e = dalloc(&h->x0_dev, 8);
+  if (e == cudaSuccess) e = dalloc(&h->V_dev, TN);
+  if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(DevState));
+  if (e == cudaSuccess) e = cudaMemset(h->U, 0, sizeof(float) * K * TN);
+  if (e == cudaSuccess) e = prepare(h);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? RA_MPPI_ENOMEM : RA_MPPI_ECUDA;
+    std::fprintf(stderr, "ra_mppi_create: %s\n", cudaGetErrorString(e));
+    release(h);
+    delete h;
+    return code;
+  }
+  *out = h;
+  return RA_MPPI_OK;
+}
+
+void ra_mppi_destroy(ra_mppi_t* h) {
+  if (h == nullptr) return;
+  release(h);
+  delete h;
+}
+
+int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* stream) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (n_obs < 0 || n_obs > h->obs_cap) return fail(h, RA_MPPI_EINVAL, "n_obs exceeds max_obstacles");
+  if (n_obs > 0 && xyr == nullptr) return fail(h, RA_MPPI_EINVAL, "xyr is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // packed as (x, y, r, r^2) so the indicator compares squared distances
+  float4* host = nullptr;
+  if (n_obs > 0) {
+    host = static_cast<float4*>(std::malloc(sizeof(float4) * n_obs));
+    if (host == nullptr) return fail(h, RA_MPPI_ENOMEM, "host buffer");
+    float* tmp = static_cast<float*>(std::malloc(sizeof(float) * 3 * n_obs));
+    if (tmp == nullptr) {
+      std::free(host);
+      return fail(h, RA_MPPI_ENOMEM, "host buffer");
+    }
+    cudaError_t e = cudaMemcpy(tmp, xyr, sizeof(float) * 3 * n_obs, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+      std::free(tmp);
+      std::free(host);
+      return cuda_fail(h, e, "set_obstacles copy");
+    }
+    for (int i = 0; i < n_obs; ++i) {
+      const float r = tmp[3 * i + 2];
+      if (!(r >= 0.0f) || !std::isfinite(tmp[3 * i]) || !std::isfinite(tmp[3 * i + 1])) {
+        std::free(tmp);
+        std::free(host);
+        return fail(h, RA_MPPI_EINVAL, "obstacle radius must be >= 0 and centres finite");
+      }
+      host[i] = make_float4(tmp[3 * i], tmp[3 * i + 1], r, r * r);
+    }
+    std::free(tmp);
+    e = cudaMemcpyAsync(h->obs, host, sizeof(float4) * n_obs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    std::free(host);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_obstacles upload");
+  }
+  const cudaError_t e = cudaMemcpyAsync(&h->st->n_obs, &n_obs, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "set_obstacles sync");
+  } else {
+    return cuda_fail(h, e, "set_obstacles count");
+  }
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out, float* S_tilde, float* cvar,
+                 void* stream) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (x0 == nullptr || V_in == nullptr || V_out == nullptr) return fail(h, RA_MPPI_EINVAL, "x0, V_in and V_out are required");
+  if (fault("launch")) return fail(h, RA_MPPI_ECUDA, "injected launch failure");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const ra_mppi_problem& p = h->prob;
+  ramppi::RolloutArgs a{};
+  a.x0 = x0;
+  a.V = V_in;
+  a.obs = h->obs;
+  a.st = h->st;
+  a.U = h->U;
+  a.S = h->S;
+  a.cvar = h->cvar;
+  a.L = h->L;
+  a.nb_nom = (p.K + 32 * h->warps - 1) / (32 * h->warps);
+  a.obs_cap = h->obs_cap;
+  const int nb_dist = (p.K + h->warps - 1) / h->warps;
+  cudaError_t e;
+  if (h->ev_begin != nullptr) {
+    e = cudaEventRecord(h->ev_begin, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
+  }
+  switch (p.model) {
+    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, h->smem, a.nb_nom + nb_dist, s); break;
+    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, h->smem, a.nb_nom + nb_dist, s); break;
+    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, h->smem, a.nb_nom + nb_dist, s); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
+  if (h->ev_end != nullptr) {
+    e = cudaEventRecord(h->ev_end, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
+  }
+  ramppi::UpdateArgs u{};
+  u.S = h->S;
+  u.cvar = h->cvar;
+  u.U = h->U;
+  u.S_tilde = S_tilde != nullptr ? S_tilde : h->S_tilde;
+  u.V_out = V_out;
+  u.partials = h->partials;
+  u.st = h->st;
+  e = ramppi::launch_update(h->dp, u, h->nb_upd, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "update launch");
+  if (cvar != nullptr) {
+    e = cudaMemcpyAsync(cvar, h->cvar, sizeof(float) * p.K, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cvar copy");
+  }
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_step_host(ra_mppi_t* h, const float* x0_host, const float* V_in_host, float* V_out_host,
+                      float* S_tilde_host, void* stream) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (x0_host == nullptr || V_in_host == nullptr || V_out_host == nullptr)
+    return fail(h, RA_MPPI_EINVAL, "x0, V_in and V_out are required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t TN = (size_t)h->prob.T * h->nu;
+  cudaError_t e = cudaMemcpyAsync(h->x0_dev, x0_host, sizeof(float) * h->nx, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->V_dev, V_in_host, sizeof(float) * TN, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_host upload");
+  const int rc = ra_mppi_step(h, h->x0_dev, h->V_dev, h->V_dev, nullptr, nullptr, stream);
+  if (rc != RA_MPPI_OK) return rc;
+  e = cudaMemcpyAsync(V_out_host, h->V_dev, sizeof(float) * TN, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && S_tilde_host != nullptr)
+    e = cudaMemcpyAsync(S_tilde_host, h->S_tilde, sizeof(float) * h->prob.K, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_host download");
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_workspace(ra_mppi_t* h, const float** U, const float** S, const float** cvar, const float** L) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (U) *U = h->U;
+  if (S) *S = h->S;
+  if (cvar) *cvar = h->cvar;
+  if (L) *L = h->L;
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_copy_workspace(ra_mppi_t* h, float* U, float* S, float* cvar, float* L, void* stream) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (L != nullptr && h->L == nullptr) return fail(h, RA_MPPI_EINVAL, "risk costs were not kept");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t K = (size_t)h->prob.K;
+  cudaError_t e = cudaSuccess;
+  if (U) e = cudaMemcpyAsync(U, h->U, sizeof(float) * K * h->prob.T * h->nu, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && S) e = cudaMemcpyAsync(S, h->S, sizeof(float) * K, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && cvar) e = cudaMemcpyAsync(cvar, h->cvar, sizeof(float) * K, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && L) e = cudaMemcpyAsync(L, h->L, sizeof(float) * K * h->prob.M, cudaMemcpyDefault, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy_workspace");
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_get_iteration(ra_mppi_t* h, uint64_t* iteration) {
+  if (h == nullptr || iteration == nullptr) return RA_MPPI_EINVAL;
+  unsigned long long it = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&it, &h->st->iteration, sizeof(it), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_iteration");
+  *iteration = it;
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_set_iteration(ra_mppi_t* h, uint64_t iteration) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  const unsigned long long it = iteration;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h->st->iteration, &it, sizeof(it), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_iteration");
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_get_status(ra_mppi_t* h) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  int status = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&status, &h->st->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(&h->st->status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_status");
+  return status == 0 ? RA_MPPI_OK : RA_MPPI_ENONFINITE;
+}
+
+const char* ra_mppi_last_error(const ra_mppi_t* h) { return h == nullptr ? "null handle" : h->err.c_str(); }
+
+int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  const int w = warps_per_block == 0 ? h->warps : warps_per_block;
+  const int i = ilp == 0 ? h->ilp : ilp;
+  if (w < 1 || w > 16) return fail(h, RA_MPPI_EINVAL, "warps_per_block must be in [1, 16]");
+  if (i != 1 && i != 2 && i != 4) return fail(h, RA_MPPI_EINVAL, "ilp must be 1, 2 or 4");
+  const int R = (h->prob.M + 31) / 32;
+  if (R % i != 0) return fail(h, RA_MPPI_EINVAL, "ilp must divide ceil(M / 32)");
+  const int old_w = h->warps, old_i = h->ilp;
+  h->warps = w;
+  h->ilp = i;
+  const cudaError_t e = prepare(h);
+  if (e != cudaSuccess) {
+    h->warps = old_w;
+    h->ilp = old_i;
+    prepare(h);
+    return cuda_fail(h, e, "set_launch");
+  }
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_set_timing_events(ra_mppi_t* h, void* rollout_begin, void* rollout_end) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if ((rollout_begin == nullptr) != (rollout_end == nullptr))
+    return fail(h, RA_MPPI_EINVAL, "set both timing events or neither");
+  h->ev_begin = static_cast<cudaEvent_t>(rollout_begin);
+  h->ev_end = static_cast<cudaEvent_t>(rollout_end);
+  return RA_MPPI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// Device math of the RA-MPPI update: counter-based noise, vehicle models,
+// track geometry and running costs.  Everything here runs in registers; the
+// kernels in ra_rollout.cuh compose it.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ramppi {
+
+constexpr float kPi = 3.14159265358979323846f;
+#define RA_MPPI_MAX_M_DEV 256
+#define RA_MPPI_MAX_T_DEV 256
+
+// Constants of one problem, precomputed on the host (ra_api.cu) and passed to
+// the kernels by value.
+struct DevParams {
+  int K, M, T, nu, substeps;
+  int noise_type, obs_mode, cvar_mode;
+  unsigned risk_mask;
+  int n_warm;         // samples k < n_warm are drawn around V (Alg. 1)
+  int j_var;          // ceil(alpha M): rank (1-based) of VaR = L_(j) (Eq. 11)
+  float frac_j;       // j - alpha M: weight of L_(j) in the fractional tail
+  float tail_denom;   // (1 - alpha) M
+  float h;            // integration step dt / substeps
+  float mp[8];        // model parameters (see ra_mppi.h)
+  float dfz_f, dfz_r, inv_m, inv_iz;  // dynamic model: D Fz per axle, 1/m, 1/Iz
+  float sigma_u[2], inv_sig2[2], u_lo[2], u_hi[2];
+  float w_scale[4];
+  uint32_t mix_thresh;    // floor(mix_p 2^32): Gaussian branch iff selector word < it
+  float mix_gauss[4];     // mix_scale * w_scale[s] * sqrt(2)
+  float w_dev, w_speed, v_target, gamma, w_obs, w_bdry, c4, c5, c_lin, kappa, inv_kappa;
+  float track_S, track_R, track_hw;
+  float inv_lambda, A, B, C_u;
+  uint32_t seed_lo, seed_hi, instance;
+};
+
+// Mutable per-handle state in device memory, read at kernel start so that a
+// replayed launch sees the current update counter and obstacle count.
+struct DevState {
+  unsigned long long iteration;
+  int status;        // bit 0: non-finite cost, bit 1: all weights vanished
+  int n_obs;
+  unsigned int arrive;  // last-block-done counter of the update kernel
+  int pad;
+};
+
+enum : int { kStatusNonFinite = 1, kStatusNoWeight = 2 };
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// 4x32 S-box, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key bumps
+// 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = c.x * 0xD2511F53u, hi0 = __umulhi(c.x, 0xD2511F53u);
+    const uint32_t lo1 = c.z * 0xCD9E8D57u, hi1 = __umulhi(c.z, 0xCD9E8D57u);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniform (x + 1/2) 2^-32 in (0, 1): exact for x < 2^24, otherwise rounded once
+__device__ __forceinline__ float u01(uint32_t x) {
+  return __fmaf_rn(__uint2float_rn(x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+
+// Box-Muller pair from two words: sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2)
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+  const float rad = sqrtf(-2.0f * logf(u01(a)));
+  float s, c;
+  sincospif(2.0f * u01(b), &s, &c);
+  return make_float2(__fmul_rn(rad, c), __fmul_rn(rad, s));
+}
+
+// Heavy-tailed slot value: Laplace(0, b) by its inverse CDF; with the
+// selector word below floor(p 2^32), N(0, (mix_scale b)^2) by the Gaussian
+// inverse CDF instead.  Both use the tail mass v = 2 min(a, 1 - a) of the
+// uniform a = (word + 1/2) 2^-32, computed from the integer so no precision
+// is lost near a = 1, and the sign of a - 1/2.
+__device__ __forceinline__ float mix_value(uint32_t sel, uint32_t word, float b, float gfac,
+                                           uint32_t thresh) {
+  const bool hi = (word >> 31) != 0u;
+  const uint32_t r = hi ? ~word : word;
+  const float v = __fmaf_rn(__uint2float_rn(r), 4.656612873077393e-10f, 2.3283064365386963e-10f);
+  float mag;
+  if (sel < thresh) mag = gfac * erfcinvf(v);
+  else mag = -b * logf(v);
+  return hi ? mag : -mag;
+}
+
+// ---------------------------------------------------------------- models
+// Per-step control quantities shared by all rollouts of a sample:
+//   KIN  (steer, accel, tan(steer) / wheelbase, 0)
+//   DYN  (steer, accel, sin(steer), cos(steer))
+//   LIN  (u, 0, 0, 0)
+template <int MODEL>
+struct Model;
+
+template <>
+struct Model<0> {  // kinematic bicycle, explicit Euler
+  static constexpr int NX = 4, NU = 2, NS = 4;
+  __device__ static __forceinline__ int slot_dim(int s) { return s; }
+  __device__ static __forceinline__ float4 ctl(const DevParams& p, float u0, float u1) {
+    return make_float4(u0, u1, tanf(u0) / p.mp[0], 0.0f);
+  }
+  __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
+    for (int s = 0; s < p.substeps; ++s) {
+      float sp, cp;
+      sincosf(x[2], &sp, &cp);
+      const float hv = p.h * x[3];
+      x[0] = fmaf(hv, cp, x[0]);
+      x[1] = fmaf(hv, sp, x[1]);
+      x[2] = fmaf(hv, c.z, x[2]);
+      x[3] = fmaf(p.h, c.y, x[3]);
+    }
+  }
+  __device__ static __forceinline__ float speed(const float* x) { return x[3]; }
+};
+
+template <>
+struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heun
+  static constexpr int NX = 6, NU = 2, NS = 3;
+  __device__ static __forceinline__ int slot_dim(int s) { return 3 + s; }
+  __device__ static __forceinline__ float4 ctl(const DevParams& p, float u0, float u1) {
+    float s, c;
+    sincosf(u0, &s, &c);
+    return make_float4(u0, u1, s, c);
+  }
+  __device__ static __forceinline__ void deriv(const DevParams& p, const float* x, const float4 c,
+                                               float* f) {
+    const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], Ct = p.mp[5], vfloor = p.mp[7];
+    const float vx = x[3], vy = x[4], r = x[5];
+    const float vxs = fmaxf(vx, vfloor);
+    const float af = c.x - atan2f(fmaf(lf, r, vy), vxs);
+    const float ar = -atan2f(fmaf(-lr, r, vy), vxs);
+    const float fyf = p.dfz_f * sinf(Ct * atanf(Bt * af));
+    const float fyr = p.dfz_r * sinf(Ct * atanf(Bt * ar));
+    float sp, cp;
+    sincosf(x[2], &sp, &cp);
+    f[0] = vx * cp - vy * sp;
+    f[1] = vx * sp + vy * cp;
+    f[2] = r;
+    f[3] = c.y - fyf * c.z * p.inv_m + r * vy;
+    f[4] = (fyf * c.w + fyr) * p.inv_m - r * vx;
+    f[5] = (lf * fyf * c.w - lr * fyr) * p.inv_iz;
+  }
+  __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
+    for (int s = 0; s < p.substeps; ++s) {
+      float k1[6], k2[6], xp[6];
+      deriv(p, x, c, k1);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) xp[i] = fmaf(p.h, k1[i], x[i]);
+      deriv(p, xp, c, k2);
+      const float hh = 0.5f * p.h;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) x[i] = fmaf(hh, k1[i] + k2[i], x[i]);
+    }
+  }
+  __device__ static __forceinline__ float speed(const float* x) { return x[3]; }
+};
+
+template <>
+struct Model<2> {  // linear test system x+ = x + h u
+  static constexpr int NX = 1, NU = 1, NS = 1;
+  __device__ static __forceinline__ int slot_dim(int s) { return s; }
+  __device__ static __forceinline__ float4 ctl(const DevParams&, float u0, float) {
+    return make_float4(u0, 0.f, 0.f, 0.f);
+  }
+  __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
+    for (int s = 0; s < p.substeps; ++s) x[0] = fmaf(p.h, c.x, x[0]);
+  }
+  __device__ static __forceinline__ float speed(const float*) { return 0.f; }
+};
+
+// ---------------------------------------------------------------- noise
+// Process noise of rollout m of sample k at step t, added to the state:
+// counter (t | draw << 16, m, k, instance).
+template <int MODEL>
+__device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k0, uint32_t k1,
+                                                  uint32_t t, uint32_t m, uint32_t k, float* x) {
+  using Md = Model<MODEL>;
+  if (p.noise_type == 0) {
+    const uint4 w = philox4x32_10(make_uint4(t, m, k, p.instance), k0, k1);
+    const float2 z01 = box_muller(w.x, w.y);
+    x[Md::slot_dim(0)] = fmaf(p.w_scale[0], z01.x, x[Md::slot_dim(0)]);
+    if (Md::NS > 1) {
+      x[Md::slot_dim(1)] = fmaf(p.w_scale[1], z01.y, x[Md::slot_dim(1)]);
+      const float2 z23 = box_muller(w.z, w.w);
+      x[Md::slot_dim(2)] = fmaf(p.w_scale[2], z23.x, x[Md::slot_dim(2)]);
+      if (Md::NS > 3) x[Md::slot_dim(3)] = fmaf(p.w_scale[3], z23.y, x[Md::slot_dim(3)]);
+    }
+  } else {
+    const uint4 sel = philox4x32_10(make_uint4(t, m, k, p.instance), k0, k1);
+    const uint4 val = philox4x32_10(make_uint4(t | (1u << 16), m, k, p.instance), k0, k1);
+    const uint32_t sw[4] = {sel.x, sel.y, sel.z, sel.w};
+    const uint32_t vw[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+    for (int s = 0; s < Md::NS; ++s) {
+      if (p.w_scale[s] != 0.0f)
+        x[Md::slot_dim(s)] += mix_value(sw[s], vw[s], p.w_scale[s], p.mix_gauss[s], p.mix_thresh);
+    }
+  }
+}
+
+// Control sample U^k_t = clip(base + sigma eps): counter (t, 0xFFFFFFFF, k, instance).
+// Rounding is pinned (explicit _rn intrinsics) so every thread that draws the
+// same (k, t) gets the same bits.
+__device__ __forceinline__ float2 control_sample(const DevParams& p, uint32_t k0, uint32_t k1, int k,
+                                                 int t, float v0, float v1) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0xFFFFFFFFu, (uint32_t)k, p.instance), k0, k1);
+  const float2 z = box_muller(w.x, w.y);
+  const bool warm = k < p.n_warm;
+  const float b0 = warm ? v0 : 0.0f, b1 = warm ? v1 : 0.0f;
+  float u0 = __fmaf_rn(p.sigma_u[0], z.x, b0);
+  float u1 = __fmaf_rn(p.sigma_u[1], z.y, b1);
+  u0 = fminf(fmaxf(u0, p.u_lo[0]), p.u_hi[0]);
+  u1 = fminf(fmaxf(u1, p.u_lo[1]), p.u_hi[1]);
+  return make_float2(u0, u1);
+}
+
+// ---------------------------------------------------------------- costs
+// Stadium track: lateral deviation e (outward +), CCW arc length s from
+// (0, -R), distance to the nearest boundary d = hw - |e|.
+__device__ __forceinline__ float track_e(const DevParams& p, float px, float py) {
+  const float half = 0.5f * p.track_S;
+  const float ax = fabsf(px);
+  if (ax <= half) return fabsf(py) - p.track_R;
+  const float dx = ax - half;
+  return sqrtf(fmaf(dx, dx, py * py)) - p.track_R;
+}
+
+__device__ __forceinline__ float track_s(const DevParams& p, float px, float py) {
+  const float S = p.track_S, R = p.track_R, half = 0.5f * S;
+  const float total = 2.0f * S + 2.0f * kPi * R;
+  if (fabsf(px) <= half) {
+    if (py < 0.0f) return px >= 0.0f ? px : total + px;
+    return half + kPi * R + (half - px);
+  }
+  if (px > half) return half + R * (atan2f(py, px - half) + 0.5f * kPi);
+  const float th = atan2f(py, px + half);
+  const float phi = th > 0.0f ? th - 0.5f * kPi : th + 1.5f * kPi;
+  return half + kPi * R + S + R * phi;
+}
+
+// obstacle term: obstacles are (x, y, r, r^2)
+__device__ __forceinline__ float obstacle_term(const DevParams& p, float px, float py,
+                                               const float4* __restrict__ obs, int n_obs) {
+  float acc = 0.0f;
+  if (p.obs_mode == 0) {
+    for (int i = 0; i < n_obs; ++i) {
+      const float4 o = obs[i];
+      const float dx = px - o.x, dy = py - o.y;
+      acc += (fmaf(dx, dx, dy * dy) < o.w) ? 1.0f : 0.0f;
+    }
+  } else {
+    for (int i = 0; i < n_obs; ++i) {
+      const float4 o = obs[i];
+      const float dx = px - o.x, dy = py - o.y;
+      const float z = p.kappa * (o.z - sqrtf(fmaf(dx, dx, dy * dy)));
+      const float sp = z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
+      acc += sp;
+    }
+    acc *= p.inv_kappa;
+  }
+  return acc;
+}
+
+// running cost of the terms in `mask` (Eq. 20 family; Eqs. 21, 22)
+template <int MODEL>
+__device__ __forceinline__ float state_cost(const DevParams& p, const float* x, unsigned mask,
+                                            const float4* __restrict__ obs, int n_obs) {
+  float c = 0.0f;
+  if (MODEL == 2) {
+    if (mask & 16u) c = p.c_lin * x[0];
+    return c;
+  }
+  if (mask & 9u) {  // deviation or boundary needs e(x)
+    const float e = track_e(p, x[0], x[1]);
+    if (mask & 1u) c = fmaf(p.w_dev, e * e, c);
+    if (mask & 8u) {
+      const float d = p.track_hw - fabsf(e);
+      const float b = atanf(-100.0f * d) * (1.0f / kPi) + 0.5f;
+      c = fmaf(p.w_bdry, fmaxf(b, 0.0f), c);
+    }
+  }
+  if (mask & 2u) {
+    const float dv = Model<MODEL>::speed(x) - p.v_target;
+    c = fmaf(p.w_speed, dv * dv, c);
+  }
+  if (mask & 4u) c = fmaf(p.w_obs, obstacle_term(p, x[0], x[1], obs, n_obs), c);
+  if (mask & 16u) c = fmaf(p.c_lin, x[0], c);
+  return c;
+}
+
+// terminal cost phi(x) = c4 - c5 s(x) (Eq. 23)
+template <int MODEL>
+__device__ __forceinline__ float terminal_cost(const DevParams& p, const float* x) {
+  if (MODEL == 2) return 0.0f;
+  if (p.c5 == 0.0f) return p.c4;
+  return p.c4 - p.c5 * track_s(p, x[0], x[1]);
+}
+
+}  // namespace ramppi

@@ -1,0 +1,182 @@
+// Softmin weights and the weighted update of the RA-MPPI controls
+// (Eqs. 4, 5, 14-17).
+//
+// Each block owns a contiguous range of samples.  It forms
+// S~_k = S_k + A CVaR_k 1{CVaR_k > C_u}, takes its own minimum m_b, and
+// accumulates e_k = exp(-(S~_k - m_b) / lambda), s_b = sum e_k and
+// y_b[t, j] = sum e_k U[k, t, j] in FP32 with Neumaier compensation.  The
+// last block to finish (arrival counter, no waiting) merges the partials:
+// with m = min_b m_b every partial is rescaled by exp(-(m_b - m) / lambda),
+// so the result equals subtracting the global minimum first (Eq. 17); the
+// column sums merge in compensated FP32, the normalisation sum over K in
+// FP64, and V+ = sum y / sum s (Eq. 4).
+#include "ra_kernels.h"
+
+namespace ramppi {
+
+namespace {
+
+__device__ __forceinline__ void neumaier_add(float& sum, float& comp, float v) {
+  const float t = sum + v;
+  if (fabsf(sum) >= fabsf(v)) comp += (sum - t) + v;
+  else comp += (v - t) + sum;
+  sum = t;
+}
+
+__device__ __forceinline__ float block_min(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : __int_as_float(0x7F800000);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ float s_tilde_of(const DevParams& p, float S, float cv) {
+  // violation cost J_C = A CVaR 1{CVaR > C_u} (Eqs. 14, 15)
+  return S + ((cv > p.C_u) ? p.A * cv : 0.0f);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const DevParams p, const UpdateArgs a) {
+  __shared__ float red[32];
+  __shared__ double redd[32];
+  __shared__ float e_s[kUpdateThreads];
+  __shared__ float scale_s[kMaxUpdateBlocks];
+  __shared__ unsigned int is_last;
+  const int K = p.K, TN = p.T * p.nu;
+  const int per = (K + gridDim.x - 1) / gridDim.x;
+  const int kb = blockIdx.x * per;
+  const int ke = min(K, kb + per);
+  float* part = a.partials + (size_t)blockIdx.x * (2 + TN);
+
+  // block minimum of the finite S~ (non-finite samples get zero weight)
+  float mloc = __int_as_float(0x7F800000);
+  for (int k = kb + threadIdx.x; k < ke; k += blockDim.x) {
+    const float st = s_tilde_of(p, a.S[k], a.cvar[k]);
+    a.S_tilde[k] = st;
+    if (isfinite(st)) mloc = fminf(mloc, st);
+    else atomicOr(&a.st->status, kStatusNonFinite);
+  }
+  const float mb = block_min(mloc, red);
+
+  // compensated partial sums over this block's samples, 256 at a time
+  float s_sum = 0.0f, s_comp = 0.0f;
+  constexpr int kColsPerThread = (2 * RA_MPPI_MAX_T_DEV + kUpdateThreads - 1) / kUpdateThreads;
+  float y_sum[kColsPerThread], y_comp[kColsPerThread];
+#pragma unroll
+  for (int c = 0; c < kColsPerThread; ++c) { y_sum[c] = 0.0f; y_comp[c] = 0.0f; }
+  for (int k0 = kb; k0 < ke; k0 += blockDim.x) {
+    const int k = k0 + threadIdx.x;
+    float e = 0.0f;
+    if (k < ke) {
+      const float st = a.S_tilde[k];
+      if (isfinite(st) && isfinite(mb)) e = expf((mb - st) * p.inv_lambda);
+    }
+    e_s[threadIdx.x] = e;
+    neumaier_add(s_sum, s_comp, e);
+    __syncthreads();
+    const int n = min((int)blockDim.x, ke - k0);
+#pragma unroll
+    for (int c = 0; c < kColsPerThread; ++c) {
+      const int col = threadIdx.x + c * blockDim.x;
+      if (col < TN) {
+        const float* Ucol = a.U + (size_t)k0 * TN + col;
+        for (int i = 0; i < n; ++i) {
+          const float ei = e_s[i];
+          if (ei != 0.0f) neumaier_add(y_sum[c], y_comp[c], ei * Ucol[(size_t)i * TN]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // block total of e in FP64 (one value per thread, so the compensation is exact enough)
+  const double sb = block_sum_d((double)s_sum + (double)s_comp, redd);
+#pragma unroll
+  for (int c = 0; c < kColsPerThread; ++c) {
+    const int col = threadIdx.x + c * blockDim.x;
+    if (col < TN) part[2 + col] = y_sum[c] + y_comp[c];
+  }
+  if (threadIdx.x == 0) {
+    part[0] = mb;
+    part[1] = (float)sb;
+  }
+
+  // last block merges the partials
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int ticket = atomicAdd(&a.st->arrive, 1u);
+    is_last = (ticket == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+
+  // rescale each block's partials to the global minimum: exp(-(m_b - m) / lambda)
+  const int nb = gridDim.x;
+  const int stride = 2 + TN;
+  const volatile float* parts = a.partials;
+  float m = __int_as_float(0x7F800000);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fminf(m, parts[(size_t)b * stride]);
+  m = block_min(m, red);
+  double s_loc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const float mbb = parts[(size_t)b * stride];
+    const float sbb = parts[(size_t)b * stride + 1];
+    const float sc = (isfinite(mbb) && sbb > 0.0f) ? expf((m - mbb) * p.inv_lambda) : 0.0f;
+    scale_s[b] = sc;
+    s_loc += (double)sbb * (double)sc;
+  }
+  // the normalisation sum over all K samples, in FP64
+  const double s_tot = block_sum_d(s_loc, redd);
+  const bool ok = isfinite(m) && s_tot > 0.0 && isfinite(s_tot);
+  for (int col = threadIdx.x; col < TN; col += blockDim.x) {
+    float y = 0.0f, yc = 0.0f;
+    for (int b = 0; b < nb; ++b) {
+      const float sc = scale_s[b];
+      if (sc != 0.0f) neumaier_add(y, yc, parts[(size_t)b * stride + 2 + col] * sc);
+    }
+    if (ok) a.V_out[col] = (float)(((double)y + (double)yc) / s_tot);
+  }
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(&a.st->status, kStatusNoWeight);
+    a.st->arrive = 0u;        // ready for the next launch on this stream
+    a.st->iteration += 1ull;  // the next update draws fresh noise
+  }
+}
+
+cudaError_t launch_update(const DevParams& p, const UpdateArgs& a, int nblocks, cudaStream_t s) {
+  softmin_update_kernel<<<nblocks, kUpdateThreads, 0, s>>>(p, a);
+  return cudaGetLastError();
+}
+
+}  // namespace ramppi

@@ -122,7 +122,8 @@ def test_band_bounds_bracket(orc):
     p = rs.preset("c1_plain")
     out = orc.samples(p, rs.initial_state(0), rs.zero_controls(0, p["T"]), _scene(p), band_delta=1e-3)
     assert np.all(out["cvar_lo"] <= out["cvar"]) and np.all(out["cvar"] <= out["cvar_hi"])
-    assert np.all(out["S_lo"] <= out["S_tilde"]) and np.all(out["S_tilde"] <= out["S_hi"])
+    assert np.all(out["S_lo"] <= out["S"]) and np.all(out["S"] <= out["S_hi"])
+    assert np.all(out["St_lo"] <= out["S_tilde"]) and np.all(out["S_tilde"] <= out["St_hi"])
     assert np.any(out["cvar_lo"] < out["cvar_hi"])
 
 

@@ -1,0 +1,258 @@
+"""GPU parity of the RA-MPPI update against the FP64 oracle (needs a GB300).
+
+Every call goes through the C ABI (libramppi.so via paper_2209_12842_gb300);
+the oracle runs on the same seeded inputs.  Stages:
+  1. sampled controls U (noise + clipping)
+  2. per-sample S_k, CVaR_k, S~_k (with FP64 band bounds for indicator flips)
+  3. CVaR of the GPU's own risk costs L (select + tail arithmetic alone)
+  4. V+ from the GPU's S~ and U (softmin + weighted update alone)
+Sizes: small cases spanning several blocks with ragged tails, config 1 in
+full, and configs 2 and 5 at full size on sampled samples k.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import ra_scenes as rs
+from parity_util import check_banded
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_12842_gb300 import build as b
+
+    b.build()
+
+
+def run_gpu(p, obs, x0, V, keep_L=True, launch=None, iteration=None):
+    from paper_2209_12842_gb300 import RaMppi
+
+    ctl = RaMppi(p, obs, keep_risk_costs=keep_L)
+    if launch is not None:
+        ctl.set_launch(*launch)
+    if iteration is not None:
+        ctl.iteration = iteration
+    Vp = ctl.step(torch.from_numpy(np.asarray(x0, np.float32)).cuda(),
+                  torch.from_numpy(np.asarray(V, np.float32)).cuda())
+    ws = ctl.workspace()
+    torch.cuda.synchronize()
+    g = dict(V_plus=Vp.cpu().numpy(), S_tilde=ctl.S_tilde.cpu().numpy(),
+             cvar=ctl.cvar.cpu().numpy(), U=ws["U"].cpu().numpy(), S=ws["S"].cpu().numpy(),
+             L=ws["L"].cpu().numpy() if keep_L else None, status=ctl.status(),
+             iteration=ctl.iteration)
+    ctl.close()
+    return g
+
+
+def compare(p, g, ref, check_update=True):
+    ks = ref["ks"]
+    # 1. sampled controls
+    np.testing.assert_allclose(g["U"][ks], ref["U"], rtol=2e-6, atol=2e-6)
+    # 2. per-sample stage
+    nS = check_banded("S", g["S"][ks], ref["S"], ref["S_lo"], ref["S_hi"])
+    nC = check_banded("CVaR", g["cvar"][ks], ref["cvar"], ref["cvar_lo"], ref["cvar_hi"],
+                      floor=1e-4 * max(1.0, float(np.median(np.abs(ref["S_tilde"])))))
+    nT = check_banded("S_tilde", g["S_tilde"][ks], ref["S_tilde"], ref["St_lo"], ref["St_hi"])
+    # 3. CVaR on the GPU's own risk costs
+    if g["L"] is not None:
+        alpha = float(np.float32(p["alpha"]))
+        Bs = float(np.float32(p["B"]))
+        for i, k in enumerate(ks):
+            want = oracle.cvar(g["L"][k].astype(np.float64), alpha, Bs, p["cvar_mode"])
+            assert abs(g["cvar"][k] - want) <= 1e-5 * max(1.0, abs(want)), (k, g["cvar"][k], want)
+    # 4. update stage on the GPU's S~ and U
+    if check_update:
+        Vo, _ = oracle.update(g["S_tilde"].astype(np.float64), g["U"].astype(np.float64),
+                              float(np.float32(p["lam"])))
+        np.testing.assert_allclose(g["V_plus"], Vo, atol=1e-5, rtol=0)
+    return nS, nC, nT
+
+
+def _inputs(p, obs_kind="ahead", seed=1, V_seed=3):
+    model = p["model"]
+    if obs_kind == "ahead":
+        obs = rs.obstacles_ahead(seed, max(p["n_obs"], 1), *p["obs_r"],
+                                 x_from=0.1 if model == 1 else 0.3,
+                                 x_to=1.5 if model == 1 else 2.5)
+    elif obs_kind == "none":
+        obs = np.zeros((0, 3), np.float32)
+    else:
+        obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
+    x0 = rs.initial_state(model)
+    V = rs.random_controls(model, p["T"], p["u_lo"], p["u_hi"], V_seed)
+    return obs, x0, V
+
+
+@pytest.mark.parametrize("name", ["small_kin", "small_dyn"])
+@pytest.mark.parametrize("mode", ["RU", "TCE"])
+def test_small_cases_full_parity(name, mode):
+    p = rs.preset(name, cvar_mode=rs.CVAR_RU if mode == "RU" else rs.CVAR_TCE)
+    obs, x0, V = _inputs(p)
+    g = run_gpu(p, obs, x0, V)
+    assert g["status"] == 0
+    ref = oracle.samples(p, x0, V, obs, n_threads=8)
+    compare(p, g, ref)
+    assert np.mean(g["cvar"] > 0) > 0.2  # the scene exercises the risk term
+
+
+def test_config1_full():
+    p = rs.preset("c1_plain")
+    for obs_kind in ("track", "ahead"):
+        obs, x0, _ = _inputs(p, obs_kind)
+        V = rs.zero_controls(p["model"], p["T"])
+        g = run_gpu(p, obs, x0, V)
+        ref = oracle.samples(p, x0, V, obs, n_threads=8)
+        nS, nC, nT = compare(p, g, ref)
+        print(f"config 1 ({obs_kind}): banded S {nS}, CVaR {nC}, S~ {nT} of {p['K']}")
+
+
+def test_config2_full_size_sampled():
+    p = rs.preset("c2_closed_loop")
+    obs, x0, V = _inputs(p, "ahead")
+    g = run_gpu(p, obs, x0, V)
+    K = p["K"]
+    ks = np.unique(np.concatenate([[0, 1, K // 2, K - 2, K - 1],
+                                   np.random.default_rng(0).integers(0, K, 27)])).astype(np.int32)
+    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=8)
+    compare(p, g, ref)
+    # the default scene (obstacles spread over the track) as well
+    obs2, _, _ = _inputs(p, "track")
+    g2 = run_gpu(p, obs2, x0, V, keep_L=False)
+    ref2 = oracle.samples(p, x0, V, obs2, ks=ks[:12], n_threads=8)
+    compare(p, g2, ref2)
+
+
+@pytest.mark.parametrize("M,alpha", [(32, 0.8), (256, 0.95)])
+def test_config5_full_size_sampled(M, alpha):
+    p = rs.preset("c5_stress", M=M, alpha=alpha)
+    obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
+    obs = np.concatenate([obs, rs.obstacles_ahead(5, 6, 0.2, 0.5, x_from=0.1, x_to=1.5)])[: p["n_obs"]]
+    x0 = rs.initial_state(p["model"])
+    V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 9)
+    g = run_gpu(p, obs, x0, V, keep_L=False)
+    K = p["K"]
+    ks = np.array([0, 777, 40000, K - 1], dtype=np.int32)
+    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=8)
+    compare(p, g, ref)
+
+
+@pytest.mark.parametrize("K,M,T", [(1, 1, 1), (1, 32, 5), (3, 16, 4), (70, 33, 6), (129, 64, 3),
+                                   (33, 256, 2), (5, 100, 7)])
+def test_edge_sizes(K, M, T):
+    p = rs.preset("small_kin", K=K, M=M, T=T)
+    obs, x0, V = _inputs(p)
+    g = run_gpu(p, obs, x0, V)
+    ref = oracle.samples(p, x0, V, obs, n_threads=8)
+    compare(p, g, ref)
+    if K == 1:
+        np.testing.assert_array_equal(g["V_plus"], g["U"][0])
+
+
+def test_no_obstacles_and_options():
+    p = rs.preset("small_kin", eta=0.3, B=2.5, A=3.0, C_u=50.0, gamma=0.7,
+                  risk_mask=rs.RISK_DEV | rs.RISK_SPEED | rs.RISK_OBS | rs.RISK_BDRY,
+                  w_bdry=2.0, c4=0.6, c5=2.0)
+    for kind in ("none", "ahead"):
+        obs, x0, V = _inputs(p, kind)
+        g = run_gpu(p, obs, x0, V)
+        ref = oracle.samples(p, x0, V, obs, n_threads=8)
+        compare(p, g, ref)
+
+
+def test_dynamic_gaussian_noise_and_softplus():
+    p = rs.preset("small_dyn", noise_type=rs.NOISE_GAUSS, obs_mode=rs.OBS_SOFTPLUS, kappa=20.0)
+    obs, x0, V = _inputs(p)
+    g = run_gpu(p, obs, x0, V)
+    ref = oracle.samples(p, x0, V, obs, n_threads=8)
+    compare(p, g, ref)
+    p = rs.preset("c4_gradient", K=300)
+    obs, x0, V = _inputs(p)
+    g = run_gpu(p, obs, x0, V)
+    ref = oracle.samples(p, x0, V, obs, n_threads=8)
+    compare(p, g, ref)
+
+
+@pytest.mark.parametrize("launch", [(1, 1), (4, 2), (8, 4), (16, 1)])
+def test_launch_shapes_are_bitwise_identical(launch):
+    p = rs.preset("small_kin", K=200, M=128)
+    obs, x0, V = _inputs(p)
+    base = run_gpu(p, obs, x0, V)
+    g = run_gpu(p, obs, x0, V, launch=launch)
+    for key in ("U", "S", "cvar", "S_tilde", "L"):
+        np.testing.assert_array_equal(g[key], base[key])
+    np.testing.assert_allclose(g["V_plus"], base["V_plus"], atol=1e-6)
+
+
+def test_iteration_keys_the_noise():
+    p = rs.preset("small_kin")
+    obs, x0, V = _inputs(p)
+    a = run_gpu(p, obs, x0, V, iteration=5)
+    b = run_gpu(p, obs, x0, V, iteration=5)
+    c = run_gpu(p, obs, x0, V, iteration=6)
+    np.testing.assert_array_equal(a["V_plus"], b["V_plus"])
+    assert not np.array_equal(a["U"], c["U"])
+    assert a["iteration"] == 6
+    ref = oracle.samples(p, x0, V, obs, iteration=6, n_threads=8)
+    compare(p, c, ref)
+
+
+def test_linear_gaussian_cvar_statistics():
+    """P2 on the GPU: identical samples (sigma_u = 0), Gaussian risk cost;
+    the mean of CVaR_k over K samples matches the closed form within the
+    bias and 4 standard errors of the M = 256 estimator."""
+    from scipy import stats
+
+    T, M, K = 10, 256, 4096
+    sw, alpha = float(np.float32(0.5)), float(np.float32(0.9))
+    p = rs.preset("linear_test", K=K, M=M, T=T, w_scale=(sw, 0, 0, 0), alpha=alpha)
+    V = (np.arange(T) * 0.1 - 0.3).astype(np.float32).reshape(T, 1)
+    x0 = np.array([0.25], np.float32)
+    g = run_gpu(p, np.zeros((0, 3), np.float32), x0, V, keep_L=False)
+    xs = 0.25 + np.concatenate([[0.0], np.cumsum(V[:, 0].astype(np.float64))])[:T]
+    mu = xs.sum()
+    s = sw * np.sqrt((T - 1) * T * (2 * T - 1) / 6.0)
+    want = mu + s * stats.norm.pdf(stats.norm.ppf(alpha)) / (1 - alpha)
+    # spread of CVaR_k across samples gives the standard error of the mean;
+    # the finite-M bias of the fractional tail is O(1/M), bounded by s / M here
+    se = np.std(g["cvar"]) / np.sqrt(K)
+    assert abs(np.mean(g["cvar"]) - want) < 4 * se + 2 * s / M, (np.mean(g["cvar"]), want, se)
+    np.testing.assert_allclose(g["S"], mu, rtol=1e-6)
+
+
+def test_step_host_matches_step():
+    from paper_2209_12842_gb300 import RaMppi
+
+    p = rs.preset("small_dyn")
+    obs, x0, V = _inputs(p)
+    a = RaMppi(p, obs)
+    a.iteration = 3
+    Vd = a.step(torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda()).cpu().numpy()
+    a.iteration = 3
+    Vh, St = a.step_host(x0, V, S_tilde=True)
+    np.testing.assert_array_equal(Vh, Vd)
+    np.testing.assert_array_equal(St, a.S_tilde.cpu().numpy())
+    # in-place update (V_out aliases V_in)
+    a.iteration = 3
+    Vt = torch.from_numpy(V.copy()).cuda()
+    a.step(torch.from_numpy(x0).cuda(), Vt, V_out=Vt)
+    np.testing.assert_array_equal(Vt.cpu().numpy(), Vd)
+    a.close()
+
+
+def test_non_finite_state_sets_status():
+    p = rs.preset("small_kin")
+    obs, x0, V = _inputs(p)
+    x0 = x0.copy()
+    x0[0] = np.nan
+    g = run_gpu(p, obs, x0, V)
+    from paper_2209_12842_gb300.binding import RA_MPPI_ENONFINITE
+
+    assert g["status"] == RA_MPPI_ENONFINITE
+    assert np.all(np.isinf(g["cvar"]))
