@@ -247,12 +247,23 @@ def test_step_host_matches_step():
 
 
 def test_non_finite_state_sets_status():
+    from paper_2209_12842_gb300.binding import RA_MPPI_ENONFINITE
+
     p = rs.preset("small_kin")
     obs, x0, V = _inputs(p)
     x0 = x0.copy()
     x0[0] = np.nan
+    # obstacle-only risk cost: a NaN position never satisfies d < r, so L = 0
+    # (as in the oracle); the deviation term of q makes every S~ NaN
     g = run_gpu(p, obs, x0, V)
-    from paper_2209_12842_gb300.binding import RA_MPPI_ENONFINITE
-
     assert g["status"] == RA_MPPI_ENONFINITE
-    assert np.all(np.isinf(g["cvar"]))
+    assert np.all(np.isnan(g["S_tilde"]))
+    ref = oracle.samples(p, x0, V, obs, ks=[0, 1])
+    np.testing.assert_array_equal(g["cvar"][:2], ref["cvar"])
+    # a risk cost with the deviation term is NaN itself: CVaR = +inf
+    p = rs.preset("small_kin", risk_mask=rs.RISK_OBS | rs.RISK_DEV)
+    g = run_gpu(p, obs, x0, V)
+    assert g["status"] == RA_MPPI_ENONFINITE
+    assert np.all(np.isinf(g["cvar"])) and np.all(g["cvar"] > 0)
+    ref = oracle.samples(p, x0, V, obs, ks=[0, 1])
+    assert np.all(np.isinf(ref["cvar"]))
