@@ -323,14 +323,31 @@ def run_ours(args, p, x0, V, obs):
         dist.destroy_process_group()
 
 
+def kernel_source_sha():
+    """Hash of the sources of the rollout kernel (names and bytes), to tie ncu
+    counters to a kernel version."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2209_12842_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith(("ra_rollout", "ra_device", "ra_api")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def load_traffic(workload):
-    """DRAM bytes per rollout-kernel launch from the committed ncu summary,
-    or None when no summary matches the current kernel."""
+    """DRAM bytes per rollout-kernel launch from the committed ncu summary, or
+    None when none exists or it was taken on a different kernel version."""
     path = os.path.join(ROOT, "profiles", f"rollout_cvar_{workload}.json")
     try:
-        return json.load(open(path)).get("dram_bytes_per_launch")
+        rec = json.load(open(path))
     except (OSError, ValueError):
         return None
+    if rec.get("source_sha") != kernel_source_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def main():

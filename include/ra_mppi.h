@@ -202,7 +202,7 @@ int ra_mppi_get_status(ra_mppi_t* h);
 /* Human-readable reason of the last error on this handle ("" if none). */
 const char* ra_mppi_last_error(const ra_mppi_t* h);
 
-/* Kernel launch tuning: disturbed-rollout warps per block (1..16) and
+/* Kernel launch tuning: disturbed-rollout warps per block (1..8) and
  * rollouts each lane interleaves (1, 2 or 4); 0 keeps the default. */
 int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp);
 

@@ -132,6 +132,7 @@ DevParams make_params(const ra_mppi_problem& p) {
     d.dfz_r = (float)(D * m * g * lf / (lf + lr));
     d.inv_m = (float)(1.0 / m);
     d.inv_iz = (float)(1.0 / Iz);
+    d.pacejka_c15 = p.model_params[5] == 1.5f ? 1 : 0;
   }
   for (int j2 = 0; j2 < 2; ++j2) {
     d.sigma_u[j2] = p.sigma_u[j2];
@@ -205,7 +206,9 @@ cudaError_t prepare(ra_mppi* h) {
 // largest interleave in {4, 2, 1} that divides the rollouts per lane
 int default_ilp(int M, int model) {
   const int R = (M + 31) / 32;
-  const int cap = model == RA_MPPI_DYN_SINGLE_TRACK ? 2 : 4;
+  // measured on GB300: the dynamic model is register-bound (no interleave is
+  // fastest), the kinematic model gains from 2
+  const int cap = model == RA_MPPI_DYN_SINGLE_TRACK ? 1 : 2;
   for (int ilp = cap; ilp > 1; ilp >>= 1)
     if (R % ilp == 0) return ilp;
   return 1;
@@ -442,7 +445,7 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp) {
   if (h == nullptr) return RA_MPPI_EINVAL;
   const int w = warps_per_block == 0 ? h->warps : warps_per_block;
   const int i = ilp == 0 ? h->ilp : ilp;
-  if (w < 1 || w > 16) return fail(h, RA_MPPI_EINVAL, "warps_per_block must be in [1, 16]");
+  if (w < 1 || w > 8) return fail(h, RA_MPPI_EINVAL, "warps_per_block must be in [1, 8]");
   if (i != 1 && i != 2 && i != 4) return fail(h, RA_MPPI_EINVAL, "ilp must be 1, 2 or 4");
   const int R = (h->prob.M + 31) / 32;
   if (R % i != 0) return fail(h, RA_MPPI_EINVAL, "ilp must divide ceil(M / 32)");

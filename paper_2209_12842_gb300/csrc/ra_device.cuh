@@ -25,6 +25,7 @@ struct DevParams {
   float h;            // integration step dt / substeps
   float mp[8];        // model parameters (see ra_mppi.h)
   float dfz_f, dfz_r, inv_m, inv_iz;  // dynamic model: D Fz per axle, 1/m, 1/Iz
+  int pacejka_c15;    // Pacejka shape factor C is exactly 3/2 (closed form below)
   float sigma_u[2], inv_sig2[2], u_lo[2], u_hi[2];
   float w_scale[4];
   uint32_t mix_thresh;    // floor(mix_p 2^32): Gaussian branch iff selector word < it
@@ -92,6 +93,16 @@ __device__ __forceinline__ float mix_value(uint32_t sel, uint32_t word, float b,
   return hi ? mag : -mag;
 }
 
+// sin and cos of a heading angle: reduce to [-pi, pi] with a two-constant
+// split of 2 pi (Cody-Waite), then the hardware approximations, whose absolute
+// error is about 2^-21 on that interval.
+__device__ __forceinline__ void heading_sincos(float a, float* s, float* c) {
+  const float n = rintf(a * 0.15915494309189535f);  // a / (2 pi)
+  float r = fmaf(-n, 6.28318548202514648f, a);       // 2 pi rounded to float
+  r = fmaf(n, 1.7484556e-7f, r);                      // 2 pi - float(2 pi)
+  __sincosf(r, s, c);
+}
+
 // ---------------------------------------------------------------- models
 // Per-step control quantities shared by all rollouts of a sample:
 //   KIN  (steer, accel, tan(steer) / wheelbase, 0)
@@ -110,7 +121,7 @@ struct Model<0> {  // kinematic bicycle, explicit Euler
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
     for (int s = 0; s < p.substeps; ++s) {
       float sp, cp;
-      sincosf(x[2], &sp, &cp);
+      heading_sincos(x[2], &sp, &cp);
       const float hv = p.h * x[3];
       x[0] = fmaf(hv, cp, x[0]);
       x[1] = fmaf(hv, sp, x[1]);
@@ -130,17 +141,28 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     sincosf(u0, &s, &c);
     return make_float4(u0, u1, s, c);
   }
+  // sin(C atan(z)) of the Pacejka lateral force.  For C = 3/2 it has the
+  // closed form z (q + 2) / (q sqrt(2 q (q + 1))), q = sqrt(1 + z^2)
+  // (half-angle identities with cos(atan z) = 1/q; no cancellation near 0).
+  __device__ static __forceinline__ float pacejka_shape(const DevParams& p, float z) {
+    if (p.pacejka_c15) {
+      const float q = sqrtf(fmaf(z, z, 1.0f));
+      return z * (q + 2.0f) / (q * sqrtf(2.0f * q * (q + 1.0f)));
+    }
+    return sinf(p.mp[5] * atanf(z));
+  }
   __device__ static __forceinline__ void deriv(const DevParams& p, const float* x, const float4 c,
                                                float* f) {
-    const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], Ct = p.mp[5], vfloor = p.mp[7];
+    const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], vfloor = p.mp[7];
     const float vx = x[3], vy = x[4], r = x[5];
-    const float vxs = fmaxf(vx, vfloor);
-    const float af = c.x - atan2f(fmaf(lf, r, vy), vxs);
-    const float ar = -atan2f(fmaf(-lr, r, vy), vxs);
-    const float fyf = p.dfz_f * sinf(Ct * atanf(Bt * af));
-    const float fyr = p.dfz_r * sinf(Ct * atanf(Bt * ar));
+    // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx)
+    const float inv_vx = 1.0f / fmaxf(vx, vfloor);
+    const float af = c.x - atanf(fmaf(lf, r, vy) * inv_vx);
+    const float ar = -atanf(fmaf(-lr, r, vy) * inv_vx);
+    const float fyf = p.dfz_f * pacejka_shape(p, Bt * af);
+    const float fyr = p.dfz_r * pacejka_shape(p, Bt * ar);
     float sp, cp;
-    sincosf(x[2], &sp, &cp);
+    heading_sincos(x[2], &sp, &cp);
     f[0] = vx * cp - vy * sp;
     f[1] = vx * sp + vy * cp;
     f[2] = r;

@@ -104,7 +104,7 @@ __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP
 }
 
 template <int MODEL, int ILP>
-__global__ void __launch_bounds__(512) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
+__global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
   using Md = Model<MODEL>;
   extern __shared__ float4 smem[];
   float4* obs_s = smem;

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const De
   __shared__ float red[32];
   __shared__ double redd[32];
   __shared__ float e_s[kUpdateThreads];
+  __shared__ float col_s[(kUpdateThreads / 32) * 2 * RA_MPPI_MAX_T_DEV];
   __shared__ float scale_s[kMaxUpdateBlocks];
   __shared__ unsigned int is_last;
   const int K = p.K, TN = p.T * p.nu;
@@ -88,12 +89,17 @@ __global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const De
   }
   const float mb = block_min(mloc, red);
 
-  // compensated partial sums over this block's samples, 256 at a time
+  // compensated partial sums over this block's samples, 256 at a time.
+  // Columns (t, j) of U: warp w takes rows i = w, w + 8, ... of each chunk and
+  // lane l the columns l, l + 32, ...; four rows are in flight per iteration.
+  constexpr int kWarps = kUpdateThreads / 32;
+  constexpr int kColChunks = (2 * RA_MPPI_MAX_T_DEV + 31) / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nj = (TN + 31) >> 5;
   float s_sum = 0.0f, s_comp = 0.0f;
-  constexpr int kColsPerThread = (2 * RA_MPPI_MAX_T_DEV + kUpdateThreads - 1) / kUpdateThreads;
-  float y_sum[kColsPerThread], y_comp[kColsPerThread];
+  float y_sum[kColChunks], y_comp[kColChunks];
 #pragma unroll
-  for (int c = 0; c < kColsPerThread; ++c) { y_sum[c] = 0.0f; y_comp[c] = 0.0f; }
+  for (int j = 0; j < kColChunks; ++j) { y_sum[j] = 0.0f; y_comp[j] = 0.0f; }
   for (int k0 = kb; k0 < ke; k0 += blockDim.x) {
     const int k = k0 + threadIdx.x;
     float e = 0.0f;
@@ -105,14 +111,25 @@ __global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const De
     neumaier_add(s_sum, s_comp, e);
     __syncthreads();
     const int n = min((int)blockDim.x, ke - k0);
+    for (int i0 = warp; i0 < n; i0 += 4 * kWarps) {
+      float ev[4];
+      const float* rows[4];
 #pragma unroll
-    for (int c = 0; c < kColsPerThread; ++c) {
-      const int col = threadIdx.x + c * blockDim.x;
-      if (col < TN) {
-        const float* Ucol = a.U + (size_t)k0 * TN + col;
-        for (int i = 0; i < n; ++i) {
-          const float ei = e_s[i];
-          if (ei != 0.0f) neumaier_add(y_sum[c], y_comp[c], ei * Ucol[(size_t)i * TN]);
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * kWarps;
+        ev[u] = i < n ? e_s[i] : 0.0f;
+        rows[u] = a.U + (size_t)(k0 + (i < n ? i : 0)) * TN;
+      }
+#pragma unroll
+      for (int j = 0; j < kColChunks; ++j) {
+        const int col = lane + 32 * j;
+        if (j < nj && col < TN) {
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = ev[u] != 0.0f ? rows[u][col] : 0.0f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (ev[u] != 0.0f) neumaier_add(y_sum[j], y_comp[j], ev[u] * v[u]);
         }
       }
     }
@@ -120,10 +137,18 @@ __global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const De
   }
   // block total of e in FP64 (one value per thread, so the compensation is exact enough)
   const double sb = block_sum_d((double)s_sum + (double)s_comp, redd);
+  // merge the 8 warps' column sums through shared memory
 #pragma unroll
-  for (int c = 0; c < kColsPerThread; ++c) {
-    const int col = threadIdx.x + c * blockDim.x;
-    if (col < TN) part[2 + col] = y_sum[c] + y_comp[c];
+  for (int j = 0; j < kColChunks; ++j) {
+    const int col = lane + 32 * j;
+    if (j < nj && col < TN) col_s[warp * 2 * RA_MPPI_MAX_T_DEV + col] = y_sum[j] + y_comp[j];
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < TN; col += blockDim.x) {
+    float y = 0.0f, yc = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) neumaier_add(y, yc, col_s[w * 2 * RA_MPPI_MAX_T_DEV + col]);
+    part[2 + col] = y + yc;
   }
   if (threadIdx.x == 0) {
     part[0] = mb;

@@ -179,7 +179,7 @@ def test_dynamic_gaussian_noise_and_softplus():
     compare(p, g, ref)
 
 
-@pytest.mark.parametrize("launch", [(1, 1), (4, 2), (8, 4), (16, 1)])
+@pytest.mark.parametrize("launch", [(1, 1), (4, 2), (8, 4), (2, 1)])
 def test_launch_shapes_are_bitwise_identical(launch):
     p = rs.preset("small_kin", K=200, M=128)
     obs, x0, V = _inputs(p)
