@@ -212,6 +212,33 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp);
  * alone.  NULL, NULL turns the hook off. */
 int ra_mppi_set_timing_events(ra_mppi_t* h, void* rollout_begin, void* rollout_end);
 
+/* Allocation-free softmin-weighted update.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * where they run the update, such as a controller on a real-time thread that
+ * may not call cudaMalloc/cudaFree (they can block and synchronise the
+ * device), or a host program that owns all device memory through its own
+ * pool and hands the library only pointers.  It computes step 6 above on
+ * caller-supplied inputs:
+ *   S_tilde [K]        device, costs S~_k (non-finite entries get weight 0)
+ *   U       [K][T][nu] device, sampled controls
+ *   V_out   [T][nu]    device, receives V+ = sum_k w_k U^k / sum_k w_k,
+ *                      w_k = exp(-(S~_k - min S~) / lambda); left unchanged
+ *                      when no S~_k is finite
+ * Limits: 1 <= K <= 2^24, 1 <= T nu <= RA_MPPI_NOALLOC_MAX_COLS, lambda > 0
+ * and finite; anything else returns RA_MPPI_EINVAL before any work is
+ * enqueued.  The call allocates nothing: its per-block partials and arrival
+ * counter live in one fixed device array of about 130 KB, which every GPU
+ * that loads this library keeps until the process exits; the counter is
+ * cleared with cudaMemsetAsync before each launch.  The first call on a
+ * device looks up that array's device address with the device current;
+ * make this first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents: calls that overlap on the
+ * GPU (different streams, or threads without ordering between them) race;
+ * calls ordered on one stream do not. */
+#define RA_MPPI_NOALLOC_MAX_COLS 512
+int ra_mppi_softmin_update_noalloc(const float* S_tilde, const float* U, int32_t K, int32_t T, int32_t nu,
+                                   float lambda, float* V_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

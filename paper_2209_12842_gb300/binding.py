@@ -76,6 +76,9 @@ def _declare(L):
     L.ra_mppi_last_error.restype = ctypes.c_char_p
     L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
     L.ra_mppi_set_timing_events.argtypes = [_VP, _VP, _VP]
+    L.ra_mppi_softmin_update_noalloc.argtypes = [_FP, _FP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_float, _FP, _VP]
+    L.ra_mppi_softmin_update_noalloc.restype = ctypes.c_int
     for name in ("ra_mppi_create", "ra_mppi_set_obstacles", "ra_mppi_step", "ra_mppi_step_host",
                  "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_get_iteration", "ra_mppi_set_iteration",
                  "ra_mppi_get_status", "ra_mppi_set_launch", "ra_mppi_set_timing_events"):
@@ -207,3 +210,9 @@ def ra_mppi_set_launch(h, warps_per_block=0, ilp=0):
 def ra_mppi_set_timing_events(h, begin_event_handle=None, end_event_handle=None):
     _check(lib().ra_mppi_set_timing_events(h, begin_event_handle, end_event_handle),
            "ra_mppi_set_timing_events", h)
+
+
+def ra_mppi_softmin_update_noalloc(S_tilde_ptr, U_ptr, K, T, nu, lam, V_out_ptr, stream=0):
+    """Softmin-weighted update from caller buffers, without any allocation."""
+    return lib().ra_mppi_softmin_update_noalloc(S_tilde_ptr, U_ptr, int(K), int(T), int(nu), float(lam),
+                                                V_out_ptr, stream)
