@@ -178,6 +178,22 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
 int ra_mppi_step_host(ra_mppi_t* h, const float* x0_host, const float* V_in_host, float* V_out_host,
                       float* S_tilde_host, void* stream);
 
+/* One pass of Algorithm 1's receding-horizon loop on a simulated plant:
+ * the state estimate is the plant state x, one update (ra_mppi_step) gives
+ * V+, the first control v0+ is executed on the plant
+ * x <- F(x, v0+) + w (Eqs. 1, 6; the plant's noise has its own Philox
+ * stream, counter (draw << 16, 0xFFFFFFFE, 0xFFFFFFFF, instance) at the
+ * update's iteration), and V is warm-started from V+ ("V = V+", Alg. 1),
+ * shifted left by one step with the last control repeated when shift != 0.
+ *   x          [nx]     device, in: plant state; out: next plant state
+ *   V          [T][nu]  device, in: mean controls; out: next warm start
+ *   S_tilde    [K]      device or NULL: receives the update's S~_k
+ *   collisions [1]      device int32 or NULL: incremented when the new plant
+ *                       state lies inside an obstacle or off the track
+ * Enqueued on `stream` (three kernels), no synchronisation. */
+int ra_mppi_closed_loop_step(ra_mppi_t* h, float* x, float* V, float* S_tilde, int32_t* collisions,
+                             int32_t shift, void* stream);
+
 /* Device views of the last update's workspace, valid until destroy:
  *   U [K][T][nu] sampled (clipped) controls, S [K] nominal costs (Eq. 3),
  *   cvar [K] CVaR values, L [K][M] risk costs (NULL unless the problem had
@@ -211,6 +227,72 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp);
  * rollout kernel on the step's stream, so the caller can time that kernel
  * alone.  NULL, NULL turns the hook off. */
 int ra_mppi_set_timing_events(ra_mppi_t* h, void* rollout_begin, void* rollout_end);
+
+/* ------------------------------------------------------------------ */
+/* Batched updates: B independent problems in one persistent launch    */
+/* replayed from a CUDA graph.  The paper updates one controller; this  */
+/* runs many (different K, M, T, seed and obstacles, common model, cost */
+/* and risk parameters) at once, each with exactly the single-problem   */
+/* arithmetic.                                                          */
+/* ------------------------------------------------------------------ */
+typedef struct ra_mppi_instance {
+  int32_t K, M, T;          /* sizes of this problem (as in ra_mppi_problem) */
+  int32_t max_obstacles;    /* obstacle capacity of this problem            */
+  uint64_t seed;            /* Philox key of this problem                   */
+  uint32_t instance_id;     /* fourth Philox counter word                   */
+  int32_t reserved;
+} ra_mppi_instance;
+
+typedef struct ra_mppi_batch ra_mppi_batch_t;
+
+/* Validate every problem (common fields + inst[i]) as ra_mppi_create would,
+ * allocate packed buffers, order the work items (nominal items first, then
+ * the disturbed samples of the costliest problems first) and capture the
+ * graph (queue reset, persistent rollout kernel, batched update kernel). */
+int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* inst, int32_t B,
+                         ra_mppi_batch_t** out);
+void ra_mppi_batch_destroy(ra_mppi_batch_t* b);
+
+/* Offsets of problem i in the packed buffers, offsets[4 i + 0..3] =
+ * (x0, V / V_out, per-sample arrays, U), counted in floats except the
+ * per-sample offset, counted in samples. */
+int ra_mppi_batch_layout(ra_mppi_batch_t* b, int64_t* offsets);
+
+/* Library-owned packed device buffers, stable for the handle's life (the
+ * graph reads and writes them): x0 [sum nx], V [sum T_i nu] (input mean
+ * controls), V_out [sum T_i nu] (V+), S_tilde [sum K_i]. */
+int ra_mppi_batch_buffers(ra_mppi_batch_t* b, float** x0, float** V, float** V_out, float** S_tilde);
+
+/* Copy packed inputs in (x0 [sum nx], V [sum T_i nu]) and outputs out
+ * (V_out [sum T_i nu], S_tilde [sum K_i]) between caller buffers (host or
+ * device; NULL skips one) and the library's buffers, on `stream`. */
+int ra_mppi_batch_write_inputs(ra_mppi_batch_t* b, const float* x0, const float* V, void* stream);
+int ra_mppi_batch_read_outputs(ra_mppi_batch_t* b, float* V_out, float* S_tilde, void* stream);
+
+/* Obstacles of problem i, as ra_mppi_set_obstacles (synchronous). */
+int ra_mppi_batch_set_obstacles(ra_mppi_batch_t* b, int32_t i, const float* xyr, int32_t n_obs, void* stream);
+
+/* One update of every problem: replay of the captured graph on `stream`. */
+int ra_mppi_step_batched(ra_mppi_batch_t* b, void* stream);
+/* The same kernels launched directly (no graph), for comparison. */
+int ra_mppi_step_batched_eager(ra_mppi_batch_t* b, void* stream);
+
+/* Packed copies of the last update's U, S and CVaR (any may be NULL). */
+int ra_mppi_batch_copy_workspace(ra_mppi_batch_t* b, float* U, float* S, float* cvar, void* stream);
+
+/* Update counter of every problem; status word of all problems (waits). */
+int ra_mppi_batch_set_iteration(ra_mppi_batch_t* b, uint64_t iteration);
+int ra_mppi_batch_get_status(ra_mppi_batch_t* b);
+
+/* Launch shape of the persistent kernel (warps per block 1..8, rollouts a
+ * lane interleaves 1 or 2; the grid fills every SM to its occupancy).  tune
+ * times the candidate shapes on the current inputs (`replays` graph replays
+ * each), keeps the fastest, recaptures the graph and restores the update
+ * counters; results do not depend on the shape. */
+int ra_mppi_batch_set_launch(ra_mppi_batch_t* b, int32_t warps_per_block, int32_t ilp);
+int ra_mppi_batch_get_launch(ra_mppi_batch_t* b, int32_t* warps_per_block, int32_t* ilp, int32_t* grid);
+int ra_mppi_batch_tune(ra_mppi_batch_t* b, int32_t replays, float* best_ms);
+const char* ra_mppi_batch_last_error(const ra_mppi_batch_t* b);
 
 /* Allocation-free softmin-weighted update.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory

@@ -103,6 +103,8 @@ def lib():
         L.orc_sizeof_problem.restype = ctypes.c_int32
         L.orc_n_warm.argtypes = [_P]
         L.orc_n_warm.restype = ctypes.c_int32
+        L.orc_backward.argtypes = [_P, _D, _D, _D, ctypes.c_int32, _D, _D, _D, _D]
+        L.orc_backward.restype = ctypes.c_int32
         assert L.orc_sizeof_problem() == ctypes.sizeof(Problem)
         _lib = L
     return _lib
@@ -122,8 +124,10 @@ def _ptr(a, typ=_D):
     return a.ctypes.data_as(typ)
 
 
-def make_problem(p, iteration=0, band_delta=1e-4, n_threads=1):
-    """Oracle problem from a preset dict; reals are rounded to float32 first."""
+def make_problem(p, iteration=0, band_delta=1e-4, n_threads=1, exact=False):
+    """Oracle problem from a preset dict; reals are rounded to float32 first
+    (exact=True keeps them as given, for finite differences)."""
+    _f32 = (lambda v: float(v)) if exact else globals()["_f32"]
     pr = Problem()
     for name in ("model", "K", "M", "T", "substeps", "noise_type", "obs_mode", "cvar_mode"):
         setattr(pr, name, int(p[name]))
@@ -230,15 +234,16 @@ def n_warm(prob):
 
 # ---------------------------------------------------------------- pipeline
 
-def samples(p, x0, V, obs, ks=None, iteration=0, band_delta=1e-4, n_threads=1, want_L=False):
+def samples(p, x0, V, obs, ks=None, iteration=0, band_delta=1e-4, n_threads=1, want_L=False, exact=False):
     """Per-sample stage of one update for the sample indices ks (default all)."""
-    prob = make_problem(p, iteration, band_delta, n_threads)
+    prob = make_problem(p, iteration, band_delta, n_threads, exact=exact)
     nx, nu = nx_nu(p)
     K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
     ks = np.arange(K, dtype=np.int32) if ks is None else _arr(ks, np.int32)
     nk = int(ks.size)
-    x0 = _arr(np.asarray(x0, dtype=np.float32))
-    V = _arr(np.asarray(V, dtype=np.float32).reshape(T, nu))
+    cast = np.float64 if exact else np.float32
+    x0 = _arr(np.asarray(x0, dtype=cast))
+    V = _arr(np.asarray(V, dtype=cast).reshape(T, nu))
     o = _arr(np.asarray(obs, dtype=np.float32).reshape(-1, 3)) if len(obs) else np.zeros((0, 3))
     out = {name: np.zeros(nk) for name in ("S", "cvar", "S_tilde", "S_lo", "S_hi", "cvar_lo",
                                           "cvar_hi", "St_lo", "St_hi")}
@@ -270,10 +275,10 @@ def update(S_tilde, U, lam):
     return Vp, w
 
 
-def step(p, x0, V, obs, iteration=0, band_delta=1e-4, n_threads=1, want_L=False):
+def step(p, x0, V, obs, iteration=0, band_delta=1e-4, n_threads=1, want_L=False, exact=False):
     """One full RA-MPPI update: per-sample stage for all k, then the update."""
-    out = samples(p, x0, V, obs, None, iteration, band_delta, n_threads, want_L)
-    Vp, w = update(out["S_tilde"], out["U"], _f32(p["lam"]))
+    out = samples(p, x0, V, obs, None, iteration, band_delta, n_threads, want_L, exact=exact)
+    Vp, w = update(out["S_tilde"], out["U"], float(p["lam"]) if exact else _f32(p["lam"]))
     out["V_plus"] = Vp
     out["weights"] = w
     return out
@@ -310,3 +315,42 @@ def closed_loop(p, x0, V0, obs, n_updates, shift=True, iteration0=0, n_threads=1
         xs.append(x.copy())
         V = np.concatenate([Vp[1:], Vp[-1:]], 0) if shift else Vp
     return np.array(xs), np.array(Vs), hits
+
+
+THETA_NAMES = ("w_dev", "w_speed", "gamma", "w_obs")
+
+
+def backward(p, x0, V, obs, gV_plus, gS_tilde=None, iteration=0, exact=False):
+    """Analytic vector-Jacobian product of one update: gradients of
+    <gV_plus, V+> + <gS_tilde, S~> w.r.t. V [T, nu] and theta =
+    (w_dev, w_speed, gamma, w_obs)."""
+    prob = make_problem(p, iteration, exact=exact)
+    nx, nu = nx_nu(p)
+    T, K = int(p["T"]), int(p["K"])
+    cast = np.float64 if exact else np.float32
+    x0 = _arr(np.asarray(x0, dtype=cast))
+    V = _arr(np.asarray(V, dtype=cast).reshape(T, nu))
+    o = _arr(np.asarray(obs, dtype=np.float32).reshape(-1, 3)) if len(obs) else np.zeros((0, 3))
+    gVp = _arr(np.asarray(gV_plus, dtype=np.float64).reshape(T, nu))
+    gS = None if gS_tilde is None else _arr(np.asarray(gS_tilde, dtype=np.float64).reshape(K))
+    gV = np.zeros((T, nu))
+    gth = np.zeros(4)
+    rc = lib().orc_backward(ctypes.byref(prob), _ptr(x0), _ptr(V), _ptr(o), int(len(o)), _ptr(gVp),
+                            _ptr(gS), _ptr(gV), _ptr(gth))
+    if rc != 0:
+        raise RuntimeError(f"orc_backward failed: {rc}")
+    return gV, gth
+
+
+def objective(p, x0, V, obs, gV_plus, gS_tilde=None, iteration=0, theta=None):
+    """<gV_plus, V+> + <gS_tilde, S~> of one update in float64 (for finite
+    differences); theta overrides (w_dev, w_speed, gamma, w_obs)."""
+    q = dict(p)
+    if theta is not None:
+        for name, v in zip(THETA_NAMES, theta):
+            q[name] = float(v)
+    out = step(q, x0, V, obs, iteration=iteration, exact=True)
+    val = float(np.sum(np.asarray(gV_plus) * out["V_plus"]))
+    if gS_tilde is not None:
+        val += float(np.sum(np.asarray(gS_tilde) * out["S_tilde"]))
+    return val

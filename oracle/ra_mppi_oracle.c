@@ -541,3 +541,289 @@ double orc_state_cost(const orc_problem* p, const double* x, const double* obs, 
 double orc_terminal_cost(const orc_problem* p, const double* x) { return terminal_cost(p, x); }
 int32_t orc_sizeof_problem(void) { return (int32_t)sizeof(orc_problem); }
 int32_t orc_n_warm(const orc_problem* p) { return n_warm_of(p); }
+
+/* ------------------------------------------------------------------ */
+/* Adjoint (vector-Jacobian product) of one update.                      */
+/*                                                                       */
+/* For fixed noise, one update maps the mean controls V and the cost      */
+/* weights theta = (w_dev, w_speed, gamma, w_obs) to (V+, S~).  Given     */
+/* cotangents gV+ [T][nu] and gS~ [K], this returns                      */
+/*   gV = d<gV+, V+> / dV + d<gS~, S~> / dV,  gtheta likewise.            */
+/* Steps, each the derivative of the corresponding forward step:        */
+/*   Eq. 4/17: V+ = sum w U / sum w  =>  dV+/dU_k = w^_k I and            */
+/*             dV+/dS~_k = -(w^_k / lambda) (U_k - V+)                    */
+/*   Eqs. 14-16: dS~/dS = 1, dS~/dCVaR = A 1{CVaR > C_u}                  */
+/*   Eqs. 10-13, 18, 19: CVaR is piecewise linear in L; its weights are   */
+/*             1/((1-alpha)M) above VaR, the remaining weight shared      */
+/*             equally by the values equal to VaR, 0 below; the scaling   */
+/*             adds (1-B)/M to every weight times B                       */
+/*   Eqs. 3, 9: reverse sweeps lambda_t = dc/dx_t + (dF/dx)' lambda_{t+1} */
+/*             through the stored states, u-bar_t += (dF/du)' lambda_{t+1}*/
+/*   Alg. 1:   U = clip(V + eps) passes the cotangent to V inside the box */
+/*             for the samples drawn around V; the control cost            */
+/*             gamma v' Sigma^-1 u depends on V directly as well.          */
+/* The indicator obstacle term has zero derivative almost everywhere.    */
+/* Only the kinematic and linear models are differentiated (returns -6   */
+/* for the dynamic model).                                               */
+/* ------------------------------------------------------------------ */
+
+/* gradient of the track deviation e and arc length s w.r.t. (px, py) */
+static void track_grad(const orc_problem* p, double px, double py, double de[2], double ds[2]) {
+  double half = 0.5 * p->track_straight;
+  de[0] = de[1] = ds[0] = ds[1] = 0.0;
+  if (fabs(px) <= half) {
+    if (py < 0.0) { de[1] = -1.0; ds[0] = 1.0; }
+    else { de[1] = 1.0; ds[0] = -1.0; }
+  } else {
+    double cx = px > half ? half : -half;
+    double dx = px - cx, rho = sqrt(dx * dx + py * py);
+    if (rho > 0.0) {
+      de[0] = dx / rho;
+      de[1] = py / rho;
+      /* s = const + R atan2(py, dx): ds = R (-py, dx) / rho^2 */
+      ds[0] = p->track_radius * (-py) / (rho * rho);
+      ds[1] = p->track_radius * dx / (rho * rho);
+    }
+  }
+}
+
+/* gradient w.r.t. the state of the cost terms in mask, scaled by c, added to
+ * gx; theta-gradient (dev, speed, -, obs) of the same terms added to gth */
+static void state_cost_grad(const orc_problem* p, const double* x, const double* obs, int n_obs,
+                            uint32_t mask, double c, double* gx, double* gth) {
+  if (p->model == ORC_LIN) {
+    if (mask & ORC_R_LIN) gx[0] += c * p->c_lin;
+    return;
+  }
+  double tr[3], de[2], ds[2];
+  orc_track(p, x[0], x[1], tr);
+  track_grad(p, x[0], x[1], de, ds);
+  if (mask & ORC_R_DEV) {
+    gx[0] += c * p->w_dev * 2.0 * tr[0] * de[0];
+    gx[1] += c * p->w_dev * 2.0 * tr[0] * de[1];
+    gth[0] += c * tr[0] * tr[0];
+  }
+  if (mask & ORC_R_SPEED) {
+    gx[3] += c * p->w_speed * 2.0 * (x[3] - p->v_target);
+    gth[1] += c * (x[3] - p->v_target) * (x[3] - p->v_target);
+  }
+  if (mask & ORC_R_OBS) {
+    double val = 0.0, g0 = 0.0, g1 = 0.0;
+    for (int i = 0; i < n_obs; ++i) {
+      double dx = x[0] - obs[3 * i], dy = x[1] - obs[3 * i + 1];
+      double d = sqrt(dx * dx + dy * dy), r = obs[3 * i + 2];
+      if (p->obs_mode == ORC_OBS_INDICATOR) {
+        if (d < r) val += 1.0;
+      } else {
+        double z = p->kappa * (r - d);
+        double sp = z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
+        val += sp / p->kappa;
+        double sig = 1.0 / (1.0 + exp(-z));
+        if (d > 0.0) { g0 += -sig * dx / d; g1 += -sig * dy / d; }
+      }
+    }
+    gx[0] += c * p->w_obs * g0;
+    gx[1] += c * p->w_obs * g1;
+    gth[3] += c * val;
+  }
+  if (mask & ORC_R_BDRY) {
+    /* b = atan(-100 d)/pi + 1/2 > 0, d = hw - |e| */
+    double d = tr[2];
+    double db_dd = (-100.0 / ORC_PI) / (1.0 + 1e4 * d * d);
+    double sgn = tr[0] > 0.0 ? 1.0 : (tr[0] < 0.0 ? -1.0 : 0.0);
+    gx[0] += c * p->w_bdry * db_dd * (-sgn) * de[0];
+    gx[1] += c * p->w_bdry * db_dd * (-sgn) * de[1];
+  }
+  if (mask & ORC_R_LIN) gx[0] += c * p->c_lin;
+}
+
+/* one integration sub-step G of the kinematic / linear model and its
+ * transposed Jacobians applied to lam: lam_out = (dG/ds)' lam, gu += (dG/du)' lam */
+static void substep_vjp(const orc_problem* p, const double* s, const double* u, const double* lam,
+                        double* lam_out, double* gu) {
+  double h = p->dt / (p->substeps > 0 ? p->substeps : 1);
+  if (p->model == ORC_KIN) {
+    double L = p->model_params[0], psi = s[2], v = s[3];
+    double cs = cos(psi), sn = sin(psi), tn = tan(u[0]), sec2 = 1.0 / (cos(u[0]) * cos(u[0]));
+    lam_out[0] = lam[0];
+    lam_out[1] = lam[1];
+    lam_out[2] = lam[2] + lam[0] * (-h * v * sn) + lam[1] * (h * v * cs);
+    lam_out[3] = lam[3] + lam[0] * (h * cs) + lam[1] * (h * sn) + lam[2] * (h * tn / L);
+    gu[0] += lam[2] * h * v * sec2 / L;
+    gu[1] += lam[3] * h;
+  } else {
+    lam_out[0] = lam[0];
+    gu[0] += lam[0] * h;
+  }
+}
+
+static void substep_fwd(const orc_problem* p, const double* s, const double* u, double* out) {
+  orc_problem q = *p;
+  q.dt = p->dt / (p->substeps > 0 ? p->substeps : 1);
+  q.substeps = 1;
+  orc_dynamics(&q, s, u, out);
+}
+
+/* reverse sweep of one rollout with stored states xs[(T+1)][nx]; cost
+ * weight c on the running terms `mask` (and on phi when with_phi);
+ * accumulates gU [T][nu] and gth [4] */
+static void rollout_vjp(const orc_problem* p, const double* xs, const double* Uk, const double* obs, int n_obs,
+                        uint32_t mask, int with_phi, double c, double* gU, double* gth) {
+  const int nx = nx_of(p->model), nu = nu_of(p->model), T = p->T;
+  const int ns = p->substeps > 0 ? p->substeps : 1;
+  double lam[6] = {0, 0, 0, 0, 0, 0};
+  if (with_phi && p->model != ORC_LIN && p->c5 != 0.0) {
+    double de[2], ds[2];
+    const double* xT = xs + (size_t)T * nx;
+    track_grad(p, xT[0], xT[1], de, ds);
+    lam[0] += c * (-p->c5) * ds[0];
+    lam[1] += c * (-p->c5) * ds[1];
+  }
+  double sub[65][6];
+  for (int t = T - 1; t >= 0; --t) {
+    const double* xt = xs + (size_t)t * nx;
+    const double* ut = Uk + (size_t)t * nu;
+    /* through F(x_t, u_t): recompute the sub-step states, reverse them */
+    for (int a = 0; a < nx; ++a) sub[0][a] = xt[a];
+    for (int i = 0; i < ns; ++i) substep_fwd(p, sub[i], ut, sub[i + 1]);
+    for (int i = ns - 1; i >= 0; --i) {
+      double lo[6] = {0, 0, 0, 0, 0, 0};
+      substep_vjp(p, sub[i], ut, lam, lo, gU + (size_t)t * nu);
+      for (int a = 0; a < nx; ++a) lam[a] = lo[a];
+    }
+    /* running cost at x_t */
+    state_cost_grad(p, xt, obs, n_obs, mask, c, lam, gth);
+  }
+}
+
+int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, const double* obs, int32_t n_obs,
+                     const double* gVp, const double* gSt, double* gV, double* gtheta) {
+  if (p->model == ORC_DYN) return -6;
+  if (p->substeps > 64) return -1;
+  const int K = p->K, M = p->M, T = p->T, nx = nx_of(p->model), nu = nu_of(p->model);
+  const int n_warm = n_warm_of(p);
+  double inv_sig2[2];
+  for (int j = 0; j < 2; ++j) inv_sig2[j] = p->sigma_u[j] > 0.0 ? 1.0 / (p->sigma_u[j] * p->sigma_u[j]) : 0.0;
+  double* U = (double*)calloc((size_t)K * T * nu, sizeof(double));
+  double* inside = (double*)calloc((size_t)K * T * nu, sizeof(double));
+  double* S = (double*)calloc((size_t)K, sizeof(double));
+  double* cv = (double*)calloc((size_t)K, sizeof(double));
+  double* St = (double*)calloc((size_t)K, sizeof(double));
+  double* Xn = (double*)calloc((size_t)K * (T + 1) * nx, sizeof(double));
+  double* Xd = (double*)calloc((size_t)K * M * (T + 1) * nx, sizeof(double));
+  double* Lm = (double*)calloc((size_t)K * M, sizeof(double));
+  /* forward with stored states (same steps as orc_samples) */
+  for (int k = 0; k < K; ++k) {
+    double* Uk = U + (size_t)k * T * nu;
+    for (int t = 0; t < T; ++t) {
+      double eps[2];
+      orc_control_noise(p, k, t, eps);
+      for (int j = 0; j < nu; ++j) {
+        double raw = ((k < n_warm) ? V[t * nu + j] : 0.0) + eps[j];
+        Uk[t * nu + j] = clampd(raw, p->u_lo[j], p->u_hi[j]);
+        inside[(size_t)k * T * nu + t * nu + j] = (k < n_warm && raw > p->u_lo[j] && raw < p->u_hi[j]) ? 1.0 : 0.0;
+      }
+    }
+    double* xs = Xn + (size_t)k * (T + 1) * nx;
+    for (int a = 0; a < nx; ++a) xs[a] = x0[a];
+    double Sk = 0.0;
+    for (int t = 0; t < T; ++t) {
+      double ctrl = 0.0;
+      for (int j = 0; j < nu; ++j) ctrl += V[t * nu + j] * inv_sig2[j] * Uk[t * nu + j];
+      Sk += state_cost(p, xs + (size_t)t * nx, obs, n_obs, 0xFFFFFFFFu, 0.0) + p->gamma * ctrl;
+      orc_dynamics(p, xs + (size_t)t * nx, Uk + t * nu, xs + (size_t)(t + 1) * nx);
+    }
+    Sk += terminal_cost(p, xs + (size_t)T * nx);
+    S[k] = Sk;
+    for (int m = 0; m < M; ++m) {
+      double* xd = Xd + ((size_t)k * M + m) * (T + 1) * nx;
+      for (int a = 0; a < nx; ++a) xd[a] = x0[a];
+      double Lv = 0.0;
+      for (int t = 0; t < T; ++t) {
+        Lv += state_cost(p, xd + (size_t)t * nx, obs, n_obs, p->risk_mask, 0.0);
+        double w[4];
+        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, w);
+        orc_dynamics(p, xd + (size_t)t * nx, Uk + t * nu, xd + (size_t)(t + 1) * nx);
+        for (int s = 0; s < nslots_of(p->model); ++s) xd[(size_t)(t + 1) * nx + slot_dim(p->model, s)] += w[s];
+      }
+      Lm[(size_t)k * M + m] = Lv;
+    }
+    cv[k] = orc_cvar(Lm + (size_t)k * M, M, p->alpha, p->B, p->cvar_mode);
+    St[k] = S[k] + ((cv[k] > p->C_u) ? p->A * cv[k] : 0.0);
+  }
+  /* update and its weights */
+  double beta = INFINITY;
+  for (int k = 0; k < K; ++k) if (isfinite(St[k]) && St[k] < beta) beta = St[k];
+  double* wh = (double*)calloc((size_t)K, sizeof(double));
+  double* Vp = (double*)calloc((size_t)T * nu, sizeof(double));
+  double sum = 0.0;
+  for (int k = 0; k < K; ++k) { wh[k] = isfinite(St[k]) ? exp(-(St[k] - beta) / p->lam) : 0.0; sum += wh[k]; }
+  for (int k = 0; k < K; ++k) wh[k] /= sum;
+  for (int k = 0; k < K; ++k)
+    for (int c = 0; c < T * nu; ++c) Vp[c] += wh[k] * U[(size_t)k * T * nu + c];
+  for (int c = 0; c < T * nu; ++c) gV[c] = 0.0;
+  for (int i = 0; i < 4; ++i) gtheta[i] = 0.0;
+  double* gU = (double*)calloc((size_t)T * nu, sizeof(double));
+  double* La = (double*)calloc((size_t)M, sizeof(double));
+  double* srt = (double*)calloc((size_t)M, sizeof(double));
+  for (int k = 0; k < K; ++k) {
+    const double* Uk = U + (size_t)k * T * nu;
+    /* cotangent of S~_k */
+    double dot = 0.0;
+    for (int c = 0; c < T * nu; ++c) dot += gVp[c] * (Uk[c] - Vp[c]);
+    double sbar = (gSt ? gSt[k] : 0.0) - wh[k] / p->lam * dot;
+    double cvbar = (cv[k] > p->C_u) ? sbar * p->A : 0.0;
+    for (int c = 0; c < T * nu; ++c) gU[c] = wh[k] * gVp[c];
+    /* nominal: S_k */
+    rollout_vjp(p, Xn + (size_t)k * (T + 1) * nx, Uk, obs, n_obs, 0xFFFFFFFFu, 1, sbar, gU, gtheta);
+    for (int t = 0; t < T; ++t) {
+      double ctrl = 0.0;
+      for (int j = 0; j < nu; ++j) {
+        ctrl += V[t * nu + j] * inv_sig2[j] * Uk[t * nu + j];
+        gU[t * nu + j] += sbar * p->gamma * inv_sig2[j] * V[t * nu + j];
+        gV[t * nu + j] += sbar * p->gamma * inv_sig2[j] * Uk[t * nu + j];
+      }
+      gtheta[2] += sbar * ctrl;
+    }
+    /* disturbed: weights of CVaR in each L_{k,m} */
+    if (cvbar != 0.0) {
+      const double* Lk = Lm + (size_t)k * M;
+      double mean = 0.0;
+      for (int m = 0; m < M; ++m) mean += Lk[m];
+      mean /= M;
+      for (int m = 0; m < M; ++m) { La[m] = p->B * (Lk[m] - mean) + mean; srt[m] = La[m]; }
+      qsort(srt, (size_t)M, sizeof(double), cmp_double);
+      double aM = p->alpha * M;
+      int j = (int)ceil(aM);
+      if (j < 1) j = 1;
+      if (j > M) j = M;
+      double var = srt[j - 1];
+      int c_gt = 0, c_eq = 0;
+      for (int m = 0; m < M; ++m) { if (La[m] > var) ++c_gt; else if (La[m] == var) ++c_eq; }
+      double denom = (1.0 - p->alpha) * M;
+      for (int m = 0; m < M; ++m) {
+        double wa;
+        if (p->cvar_mode == ORC_CVAR_RU)
+          wa = La[m] > var ? 1.0 / denom : (La[m] == var ? ((double)(M - c_gt) - aM) / denom / c_eq : 0.0);
+        else
+          wa = La[m] >= var ? 1.0 / (c_gt + c_eq) : 0.0;
+        double lbar = cvbar * (p->B * wa + (1.0 - p->B) / M);
+        if (lbar != 0.0)
+          rollout_vjp(p, Xd + ((size_t)k * M + m) * (T + 1) * nx, Uk, obs, n_obs, p->risk_mask, 0, lbar, gU, gtheta);
+      }
+    }
+    /* through U = clip(V + eps) to V */
+    for (int c = 0; c < T * nu; ++c) gV[c] += gU[c] * inside[(size_t)k * T * nu + c];
+  }
+  free(U); free(inside); free(S); free(cv); free(St); free(Xn); free(Xd); free(Lm);
+  free(wh); free(Vp); free(gU); free(La); free(srt);
+  return 0;
+}
+
+/* set theta = (w_dev, w_speed, gamma, w_obs) on a problem copy */
+void orc_set_theta(orc_problem* p, const double* theta) {
+  p->w_dev = theta[0];
+  p->w_speed = theta[1];
+  p->gamma = theta[2];
+  p->w_obs = theta[3];
+}

@@ -53,6 +53,12 @@ class ra_mppi_problem(ctypes.Structure):
     ]
 
 
+class ra_mppi_instance(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("M", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("max_obstacles", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("instance_id", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
 _VP = ctypes.c_void_p
 _FP = ctypes.c_void_p  # float* passed as integer address
 _lib = None
@@ -76,9 +82,38 @@ def _declare(L):
     L.ra_mppi_last_error.restype = ctypes.c_char_p
     L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
     L.ra_mppi_set_timing_events.argtypes = [_VP, _VP, _VP]
+    L.ra_mppi_closed_loop_step.argtypes = [_VP, _FP, _FP, _FP, _FP, ctypes.c_int32, _VP]
+    L.ra_mppi_closed_loop_step.restype = ctypes.c_int
     L.ra_mppi_softmin_update_noalloc.argtypes = [_FP, _FP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_float, _FP, _VP]
     L.ra_mppi_softmin_update_noalloc.restype = ctypes.c_int
+    _I64P = ctypes.POINTER(ctypes.c_int64)
+    _I32P = ctypes.POINTER(ctypes.c_int32)
+    L.ra_mppi_batch_create.argtypes = [ctypes.POINTER(ra_mppi_problem), ctypes.POINTER(ra_mppi_instance),
+                                       ctypes.c_int32, ctypes.POINTER(_VP)]
+    L.ra_mppi_batch_destroy.argtypes = [_VP]
+    L.ra_mppi_batch_destroy.restype = None
+    L.ra_mppi_batch_layout.argtypes = [_VP, _I64P]
+    L.ra_mppi_batch_buffers.argtypes = [_VP] + [ctypes.POINTER(_VP)] * 4
+    L.ra_mppi_batch_set_obstacles.argtypes = [_VP, ctypes.c_int32, _FP, ctypes.c_int32, _VP]
+    L.ra_mppi_batch_write_inputs.argtypes = [_VP, _FP, _FP, _VP]
+    L.ra_mppi_batch_read_outputs.argtypes = [_VP, _FP, _FP, _VP]
+    L.ra_mppi_step_batched.argtypes = [_VP, _VP]
+    L.ra_mppi_step_batched_eager.argtypes = [_VP, _VP]
+    L.ra_mppi_batch_copy_workspace.argtypes = [_VP, _FP, _FP, _FP, _VP]
+    L.ra_mppi_batch_set_iteration.argtypes = [_VP, ctypes.c_uint64]
+    L.ra_mppi_batch_get_status.argtypes = [_VP]
+    L.ra_mppi_batch_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
+    L.ra_mppi_batch_get_launch.argtypes = [_VP, _I32P, _I32P, _I32P]
+    L.ra_mppi_batch_tune.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+    L.ra_mppi_batch_last_error.argtypes = [_VP]
+    L.ra_mppi_batch_last_error.restype = ctypes.c_char_p
+    for name in ("ra_mppi_batch_create", "ra_mppi_batch_layout", "ra_mppi_batch_buffers",
+                 "ra_mppi_batch_set_obstacles", "ra_mppi_step_batched", "ra_mppi_step_batched_eager",
+                 "ra_mppi_batch_write_inputs", "ra_mppi_batch_read_outputs",
+                 "ra_mppi_batch_copy_workspace", "ra_mppi_batch_set_iteration", "ra_mppi_batch_get_status",
+                 "ra_mppi_batch_set_launch", "ra_mppi_batch_get_launch", "ra_mppi_batch_tune"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("ra_mppi_create", "ra_mppi_set_obstacles", "ra_mppi_step", "ra_mppi_step_host",
                  "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_get_iteration", "ra_mppi_set_iteration",
                  "ra_mppi_get_status", "ra_mppi_set_launch", "ra_mppi_set_timing_events"):
@@ -173,6 +208,11 @@ def ra_mppi_step_host(h, x0_ptr, V_in_ptr, V_out_ptr, S_tilde_ptr=None, stream=0
            "ra_mppi_step_host", h)
 
 
+def ra_mppi_closed_loop_step(h, x_ptr, V_ptr, S_tilde_ptr=None, collisions_ptr=None, shift=1, stream=0):
+    _check(lib().ra_mppi_closed_loop_step(h, x_ptr, V_ptr, S_tilde_ptr, collisions_ptr, int(shift), stream),
+           "ra_mppi_closed_loop_step", h)
+
+
 def ra_mppi_workspace(h):
     ptrs = [_VP() for _ in range(4)]
     _check(lib().ra_mppi_workspace(h, *[ctypes.byref(p) for p in ptrs]), "ra_mppi_workspace", h)
@@ -216,3 +256,89 @@ def ra_mppi_softmin_update_noalloc(S_tilde_ptr, U_ptr, K, T, nu, lam, V_out_ptr,
     """Softmin-weighted update from caller buffers, without any allocation."""
     return lib().ra_mppi_softmin_update_noalloc(S_tilde_ptr, U_ptr, int(K), int(T), int(nu), float(lam),
                                                 V_out_ptr, stream)
+
+
+# ------------------------------------------------------------------ batched path
+
+def _bcheck(rc, where, b=None):
+    if rc != RA_MPPI_OK:
+        detail = ""
+        if b:
+            msg = lib().ra_mppi_batch_last_error(b)
+            detail = msg.decode() if msg else ""
+        raise RaMppiError(rc, where, detail)
+
+
+def ra_mppi_batch_create(problem, instances):
+    arr = (ra_mppi_instance * len(instances))(*instances)
+    b = _VP()
+    _bcheck(lib().ra_mppi_batch_create(ctypes.byref(problem), arr, len(instances), ctypes.byref(b)),
+            "ra_mppi_batch_create")
+    return b
+
+
+def ra_mppi_batch_destroy(b):
+    lib().ra_mppi_batch_destroy(b)
+
+
+def ra_mppi_batch_layout(b, n):
+    off = (ctypes.c_int64 * (4 * n))()
+    _bcheck(lib().ra_mppi_batch_layout(b, off), "ra_mppi_batch_layout", b)
+    return [tuple(off[4 * i:4 * i + 4]) for i in range(n)]
+
+
+def ra_mppi_batch_buffers(b):
+    ptrs = [_VP() for _ in range(4)]
+    _bcheck(lib().ra_mppi_batch_buffers(b, *[ctypes.byref(p) for p in ptrs]), "ra_mppi_batch_buffers", b)
+    return [p.value for p in ptrs]
+
+
+def ra_mppi_batch_set_obstacles(b, i, xyr_ptr, n_obs, stream=0):
+    _bcheck(lib().ra_mppi_batch_set_obstacles(b, int(i), xyr_ptr, int(n_obs), stream),
+            "ra_mppi_batch_set_obstacles", b)
+
+
+def ra_mppi_batch_write_inputs(b, x0_ptr=None, V_ptr=None, stream=0):
+    _bcheck(lib().ra_mppi_batch_write_inputs(b, x0_ptr, V_ptr, stream), "ra_mppi_batch_write_inputs", b)
+
+
+def ra_mppi_batch_read_outputs(b, V_out_ptr=None, S_tilde_ptr=None, stream=0):
+    _bcheck(lib().ra_mppi_batch_read_outputs(b, V_out_ptr, S_tilde_ptr, stream), "ra_mppi_batch_read_outputs", b)
+
+
+def ra_mppi_step_batched(b, stream=0):
+    _bcheck(lib().ra_mppi_step_batched(b, stream), "ra_mppi_step_batched", b)
+
+
+def ra_mppi_step_batched_eager(b, stream=0):
+    _bcheck(lib().ra_mppi_step_batched_eager(b, stream), "ra_mppi_step_batched_eager", b)
+
+
+def ra_mppi_batch_copy_workspace(b, U_ptr=None, S_ptr=None, cvar_ptr=None, stream=0):
+    _bcheck(lib().ra_mppi_batch_copy_workspace(b, U_ptr, S_ptr, cvar_ptr, stream),
+            "ra_mppi_batch_copy_workspace", b)
+
+
+def ra_mppi_batch_set_iteration(b, iteration):
+    _bcheck(lib().ra_mppi_batch_set_iteration(b, int(iteration)), "ra_mppi_batch_set_iteration", b)
+
+
+def ra_mppi_batch_get_status(b):
+    return lib().ra_mppi_batch_get_status(b)
+
+
+def ra_mppi_batch_set_launch(b, warps_per_block, ilp):
+    _bcheck(lib().ra_mppi_batch_set_launch(b, int(warps_per_block), int(ilp)), "ra_mppi_batch_set_launch", b)
+
+
+def ra_mppi_batch_get_launch(b):
+    w, i, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _bcheck(lib().ra_mppi_batch_get_launch(b, ctypes.byref(w), ctypes.byref(i), ctypes.byref(g)),
+            "ra_mppi_batch_get_launch", b)
+    return w.value, i.value, g.value
+
+
+def ra_mppi_batch_tune(b, replays=3):
+    ms = ctypes.c_float()
+    _bcheck(lib().ra_mppi_batch_tune(b, int(replays), ctypes.byref(ms)), "ra_mppi_batch_tune", b)
+    return ms.value

@@ -66,6 +66,14 @@ class RaMppi:
                        self.cvar.data_ptr() if want_cvar else None, _stream_ptr(stream))
         return out
 
+    def closed_loop_step(self, x, V, collisions=None, shift=True, stream=None):
+        """One receding-horizon iteration on a simulated plant; x and V are
+        device tensors updated in place (plant state, warm start)."""
+        assert x.is_cuda and V.is_cuda and x.is_contiguous() and V.is_contiguous()
+        B.ra_mppi_closed_loop_step(self.h, x.data_ptr(), V.data_ptr(), self.S_tilde.data_ptr(),
+                                   collisions.data_ptr() if collisions is not None else None,
+                                   1 if shift else 0, _stream_ptr(stream))
+
     def step_host(self, x0, V, S_tilde=False, stream=None):
         """One update on host arrays (copies inside); returns V+ (numpy)."""
         x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float32))
@@ -111,3 +119,97 @@ class RaMppi:
                 ev.record()
         self._timing = (begin, end)
         B.ra_mppi_set_timing_events(self.h, begin.cuda_event, end.cuda_event)
+
+
+class RaMppiBatch:
+    """B RA-MPPI problems updated together (one persistent launch replayed
+    from a CUDA graph).  problem: common preset dict; instances: list of dicts
+    with K, M, T, max_obstacles, seed, instance_id."""
+
+    def __init__(self, problem, instances):
+        if not torch.cuda.is_available():
+            raise RuntimeError("RaMppiBatch needs a CUDA device (there is no CPU path)")
+        self.p = dict(problem)
+        self.inst = [dict(i) for i in instances]
+        prob = B.ra_mppi_problem_from(self.p, max_obstacles=1)
+        recs = [B.ra_mppi_instance(int(i["K"]), int(i["M"]), int(i["T"]), int(i["max_obstacles"]),
+                                   int(i["seed"]) & 0xFFFFFFFFFFFFFFFF, int(i["instance_id"]) & 0xFFFFFFFF, 0)
+                for i in self.inst]
+        self.b = B.ra_mppi_batch_create(prob, recs)
+        self.B = len(self.inst)
+        self.nx, self.nu = {0: (4, 2), 1: (6, 2), 2: (1, 1)}[int(self.p["model"])]
+        self.offsets = B.ra_mppi_batch_layout(self.b, self.B)
+        self.ptr_x0, self.ptr_V, self.ptr_V_out, self.ptr_S_tilde = B.ra_mppi_batch_buffers(self.b)
+        self.n_V = sum(int(i["T"]) * self.nu for i in self.inst)
+        self.n_k = sum(int(i["K"]) for i in self.inst)
+        self.n_U = sum(int(i["K"]) * int(i["T"]) * self.nu for i in self.inst)
+
+    def close(self):
+        if getattr(self, "b", None):
+            B.ra_mppi_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_obstacles(self, i, xyr):
+        arr = np.ascontiguousarray(np.asarray(xyr, dtype=np.float32).reshape(-1, 3))
+        B.ra_mppi_batch_set_obstacles(self.b, i, arr.ctypes.data if arr.size else None, arr.shape[0])
+
+    def set_inputs(self, x0s, Vs):
+        """Per-problem x0 [nx] and V [T_i, nu] into the packed input buffers."""
+        x0 = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in x0s]))
+        V = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float32).ravel() for v in Vs]))
+        B.ra_mppi_batch_write_inputs(self.b, x0.ctypes.data, V.ctypes.data, _stream_ptr(None))
+        torch.cuda.synchronize()
+
+    def step(self, stream=None, graph=True):
+        if graph:
+            B.ra_mppi_step_batched(self.b, _stream_ptr(stream))
+        else:
+            B.ra_mppi_step_batched_eager(self.b, _stream_ptr(stream))
+
+    def outputs(self):
+        """V+ per problem (list of [T_i, nu]) and S~ per problem (list of [K_i])."""
+        Vo = np.empty(self.n_V, dtype=np.float32)
+        St = np.empty(self.n_k, dtype=np.float32)
+        B.ra_mppi_batch_read_outputs(self.b, Vo.ctypes.data, St.ctypes.data, _stream_ptr(None))
+        torch.cuda.synchronize()
+        Vs, Ss = [], []
+        for i, inst in enumerate(self.inst):
+            _, vo, ko, _ = self.offsets[i]
+            Vs.append(Vo[vo:vo + int(inst["T"]) * self.nu].reshape(int(inst["T"]), self.nu).copy())
+            Ss.append(St[ko:ko + int(inst["K"])].copy())
+        return Vs, Ss
+
+    def workspace(self):
+        U = torch.empty(self.n_U, dtype=torch.float32, device="cuda")
+        S = torch.empty(self.n_k, dtype=torch.float32, device="cuda")
+        cv = torch.empty(self.n_k, dtype=torch.float32, device="cuda")
+        B.ra_mppi_batch_copy_workspace(self.b, U.data_ptr(), S.data_ptr(), cv.data_ptr(), _stream_ptr(None))
+        U, S, cv = U.cpu().numpy(), S.cpu().numpy(), cv.cpu().numpy()
+        out = []
+        for i, inst in enumerate(self.inst):
+            _, _, ko, uo = self.offsets[i]
+            K, T = int(inst["K"]), int(inst["T"])
+            out.append(dict(U=U[uo:uo + K * T * self.nu].reshape(K, T, self.nu), S=S[ko:ko + K],
+                            cvar=cv[ko:ko + K]))
+        return out
+
+    def set_iteration(self, it):
+        B.ra_mppi_batch_set_iteration(self.b, it)
+
+    def status(self):
+        return B.ra_mppi_batch_get_status(self.b)
+
+    def tune(self, replays=3):
+        return B.ra_mppi_batch_tune(self.b, replays)
+
+    def set_launch(self, warps_per_block, ilp):
+        B.ra_mppi_batch_set_launch(self.b, warps_per_block, ilp)
+
+    def get_launch(self):
+        return B.ra_mppi_batch_get_launch(self.b)

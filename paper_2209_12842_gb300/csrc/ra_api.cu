@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "ra_kernels.h"
@@ -32,6 +33,7 @@ struct ra_mppi {
   DevState* st = nullptr;
   float* x0_dev = nullptr;  // staging for ra_mppi_step_host
   float* V_dev = nullptr;
+  float* V_plus = nullptr;  // V+ of ra_mppi_closed_loop_step before the warm-start shift
   cudaEvent_t ev_begin = nullptr;  // optional timing hook around the rollout kernel
   cudaEvent_t ev_end = nullptr;
   std::string err;
@@ -187,7 +189,13 @@ void release(ra_mppi* h) {
   cudaFree(h->st);
   cudaFree(h->x0_dev);
   cudaFree(h->V_dev);
+  cudaFree(h->V_plus);
 }
+
+// The limit is a property of the kernel, shared by every handle: raise it
+// to what this handle launches with, never lower it below another handle's.
+std::mutex g_smem_mutex;
+size_t g_smem_limit[64][3] = {};  // per device, per model
 
 size_t rollout_smem(const ra_mppi* h) {
   return (size_t)h->obs_cap * sizeof(float4) + (size_t)h->warps * h->prob.T * sizeof(float4) +
@@ -196,11 +204,19 @@ size_t rollout_smem(const ra_mppi* h) {
 
 cudaError_t prepare(ra_mppi* h) {
   h->smem = rollout_smem(h);
-  switch (h->prob.model) {
-    case 0: return ramppi::prepare_rollout<0>(h->smem);
-    case 1: return ramppi::prepare_rollout<1>(h->smem);
-    default: return ramppi::prepare_rollout<2>(h->smem);
+  const int m = h->prob.model < 0 || h->prob.model > 2 ? 2 : h->prob.model;
+  std::lock_guard<std::mutex> lock(g_smem_mutex);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (h->smem <= g_smem_limit[dev][m]) return cudaSuccess;
+  cudaError_t e;
+  switch (m) {
+    case 0: e = ramppi::prepare_rollout<0>(h->smem); break;
+    case 1: e = ramppi::prepare_rollout<1>(h->smem); break;
+    default: e = ramppi::prepare_rollout<2>(h->smem); break;
   }
+  if (e == cudaSuccess) g_smem_limit[dev][m] = h->smem;
+  return e;
 }
 
 // largest interleave in {4, 2, 1} that divides the rollouts per lane
@@ -215,6 +231,12 @@ int default_ilp(int M, int model) {
 }
 
 }  // namespace
+
+// shared with the batched path (ra_batch.cu)
+namespace ramppi_api {
+std::string validate_problem(const ra_mppi_problem& p) { return validate(p); }
+DevParams make_params(const ra_mppi_problem& p) { return ::make_params(p); }
+}  // namespace ramppi_api
 
 extern "C" {
 
@@ -250,6 +272,7 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   if (e == cudaSuccess) e = dalloc(&h->st, 1);
   if (e == cudaSuccess) e = dalloc(&h->x0_dev, 8);
   if (e == cudaSuccess) e = dalloc(&h->V_dev, TN);
+  if (e == cudaSuccess) e = dalloc(&h->V_plus, TN);
   if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMemset(h->U, 0, sizeof(float) * K * TN);
   if (e == cudaSuccess) e = prepare(h);
@@ -384,6 +407,18 @@ int ra_mppi_step_host(ra_mppi_t* h, const float* x0_host, const float* V_in_host
     e = cudaMemcpyAsync(S_tilde_host, h->S_tilde, sizeof(float) * h->prob.K, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step_host download");
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_closed_loop_step(ra_mppi_t* h, float* x, float* V, float* S_tilde, int32_t* collisions,
+                             int32_t shift, void* stream) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (x == nullptr || V == nullptr) return fail(h, RA_MPPI_EINVAL, "x and V are required");
+  const int rc = ra_mppi_step(h, x, V, h->V_plus, S_tilde, nullptr, stream);
+  if (rc != RA_MPPI_OK) return rc;
+  const cudaError_t e = ramppi::launch_plant(h->prob.model, h->dp, h->obs, h->st, x, h->V_plus, V, collisions,
+                                             shift ? 1 : 0, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "plant launch");
   return RA_MPPI_OK;
 }
 

@@ -43,7 +43,8 @@ struct DevState {
   int status;        // bit 0: non-finite cost, bit 1: all weights vanished
   int n_obs;
   unsigned int arrive;  // last-block-done counter of the update kernel
-  int pad;
+  float last_min;       // min S~ of the last update (softmin shift)
+  double last_sum;      // sum_k exp(-(S~_k - min) / lambda) of the last update
 };
 
 enum : int { kStatusNonFinite = 1, kStatusNoWeight = 2 };
@@ -118,16 +119,18 @@ struct Model<0> {  // kinematic bicycle, explicit Euler
   __device__ static __forceinline__ float4 ctl(const DevParams& p, float u0, float u1) {
     return make_float4(u0, u1, tanf(u0) / p.mp[0], 0.0f);
   }
+  // one Euler sub-step of size h
+  __device__ static __forceinline__ void substep(const DevParams& p, float* x, const float4 c) {
+    float sp, cp;
+    heading_sincos(x[2], &sp, &cp);
+    const float hv = p.h * x[3];
+    x[0] = fmaf(hv, cp, x[0]);
+    x[1] = fmaf(hv, sp, x[1]);
+    x[2] = fmaf(hv, c.z, x[2]);
+    x[3] = fmaf(p.h, c.y, x[3]);
+  }
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
-    for (int s = 0; s < p.substeps; ++s) {
-      float sp, cp;
-      heading_sincos(x[2], &sp, &cp);
-      const float hv = p.h * x[3];
-      x[0] = fmaf(hv, cp, x[0]);
-      x[1] = fmaf(hv, sp, x[1]);
-      x[2] = fmaf(hv, c.z, x[2]);
-      x[3] = fmaf(p.h, c.y, x[3]);
-    }
+    for (int s = 0; s < p.substeps; ++s) substep(p, x, c);
   }
   __device__ static __forceinline__ float speed(const float* x) { return x[3]; }
 };
@@ -192,8 +195,11 @@ struct Model<2> {  // linear test system x+ = x + h u
   __device__ static __forceinline__ float4 ctl(const DevParams&, float u0, float) {
     return make_float4(u0, 0.f, 0.f, 0.f);
   }
+  __device__ static __forceinline__ void substep(const DevParams& p, float* x, const float4 c) {
+    x[0] = fmaf(p.h, c.x, x[0]);
+  }
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
-    for (int s = 0; s < p.substeps; ++s) x[0] = fmaf(p.h, c.x, x[0]);
+    for (int s = 0; s < p.substeps; ++s) substep(p, x, c);
   }
   __device__ static __forceinline__ float speed(const float*) { return 0.f; }
 };
@@ -203,10 +209,11 @@ struct Model<2> {  // linear test system x+ = x + h u
 // counter (t | draw << 16, m, k, instance).
 template <int MODEL>
 __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k0, uint32_t k1,
-                                                  uint32_t t, uint32_t m, uint32_t k, float* x) {
+                                                  uint32_t t, uint32_t m, uint32_t k, uint32_t instance,
+                                                  float* x) {
   using Md = Model<MODEL>;
   if (p.noise_type == 0) {
-    const uint4 w = philox4x32_10(make_uint4(t, m, k, p.instance), k0, k1);
+    const uint4 w = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
     const float2 z01 = box_muller(w.x, w.y);
     x[Md::slot_dim(0)] = fmaf(p.w_scale[0], z01.x, x[Md::slot_dim(0)]);
     if (Md::NS > 1) {
@@ -216,8 +223,8 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
       if (Md::NS > 3) x[Md::slot_dim(3)] = fmaf(p.w_scale[3], z23.y, x[Md::slot_dim(3)]);
     }
   } else {
-    const uint4 sel = philox4x32_10(make_uint4(t, m, k, p.instance), k0, k1);
-    const uint4 val = philox4x32_10(make_uint4(t | (1u << 16), m, k, p.instance), k0, k1);
+    const uint4 sel = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
+    const uint4 val = philox4x32_10(make_uint4(t | (1u << 16), m, k, instance), k0, k1);
     const uint32_t sw[4] = {sel.x, sel.y, sel.z, sel.w};
     const uint32_t vw[4] = {val.x, val.y, val.z, val.w};
 #pragma unroll
@@ -232,10 +239,10 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
 // Rounding is pinned (explicit _rn intrinsics) so every thread that draws the
 // same (k, t) gets the same bits.
 __device__ __forceinline__ float2 control_sample(const DevParams& p, uint32_t k0, uint32_t k1, int k,
-                                                 int t, float v0, float v1) {
-  const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0xFFFFFFFFu, (uint32_t)k, p.instance), k0, k1);
+                                                 int t, float v0, float v1, int n_warm, uint32_t instance) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0xFFFFFFFFu, (uint32_t)k, instance), k0, k1);
   const float2 z = box_muller(w.x, w.y);
-  const bool warm = k < p.n_warm;
+  const bool warm = k < n_warm;
   const float b0 = warm ? v0 : 0.0f, b1 = warm ? v1 : 0.0f;
   float u0 = __fmaf_rn(p.sigma_u[0], z.x, b0);
   float u1 = __fmaf_rn(p.sigma_u[1], z.y, b1);

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "ra_batch.cuh"
 #include "ra_device.cuh"
 #include "ra_rollout.cuh"
 
@@ -27,6 +28,62 @@ template <int MODEL>
 cudaError_t prepare_rollout(size_t smem);
 
 cudaError_t launch_update(const DevParams& p, const UpdateArgs& a, int nblocks, cudaStream_t s);
+
+// Adjoint of the last update (ra_adjoint.cu).
+struct BwdArgs {
+  const float* x0;      // [nx] state of the differentiated update
+  const float* V;       // [T][nu] its mean controls
+  const float* U;       // [K][T][nu] its samples
+  const float* S;       // [K]
+  const float* cvar;    // [K]
+  const float4* obs;
+  DevState* st;
+  const float* gVp;     // [T][nu]
+  const float* gS;      // [K] or nullptr
+  float* dk;            // [K]
+  float* wk;            // [K]
+  double* prep_part;    // [nb_prep]
+  double* c_out;        // [1]
+  unsigned int* arrive; // [2] counters of the prep and reduce merges
+  float* Gnom;          // [K][T][nu]
+  float* mask;          // [K][T][nu]
+  float* gUd;           // [K][T][nu]
+  float* thn;           // [K][4]
+  float* thd;           // [K][4]
+  float* red_part;      // [nb_red][T nu + 4]
+  float* gV;            // [T][nu] out
+  float* gtheta;        // [4] out
+  int nb_nom, obs_cap;
+};
+cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
+                            size_t smem, int nb_red, cudaStream_t s);
+
+// Batched path (ra_batch.cuh, ra_batch.cu): persistent rollout kernel of one
+// model, its shared-memory limit and occupancy, and the batched update.
+template <int MODEL>
+cudaError_t launch_batch_rollout(const DevParams& p, const BatchArgs& a, int warps, int ilp, size_t smem,
+                                 int grid, cudaStream_t s);
+template <int MODEL>
+cudaError_t prepare_batch_rollout(size_t smem);
+template <int MODEL>
+cudaError_t batch_rollout_occupancy(int warps, int ilp, size_t smem, int* blocks_per_sm);
+
+struct BatchUpdateArgs {
+  const InstDesc* desc;
+  int B;
+  DevState* st;
+  const float* S;
+  const float* cvar;
+  const float* U;
+  float* S_tilde;
+  float* V_out;
+  float* partials;
+};
+cudaError_t launch_batch_update(const DevParams& p, const BatchUpdateArgs& a, int nblocks, cudaStream_t s);
+
+// Plant step of the receding-horizon loop (ra_plant.cu).
+cudaError_t launch_plant(int model, const DevParams& p, const float4* obs, DevState* st, float* x,
+                         const float* V_plus, float* V_next, int* collisions, int shift, cudaStream_t s);
 
 constexpr int kUpdateThreads = 256;
 constexpr int kMaxUpdateBlocks = 1024;

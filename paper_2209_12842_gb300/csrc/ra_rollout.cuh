@@ -1,25 +1,49 @@
-// Fused sample + rollout + cost + CVaR kernel of the RA-MPPI update
+// Fused sample + rollout + cost + CVaR work of the RA-MPPI update
 // (Algorithm 1, the parallel loop over samples and its inner parallel loop
 // over disturbed rollouts; Eqs. 3, 6, 9-13, 18, 19).
 //
-// One launch holds two kinds of blocks:
-//   - nominal blocks (the first nb_nom): one thread per sample k draws its
-//     control sequence, writes U^k to HBM and rolls it out on the nominal
-//     dynamics with the full running cost q, giving S_k (Eq. 3);
-//   - disturbed blocks: one warp per sample k; the lanes redraw U^k into
-//     shared memory (same counter, same bits), then each lane runs the
-//     rollouts m = lane + 32 r on x~_{t+1} = F(x~_t, u_t) + w_t, ILP of them
-//     interleaved, with states and noise in registers, and stores the M
-//     risk costs L_{k,m} (Eq. 9) in shared memory; the warp then forms CVaR_k
-//     by a radix select of VaR = L_(j) and warp reductions of the tail.
-// The two kinds are independent, so the nominal work (1/M of the total)
-// overlaps the disturbed work inside one launch.  S~_k is formed by the
-// update kernel, which is the first point where both S_k and CVaR_k exist.
+// Two kinds of work items:
+//   - nominal: one thread per sample k draws its control sequence, writes
+//     U^k to HBM and rolls it out on the nominal dynamics with the full
+//     running cost q, giving S_k (Eq. 3);
+//   - disturbed: one warp per sample k; the lanes redraw U^k into shared
+//     memory (same counter, same bits), then each lane runs the rollouts
+//     m = lane + 32 r on x~_{t+1} = F(x~_t, u_t) + w_t, ILP of them
+//     interleaved, with states and noise in registers, and stores the M risk
+//     costs L_{k,m} (Eq. 9) in shared memory; the warp then forms CVaR_k by a
+//     radix select of VaR = L_(j) and warp reductions of the tail.
+// The single-problem kernel below puts nominal blocks first and disturbed
+// blocks after them in one launch, so the nominal work (1/M of the total)
+// overlaps the disturbed work; the batched kernel (ra_batch.cu) pulls the
+// same items from a work queue.  S~_k is formed by the update, the first
+// point where both S_k and CVaR_k exist.
 #pragma once
 
 #include "ra_device.cuh"
 
 namespace ramppi {
+
+// Per-problem quantities the work items need besides the common DevParams.
+struct Inst {
+  int K, M, T, n_warm, j_var;
+  float frac_j, tail_denom;
+  uint32_t instance, k0, k1;  // Philox counter word 3 and key
+};
+
+__device__ __forceinline__ Inst inst_of(const DevParams& p, uint32_t iteration) {
+  Inst in;
+  in.K = p.K;
+  in.M = p.M;
+  in.T = p.T;
+  in.n_warm = p.n_warm;
+  in.j_var = p.j_var;
+  in.frac_j = p.frac_j;
+  in.tail_denom = p.tail_denom;
+  in.instance = p.instance;
+  in.k0 = p.seed_lo;
+  in.k1 = p.seed_hi ^ iteration;
+  return in;
+}
 
 struct RolloutArgs {
   const float* x0;
@@ -49,20 +73,22 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
+// Nominal rollout of sample k: writes U^k [T][nu] and S_k.
 template <int MODEL>
-__device__ __forceinline__ void nominal_rollout(const DevParams& p, const RolloutArgs& a, int k,
-                                                uint32_t k0, uint32_t k1, const float4* obs_s,
+__device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& in, const float* __restrict__ x0,
+                                                const float* __restrict__ V, float* __restrict__ U,
+                                                float* __restrict__ S_out, int k, const float4* obs_s,
                                                 int n_obs) {
   using Md = Model<MODEL>;
   float x[Md::NX];
 #pragma unroll
-  for (int i = 0; i < Md::NX; ++i) x[i] = a.x0[i];
+  for (int i = 0; i < Md::NX; ++i) x[i] = x0[i];
   float S = 0.0f;
-  for (int t = 0; t < p.T; ++t) {
-    const float v0 = a.V[t * Md::NU];
-    const float v1 = Md::NU > 1 ? a.V[t * Md::NU + 1] : 0.0f;
-    const float2 u = control_sample(p, k0, k1, k, t, v0, v1);
-    float* Uk = a.U + ((size_t)k * p.T + t) * Md::NU;
+  for (int t = 0; t < in.T; ++t) {
+    const float v0 = V[t * Md::NU];
+    const float v1 = Md::NU > 1 ? V[t * Md::NU + 1] : 0.0f;
+    const float2 u = control_sample(p, in.k0, in.k1, k, t, v0, v1, in.n_warm, in.instance);
+    float* Uk = U + ((size_t)k * in.T + t) * Md::NU;
     Uk[0] = u.x;
     if (Md::NU > 1) Uk[1] = u.y;
     float ctrl = v0 * p.inv_sig2[0] * u.x;
@@ -71,7 +97,7 @@ __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Rollou
     Md::step(p, x, Md::ctl(p, u.x, u.y));
   }
   S += terminal_cost<MODEL>(p, x);
-  a.S[k] = S;
+  S_out[k] = S;
 }
 
 // risk cost l of ILP states; the obstacle list is read once for all of them
@@ -103,67 +129,63 @@ __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP
   }
 }
 
+// ILP disturbed rollouts of one lane (rollouts lane + 32 (r0 + i)); risk costs to Ls
 template <int MODEL, int ILP>
-__global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
+__device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in, const float* x0, int k, int lane,
+                                             int r0, const float4* ctl, float* Ls, const float4* obs_s,
+                                             int n_obs) {
   using Md = Model<MODEL>;
-  extern __shared__ float4 smem[];
-  float4* obs_s = smem;
-  const int n_obs = a.st->n_obs;
-  const uint32_t iter = (uint32_t)a.st->iteration;
-  const uint32_t k0 = p.seed_lo, k1 = p.seed_hi ^ iter;
-  for (int i = threadIdx.x; i < n_obs; i += blockDim.x) obs_s[i] = a.obs[i];
-  __syncthreads();
-
-  if ((int)blockIdx.x < a.nb_nom) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < p.K) nominal_rollout<MODEL>(p, a, k, k0, k1, obs_s, n_obs);
-    return;
+  float x[ILP][Md::NX];
+  float L[ILP];
+  uint32_t m[ILP];
+#pragma unroll
+  for (int i = 0; i < ILP; ++i) {
+    m[i] = (uint32_t)(lane + 32 * (r0 + i));
+    L[i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < Md::NX; ++j) x[i][j] = x0[j];
   }
+  for (int t = 0; t < in.T; ++t) {
+    const float4 c = ctl[t];
+    risk_cost_ilp<MODEL, ILP>(p, x, L, obs_s, n_obs);
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) Md::step(p, x[i], c);
+#pragma unroll
+    for (int i = 0; i < ILP; ++i)
+      add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, m[i], (uint32_t)k, in.instance, x[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < ILP; ++i)
+    if ((int)m[i] < in.M) Ls[m[i]] = L[i];
+}
 
-  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
-  if (k >= p.K) return;
-  float4* ctl = smem + a.obs_cap + w * p.T;
-  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * p.T) + w * p.M;
-
+// One warp: the M disturbed rollouts of sample k and CVaR_k (written to cvar[k]).
+// ctl [T] and Ls [M] are this warp's shared-memory scratch.
+template <int MODEL, int ILP>
+__device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst& in, const float* __restrict__ x0g,
+                                                 const float* __restrict__ V, int k, int lane, float4* ctl, float* Ls,
+                                                 const float4* obs_s, int n_obs, float* __restrict__ cvar,
+                                                 float* __restrict__ Lout, int* status) {
+  using Md = Model<MODEL>;
   // U^k into shared memory (the nominal thread of sample k draws the same bits)
-  for (int t = lane; t < p.T; t += 32) {
-    const float v0 = a.V[t * Md::NU];
-    const float v1 = Md::NU > 1 ? a.V[t * Md::NU + 1] : 0.0f;
-    const float2 u = control_sample(p, k0, k1, k, t, v0, v1);
+  for (int t = lane; t < in.T; t += 32) {
+    const float v0 = V[t * Md::NU];
+    const float v1 = Md::NU > 1 ? V[t * Md::NU + 1] : 0.0f;
+    const float2 u = control_sample(p, in.k0, in.k1, k, t, v0, v1, in.n_warm, in.instance);
     ctl[t] = Md::ctl(p, u.x, u.y);
   }
   __syncwarp();
 
   float x0[Md::NX];
 #pragma unroll
-  for (int i = 0; i < Md::NX; ++i) x0[i] = a.x0[i];
+  for (int i = 0; i < Md::NX; ++i) x0[i] = x0g[i];
 
   // disturbed rollouts and their risk costs (Eq. 9)
-  const int R = (p.M + 31) >> 5;
-  for (int r0 = 0; r0 < R; r0 += ILP) {
-    float x[ILP][Md::NX];
-    float L[ILP];
-    uint32_t m[ILP];
-#pragma unroll
-    for (int i = 0; i < ILP; ++i) {
-      m[i] = (uint32_t)(lane + 32 * (r0 + i));
-      L[i] = 0.0f;
-#pragma unroll
-      for (int j = 0; j < Md::NX; ++j) x[i][j] = x0[j];
-    }
-    for (int t = 0; t < p.T; ++t) {
-      const float4 c = ctl[t];
-      risk_cost_ilp<MODEL, ILP>(p, x, L, obs_s, n_obs);
-#pragma unroll
-      for (int i = 0; i < ILP; ++i) Md::step(p, x[i], c);
-#pragma unroll
-      for (int i = 0; i < ILP; ++i) add_process_noise<MODEL>(p, k0, k1, (uint32_t)t, m[i], (uint32_t)k, x[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < ILP; ++i)
-      if ((int)m[i] < p.M) Ls[m[i]] = L[i];
-  }
+  const int R = (in.M + 31) >> 5;
+  int r0 = 0;
+  for (; r0 + ILP <= R; r0 += ILP) rollouts_ilp<MODEL, ILP>(p, in, x0, k, lane, r0, ctl, Ls, obs_s, n_obs);
+  if (ILP > 1)
+    for (; r0 < R; ++r0) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r0, ctl, Ls, obs_s, n_obs);
   __syncwarp();
 
   // CVaR_k over the M risk costs (Eqs. 10-13, 18, 19)
@@ -175,28 +197,29 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) {
     const int idx = lane + 32 * r;
-    const bool valid = idx < p.M;
+    const bool valid = idx < in.M;
     const float v = valid ? Ls[idx] : 0.0f;
     val[r] = v;
     bad |= valid && !isfinite(v);
     sum += v;
     key[r] = valid ? fkey(v) : 0xFFFFFFFFu;
   }
-  if (a.L != nullptr) {
-    for (int idx = lane; idx < p.M; idx += 32) a.L[(size_t)k * p.M + idx] = Ls[idx];
+  if (Lout != nullptr) {
+    for (int idx = lane; idx < in.M; idx += 32) Lout[(size_t)k * in.M + idx] = Ls[idx];
   }
   if (__any_sync(0xFFFFFFFFu, bad)) {
     if (lane == 0) {
-      a.cvar[k] = __int_as_float(0x7F800000);  // +inf: the sample gets zero weight
-      atomicOr(&a.st->status, kStatusNonFinite);
+      cvar[k] = __int_as_float(0x7F800000);  // +inf: the sample gets zero weight
+      atomicOr(status, kStatusNonFinite);
     }
+    __syncwarp();
     return;
   }
-  const float mean = warp_sum(sum) / (float)p.M;
+  const float mean = warp_sum(sum) / (float)in.M;
 
   // radix select of the j-th smallest key (VaR = L_(j), Eq. 11)
   uint32_t prefix = 0u;
-  int kth = p.j_var - 1;
+  int kth = in.j_var - 1;
 #pragma unroll 1
   for (int b = 31; b >= 0; --b) {
     const uint32_t hi_mask = (b == 31) ? 0u : (0xFFFFFFFFu << (b + 1));
@@ -204,7 +227,7 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) {
       const uint32_t kk = key[r];
-      cnt += ((kk & hi_mask) == prefix && ((kk >> b) & 1u) == 0u && (lane + 32 * r) < p.M) ? 1 : 0;
+      cnt += ((kk & hi_mask) == prefix && ((kk >> b) & 1u) == 0u && (lane + 32 * r) < in.M) ? 1 : 0;
     }
     cnt = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
     if (kth >= cnt) {
@@ -218,7 +241,7 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   float s_gt = 0.0f;
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) {
-    if (lane + 32 * r < p.M) {
+    if (lane + 32 * r < in.M) {
       const float v = val[r];
       if (v > var) { ++c_gt; s_gt += v; }
       else if (v == var) ++c_eq;
@@ -231,15 +254,38 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   if (p.cvar_mode == 0) {
     // fractional tail: weight (j - alpha M) on L_(j), 1 on every later order
     // statistic; ties with L_(j) beyond rank j count at full weight
-    const float n_eq_tail = (float)(p.M - p.j_var - c_gt);
-    cv = (s_gt + (n_eq_tail + p.frac_j) * var) / p.tail_denom;
+    const float n_eq_tail = (float)(in.M - in.j_var - c_gt);
+    cv = (s_gt + (n_eq_tail + in.frac_j) * var) / in.tail_denom;
   } else {
     cv = (s_gt + (float)c_eq * var) / (float)(c_gt + c_eq);
   }
   // sensitivity scaling L_a = B (L - mean) + mean commutes with the tail
   // average for B >= 0: CVaR(L_a) = B CVaR(L) + (1 - B) mean
   if (p.B != 1.0f) cv = fmaf(p.B, cv, (1.0f - p.B) * mean);
-  if (lane == 0) a.cvar[k] = cv;
+  if (lane == 0) cvar[k] = cv;
+  __syncwarp();
+}
+
+template <int MODEL, int ILP>
+__global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
+  extern __shared__ float4 smem[];
+  float4* obs_s = smem;
+  const int n_obs = a.st->n_obs;
+  const Inst in = inst_of(p, (uint32_t)a.st->iteration);
+  for (int i = threadIdx.x; i < n_obs; i += blockDim.x) obs_s[i] = a.obs[i];
+  __syncthreads();
+
+  if ((int)blockIdx.x < a.nb_nom) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < in.K) nominal_rollout<MODEL>(p, in, a.x0, a.V, a.U, a.S, k, obs_s, n_obs);
+    return;
+  }
+  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
+  if (k >= in.K) return;
+  float4* ctl = smem + a.obs_cap + w * in.T;
+  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * in.M;
+  disturbed_sample<MODEL, ILP>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L, &a.st->status);
 }
 
 }  // namespace ramppi

@@ -66,18 +66,20 @@ __device__ __forceinline__ float s_tilde_of(const DevParams& p, float S, float c
 
 }  // namespace
 
-__global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const DevParams p, const UpdateArgs a) {
+// One block of the update of one problem: `block` of `nblocks` blocks that
+// share the problem's samples, partials and arrival counter.
+__device__ __forceinline__ void update_block(const DevParams& p, const UpdateArgs& a, int K, int TN, int block,
+                                             int nblocks) {
   __shared__ float red[32];
   __shared__ double redd[32];
   __shared__ float e_s[kUpdateThreads];
   __shared__ float col_s[(kUpdateThreads / 32) * 2 * RA_MPPI_MAX_T_DEV];
   __shared__ float scale_s[kMaxUpdateBlocks];
   __shared__ unsigned int is_last;
-  const int K = p.K, TN = p.T * p.nu;
-  const int per = (K + gridDim.x - 1) / gridDim.x;
-  const int kb = blockIdx.x * per;
+  const int per = (K + nblocks - 1) / nblocks;
+  const int kb = block * per;
   const int ke = min(K, kb + per);
-  float* part = a.partials + (size_t)blockIdx.x * (2 + TN);
+  float* part = a.partials + (size_t)block * (2 + TN);
 
   // block minimum of the finite S~ (non-finite samples get zero weight)
   float mloc = __int_as_float(0x7F800000);
@@ -160,14 +162,14 @@ __global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const De
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int ticket = atomicAdd(&a.st->arrive, 1u);
-    is_last = (ticket == gridDim.x - 1) ? 1u : 0u;
+    is_last = (ticket == (unsigned int)nblocks - 1) ? 1u : 0u;
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
 
   // rescale each block's partials to the global minimum: exp(-(m_b - m) / lambda)
-  const int nb = gridDim.x;
+  const int nb = nblocks;
   const int stride = 2 + TN;
   const volatile float* parts = a.partials;
   float m = __int_as_float(0x7F800000);
@@ -194,9 +196,41 @@ __global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const De
   }
   if (threadIdx.x == 0) {
     if (!ok) atomicOr(&a.st->status, kStatusNoWeight);
+    a.st->last_min = m;
+    a.st->last_sum = s_tot;
     a.st->arrive = 0u;        // ready for the next launch on this stream
     a.st->iteration += 1ull;  // the next update draws fresh noise
   }
+}
+
+__global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const DevParams p, const UpdateArgs a) {
+  update_block(p, a, p.K, p.T * p.nu, blockIdx.x, gridDim.x);
+}
+
+// Updates of B problems in one launch: problem i owns blocks
+// [upd_block_base_i, upd_block_base_i + nb_upd_i).
+__global__ void __launch_bounds__(kUpdateThreads) batch_update_kernel(const DevParams p, const BatchUpdateArgs b) {
+  int lo = 0, hi = b.B;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (b.desc[mid].upd_block_base <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const InstDesc& d = b.desc[lo];
+  UpdateArgs a;
+  a.S = b.S + d.k_off;
+  a.cvar = b.cvar + d.k_off;
+  a.U = b.U + d.U_off;
+  a.S_tilde = b.S_tilde + d.k_off;
+  a.V_out = b.V_out + d.V_off;
+  a.partials = b.partials + d.part_off;
+  a.st = b.st + lo;
+  update_block(p, a, d.K, d.T * p.nu, (int)blockIdx.x - d.upd_block_base, d.nb_upd);
+}
+
+cudaError_t launch_batch_update(const DevParams& p, const BatchUpdateArgs& a, int nblocks, cudaStream_t s) {
+  batch_update_kernel<<<nblocks, kUpdateThreads, 0, s>>>(p, a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_update(const DevParams& p, const UpdateArgs& a, int nblocks, cudaStream_t s) {

@@ -14,6 +14,8 @@ Tolerances (stage-wise protocol):
 
 import numpy as np
 
+import oracle
+
 RTOL = 1e-4
 
 
@@ -35,3 +37,27 @@ def check_banded(name, gpu, ref, lo, hi, rtol=RTOL, floor=None):
         f"{name}: {bad.size} of {gpu.size} outside tolerance, first {bad[:5]}: "
         f"gpu={gpu[bad[:5]]} ref={ref[bad[:5]]} band=({lo[bad[:5]]}, {hi[bad[:5]]})")
     return int(np.sum(banded & ~close))
+
+
+def compare(p, g, ref, check_update=True):
+    ks = ref["ks"]
+    # 1. sampled controls
+    np.testing.assert_allclose(g["U"][ks], ref["U"], rtol=2e-6, atol=2e-6)
+    # 2. per-sample stage
+    nS = check_banded("S", g["S"][ks], ref["S"], ref["S_lo"], ref["S_hi"])
+    nC = check_banded("CVaR", g["cvar"][ks], ref["cvar"], ref["cvar_lo"], ref["cvar_hi"],
+                      floor=1e-4 * max(1.0, float(np.median(np.abs(ref["S_tilde"])))))
+    nT = check_banded("S_tilde", g["S_tilde"][ks], ref["S_tilde"], ref["St_lo"], ref["St_hi"])
+    # 3. CVaR on the GPU's own risk costs
+    if g["L"] is not None:
+        alpha = float(np.float32(p["alpha"]))
+        Bs = float(np.float32(p["B"]))
+        for i, k in enumerate(ks):
+            want = oracle.cvar(g["L"][k].astype(np.float64), alpha, Bs, p["cvar_mode"])
+            assert abs(g["cvar"][k] - want) <= 1e-5 * max(1.0, abs(want)), (k, g["cvar"][k], want)
+    # 4. update stage on the GPU's S~ and U
+    if check_update:
+        Vo, _ = oracle.update(g["S_tilde"].astype(np.float64), g["U"].astype(np.float64),
+                              float(np.float32(p["lam"])))
+        np.testing.assert_allclose(g["V_plus"], Vo, atol=1e-5, rtol=0)
+    return nS, nC, nT

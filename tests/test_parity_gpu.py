@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 import ra_scenes as rs
-from parity_util import check_banded
+from parity_util import check_banded, compare  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -49,30 +49,6 @@ def run_gpu(p, obs, x0, V, keep_L=True, launch=None, iteration=None):
              iteration=ctl.iteration)
     ctl.close()
     return g
-
-
-def compare(p, g, ref, check_update=True):
-    ks = ref["ks"]
-    # 1. sampled controls
-    np.testing.assert_allclose(g["U"][ks], ref["U"], rtol=2e-6, atol=2e-6)
-    # 2. per-sample stage
-    nS = check_banded("S", g["S"][ks], ref["S"], ref["S_lo"], ref["S_hi"])
-    nC = check_banded("CVaR", g["cvar"][ks], ref["cvar"], ref["cvar_lo"], ref["cvar_hi"],
-                      floor=1e-4 * max(1.0, float(np.median(np.abs(ref["S_tilde"])))))
-    nT = check_banded("S_tilde", g["S_tilde"][ks], ref["S_tilde"], ref["St_lo"], ref["St_hi"])
-    # 3. CVaR on the GPU's own risk costs
-    if g["L"] is not None:
-        alpha = float(np.float32(p["alpha"]))
-        Bs = float(np.float32(p["B"]))
-        for i, k in enumerate(ks):
-            want = oracle.cvar(g["L"][k].astype(np.float64), alpha, Bs, p["cvar_mode"])
-            assert abs(g["cvar"][k] - want) <= 1e-5 * max(1.0, abs(want)), (k, g["cvar"][k], want)
-    # 4. update stage on the GPU's S~ and U
-    if check_update:
-        Vo, _ = oracle.update(g["S_tilde"].astype(np.float64), g["U"].astype(np.float64),
-                              float(np.float32(p["lam"])))
-        np.testing.assert_allclose(g["V_plus"], Vo, atol=1e-5, rtol=0)
-    return nS, nC, nT
 
 
 def _inputs(p, obs_kind="ahead", seed=1, V_seed=3):
@@ -267,3 +243,25 @@ def test_non_finite_state_sets_status():
     assert np.all(np.isinf(g["cvar"])) and np.all(g["cvar"] > 0)
     ref = oracle.samples(p, x0, V, obs, ks=[0, 1])
     assert np.all(np.isinf(ref["cvar"]))
+
+
+def test_handles_with_different_shared_memory_coexist():
+    """The dynamic shared-memory limit belongs to the kernel, not the handle:
+    creating a handle with a small footprint must not break a larger one."""
+    from paper_2209_12842_gb300 import RaMppi
+
+    big = rs.preset("small_kin", M=256, T=200, K=40)
+    small = rs.preset("small_kin", M=16, T=3, K=8)
+    obs, x0, _ = _inputs(big)
+    a = RaMppi(big, obs, max_obstacles=1000)
+    b = RaMppi(small, obs)
+    Va = torch.from_numpy(rs.random_controls(0, big["T"], big["u_lo"], big["u_hi"], 1)).cuda()
+    Vb = torch.from_numpy(rs.random_controls(0, small["T"], small["u_lo"], small["u_hi"], 1)).cuda()
+    xt = torch.from_numpy(x0).cuda()
+    a.step(xt, Va)
+    b.step(xt, Vb)
+    a.step(xt, Va)
+    torch.cuda.synchronize()
+    assert a.status() == 0 and b.status() == 0
+    a.close()
+    b.close()
