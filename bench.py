@@ -309,6 +309,10 @@ def run_ours(args, p, x0, V, obs):
                          "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock {sm_mhz:.0f} MHz",
                          "traffic": traffic},
         }
+        if world == 1 and not args.no_studies:
+            line["closed_loop"] = closed_loop_study(torch, args.loop_updates)
+            line["batched"] = batched_study(torch, 10)
+            line["adjoint"] = adjoint_study(torch, 10)
         if world == 1 and not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
             rate, n_s, dt = oracle_rate(p, x0, V, obs, args.cpu_seconds, threads)
@@ -337,6 +341,120 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def ev_time(torch, fn, n, stream):
+    """Median and p99 of n CUDA-event timings of fn (ms), after 2 warm-ups."""
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for b, e in evs:
+        b.record(stream)
+        fn()
+        e.record(stream)
+    torch.cuda.synchronize()
+    t = np.array([b.elapsed_time(e) for b, e in evs])
+    return float(np.median(t)), float(np.percentile(t, 99))
+
+
+def closed_loop_study(torch, n_updates, alphas=(0.5, 0.9, 0.99)):
+    """Config 2's receding-horizon loop on the simulated plant: update rate
+    and plant collisions of RA-MPPI at each alpha and of plain MPPI (A = 0)."""
+    from paper_2209_12842_gb300 import RaMppi
+
+    p0 = rs.preset("c2_closed_loop")
+    obs = rs.make_obstacles(p0["seed"], p0["n_obs"], *p0["obs_r"])
+    out = {"updates": n_updates}
+    runs = [("mppi", dict(A=0.0))] + [(f"ra_alpha{a}", dict(alpha=a)) for a in alphas]
+    for name, ov in runs:
+        p = rs.preset("c2_closed_loop", **ov)
+        ctl = RaMppi(p, obs)
+        x = torch.from_numpy(rs.initial_state(p["model"])).cuda()
+        V = torch.zeros((p["T"], 2), dtype=torch.float32, device="cuda")
+        hits = torch.zeros(1, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        b.record(stream)
+        for _ in range(n_updates):
+            ctl.closed_loop_step(x, V, hits)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = b.elapsed_time(e)
+        xs = x.cpu().numpy()
+        out[name] = {"collisions": int(hits.item()), "update_hz": 1e3 * n_updates / ms,
+                     "final_state": [round(float(v), 3) for v in xs[:4]], "status": ctl.status()}
+        ctl.close()
+    return out
+
+
+def batched_study(torch, steps):
+    """Config 3: B = 256 uneven kinematic problems, one graph replay per round
+    against a loop of 256 plain per-problem updates on the same stream."""
+    from paper_2209_12842_gb300 import RaMppi
+    from paper_2209_12842_gb300.controller import RaMppiBatch
+
+    insts = rs.batched_instances(256)
+    for d in insts:
+        d["max_obstacles"] = d["n_obs"]
+    p = rs.preset("c3_instance")
+    batch = RaMppiBatch(p, insts)
+    x0s, Vs, obs = [], [], []
+    for i, d in enumerate(insts):
+        o = rs.make_obstacles(d["seed"], d["n_obs"], 0.3, 0.3)
+        obs.append(o)
+        batch.set_obstacles(i, o)
+        x0s.append(rs.initial_state(0))
+        Vs.append(rs.random_controls(0, d["T"], p["u_lo"], p["u_hi"], d["seed"]))
+    batch.set_inputs(x0s, Vs)
+    units = sum(d["K"] * d["M"] * d["T"] for d in insts)
+    stream = torch.cuda.current_stream()
+    tuned_ms = batch.tune(3)
+    g50, g99 = ev_time(torch, lambda: batch.step(graph=True), steps, stream)
+    ctls = []
+    for i, d in enumerate(insts):
+        q = dict(p, K=d["K"], M=d["M"], T=d["T"], seed=d["seed"], instance_id=d["instance_id"], n_obs=d["n_obs"])
+        c = RaMppi(q, obs[i], max_obstacles=max(d["n_obs"], 1))
+        ctls.append((c, torch.from_numpy(x0s[i]).cuda(), torch.from_numpy(Vs[i]).cuda(),
+                     torch.empty((d["T"], 2), dtype=torch.float32, device="cuda")))
+
+    def loop():
+        for c, x, v, o in ctls:
+            c.step(x, v, o, want_cvar=False)
+
+    l50, l99 = ev_time(torch, loop, max(3, steps // 2), stream)
+    launch = batch.get_launch()
+    for c, *_ in ctls:
+        c.close()
+    batch.close()
+    return {"problems": 256, "rollout_steps_per_round": units,
+            "batched_graph": {"p50_ms": g50, "p99_ms": g99, "rollout_steps_per_s": units / g50 * 1e3},
+            "loop_of_plain_launches": {"p50_ms": l50, "p99_ms": l99, "rollout_steps_per_s": units / l50 * 1e3},
+            "speedup_p50": l50 / g50, "tuned_launch": {"warps_per_block": launch[0], "ilp": launch[1],
+                                                       "grid": launch[2], "tune_ms": tuned_ms}}
+
+
+def adjoint_study(torch, steps):
+    """Config 4: forward update and hand-written adjoint latency (kinematic,
+    K = 1024, M = 64, T = 30, softplus barrier)."""
+    from paper_2209_12842_gb300 import RaMppi
+
+    p = rs.preset("c4_gradient")
+    obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
+    ctl = RaMppi(p, obs, differentiable=True)
+    x0 = torch.tensor([0.0, -4.0, 0.0, 1.5], device="cuda")
+    V = torch.from_numpy(rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 5)).cuda()
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 11)
+    gVp, gS = torch.from_numpy(gVp).cuda(), torch.from_numpy(gS).cuda()
+    stream = torch.cuda.current_stream()
+    f50, f99 = ev_time(torch, lambda: ctl.step(x0, V), steps, stream)
+    ctl.step(x0, V)
+    b50, b99 = ev_time(torch, lambda: ctl.backward(gVp, gS), steps, stream)
+    ctl.close()
+    units = p["K"] * p["M"] * p["T"]
+    return {"forward_p50_ms": f50, "forward_p99_ms": f99, "backward_p50_ms": b50, "backward_p99_ms": b99,
+            "backward_rollout_steps_per_s": units / b50 * 1e3}
+
+
 def load_traffic(workload):
     """DRAM bytes per rollout-kernel launch from the committed ncu summary, or
     None when none exists or it was taken on a different kernel version."""
@@ -359,6 +477,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-studies", action="store_true",
+                    help="skip the closed-loop, batched and adjoint sections of the line")
+    ap.add_argument("--loop-updates", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

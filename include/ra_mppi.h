@@ -103,7 +103,10 @@ enum {
 };
 
 /* flags */
-enum { RA_MPPI_KEEP_RISK_COSTS = 1 /* keep the K x M risk costs L for inspection */ };
+enum {
+  RA_MPPI_KEEP_RISK_COSTS = 1, /* keep the K x M risk costs L for inspection              */
+  RA_MPPI_DIFFERENTIABLE = 2   /* keep what ra_mppi_backward needs (x0, V of each update) */
+};
 
 #define RA_MPPI_MAX_M 256
 #define RA_MPPI_MAX_T 256
@@ -217,6 +220,28 @@ int ra_mppi_get_status(ra_mppi_t* h);
 
 /* Human-readable reason of the last error on this handle ("" if none). */
 const char* ra_mppi_last_error(const ra_mppi_t* h);
+
+/* Cost weights theta = (w_dev, w_speed, gamma, w_obs) used by the following
+ * updates (host-side, no device work).  EINVAL if any is not finite. */
+int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta);
+
+/* Vector-Jacobian product of the most recent ra_mppi_step of this handle.
+ * For the update's fixed noise, (V+, S~) is a function of the mean
+ * controls V and of theta; this computes
+ *   gV     [T][nu] device = d(<gV_plus, V+> + <gS_tilde, S~>) / dV
+ *   gtheta [4]     device = the same derivative w.r.t. theta
+ * from gV_plus [T][nu] (device) and gS_tilde [K] (device, or NULL for 0):
+ * the derivative of the softmin update (Eqs. 4, 5, 17), of the violation
+ * cost (Eqs. 14-16: A where CVaR > C_u, else 0), of the fractional-tail or
+ * literal CVaR (Eqs. 10-13: the tail weights; Eqs. 18, 19: the scaling), of
+ * the costs and dynamics along every nominal and disturbed rollout (Eqs. 3,
+ * 6, 9, 20-23; states recomputed from checkpoints every 8 steps), and of the
+ * clip U = clip(V + eps) (Alg. 1).  The obstacle indicator (Eq. 22) has
+ * zero derivative; use the softplus barrier to differentiate through
+ * obstacles.  Needs RA_MPPI_DIFFERENTIABLE; the kinematic and linear models
+ * only (EUNSUPPORTED for the dynamic model).  Enqueued on `stream`. */
+int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, float* gV, float* gtheta,
+                     void* stream);
 
 /* Kernel launch tuning: disturbed-rollout warps per block (1..8) and
  * rollouts each lane interleaves (1, 2 or 4); 0 keeps the default. */

@@ -13,8 +13,8 @@ from .binding import RaMppiError, lib  # noqa: F401
 
 def __getattr__(name):
     # the controller imports torch; keep `import paper_2209_12842_gb300` light
-    if name == "RaMppi":
-        from .controller import RaMppi
+    if name in ("RaMppi", "RaMppiBatch", "RaMppiUpdate"):
+        from . import controller
 
-        return RaMppi
+        return getattr(controller, name)
     raise AttributeError(name)

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT"
                 -5: "ENONFINITE", -6: "EUNSUPPORTED"}
 
 RA_MPPI_KEEP_RISK_COSTS = 1
+RA_MPPI_DIFFERENTIABLE = 2
 
 
 class RaMppiError(RuntimeError):
@@ -82,6 +83,10 @@ def _declare(L):
     L.ra_mppi_last_error.restype = ctypes.c_char_p
     L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
     L.ra_mppi_set_timing_events.argtypes = [_VP, _VP, _VP]
+    L.ra_mppi_set_cost_weights.argtypes = [_VP, ctypes.POINTER(ctypes.c_float)]
+    L.ra_mppi_set_cost_weights.restype = ctypes.c_int
+    L.ra_mppi_backward.argtypes = [_VP, _FP, _FP, _FP, _FP, _VP]
+    L.ra_mppi_backward.restype = ctypes.c_int
     L.ra_mppi_closed_loop_step.argtypes = [_VP, _FP, _FP, _FP, _FP, ctypes.c_int32, _VP]
     L.ra_mppi_closed_loop_step.restype = ctypes.c_int
     L.ra_mppi_softmin_update_noalloc.argtypes = [_FP, _FP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -211,6 +216,15 @@ def ra_mppi_step_host(h, x0_ptr, V_in_ptr, V_out_ptr, S_tilde_ptr=None, stream=0
 def ra_mppi_closed_loop_step(h, x_ptr, V_ptr, S_tilde_ptr=None, collisions_ptr=None, shift=1, stream=0):
     _check(lib().ra_mppi_closed_loop_step(h, x_ptr, V_ptr, S_tilde_ptr, collisions_ptr, int(shift), stream),
            "ra_mppi_closed_loop_step", h)
+
+
+def ra_mppi_set_cost_weights(h, theta):
+    arr = (ctypes.c_float * 4)(*[float(v) for v in theta])
+    _check(lib().ra_mppi_set_cost_weights(h, arr), "ra_mppi_set_cost_weights", h)
+
+
+def ra_mppi_backward(h, gV_plus_ptr, gS_tilde_ptr, gV_ptr, gtheta_ptr, stream=0):
+    _check(lib().ra_mppi_backward(h, gV_plus_ptr, gS_tilde_ptr, gV_ptr, gtheta_ptr, stream), "ra_mppi_backward", h)
 
 
 def ra_mppi_workspace(h):

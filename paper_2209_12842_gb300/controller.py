@@ -23,13 +23,14 @@ class RaMppi:
     obstacles: (n, 3) array-like of (x, y, r), optional.
     """
 
-    def __init__(self, problem, obstacles=None, keep_risk_costs=False, max_obstacles=None):
+    def __init__(self, problem, obstacles=None, keep_risk_costs=False, max_obstacles=None, differentiable=False):
         if not torch.cuda.is_available():
             raise RuntimeError("RaMppi needs a CUDA device (there is no CPU path)")
         self.p = dict(problem)
         n_obs = 0 if obstacles is None else len(obstacles)
         cap = max_obstacles if max_obstacles is not None else max(n_obs, int(self.p.get("n_obs", 0)), 1)
-        flags = B.RA_MPPI_KEEP_RISK_COSTS if keep_risk_costs else 0
+        flags = (B.RA_MPPI_KEEP_RISK_COSTS if keep_risk_costs else 0) | \
+            (B.RA_MPPI_DIFFERENTIABLE if differentiable else 0)
         self.keep_risk_costs = keep_risk_costs
         self._prob = B.ra_mppi_problem_from(self.p, flags=flags, max_obstacles=cap)
         self.h = B.ra_mppi_create(self._prob)
@@ -108,6 +109,21 @@ class RaMppi:
 
     def set_launch(self, warps_per_block=0, ilp=0):
         B.ra_mppi_set_launch(self.h, warps_per_block, ilp)
+
+    def set_cost_weights(self, theta):
+        """theta = (w_dev, w_speed, gamma, w_obs) for the following updates."""
+        B.ra_mppi_set_cost_weights(self.h, [float(v) for v in theta])
+
+    def backward(self, gV_plus, gS_tilde=None, stream=None):
+        """VJP of the most recent update: (dV, dtheta) of
+        <gV_plus, V+> + <gS_tilde, S~>."""
+        gVp = gV_plus.contiguous().float()
+        gS = gS_tilde.contiguous().float() if gS_tilde is not None else None
+        gV = torch.empty_like(gVp)
+        gth = torch.empty(4, dtype=torch.float32, device=gVp.device)
+        B.ra_mppi_backward(self.h, gVp.data_ptr(), gS.data_ptr() if gS is not None else None, gV.data_ptr(),
+                           gth.data_ptr(), _stream_ptr(stream))
+        return gV, gth
 
     def set_timing_events(self, begin=None, end=None):
         """Record torch.cuda.Event objects around the fused rollout kernel."""
@@ -213,3 +229,30 @@ class RaMppiBatch:
 
     def get_launch(self):
         return B.ra_mppi_batch_get_launch(self.b)
+
+
+class RaMppiUpdate(torch.autograd.Function):
+    """(V+, S~) = update(V, theta) of one RA-MPPI step with the hand-written
+    adjoint as its backward; theta = (w_dev, w_speed, gamma, w_obs).
+
+    Usage: V_plus, S_tilde = RaMppiUpdate.apply(V, theta, ctl, x0) with ctl a
+    RaMppi created with differentiable=True; the backward must run before
+    the handle steps again (it differentiates the handle's latest update)."""
+
+    @staticmethod
+    def forward(ctx, V, theta, ctl, x0):
+        ctl.set_cost_weights(theta.detach().cpu().tolist())
+        V_plus = ctl.step(x0.detach(), V.detach().contiguous())
+        ctx.ctl = ctl
+        ctx.iteration = ctl.iteration
+        ctx.v_shape = V.shape
+        return V_plus, ctl.S_tilde.clone()
+
+    @staticmethod
+    def backward(ctx, gV_plus, gS_tilde):
+        if ctx.ctl.iteration != ctx.iteration:
+            raise RuntimeError("the RA-MPPI handle stepped again before backward")
+        if gV_plus is None:
+            gV_plus = torch.zeros(ctx.v_shape, dtype=torch.float32, device=ctx.ctl.S_tilde.device)
+        gV, gth = ctx.ctl.backward(gV_plus, gS_tilde)
+        return gV, gth, None, None

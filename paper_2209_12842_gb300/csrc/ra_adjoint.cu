@@ -1,0 +1,500 @@
+// Adjoint of one RA-MPPI update: the vector-Jacobian product of
+// (V+, S~) = update(V, theta) w.r.t. the mean controls V and the cost weights
+// theta = (w_dev, w_speed, gamma, w_obs), for fixed noise.
+//
+// With cotangents gV+ [T][nu] and gS~ [K] the derivative of each forward
+// step, in reverse:
+//   Eqs. 4, 17:  dV+/dU_k = w^_k I,  dV+/dS~_k = -(w^_k / lambda)(U_k - V+), so
+//                S~-bar_k = gS~_k - (w^_k / lambda)(d_k - c),
+//                d_k = <gV+, U_k>, c = sum_k w^_k d_k = <gV+, V+>
+//   Eqs. 14-16:  S-bar_k = S~-bar_k, CVaR-bar_k = S~-bar_k A 1{CVaR_k > C_u}
+//   Eqs. 10-13, 18, 19: CVaR is piecewise linear in the risk costs; its
+//                weights are 1/((1-alpha)M) above VaR, the remaining weight
+//                shared by the costs equal to VaR, 0 below; the scaling gives
+//                B w + (1 - B)/M
+//   Eqs. 3, 9:   reverse sweeps through each rollout, the states recomputed
+//                from checkpoints every 8 steps:
+//                u-bar_t = (dF/du)' lam_{t+1}, lam_t = c dq/dx + (dF/dx)' lam_{t+1}
+//   Alg. 1:      U = clip(V + eps) passes u-bar to V inside the box for the
+//                samples drawn around V; the control cost gamma v' S^-1 u
+//                depends on V directly as well.
+// Three launches: prep (d_k, w^_k, c), main (nominal blocks + one warp per
+// sample for the disturbed rollouts), reduce (sum over samples, clip mask).
+// The kinematic and linear models are differentiated; the indicator
+// obstacle term has zero derivative almost everywhere.
+#include "ra_kernels.h"
+
+namespace ramppi {
+
+namespace {
+
+constexpr int kSeg = 8;  // checkpoint spacing (steps)
+constexpr int kMaxCk = RA_MPPI_MAX_T_DEV / kSeg + 1;
+
+__device__ __forceinline__ float sgnf(float v) { return v > 0.0f ? 1.0f : (v < 0.0f ? -1.0f : 0.0f); }
+
+// e(x) and its gradient w.r.t. (px, py)
+__device__ __forceinline__ float track_e_grad(const DevParams& p, float px, float py, float* de) {
+  const float half = 0.5f * p.track_S;
+  const float ax = fabsf(px);
+  if (ax <= half) {
+    de[0] = 0.0f;
+    de[1] = py < 0.0f ? -1.0f : 1.0f;
+    return fabsf(py) - p.track_R;
+  }
+  const float dx = ax - half;
+  const float rho = sqrtf(fmaf(dx, dx, py * py));
+  de[0] = rho > 0.0f ? sgnf(px) * dx / rho : 0.0f;
+  de[1] = rho > 0.0f ? py / rho : 0.0f;
+  return rho - p.track_R;
+}
+
+// gradient of the arc length s(x) w.r.t. (px, py)
+__device__ __forceinline__ void track_s_grad(const DevParams& p, float px, float py, float* ds) {
+  const float half = 0.5f * p.track_S;
+  if (fabsf(px) <= half) {
+    ds[0] = py < 0.0f ? 1.0f : -1.0f;
+    ds[1] = 0.0f;
+    return;
+  }
+  const float dx = px > half ? px - half : px + half;
+  const float r2 = fmaf(dx, dx, py * py);
+  ds[0] = r2 > 0.0f ? p.track_R * (-py) / r2 : 0.0f;
+  ds[1] = r2 > 0.0f ? p.track_R * dx / r2 : 0.0f;
+}
+
+// c * d(cost terms in mask)/dx added to g; c * d(cost)/d(w_dev, w_speed, -, w_obs) added to gth
+template <int MODEL>
+__device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, unsigned mask, float c,
+                                          const float4* __restrict__ obs, int n_obs, float* g, float* gth) {
+  if (MODEL == 2) {
+    if (mask & 16u) g[0] = fmaf(c, p.c_lin, g[0]);
+    return;
+  }
+  if (mask & 9u) {
+    float de[2];
+    const float e = track_e_grad(p, x[0], x[1], de);
+    if (mask & 1u) {
+      const float k = c * p.w_dev * 2.0f * e;
+      g[0] = fmaf(k, de[0], g[0]);
+      g[1] = fmaf(k, de[1], g[1]);
+      gth[0] = fmaf(c, e * e, gth[0]);
+    }
+    if (mask & 8u) {
+      const float d = p.track_hw - fabsf(e);
+      const float db = (-100.0f / kPi) / fmaf(1e4f * d, d, 1.0f);
+      const float k = c * p.w_bdry * db * (-sgnf(e));
+      g[0] = fmaf(k, de[0], g[0]);
+      g[1] = fmaf(k, de[1], g[1]);
+    }
+  }
+  if (mask & 2u) {
+    const float dv = x[3] - p.v_target;
+    g[3] = fmaf(c * p.w_speed * 2.0f, dv, g[3]);
+    gth[1] = fmaf(c, dv * dv, gth[1]);
+  }
+  if (mask & 4u) {
+    float val = 0.0f, g0 = 0.0f, g1 = 0.0f;
+    for (int i = 0; i < n_obs; ++i) {
+      const float4 o = obs[i];
+      const float dx = x[0] - o.x, dy = x[1] - o.y;
+      const float d2 = fmaf(dx, dx, dy * dy);
+      if (p.obs_mode == 0) {
+        val += d2 < o.w ? 1.0f : 0.0f;
+      } else {
+        const float d = sqrtf(d2);
+        const float z = p.kappa * (o.z - d);
+        const float sp = z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
+        val += sp;
+        const float sig = 1.0f / (1.0f + expf(-z));
+        if (d > 0.0f) {
+          g0 -= sig * dx / d;
+          g1 -= sig * dy / d;
+        }
+      }
+    }
+    if (p.obs_mode != 0) val *= p.inv_kappa;
+    g[0] = fmaf(c * p.w_obs, g0, g[0]);
+    g[1] = fmaf(c * p.w_obs, g1, g[1]);
+    gth[3] = fmaf(c, val, gth[3]);
+  }
+  if (mask & 16u) g[0] = fmaf(c, p.c_lin, g[0]);
+}
+
+// (dG/ds)' lam and (dG/du)' lam of one integration sub-step G at state s
+template <int MODEL>
+__device__ __forceinline__ void substep_vjp(const DevParams& p, const float* s, const float4 c, float* lam,
+                                            float* gu) {
+  if (MODEL == 0) {
+    float sp, cp;
+    heading_sincos(s[2], &sp, &cp);
+    const float h = p.h, v = s[3], L = p.mp[0];
+    const float tl = c.z * L;                 // tan(steer)
+    const float sec2_over_L = fmaf(tl, tl, 1.0f) / L;
+    const float l0 = lam[0], l1 = lam[1], l2 = lam[2], l3 = lam[3];
+    lam[2] = l2 + h * v * (cp * l1 - sp * l0);
+    lam[3] = l3 + h * (cp * l0 + sp * l1 + c.z * l2);
+    gu[0] = fmaf(l2 * h * v, sec2_over_L, gu[0]);
+    gu[1] = fmaf(l3, h, gu[1]);
+  } else {
+    gu[0] = fmaf(lam[0], p.h, gu[0]);
+  }
+}
+
+// reverse through one control step from x_t (sub-steps recomputed)
+template <int MODEL>
+__device__ __forceinline__ void step_vjp(const DevParams& p, const float* xt, const float4 c, float* lam,
+                                         float* gu) {
+  using Md = Model<MODEL>;
+  if (p.substeps == 1) {
+    substep_vjp<MODEL>(p, xt, c, lam, gu);
+    return;
+  }
+  for (int i = p.substeps - 1; i >= 0; --i) {
+    float s[Md::NX];
+#pragma unroll
+    for (int a = 0; a < Md::NX; ++a) s[a] = xt[a];
+    for (int j = 0; j < i; ++j) Md::substep(p, s, c);
+    substep_vjp<MODEL>(p, s, c, lam, gu);
+  }
+}
+
+__device__ __forceinline__ float s_tilde_of(const DevParams& p, float S, float cv) {
+  return S + ((cv > p.C_u) ? p.A * cv : 0.0f);
+}
+
+}  // namespace
+
+// d_k = <gV+, U_k>, w^_k, and c = sum_k w^_k d_k (last block merges, FP64)
+__global__ void __launch_bounds__(256) bwd_prep_kernel(const DevParams p, const BwdArgs a) {
+  __shared__ double red[8];
+  __shared__ unsigned int is_last;
+  const int TN = p.T * p.nu;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const float m = a.st->last_min;
+  const double s_tot = a.st->last_sum;
+  double part = 0.0;
+  if (k < p.K) {
+    float d = 0.0f;
+    const float* Uk = a.U + (size_t)k * TN;
+    for (int c = 0; c < TN; ++c) d = fmaf(a.gVp[c], Uk[c], d);
+    const float st = s_tilde_of(p, a.S[k], a.cvar[k]);
+    const float w = (isfinite(st) && s_tot > 0.0) ? (float)((double)expf((m - st) * p.inv_lambda) / s_tot) : 0.0f;
+    a.dk[k] = d;
+    a.wk[k] = w;
+    part = (double)w * (double)d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    a.prep_part[blockIdx.x] = t;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&a.arrive[0], 1u);
+    is_last = ticket == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile double* pp = a.prep_part;
+    double c = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) c += pp[b];
+    *a.c_out = c;
+    a.arrive[0] = 0u;
+  }
+}
+
+template <int MODEL>
+__device__ __forceinline__ float sbar_of(const DevParams& p, const BwdArgs& a, int k) {
+  const float c = (float)*a.c_out;
+  const float g = a.gS != nullptr ? a.gS[k] : 0.0f;
+  return g - a.wk[k] * p.inv_lambda * (a.dk[k] - c);
+}
+
+// nominal sample k (one thread): cotangents of U_k from V+, the nominal cost
+// and the control cost, masked by the clip; theta partials of S_k
+template <int MODEL>
+__device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a, int k, const float4* obs_s,
+                            int n_obs) {
+  using Md = Model<MODEL>;
+  constexpr int NX = Md::NX, NU = Md::NU;
+  const int T = in.T, TN = T * NU;
+  const float sbar = sbar_of<MODEL>(p, a, k);
+  const float wk = a.wk[k];
+  const float* Uk = a.U + (size_t)k * TN;
+  float ck[kMaxCk][NX];
+  float x[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) x[i] = a.x0[i];
+  for (int t = 0; t < T; ++t) {
+    if (t % kSeg == 0) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) ck[t / kSeg][i] = x[i];
+    }
+    Md::step(p, x, Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f));
+  }
+  float lam[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) lam[i] = 0.0f;
+  float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (MODEL != 2 && p.c5 != 0.0f) {
+    float ds[2];
+    track_s_grad(p, x[0], x[1], ds);
+    lam[0] = -sbar * p.c5 * ds[0];
+    lam[1] = -sbar * p.c5 * ds[1];
+  }
+  const int nseg = (T + kSeg - 1) / kSeg;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
+    float xs[kSeg][NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) xs[0][i] = ck[sg][i];
+    for (int t = t0; t + 1 < t1; ++t) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) xs[t + 1 - t0][i] = xs[t - t0][i];
+      Md::step(p, xs[t + 1 - t0], Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f));
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      const float u0 = Uk[t * NU], u1 = NU > 1 ? Uk[t * NU + 1] : 0.0f;
+      float gu[2] = {0.0f, 0.0f};
+      step_vjp<MODEL>(p, xs[t - t0], Md::ctl(p, u0, u1), lam, gu);
+      cost_grad<MODEL>(p, xs[t - t0], 0xFFFFFFFFu, sbar, obs_s, n_obs, lam, gth);
+      // control cost gamma v_t' S^-1 u_t and the clip of U = clip(V + eps)
+      const float v0 = a.V[t * NU], v1 = NU > 1 ? a.V[t * NU + 1] : 0.0f;
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0xFFFFFFFFu, (uint32_t)k, in.instance), in.k0, in.k1);
+      const float2 z = box_muller(w.x, w.y);
+      const bool warm = k < in.n_warm;
+      const float vv[2] = {v0, v1}, uu[2] = {u0, u1}, zz[2] = {z.x, z.y};
+      gth[2] = fmaf(sbar, v0 * p.inv_sig2[0] * u0 + (NU > 1 ? v1 * p.inv_sig2[1] * u1 : 0.0f), gth[2]);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) {
+        const float raw = __fmaf_rn(p.sigma_u[j], zz[j], warm ? vv[j] : 0.0f);
+        const float msk = (warm && raw > p.u_lo[j] && raw < p.u_hi[j]) ? 1.0f : 0.0f;
+        const float gc = p.gamma * p.inv_sig2[j];
+        const size_t idx = (size_t)k * TN + t * NU + j;
+        a.mask[idx] = msk;
+        a.Gnom[idx] = msk * (wk * a.gVp[t * NU + j] + gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a.thn[(size_t)k * 4 + i] = gth[i];
+}
+
+// disturbed rollouts of sample k (one warp): cotangents of U_k through the
+// CVaR term; theta partials of the risk costs
+template <int MODEL>
+__device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs& a, int k, int lane, float4* ctl,
+                              float* Ls, float* gus, const float4* obs_s, int n_obs) {
+  using Md = Model<MODEL>;
+  constexpr int NX = Md::NX, NU = Md::NU;
+  const int T = in.T, TN = T * NU, M = in.M;
+  const float sbar = sbar_of<MODEL>(p, a, k);
+  const float cv = a.cvar[k];
+  const float cvbar = (cv > p.C_u && isfinite(cv)) ? sbar * p.A : 0.0f;
+  if (cvbar == 0.0f) {
+    for (int c = lane; c < TN; c += 32) a.gUd[(size_t)k * TN + c] = 0.0f;
+    if (lane < 4) a.thd[(size_t)k * 4 + lane] = 0.0f;
+    return;
+  }
+  const float* Uk = a.U + (size_t)k * TN;
+  for (int t = lane; t < T; t += 32) {
+    ctl[t] = Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f);
+  }
+  for (int c = lane; c < TN; c += 32) gus[c] = 0.0f;
+  __syncwarp();
+  float x0[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) x0[i] = a.x0[i];
+  const int R = (M + 31) >> 5;
+  // pass 1: the risk costs (same arithmetic as the forward rollouts)
+  for (int r = 0; r < R; ++r) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r, ctl, Ls, obs_s, n_obs);
+  __syncwarp();
+  // CVaR weights: VaR by radix select, then the tail
+  constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
+  uint32_t key[RMAX];
+  float val[RMAX];
+  float sum = 0.0f;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const int idx = lane + 32 * r;
+    const bool valid = idx < M;
+    val[r] = valid ? Ls[idx] : 0.0f;
+    sum += val[r];
+    key[r] = valid ? fkey(val[r]) : 0xFFFFFFFFu;
+  }
+  uint32_t prefix = 0u;
+  int kth = in.j_var - 1;
+#pragma unroll 1
+  for (int b = 31; b >= 0; --b) {
+    const uint32_t hi_mask = (b == 31) ? 0u : (0xFFFFFFFFu << (b + 1));
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const uint32_t kk = key[r];
+      cnt += ((kk & hi_mask) == prefix && ((kk >> b) & 1u) == 0u && (lane + 32 * r) < M) ? 1 : 0;
+    }
+    cnt = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
+    if (kth >= cnt) {
+      kth -= cnt;
+      prefix |= (1u << b);
+    }
+  }
+  const float var = fkey_inv(prefix);
+  int c_gt = 0, c_eq = 0;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    if (lane + 32 * r < M) {
+      if (val[r] > var) ++c_gt;
+      else if (val[r] == var) ++c_eq;
+    }
+  }
+  c_gt = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)c_gt);
+  c_eq = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)c_eq);
+  const float w_gt = p.cvar_mode == 0 ? 1.0f / in.tail_denom : 1.0f / (float)(c_gt + c_eq);
+  const float w_eq = p.cvar_mode == 0 ? ((float)(M - in.j_var - c_gt) + in.frac_j) / in.tail_denom / (float)c_eq
+                                      : 1.0f / (float)(c_gt + c_eq);
+  const float base = (1.0f - p.B) / (float)M;
+  // pass 2: reverse sweep of every rollout with a nonzero weight
+  float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int r = 0; r < R; ++r) {
+    const int m = lane + 32 * r;
+    const float Lm = val[r];
+    const float wt = m < M ? (Lm > var ? w_gt : (Lm == var ? w_eq : 0.0f)) : 0.0f;
+    const float lbar = m < M ? cvbar * fmaf(p.B, wt, base) : 0.0f;
+    if (!__any_sync(0xFFFFFFFFu, lbar != 0.0f)) continue;
+    float ck[kMaxCk][NX];
+    float x[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x[i] = x0[i];
+    for (int t = 0; t < T; ++t) {
+      if (t % kSeg == 0) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) ck[t / kSeg][i] = x[i];
+      }
+      Md::step(p, x, ctl[t]);
+      add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance, x);
+    }
+    float lam[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) lam[i] = 0.0f;
+    const int nseg = (T + kSeg - 1) / kSeg;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
+      float xs[kSeg][NX];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) xs[0][i] = ck[sg][i];
+      for (int t = t0; t + 1 < t1; ++t) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) xs[t + 1 - t0][i] = xs[t - t0][i];
+        Md::step(p, xs[t + 1 - t0], ctl[t]);
+        add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance,
+                                 xs[t + 1 - t0]);
+      }
+      for (int t = t1 - 1; t >= t0; --t) {
+        float gu[2] = {0.0f, 0.0f};
+        step_vjp<MODEL>(p, xs[t - t0], ctl[t], lam, gu);
+        cost_grad<MODEL>(p, xs[t - t0], p.risk_mask, lbar, obs_s, n_obs, lam, gth);
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          const float s = warp_sum(gu[j]);
+          if (lane == 0) gus[t * NU + j] += s;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  for (int c = lane; c < TN; c += 32) a.gUd[(size_t)k * TN + c] = gus[c];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float s = warp_sum(gth[i]);
+    if (lane == 0) a.thd[(size_t)k * 4 + i] = s;
+  }
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const BwdArgs a) {
+  extern __shared__ float4 smem[];
+  float4* obs_s = smem;
+  const int n_obs = a.st->n_obs;
+  // the differentiated update already advanced the counter
+  const Inst in = inst_of(p, (uint32_t)(a.st->iteration - 1ull));
+  for (int i = threadIdx.x; i < n_obs; i += blockDim.x) obs_s[i] = a.obs[i];
+  __syncthreads();
+  if ((int)blockIdx.x < a.nb_nom) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < in.K) bwd_nominal<MODEL>(p, in, a, k, obs_s, n_obs);
+    return;
+  }
+  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
+  if (k >= in.K) return;
+  float4* ctl = smem + a.obs_cap + w * in.T;
+  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * (in.M + in.T * p.nu);
+  float* gus = Ls + in.M;
+  bwd_disturbed<MODEL>(p, in, a, k, lane, ctl, Ls, gus, obs_s, n_obs);
+}
+
+// gV[c] = sum_k Gnom[k][c] + mask[k][c] gUd[k][c]; gtheta[i] = sum_k thn + thd
+__global__ void __launch_bounds__(256) bwd_reduce_kernel(const DevParams p, const BwdArgs a) {
+  __shared__ unsigned int is_last;
+  const int TN = p.T * p.nu, NC = TN + 4;
+  const int per = (p.K + gridDim.x - 1) / gridDim.x;
+  const int kb = blockIdx.x * per, ke = min(p.K, kb + per);
+  float* part = a.red_part + (size_t)blockIdx.x * NC;
+  for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+    float s = 0.0f, comp = 0.0f;
+    for (int k = kb; k < ke; ++k) {
+      float v;
+      if (c < TN) {
+        const size_t idx = (size_t)k * TN + c;
+        v = a.Gnom[idx] + a.mask[idx] * a.gUd[idx];
+      } else {
+        v = a.thn[(size_t)k * 4 + (c - TN)] + a.thd[(size_t)k * 4 + (c - TN)];
+      }
+      const float t = s + v;
+      comp += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+      s = t;
+    }
+    part[c] = s + comp;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(&a.arrive[1], 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const volatile float* pp = a.red_part;
+  for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += (double)pp[(size_t)b * NC + c];
+    if (c < TN) a.gV[c] = (float)s;
+    else a.gtheta[c - TN] = (float)s;
+  }
+  if (threadIdx.x == 0) a.arrive[1] = 0u;
+}
+
+cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
+                            size_t smem, int nb_red, cudaStream_t s) {
+  bwd_prep_kernel<<<nb_prep, 256, 0, s>>>(p, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int grid = a.nb_nom + nb_dist;
+  if (model == 0) {
+    e = cudaFuncSetAttribute(bwd_main_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) bwd_main_kernel<0><<<grid, 128, smem, s>>>(p, a);
+  } else {
+    e = cudaFuncSetAttribute(bwd_main_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) bwd_main_kernel<2><<<grid, 128, smem, s>>>(p, a);
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bwd_reduce_kernel<<<nb_red, 256, 0, s>>>(p, a);
+  return cudaGetLastError();
+}
+
+}  // namespace ramppi

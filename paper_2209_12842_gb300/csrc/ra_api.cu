@@ -34,6 +34,21 @@ struct ra_mppi {
   float* x0_dev = nullptr;  // staging for ra_mppi_step_host
   float* V_dev = nullptr;
   float* V_plus = nullptr;  // V+ of ra_mppi_closed_loop_step before the warm-start shift
+  // adjoint (RA_MPPI_DIFFERENTIABLE): inputs of the last update and scratch
+  float* keep_x0 = nullptr;
+  float* keep_V = nullptr;
+  float* b_dk = nullptr;
+  float* b_wk = nullptr;
+  double* b_prep = nullptr;
+  double* b_c = nullptr;
+  unsigned int* b_arrive = nullptr;
+  float* b_Gnom = nullptr;
+  float* b_mask = nullptr;
+  float* b_gUd = nullptr;
+  float* b_thn = nullptr;
+  float* b_thd = nullptr;
+  float* b_red = nullptr;
+  int nb_prep = 0, nb_red = 0;
   cudaEvent_t ev_begin = nullptr;  // optional timing hook around the rollout kernel
   cudaEvent_t ev_end = nullptr;
   std::string err;
@@ -190,6 +205,19 @@ void release(ra_mppi* h) {
   cudaFree(h->x0_dev);
   cudaFree(h->V_dev);
   cudaFree(h->V_plus);
+  cudaFree(h->keep_x0);
+  cudaFree(h->keep_V);
+  cudaFree(h->b_dk);
+  cudaFree(h->b_wk);
+  cudaFree(h->b_prep);
+  cudaFree(h->b_c);
+  cudaFree(h->b_arrive);
+  cudaFree(h->b_Gnom);
+  cudaFree(h->b_mask);
+  cudaFree(h->b_gUd);
+  cudaFree(h->b_thn);
+  cudaFree(h->b_thd);
+  cudaFree(h->b_red);
 }
 
 // The limit is a property of the kernel, shared by every handle: raise it
@@ -273,6 +301,24 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   if (e == cudaSuccess) e = dalloc(&h->x0_dev, 8);
   if (e == cudaSuccess) e = dalloc(&h->V_dev, TN);
   if (e == cudaSuccess) e = dalloc(&h->V_plus, TN);
+  if (e == cudaSuccess && (p->flags & RA_MPPI_DIFFERENTIABLE)) {
+    h->nb_prep = (int)((K + 255) / 256);
+    h->nb_red = (int)std::min<size_t>((K + 255) / 256, 256);
+    e = dalloc(&h->keep_x0, 8);
+    if (e == cudaSuccess) e = dalloc(&h->keep_V, TN);
+    if (e == cudaSuccess) e = dalloc(&h->b_dk, K);
+    if (e == cudaSuccess) e = dalloc(&h->b_wk, K);
+    if (e == cudaSuccess) e = dalloc(&h->b_prep, (size_t)h->nb_prep);
+    if (e == cudaSuccess) e = dalloc(&h->b_c, 1);
+    if (e == cudaSuccess) e = dalloc(&h->b_arrive, 2);
+    if (e == cudaSuccess) e = dalloc(&h->b_Gnom, K * TN);
+    if (e == cudaSuccess) e = dalloc(&h->b_mask, K * TN);
+    if (e == cudaSuccess) e = dalloc(&h->b_gUd, K * TN);
+    if (e == cudaSuccess) e = dalloc(&h->b_thn, K * 4);
+    if (e == cudaSuccess) e = dalloc(&h->b_thd, K * 4);
+    if (e == cudaSuccess) e = dalloc(&h->b_red, (size_t)h->nb_red * (TN + 4));
+    if (e == cudaSuccess) e = cudaMemset(h->b_arrive, 0, 2 * sizeof(unsigned int));
+  }
   if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMemset(h->U, 0, sizeof(float) * K * TN);
   if (e == cudaSuccess) e = prepare(h);
@@ -359,6 +405,12 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
   a.obs_cap = h->obs_cap;
   const int nb_dist = (p.K + h->warps - 1) / h->warps;
   cudaError_t e;
+  if (h->keep_x0 != nullptr) {
+    e = cudaMemcpyAsync(h->keep_x0, x0, sizeof(float) * h->nx, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->keep_V, V_in, sizeof(float) * (size_t)p.T * h->nu, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "keep inputs");
+  }
   if (h->ev_begin != nullptr) {
     e = cudaEventRecord(h->ev_begin, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
@@ -494,6 +546,61 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp) {
     prepare(h);
     return cuda_fail(h, e, "set_launch");
   }
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta) {
+  if (h == nullptr || theta == nullptr) return RA_MPPI_EINVAL;
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(theta[i])) return fail(h, RA_MPPI_EINVAL, "cost weights must be finite");
+  h->prob.w_dev = h->dp.w_dev = theta[0];
+  h->prob.w_speed = h->dp.w_speed = theta[1];
+  h->prob.gamma = h->dp.gamma = theta[2];
+  h->prob.w_obs = h->dp.w_obs = theta[3];
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, float* gV, float* gtheta,
+                     void* stream) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (gV_plus == nullptr || gV == nullptr || gtheta == nullptr)
+    return fail(h, RA_MPPI_EINVAL, "gV_plus, gV and gtheta are required");
+  if (h->keep_x0 == nullptr) return fail(h, RA_MPPI_EINVAL, "the problem was created without RA_MPPI_DIFFERENTIABLE");
+  if (h->prob.model == RA_MPPI_DYN_SINGLE_TRACK)
+    return fail(h, RA_MPPI_EUNSUPPORTED, "the adjoint covers the kinematic and linear models");
+  const ra_mppi_problem& p = h->prob;
+  ramppi::BwdArgs a{};
+  a.x0 = h->keep_x0;
+  a.V = h->keep_V;
+  a.U = h->U;
+  a.S = h->S;
+  a.cvar = h->cvar;
+  a.obs = h->obs;
+  a.st = h->st;
+  a.gVp = gV_plus;
+  a.gS = gS_tilde;
+  a.dk = h->b_dk;
+  a.wk = h->b_wk;
+  a.prep_part = h->b_prep;
+  a.c_out = h->b_c;
+  a.arrive = h->b_arrive;
+  a.Gnom = h->b_Gnom;
+  a.mask = h->b_mask;
+  a.gUd = h->b_gUd;
+  a.thn = h->b_thn;
+  a.thd = h->b_thd;
+  a.red_part = h->b_red;
+  a.gV = gV;
+  a.gtheta = gtheta;
+  constexpr int kBwdWarps = 4;
+  a.nb_nom = (p.K + 32 * kBwdWarps - 1) / (32 * kBwdWarps);
+  a.obs_cap = h->obs_cap;
+  const int nb_dist = (p.K + kBwdWarps - 1) / kBwdWarps;
+  const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * p.T * sizeof(float4) +
+                      (size_t)kBwdWarps * (p.M + (size_t)p.T * h->nu) * sizeof(float);
+  const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, h->nb_prep, nb_dist, smem, h->nb_red,
+                                                static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
   return RA_MPPI_OK;
 }
 

@@ -1,0 +1,120 @@
+"""GPU adjoint (ra_mppi_backward, RaMppiUpdate) against the oracle's analytic
+adjoint, which the CPU tests pin to central finite differences.
+
+Tolerance: relative 1e-3 in the 2-norm of each block (gV, gtheta), and per
+component with a floor of 1e-3 of the block's largest component.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import ra_scenes as rs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_12842_gb300 import build as b
+
+    b.build()
+
+
+def _close(name, got, want, rtol=1e-3):
+    got, want = np.asarray(got, np.float64).ravel(), np.asarray(want, np.float64).ravel()
+    nrm = np.linalg.norm(want)
+    assert np.linalg.norm(got - want) <= rtol * max(nrm, 1e-12), (name, got, want)
+    floor = rtol * np.abs(want).max()
+    bad = np.abs(got - want) > rtol * np.abs(want) + floor
+    assert not bad.any(), (name, np.nonzero(bad), got[bad], want[bad])
+
+
+def _run(p, obs, x0, V, gVp, gS, iteration=0):
+    from paper_2209_12842_gb300 import RaMppi
+
+    ctl = RaMppi(p, obs, differentiable=True)
+    ctl.iteration = iteration
+    ctl.step(torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda())
+    gV, gth = ctl.backward(torch.from_numpy(gVp).cuda(), torch.from_numpy(gS).cuda() if gS is not None else None)
+    torch.cuda.synchronize()
+    out = gV.cpu().numpy(), gth.cpu().numpy()
+    assert ctl.status() == 0
+    ctl.close()
+    return out
+
+
+@pytest.mark.parametrize("case", ["plain", "tce", "scaled_eta", "all_terms"])
+def test_adjoint_matches_oracle_small(case):
+    ov = dict(K=96, M=32, T=12)
+    if case == "tce":
+        ov.update(cvar_mode=rs.CVAR_TCE)
+    elif case == "scaled_eta":
+        ov.update(B=2.0, eta=0.25, A=3.0, C_u=5.0)
+    elif case == "all_terms":
+        ov.update(risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED | rs.RISK_BDRY, w_bdry=2.0, c4=0.6, c5=2.0)
+    p = rs.preset("c4_gradient", **ov)
+    obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4)
+    x0 = np.array([0.0, -4.0, 0.0, 1.0], np.float32)
+    V = rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 3)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    gV, gth = _run(p, obs, x0, V, gVp, gS)
+    rV, rth = oracle.backward(p, x0, V, obs, gVp, gS)
+    _close("gV", gV, rV)
+    _close("gtheta", gth, rth)
+
+
+def test_adjoint_config4_full_size():
+    p = rs.preset("c4_gradient")
+    obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
+    obs = np.concatenate([obs, rs.obstacles_ahead(2, 4, 0.2, 0.3, x_from=0.2, x_to=1.5)])
+    p["n_obs"] = len(obs)
+    x0 = np.array([0.0, -4.0, 0.0, 1.5], np.float32)
+    V = rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 5)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 11)
+    gV, gth = _run(p, obs, x0, V, gVp, gS)
+    rV, rth = oracle.backward(p, x0, V, obs, gVp, gS)
+    _close("gV", gV, rV)
+    _close("gtheta", gth, rth)
+
+
+def test_autograd_function_matches_backward():
+    from paper_2209_12842_gb300 import RaMppi, RaMppiUpdate
+
+    p = rs.preset("c4_gradient", K=128, M=32, T=10)
+    obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4)
+    x0 = torch.tensor([0.0, -4.0, 0.0, 1.0], device="cuda")
+    V = torch.from_numpy(rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 3)).cuda().requires_grad_(True)
+    theta = torch.tensor([p["w_dev"], p["w_speed"], p["gamma"], p["w_obs"]], device="cuda", requires_grad=True)
+    ctl = RaMppi(p, obs, differentiable=True)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    gVp_t, gS_t = torch.from_numpy(gVp).cuda(), torch.from_numpy(gS).cuda()
+    V_plus, S_tilde = RaMppiUpdate.apply(V, theta, ctl, x0)
+    loss = (V_plus * gVp_t).sum() + (S_tilde * gS_t).sum()
+    dV, dth = torch.autograd.grad(loss, (V, theta))
+    rV, rth = oracle.backward(p, x0.cpu().numpy(), V.detach().cpu().numpy(), obs, gVp, gS)
+    _close("gV", dV.cpu().numpy(), rV)
+    _close("gtheta", dth.cpu().numpy(), rth)
+    # gradient refinement of the warm start moves the objective downhill
+    ctl.close()
+
+
+def test_adjoint_rejects_dynamic_model_and_missing_flag():
+    from paper_2209_12842_gb300 import RaMppi, RaMppiError
+
+    p = rs.preset("small_dyn")
+    ctl = RaMppi(p, rs.obstacles_ahead(1, 4, 0.2, 0.3), differentiable=True)
+    ctl.step(torch.from_numpy(rs.initial_state(1)).cuda(), torch.zeros(p["T"], 2, device="cuda"))
+    with pytest.raises(RaMppiError):
+        ctl.backward(torch.ones(p["T"], 2, device="cuda"))
+    ctl.close()
+    q = rs.preset("small_kin")
+    ctl = RaMppi(q, rs.obstacles_ahead(1, 4, 0.2, 0.3))
+    ctl.step(torch.from_numpy(rs.initial_state(0)).cuda(), torch.zeros(q["T"], 2, device="cuda"))
+    with pytest.raises(RaMppiError):
+        ctl.backward(torch.ones(q["T"], 2, device="cuda"))
+    ctl.close()
