@@ -40,14 +40,18 @@ LANES_PER_SM = 128
 
 
 # ---------------------------------------------------------------- op counts
-def algorithmic_ops(p):
+def algorithmic_ops(p, tested_obstacles=None):
     """Formula count of ALU lane-operations per disturbed step and per nominal
     step: FP32 add/mul/FMA/min/max/compare/select and INT32 ops count 1 each,
     every special-function evaluation (sin, cos, tan, atan, atan2, log, exp,
-    sqrt, erfcinv, division) counts 1."""
+    sqrt, erfcinv, division) counts 1.  The indicator obstacle term of a
+    disturbed step counts the obstacles actually tested (`tested_obstacles`
+    per rollout-step, after the kernel's exact bounding-box cull) when given,
+    else all of them."""
     model, n_obs, sub = int(p["model"]), int(p["n_obs"]), int(p["substeps"])
     philox = 100  # 10 rounds x (2 mullo + 2 mulhi + 4 xor + 2 key adds)
-    obs_ind = 6 * n_obs  # 2 sub, mul, fma, compare-select, add
+    n_test = n_obs if tested_obstacles is None else tested_obstacles
+    obs_ind = 6 * n_test  # 2 sub, mul, fma, compare-select, add
     obs_sp = 10 * n_obs  # 2 sub, mul, fma, sqrt, sub, mul, exp, log1p, add
     obs = obs_ind if int(p["obs_mode"]) == 0 else obs_sp
     if model == 1:
@@ -62,7 +66,8 @@ def algorithmic_ops(p):
     risk = 1 + obs
     disturbed = dyn + noise + risk
     # nominal: control draw (Philox + Box-Muller + clip ~ 120), dynamics, full q
-    nominal = 120 + dyn + obs + 30
+    # (the nominal rollout tests every obstacle)
+    nominal = 120 + dyn + (6 * n_obs if int(p["obs_mode"]) == 0 else obs_sp) + 30
     return disturbed, nominal
 
 
@@ -221,6 +226,8 @@ def run_ours(args, p, x0, V, obs):
     kv_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kv_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
+    tune_ms = ctl.tune(x0_d, V_d, 3)  # launch-shape autotuner (results do not depend on it)
+    warps, ilp = ctl.get_launch()
     for i in range(args.warmup):
         ctl.step(x0_d, V_d, V_out)
     torch.cuda.synchronize()
@@ -246,17 +253,21 @@ def run_ours(args, p, x0, V, obs):
     ctl.set_timing_events(None)
     clk = clocks.stop() if rank == 0 else None
     status = ctl.status()
+    # obstacles tested exactly per rollout-step (one extra, untimed update)
+    cand = torch.zeros(1, dtype=torch.int64, device=dev)
+    B.ra_mppi_set_diagnostics(ctl.h, cand.data_ptr())
+    ctl.step(x0_d, V_d, V_out)
+    torch.cuda.synchronize()
+    B.ra_mppi_set_diagnostics(ctl.h, None)
+    passes = -(-((int(p["M"]) + 31) // 32) // ilp)
+    tested = float(cand.item()) / (int(p["K"]) * passes * int(p["T"]))
 
     step_ms = np.array([b.elapsed_time(e) for b, e in zip(ev_b, ev_e)])
     kern_ms = np.array([b.elapsed_time(e) for b, e in zip(kv_b, kv_e)])
-    t_step = float(step_ms.sum()) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = aggregate_over_ranks(dist if world > 1 else None, torch, float(step_ms.sum()) / 1e3, dev)
     K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
     units = K * M * T
-    value = world * units * args.steps / t_step
+    value = job_value(world, units, args.steps, t_step)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     nx = x0.size
@@ -272,15 +283,12 @@ def run_ours(args, p, x0, V, obs):
         t1 = time.perf_counter()
         B.ra_mppi_step_host(ctl.h, x0_h.data_ptr(), V_h.data_ptr(), Vo_h.data_ptr(), None, stream.cuda_stream)
         e2e_ms.append(1e3 * (time.perf_counter() - t1))
-    e2e_t = float(np.mean(e2e_ms)) / 1e3
-    if world > 1:
-        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
+    e2e_t = aggregate_over_ranks(dist if world > 1 else None, torch, float(np.mean(e2e_ms)) / 1e3, dev)
     ctl.close()
 
     if rank == 0:
-        d_ops, n_ops = algorithmic_ops(p)
+        d_ops, n_ops = algorithmic_ops(p, tested)
+        d_ops_bf, _ = algorithmic_ops(p)
         ops_per_launch = units * d_ops + K * T * n_ops
         k_mean = float(kern_ms.mean()) / 1e3
         achieved = ops_per_launch / k_mean / 1e9
@@ -297,6 +305,7 @@ def run_ours(args, p, x0, V, obs):
                            "rollout_kernel_mean": 1e3 * k_mean},
             "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
             "gpu_launches": 2 * args.steps,
+            "launch": {"warps_per_block": warps, "rollouts_interleaved": ilp, "tune_ms": tune_ms},
             "status": B.STATUS_NAMES.get(status, status),
             "clocks": clk,
             "e2e": {"value": world * units / e2e_t, "unit": "rollout-steps/s",
@@ -306,6 +315,9 @@ def run_ours(args, p, x0, V, obs):
                          "unit": "Gop/s (ALU lane-ops, formula count)", "frac": achieved / peak,
                          "ops_per_launch": ops_per_launch, "ops_per_disturbed_step": d_ops,
                          "ops_per_nominal_step": n_ops,
+                         "obstacles_tested_per_rollout_step": tested,
+                         "ops_per_disturbed_step_brute_force": d_ops_bf,
+                         "frac_brute_force_count": (units * d_ops_bf + K * T * n_ops) / k_mean / 1e9 / peak,
                          "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock {sm_mhz:.0f} MHz",
                          "traffic": traffic},
         }
@@ -339,6 +351,21 @@ def kernel_source_sha():
             h.update(f.encode())
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def aggregate_over_ranks(dist, torch, seconds, device):
+    """Max over ranks of a per-rank duration (the slowest rank sets the job
+    time); identity without a process group."""
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return float(seconds)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, steps, seconds):
+    """Whole-job rollout-steps/s: every rank processes its own problem."""
+    return world * units_per_rank * steps / seconds
 
 
 def ev_time(torch, fn, n, stream):

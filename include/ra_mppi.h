@@ -221,6 +221,13 @@ int ra_mppi_get_status(ra_mppi_t* h);
 /* Human-readable reason of the last error on this handle ("" if none). */
 const char* ra_mppi_last_error(const ra_mppi_t* h);
 
+/* Launch-shape tuner: times every valid (warps per block, interleave) pair
+ * on the given inputs (x0, V device; `replays` updates each), keeps the
+ * fastest and restores the update counter, so later results are unchanged
+ * (they never depend on the shape).  Synchronous. */
+int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays, float* best_ms);
+int ra_mppi_get_launch(ra_mppi_t* h, int32_t* warps_per_block, int32_t* ilp);
+
 /* Cost weights theta = (w_dev, w_speed, gamma, w_obs) used by the following
  * updates (host-side, no device work).  EINVAL if any is not finite. */
 int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta);
@@ -246,6 +253,12 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
 /* Kernel launch tuning: disturbed-rollout warps per block (1..8) and
  * rollouts each lane interleaves (1, 2 or 4); 0 keeps the default. */
 int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp);
+
+/* Diagnostics: when `candidates` (device uint64) is set, the disturbed
+ * rollouts add to it the number of obstacles each warp tested exactly after
+ * its bounding-box cull, summed over steps (the work actually done by the
+ * indicator term).  NULL turns it off. */
+int ra_mppi_set_diagnostics(ra_mppi_t* h, unsigned long long* candidates);
 
 /* Timing hook: when set, ra_mppi_step records the caller's CUDA events
  * (cudaEvent_t passed as void*) immediately before and after the fused

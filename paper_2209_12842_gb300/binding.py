@@ -83,6 +83,12 @@ def _declare(L):
     L.ra_mppi_last_error.restype = ctypes.c_char_p
     L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
     L.ra_mppi_set_timing_events.argtypes = [_VP, _VP, _VP]
+    L.ra_mppi_set_diagnostics.argtypes = [_VP, _VP]
+    L.ra_mppi_set_diagnostics.restype = ctypes.c_int
+    L.ra_mppi_tune.argtypes = [_VP, _FP, _FP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+    L.ra_mppi_tune.restype = ctypes.c_int
+    L.ra_mppi_get_launch.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.ra_mppi_get_launch.restype = ctypes.c_int
     L.ra_mppi_set_cost_weights.argtypes = [_VP, ctypes.POINTER(ctypes.c_float)]
     L.ra_mppi_set_cost_weights.restype = ctypes.c_int
     L.ra_mppi_backward.argtypes = [_VP, _FP, _FP, _FP, _FP, _VP]
@@ -216,6 +222,22 @@ def ra_mppi_step_host(h, x0_ptr, V_in_ptr, V_out_ptr, S_tilde_ptr=None, stream=0
 def ra_mppi_closed_loop_step(h, x_ptr, V_ptr, S_tilde_ptr=None, collisions_ptr=None, shift=1, stream=0):
     _check(lib().ra_mppi_closed_loop_step(h, x_ptr, V_ptr, S_tilde_ptr, collisions_ptr, int(shift), stream),
            "ra_mppi_closed_loop_step", h)
+
+
+def ra_mppi_set_diagnostics(h, counter_ptr=None):
+    _check(lib().ra_mppi_set_diagnostics(h, counter_ptr), "ra_mppi_set_diagnostics", h)
+
+
+def ra_mppi_tune(h, x0_ptr, V_ptr, replays=3):
+    ms = ctypes.c_float()
+    _check(lib().ra_mppi_tune(h, x0_ptr, V_ptr, int(replays), ctypes.byref(ms)), "ra_mppi_tune", h)
+    return ms.value
+
+
+def ra_mppi_get_launch(h):
+    w, i = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().ra_mppi_get_launch(h, ctypes.byref(w), ctypes.byref(i)), "ra_mppi_get_launch", h)
+    return w.value, i.value
 
 
 def ra_mppi_set_cost_weights(h, theta):

@@ -110,6 +110,13 @@ class RaMppi:
     def set_launch(self, warps_per_block=0, ilp=0):
         B.ra_mppi_set_launch(self.h, warps_per_block, ilp)
 
+    def tune(self, x0, V, replays=3):
+        """Pick the fastest launch shape on these inputs (results unchanged)."""
+        return B.ra_mppi_tune(self.h, x0.contiguous().data_ptr(), V.contiguous().data_ptr(), replays)
+
+    def get_launch(self):
+        return B.ra_mppi_get_launch(self.h)
+
     def set_cost_weights(self, theta):
         """theta = (w_dev, w_speed, gamma, w_obs) for the following updates."""
         B.ra_mppi_set_cost_weights(self.h, [float(v) for v in theta])

@@ -549,6 +549,65 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp) {
   return RA_MPPI_OK;
 }
 
+int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays, float* best_ms) {
+  if (h == nullptr || x0 == nullptr || V == nullptr) return RA_MPPI_EINVAL;
+  if (replays < 1) replays = 3;
+  unsigned long long saved_it = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&saved_it, &h->st->iteration, sizeof(saved_it), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tune");
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tune");
+  const int R = (h->prob.M + 31) / 32;
+  const int old_w = h->warps, old_i = h->ilp;
+  int bw = old_w, bi = old_i;
+  float best = 1e30f;
+  const int warps_c[] = {1, 2, 4, 8};
+  const int ilp_c[] = {1, 2, 4};
+  for (int w : warps_c) {
+    for (int il : ilp_c) {
+      if (R % il != 0) continue;
+      h->warps = w;
+      h->ilp = il;
+      if (prepare(h) != cudaSuccess) continue;
+      if (ra_mppi_step(h, x0, V, h->V_plus, nullptr, nullptr, s) != RA_MPPI_OK) continue;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < replays; ++r) ra_mppi_step(h, x0, V, h->V_plus, nullptr, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= (float)replays;
+      if (ms < best) {
+        best = ms;
+        bw = w;
+        bi = il;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  h->warps = bw;
+  h->ilp = bi;
+  e = prepare(h);
+  if (e == cudaSuccess) e = cudaMemcpy(&h->st->iteration, &saved_it, sizeof(saved_it), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tune");
+  if (best_ms) *best_ms = best;
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_get_launch(ra_mppi_t* h, int32_t* warps_per_block, int32_t* ilp) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  if (warps_per_block) *warps_per_block = h->warps;
+  if (ilp) *ilp = h->ilp;
+  return RA_MPPI_OK;
+}
+
 int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta) {
   if (h == nullptr || theta == nullptr) return RA_MPPI_EINVAL;
   for (int i = 0; i < 4; ++i)
@@ -601,6 +660,12 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, h->nb_prep, nb_dist, smem, h->nb_red,
                                                 static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_set_diagnostics(ra_mppi_t* h, unsigned long long* candidates) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  h->dp.diag = candidates;
   return RA_MPPI_OK;
 }
 

@@ -34,6 +34,7 @@ struct DevParams {
   float track_S, track_R, track_hw;
   float inv_lambda, A, B, C_u;
   uint32_t seed_lo, seed_hi, instance;
+  unsigned long long* diag;  // optional count of obstacle candidates tested (diagnostics)
 };
 
 // Mutable per-handle state in device memory, read at kernel start so that a

@@ -100,7 +100,56 @@ __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& 
   S_out[k] = S;
 }
 
-// risk cost l of ILP states; the obstacle list is read once for all of them
+// Indicator obstacle count of the ILP states of every lane of the warp
+// (called by all 32 lanes together).  The warp first bounds its positions by
+// a box (order-preserving keys, warp min/max) and tests 32 obstacles at a
+// time against the box, the lane per obstacle; only obstacles whose disc can
+// reach the box (with a relative margin far above float32 rounding) get the
+// exact per-state test, in the original obstacle order.  A skipped obstacle
+// cannot contain any state, so the counts equal the full loop's.
+template <int MODEL, int ILP>
+__device__ __forceinline__ void obstacle_hits_culled(const DevParams& p, float (&x)[ILP][Model<MODEL>::NX],
+                                                     float (&hits)[ILP], const float4* __restrict__ obs,
+                                                     int n_obs) {
+  const int lane = threadIdx.x & 31;
+  float xmn = x[0][0], xmx = x[0][0], ymn = x[0][1], ymx = x[0][1];
+#pragma unroll
+  for (int i = 1; i < ILP; ++i) {
+    xmn = fminf(xmn, x[i][0]);
+    xmx = fmaxf(xmx, x[i][0]);
+    ymn = fminf(ymn, x[i][1]);
+    ymx = fmaxf(ymx, x[i][1]);
+  }
+  xmn = fkey_inv(__reduce_min_sync(0xFFFFFFFFu, fkey(xmn)));
+  xmx = fkey_inv(__reduce_max_sync(0xFFFFFFFFu, fkey(xmx)));
+  ymn = fkey_inv(__reduce_min_sync(0xFFFFFFFFu, fkey(ymn)));
+  ymx = fkey_inv(__reduce_max_sync(0xFFFFFFFFu, fkey(ymx)));
+  for (int base = 0; base < n_obs; base += 32) {
+    const int o = base + lane;
+    bool cand = false;
+    if (o < n_obs) {
+      const float4 ob = obs[o];
+      // distance from the centre to the box; a NaN bound acts as unbounded
+      const float dx = fmaxf(fmaxf(xmn - ob.x, ob.x - xmx), 0.0f);
+      const float dy = fmaxf(fmaxf(ymn - ob.y, ob.y - ymx), 0.0f);
+      cand = fmaf(dx, dx, dy * dy) <= fmaf(ob.w, 1.0001f, 1e-12f);
+    }
+    unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+    if (p.diag != nullptr && lane == 0 && m != 0u) atomicAdd(p.diag, (unsigned long long)__popc(m));
+    while (m != 0u) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1u;
+      const float4 ob = obs[base + j];
+#pragma unroll
+      for (int i = 0; i < ILP; ++i) {
+        const float dx = x[i][0] - ob.x, dy = x[i][1] - ob.y;
+        hits[i] += (fmaf(dx, dx, dy * dy) < ob.w) ? 1.0f : 0.0f;
+      }
+    }
+  }
+}
+
+// risk cost l of ILP states of every lane (warp-collective for the indicator term)
 template <int MODEL, int ILP>
 __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP][Model<MODEL>::NX],
                                               float (&L)[ILP], const float4* __restrict__ obs,
@@ -110,14 +159,7 @@ __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP
     float hits[ILP];
 #pragma unroll
     for (int i = 0; i < ILP; ++i) hits[i] = 0.0f;
-    for (int o = 0; o < n_obs; ++o) {
-      const float4 ob = obs[o];
-#pragma unroll
-      for (int i = 0; i < ILP; ++i) {
-        const float dx = x[i][0] - ob.x, dy = x[i][1] - ob.y;
-        hits[i] += (fmaf(dx, dx, dy * dy) < ob.w) ? 1.0f : 0.0f;
-      }
-    }
+    obstacle_hits_culled<MODEL, ILP>(p, x, hits, obs, n_obs);
 #pragma unroll
     for (int i = 0; i < ILP; ++i) {
       L[i] = fmaf(p.w_obs, hits[i], L[i]);

@@ -265,3 +265,29 @@ def test_handles_with_different_shared_memory_coexist():
     assert a.status() == 0 and b.status() == 0
     a.close()
     b.close()
+
+
+def test_tuner_keeps_results_and_culling_counts_tests():
+    from paper_2209_12842_gb300 import RaMppi
+    from paper_2209_12842_gb300 import binding as B
+
+    p = rs.preset("small_dyn", K=300, M=64)
+    obs, x0, V = _inputs(p, "track")
+    base = run_gpu(p, obs, x0, V, keep_L=False, iteration=2)
+    ctl = RaMppi(p, obs)
+    xt, Vt = torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda()
+    ms = ctl.tune(xt, Vt, 2)
+    assert ms > 0
+    ctl.iteration = 2
+    cand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    B.ra_mppi_set_diagnostics(ctl.h, cand.data_ptr())
+    Vp = ctl.step(xt, Vt)
+    torch.cuda.synchronize()
+    B.ra_mppi_set_diagnostics(ctl.h, None)
+    np.testing.assert_array_equal(Vp.cpu().numpy(), base["V_plus"])
+    np.testing.assert_array_equal(ctl.cvar.cpu().numpy(), base["cvar"])
+    warps, ilp = ctl.get_launch()
+    passes = -(-((p["M"] + 31) // 32) // ilp)
+    per_step = cand.item() / (p["K"] * passes * p["T"])
+    assert 0 < per_step <= len(obs)
+    ctl.close()
