@@ -196,6 +196,8 @@ def config_dict(p, args):
                         f"{p['n_obs']} obstacles",
             "K": int(p["K"]), "M": int(p["M"]), "T": int(p["T"]), "model": int(p["model"]),
             "substeps": int(p["substeps"]), "n_obs": int(p["n_obs"]), "alpha": float(p["alpha"]),
+            "step": f"one receding-horizon iteration (update, plant step, warm start) after a "
+                    f"{args.preroll}-iteration untimed pre-roll from the track origin",
             "l2": "flushed before every timed step (256 MB write, outside the step's events)"}
 
 
@@ -226,10 +228,18 @@ def run_ours(args, p, x0, V, obs):
     kv_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kv_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
-    tune_ms = ctl.tune(x0_d, V_d, 3)  # launch-shape autotuner (results do not depend on it)
+    # The timed step is one receding-horizon iteration of Algorithm 1 (update,
+    # execute v0+ on the simulated plant, warm start), from the state the loop
+    # reaches after an untimed pre-roll, so the rollouts meet the obstacles.
+    x_d = x0_d.clone()
+    hits = torch.zeros(1, dtype=torch.int32, device=dev)
+    for i in range(args.preroll):
+        ctl.closed_loop_step(x_d, V_d, hits)
+    torch.cuda.synchronize()
+    tune_ms = ctl.tune(x_d, V_d, 3)  # launch-shape autotuner (results do not depend on it)
     warps, ilp = ctl.get_launch()
     for i in range(args.warmup):
-        ctl.step(x0_d, V_d, V_out)
+        ctl.closed_loop_step(x_d, V_d, hits)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -244,7 +254,7 @@ def run_ours(args, p, x0, V, obs):
         flush.fill_(float(i))
         ctl.set_timing_events(kv_b[i], kv_e[i])
         ev_b[i].record(stream)
-        ctl.step(x0_d, V_d, V_out)
+        ctl.closed_loop_step(x_d, V_d, hits)
         ev_e[i].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -256,7 +266,7 @@ def run_ours(args, p, x0, V, obs):
     # obstacles tested exactly per rollout-step (one extra, untimed update)
     cand = torch.zeros(1, dtype=torch.int64, device=dev)
     B.ra_mppi_set_diagnostics(ctl.h, cand.data_ptr())
-    ctl.step(x0_d, V_d, V_out)
+    ctl.step(x_d, V_d, V_out)
     torch.cuda.synchronize()
     B.ra_mppi_set_diagnostics(ctl.h, None)
     passes = -(-((int(p["M"]) + 31) // 32) // ilp)
@@ -271,7 +281,7 @@ def run_ours(args, p, x0, V, obs):
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     nx = x0.size
-    x0_h = torch.from_numpy(x0).pin_memory()
+    x0_h = x_d.cpu().pin_memory()
     V_h = torch.from_numpy(V).pin_memory()
     Vo_h = torch.empty_like(V_h).pin_memory()
     for i in range(2):
@@ -304,7 +314,7 @@ def run_ours(args, p, x0, V, obs):
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "rollout_kernel_mean": 1e3 * k_mean},
             "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "launch": {"warps_per_block": warps, "rollouts_interleaved": ilp, "tune_ms": tune_ms},
             "status": B.STATUS_NAMES.get(status, status),
             "clocks": clk,
@@ -482,6 +492,76 @@ def adjoint_study(torch, steps):
             "backward_rollout_steps_per_s": units / b50 * 1e3}
 
 
+def stress_sweep(args):
+    """Config 5: dynamic single-track, K = 65536, T = 50, 200 obstacles; M in
+    {32, 64, 128, 256} x alpha in {0.8, 0.95}; update latency p50/p99 over
+    `--steps` updates per point and the rollout kernel's roofline fraction."""
+    import torch
+
+    from paper_2209_12842_gb300 import RaMppi
+    from paper_2209_12842_gb300 import binding as B
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    base = rs.preset("c5_stress")
+    obs = rs.make_obstacles(base["seed"], base["n_obs"], *base["obs_r"])
+    x0 = torch.from_numpy(rs.initial_state(base["model"])).cuda()
+    V = torch.from_numpy(rs.random_controls(base["model"], base["T"], base["u_lo"], base["u_hi"], 3)).cuda()
+    clocks = ClockSampler(0)
+    clocks.start()
+    points = []
+    for M in (32, 64, 128, 256):
+        for alpha in (0.8, 0.95):
+            p = rs.preset("c5_stress", M=M, alpha=alpha)
+            ctl = RaMppi(p, obs)
+            Vo = torch.empty_like(V)
+            ctl.tune(x0, V, 2)
+            warps, ilp = ctl.get_launch()
+            kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            sb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            se = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            for _ in range(args.warmup):
+                ctl.step(x0, V, Vo)
+            torch.cuda.synchronize()
+            for i in range(args.steps):
+                ctl.set_timing_events(kb[i], ke[i])
+                sb[i].record(stream)
+                ctl.step(x0, V, Vo)
+                se[i].record(stream)
+            torch.cuda.synchronize()
+            ctl.set_timing_events(None)
+            cand = torch.zeros(1, dtype=torch.int64, device="cuda")
+            B.ra_mppi_set_diagnostics(ctl.h, cand.data_ptr())
+            ctl.step(x0, V, Vo)
+            torch.cuda.synchronize()
+            B.ra_mppi_set_diagnostics(ctl.h, None)
+            passes = -(-((M + 31) // 32) // ilp)
+            tested = float(cand.item()) / (p["K"] * passes * p["T"])
+            step_ms = np.array([a.elapsed_time(b) for a, b in zip(sb, se)])
+            k_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(kb, ke)]))
+            d_ops, n_ops = algorithmic_ops(p, tested)
+            ops = p["K"] * M * p["T"] * d_ops + p["K"] * p["T"] * n_ops
+            points.append({"M": M, "alpha": alpha, "p50_ms": float(np.percentile(step_ms, 50)),
+                           "p99_ms": float(np.percentile(step_ms, 99)), "rollout_kernel_ms": k_ms,
+                           "rollout_steps_per_s": p["K"] * M * p["T"] / (float(np.median(step_ms)) / 1e3),
+                           "obstacles_tested_per_rollout_step": tested, "ops_per_launch": ops,
+                           "achieved_gops": ops / (k_ms / 1e3) / 1e9, "launch": [warps, ilp]})
+            ctl.close()
+    clk = clocks.stop()
+    peak = N_SMS * LANES_PER_SM * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e9
+    for pt in points:
+        pt["roofline_frac"] = pt["achieved_gops"] / peak
+    top = [pt for pt in points if pt["M"] == 256 and pt["alpha"] == 0.95][0]
+    line = {"metric": "rollout-steps/s (K*M*T)", "value": top["rollout_steps_per_s"], "unit": "rollout-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": top["p50_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c5 stress: dynamic single-track, K=65536, T=50, 200 obstacles, sweep of M and alpha",
+                       "l2": "inputs resident; per-update working set below L2 (compute bound)"},
+            "clocks": clk, "roofline_peak_gops": peak, "sweep": points}
+    print(json.dumps(line), flush=True)
+
+
 def load_traffic(workload):
     """DRAM bytes per rollout-kernel launch from the committed ncu summary, or
     None when none exists or it was taken on a different kernel version."""
@@ -507,9 +587,15 @@ def main():
     ap.add_argument("--no-studies", action="store_true",
                     help="skip the closed-loop, batched and adjoint sections of the line")
     ap.add_argument("--loop-updates", type=int, default=1000)
+    ap.add_argument("--preroll", type=int, default=200,
+                    help="untimed receding-horizon iterations before timing (the state leaves the start area)")
+    ap.add_argument("--sweep", action="store_true", help="config 5 stress sweep over M and alpha")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.sweep:
+        stress_sweep(args)
+        return
     p = rs.preset(WORKLOADS[args.workload])
     obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
     x0 = rs.initial_state(p["model"])

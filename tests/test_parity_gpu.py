@@ -272,7 +272,7 @@ def test_tuner_keeps_results_and_culling_counts_tests():
     from paper_2209_12842_gb300 import binding as B
 
     p = rs.preset("small_dyn", K=300, M=64)
-    obs, x0, V = _inputs(p, "track")
+    obs, x0, V = _inputs(p, "ahead")
     base = run_gpu(p, obs, x0, V, keep_L=False, iteration=2)
     ctl = RaMppi(p, obs)
     xt, Vt = torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda()
