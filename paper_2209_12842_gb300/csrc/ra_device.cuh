@@ -105,6 +105,28 @@ __device__ __forceinline__ void heading_sincos(float a, float* s, float* c) {
   __sincosf(r, s, c);
 }
 
+// arctangent for the slip angles: z P(z^2) on [0, 1] with P of degree 7 in
+// z^2 (coefficients fitted here by iterated weighted least squares on
+// Chebyshev nodes for the relative error; max 2.5e-7 in float32), reflected
+// as pi/2 - atan(1/|z|) above 1, odd in z.
+__device__ __forceinline__ float atan_poly(float z) {
+  const float a = fabsf(z);
+  const bool big = a > 1.0f;
+  const float t = big ? 1.0f / a : a;
+  const float s = t * t;
+  float q = -4.693589173e-03f;
+  q = fmaf(q, s, 2.425358072e-02f);
+  q = fmaf(q, s, -5.948816240e-02f);
+  q = fmaf(q, s, 9.914427996e-02f);
+  q = fmaf(q, s, -1.401953697e-01f);
+  q = fmaf(q, s, 1.996973604e-01f);
+  q = fmaf(q, s, -3.333199322e-01f);
+  q = fmaf(q, s, 9.999998808e-01f);
+  float r = t * q;
+  r = big ? 1.57079632679489662f - r : r;
+  return copysignf(r, z);
+}
+
 // ---------------------------------------------------------------- models
 // Per-step control quantities shared by all rollouts of a sample:
 //   KIN  (steer, accel, tan(steer) / wheelbase, 0)
@@ -147,11 +169,12 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
   }
   // sin(C atan(z)) of the Pacejka lateral force.  For C = 3/2 it has the
   // closed form z (q + 2) / (q sqrt(2 q (q + 1))), q = sqrt(1 + z^2)
-  // (half-angle identities with cos(atan z) = 1/q; no cancellation near 0).
+  // (half-angle identities with cos(atan z) = 1/q; no cancellation near 0),
+  // evaluated as z (q + 2) rsqrt(2 q^3 (q + 1)).
   __device__ static __forceinline__ float pacejka_shape(const DevParams& p, float z) {
     if (p.pacejka_c15) {
       const float q = sqrtf(fmaf(z, z, 1.0f));
-      return z * (q + 2.0f) / (q * sqrtf(2.0f * q * (q + 1.0f)));
+      return z * (q + 2.0f) * rsqrtf(2.0f * q * q * q * (q + 1.0f));
     }
     return sinf(p.mp[5] * atanf(z));
   }
@@ -161,8 +184,8 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     const float vx = x[3], vy = x[4], r = x[5];
     // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx)
     const float inv_vx = 1.0f / fmaxf(vx, vfloor);
-    const float af = c.x - atanf(fmaf(lf, r, vy) * inv_vx);
-    const float ar = -atanf(fmaf(-lr, r, vy) * inv_vx);
+    const float af = c.x - atan_poly(fmaf(lf, r, vy) * inv_vx);
+    const float ar = -atan_poly(fmaf(-lr, r, vy) * inv_vx);
     const float fyf = p.dfz_f * pacejka_shape(p, Bt * af);
     const float fyr = p.dfz_r * pacejka_shape(p, Bt * ar);
     float sp, cp;

@@ -1,0 +1,63 @@
+"""The kernels' own device math against CUDA's functions and float64 (GPU).
+
+atan_poly (the slip-angle arctangent) must stay within 3e-7 relative of the
+true arctangent and within 4 float32 ulp of CUDA's atanf; the closed form of
+sin(1.5 atan z) used by the Pacejka force must agree with CUDA's
+sinf(1.5f * atanf(z)) and with float64 to 1e-6 relative.
+"""
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    out = str(tmp_path_factory.mktemp("probe") / "libprobe.so")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared",
+                    "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "paper_2209_12842_gb300", "csrc"),
+                    os.path.join(HERE, "cuda", "device_math_probe.cu"), "-o", out], check=True)
+    lib = ctypes.CDLL(out)
+    lib.device_math_probe.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    return lib
+
+
+def _run(lib, z):
+    zt = torch.from_numpy(z.astype(np.float32)).cuda()
+    out = torch.empty((z.size, 4), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    assert lib.device_math_probe(zt.data_ptr(), z.size, out.data_ptr()) == 0
+    return out.cpu().numpy().astype(np.float64)
+
+
+def test_atan_poly(probe):
+    z = np.concatenate([np.linspace(-4, 4, 400001), np.logspace(-30, 30, 20001), -np.logspace(-30, 30, 20001),
+                        [0.0, 1.0, -1.0, np.inf, -np.inf]]).astype(np.float32)
+    r = _run(probe, z)
+    exact = np.arctan(z.astype(np.float64))
+    nz = exact != 0
+    rel = np.abs(r[nz, 0] - exact[nz]) / np.abs(exact[nz])
+    assert rel.max() < 3e-7, rel.max()
+    ulp = np.spacing(np.abs(r[:, 1]).astype(np.float32)).astype(np.float64)
+    assert np.max(np.abs(r[:, 0] - r[:, 1]) / np.maximum(ulp, 1e-45)) <= 4
+    assert np.isnan(_run(probe, np.array([np.nan]))[0, 0])
+
+
+def test_pacejka_closed_form(probe):
+    z = np.concatenate([np.linspace(-40, 40, 200001), np.logspace(-20, 3, 10001)]).astype(np.float32)
+    r = _run(probe, z)
+    exact = np.sin(1.5 * np.arctan(z.astype(np.float64)))
+    nz = np.abs(exact) > 1e-30
+    assert np.max(np.abs(r[nz, 2] - exact[nz]) / np.abs(exact[nz])) < 1e-6
+    assert np.max(np.abs(r[nz, 2] - r[nz, 3]) / np.abs(exact[nz])) < 2e-6
