@@ -34,6 +34,7 @@ WORKLOADS = {
     "c1": "c1_plain",
     "c5": "c5_stress",
     "c4": "c4_gradient",
+    "paper": "paper_sim",
 }
 N_SMS = 152
 LANES_PER_SM = 128
@@ -237,7 +238,7 @@ def run_ours(args, p, x0, V, obs):
         ctl.closed_loop_step(x_d, V_d, hits)
     torch.cuda.synchronize()
     tune_ms = ctl.tune(x_d, V_d, 3)  # launch-shape autotuner (results do not depend on it)
-    warps, ilp = ctl.get_launch()
+    warps, ilp, wps = ctl.get_launch()
     for i in range(args.warmup):
         ctl.closed_loop_step(x_d, V_d, hits)
     torch.cuda.synchronize()
@@ -269,8 +270,7 @@ def run_ours(args, p, x0, V, obs):
     ctl.step(x_d, V_d, V_out)
     torch.cuda.synchronize()
     B.ra_mppi_set_diagnostics(ctl.h, None)
-    passes = -(-((int(p["M"]) + 31) // 32) // ilp)
-    tested = float(cand.item()) / (int(p["K"]) * passes * int(p["T"]))
+    tested = float(cand.item()) / (int(p["K"]) * ((int(p["M"]) + 31) // 32) * int(p["T"]))
 
     step_ms = np.array([b.elapsed_time(e) for b, e in zip(ev_b, ev_e)])
     kern_ms = np.array([b.elapsed_time(e) for b, e in zip(kv_b, kv_e)])
@@ -315,7 +315,8 @@ def run_ours(args, p, x0, V, obs):
                            "rollout_kernel_mean": 1e3 * k_mean},
             "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
             "gpu_launches": 3 * args.steps,
-            "launch": {"warps_per_block": warps, "rollouts_interleaved": ilp, "tune_ms": tune_ms},
+            "launch": {"warps_per_block": warps, "rollouts_interleaved": ilp, "warps_per_sample": wps,
+                       "tune_ms": tune_ms},
             "status": B.STATUS_NAMES.get(status, status),
             "clocks": clk,
             "e2e": {"value": world * units / e2e_t, "unit": "rollout-steps/s",
@@ -516,7 +517,7 @@ def stress_sweep(args):
             ctl = RaMppi(p, obs)
             Vo = torch.empty_like(V)
             ctl.tune(x0, V, 2)
-            warps, ilp = ctl.get_launch()
+            warps, ilp, wps = ctl.get_launch()
             kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
             ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
             sb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -536,8 +537,7 @@ def stress_sweep(args):
             ctl.step(x0, V, Vo)
             torch.cuda.synchronize()
             B.ra_mppi_set_diagnostics(ctl.h, None)
-            passes = -(-((M + 31) // 32) // ilp)
-            tested = float(cand.item()) / (p["K"] * passes * p["T"])
+            tested = float(cand.item()) / (p["K"] * ((M + 31) // 32) * p["T"])
             step_ms = np.array([a.elapsed_time(b) for a, b in zip(sb, se)])
             k_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(kb, ke)]))
             d_ops, n_ops = algorithmic_ops(p, tested)
@@ -546,7 +546,7 @@ def stress_sweep(args):
                            "p99_ms": float(np.percentile(step_ms, 99)), "rollout_kernel_ms": k_ms,
                            "rollout_steps_per_s": p["K"] * M * p["T"] / (float(np.median(step_ms)) / 1e3),
                            "obstacles_tested_per_rollout_step": tested, "ops_per_launch": ops,
-                           "achieved_gops": ops / (k_ms / 1e3) / 1e9, "launch": [warps, ilp]})
+                           "achieved_gops": ops / (k_ms / 1e3) / 1e9, "launch": [warps, ilp, wps]})
             ctl.close()
     clk = clocks.stop()
     peak = N_SMS * LANES_PER_SM * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e9
@@ -597,8 +597,8 @@ def main():
         stress_sweep(args)
         return
     p = rs.preset(WORKLOADS[args.workload])
-    obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
-    x0 = rs.initial_state(p["model"])
+    obs = rs.scene_obstacles(p)
+    x0 = rs.scene_initial_state(p)
     V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 3)
     if args.impl == "reference":
         run_reference(args, p, x0, V, obs)

@@ -77,20 +77,30 @@ enum { RA_MPPI_KIN_BICYCLE = 0, RA_MPPI_DYN_SINGLE_TRACK = 1, RA_MPPI_LINEAR_TES
  * after each control period.  Slots: KIN (px, py, psi, v); DYN (vx, vy, r);
  * LINEAR (x).  GAUSS: w_s ~ N(0, w_scale[s]^2).  LAPLACE_MIX: w_s ~
  * Laplace(0, w_scale[s]), replaced with probability mix_p by
- * N(0, (mix_scale w_scale[s])^2). */
-enum { RA_MPPI_NOISE_GAUSS = 0, RA_MPPI_NOISE_LAPLACE_MIX = 1 };
+ * N(0, (mix_scale w_scale[s])^2).  UNIFORM: w_s ~ U[-w_scale[s], w_scale[s]]
+ * (the paper's uniform disturbance, Sec. V-B).  IMPULSE: with probability
+ * mix_p a jump of size w_scale[s] per slot along a direction uniform on the
+ * unit sphere of the slots with w_scale != 0, else none (the paper's
+ * impulse disturbance, Sec. V-B). */
+enum { RA_MPPI_NOISE_GAUSS = 0, RA_MPPI_NOISE_LAPLACE_MIX = 1, RA_MPPI_NOISE_UNIFORM = 2, RA_MPPI_NOISE_IMPULSE = 3 };
 
 /* Obstacle term of q and l: the indicator 1{d_i < r_i} of Eq. 22, or a
  * smooth barrier softplus(kappa (r_i - d_i)) / kappa. */
 enum { RA_MPPI_OBS_INDICATOR = 0, RA_MPPI_OBS_SOFTPLUS = 1 };
 
-/* CVaR estimator over the M risk costs (Eqs. 10-13):
- *   RU   fractional sorted tail [(j - alpha M) L_(j) + sum_{i>j} L_(i)] /
- *        ((1 - alpha) M), j = ceil(alpha M)  (equals the Rockafellar-Uryasev
- *        minimum; continuous in L and insensitive to ties)
- *   TCE  the literal Monte-Carlo form of Eqs. 12-13: mean of {L >= VaR},
- *        VaR = L_(j) (Eq. 11). */
-enum { RA_MPPI_CVAR_RU = 0, RA_MPPI_CVAR_TCE = 1 };
+/* Risk measure of the M risk costs (field cvar_mode), after the
+ * sensitivity scaling (Eqs. 18, 19):
+ *   RU     CVaR as the fractional sorted tail [(j - alpha M) L_(j) +
+ *          sum_{i>j} L_(i)] / ((1 - alpha) M), j = ceil(alpha M) (equals the
+ *          Rockafellar-Uryasev minimum; continuous in L, tie-insensitive)
+ *   TCE    CVaR in the literal Monte-Carlo form of Eqs. 12-13: mean of
+ *          {L >= VaR}, VaR = L_(j) (Eq. 11)
+ *   VAR    VaR_alpha = L_(j) itself (Eq. 11)
+ *   CHANCE fraction of the M costs above risk_threshold (a chance constraint
+ *          in place of CVaR; the paper names the block swappable, Sec. III-A)
+ *   MEAN   the mean risk cost (risk neutral) */
+enum { RA_MPPI_CVAR_RU = 0, RA_MPPI_CVAR_TCE = 1, RA_MPPI_RISK_VAR = 2, RA_MPPI_RISK_CHANCE = 3,
+       RA_MPPI_RISK_MEAN = 4 };
 
 /* Bits of risk_mask: the running-cost terms that form the risk cost l
  * (Eq. 9).  The paper's experiments use l = q (all terms). */
@@ -108,7 +118,7 @@ enum {
   RA_MPPI_DIFFERENTIABLE = 2   /* keep what ra_mppi_backward needs (x0, V of each update) */
 };
 
-#define RA_MPPI_MAX_M 256
+#define RA_MPPI_MAX_M 512
 #define RA_MPPI_MAX_T 256
 #define RA_MPPI_MAX_OBSTACLES 1024
 
@@ -139,6 +149,7 @@ typedef struct ra_mppi_problem {
   float B;            /* risk sensitivity scale, >= 0 (Eq. 18)                */
   float C_u;          /* CVaR bound (Eq. 15)                                  */
   float eta;          /* zero-mean sample fraction in [0, 1) (Alg. 1)         */
+  float risk_threshold;  /* level of RA_MPPI_RISK_CHANCE                        */
   int32_t max_obstacles; /* capacity of the obstacle list, 0 .. RA_MPPI_MAX_OBSTACLES */
   uint32_t instance_id;  /* fourth Philox counter word                        */
   uint64_t seed;         /* Philox key                                        */
@@ -226,7 +237,7 @@ const char* ra_mppi_last_error(const ra_mppi_t* h);
  * fastest and restores the update counter, so later results are unchanged
  * (they never depend on the shape).  Synchronous. */
 int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays, float* best_ms);
-int ra_mppi_get_launch(ra_mppi_t* h, int32_t* warps_per_block, int32_t* ilp);
+int ra_mppi_get_launch(ra_mppi_t* h, int32_t* warps_per_block, int32_t* ilp, int32_t* warps_per_sample);
 
 /* Cost weights theta = (w_dev, w_speed, gamma, w_obs) used by the following
  * updates (host-side, no device work).  EINVAL if any is not finite. */
@@ -250,14 +261,17 @@ int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta);
 int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, float* gV, float* gtheta,
                      void* stream);
 
-/* Kernel launch tuning: disturbed-rollout warps per block (1..8) and
- * rollouts each lane interleaves (1, 2 or 4); 0 keeps the default. */
-int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp);
+/* Kernel launch tuning: disturbed-rollout warps per block (1..8), rollouts
+ * each lane interleaves (1, 2 or 4) and warps sharing one sample's M
+ * rollouts (1..8, dividing warps_per_block); 0 keeps the current value.
+ * Results never depend on the shape. */
+int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32_t warps_per_sample);
 
 /* Diagnostics: when `candidates` (device uint64) is set, the disturbed
- * rollouts add to it the number of obstacles each warp tested exactly after
- * its bounding-box cull, summed over steps (the work actually done by the
- * indicator term).  NULL turns it off. */
+ * rollouts add to it, per step and per row of 32 rollouts, the number of
+ * obstacles tested exactly after the warp's bounding-box cull (the work the
+ * indicator term actually does; divided by K ceil(M/32) T it is the mean
+ * per rollout-step).  NULL turns it off. */
 int ra_mppi_set_diagnostics(ra_mppi_t* h, unsigned long long* candidates);
 
 /* Timing hook: when set, ra_mppi_step records the caller's CUDA events

@@ -57,7 +57,7 @@ class Problem(ctypes.Structure):
         ("track_half_width", ctypes.c_double),
         ("lam", ctypes.c_double), ("alpha", ctypes.c_double), ("A", ctypes.c_double),
         ("B", ctypes.c_double), ("C_u", ctypes.c_double), ("eta", ctypes.c_double),
-        ("band_delta", ctypes.c_double),
+        ("band_delta", ctypes.c_double), ("risk_threshold", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("iteration", ctypes.c_uint64),
         ("instance_id", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
     ]
@@ -89,6 +89,9 @@ def lib():
         L.orc_track.argtypes = [_P, ctypes.c_double, ctypes.c_double, _D]
         L.orc_cvar.argtypes = [_D, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32]
         L.orc_cvar.restype = ctypes.c_double
+        L.orc_risk.argtypes = [_D, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                               ctypes.c_double]
+        L.orc_risk.restype = ctypes.c_double
         L.orc_samples.argtypes = [_P, _D, _D, _D, ctypes.c_int32, _I32, ctypes.c_int32] + [_D] * 11
         L.orc_samples.restype = ctypes.c_int32
         L.orc_update.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -144,7 +147,7 @@ def make_problem(p, iteration=0, band_delta=1e-4, n_threads=1, exact=False):
         pr.w_scale[i] = _f32(p["w_scale"][i])
     for name in ("mix_p", "mix_scale", "w_dev", "w_speed", "v_target", "gamma", "w_obs",
                  "w_bdry", "c4", "c5", "c_lin", "kappa", "track_straight", "track_radius",
-                 "track_half_width", "lam", "alpha", "A", "B", "C_u", "eta"):
+                 "track_half_width", "lam", "alpha", "A", "B", "C_u", "eta", "risk_threshold"):
         setattr(pr, name, _f32(p[name]))
     pr.band_delta = float(band_delta)
     pr.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
@@ -226,6 +229,12 @@ def terminal_cost(prob, x):
 def cvar(L, alpha, B=1.0, mode=0):
     L = _arr(L)
     return lib().orc_cvar(_ptr(L), int(L.size), float(alpha), float(B), int(mode))
+
+
+def risk(L, alpha, B=1.0, mode=0, threshold=0.0):
+    """Risk measure of a set of risk costs (CVaR forms, VaR, chance, mean)."""
+    L = _arr(L)
+    return lib().orc_risk(_ptr(L), int(L.size), float(alpha), float(B), int(mode), float(threshold))
 
 
 def n_warm(prob):

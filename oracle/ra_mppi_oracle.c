@@ -54,9 +54,9 @@
 #define ORC_PI 3.14159265358979323846
 
 enum { ORC_KIN = 0, ORC_DYN = 1, ORC_LIN = 2 };
-enum { ORC_GAUSS = 0, ORC_LAPLACE_MIX = 1 };
+enum { ORC_GAUSS = 0, ORC_LAPLACE_MIX = 1, ORC_UNIFORM = 2, ORC_IMPULSE = 3 };
 enum { ORC_OBS_INDICATOR = 0, ORC_OBS_SOFTPLUS = 1 };
-enum { ORC_CVAR_RU = 0, ORC_CVAR_TCE = 1 };
+enum { ORC_CVAR_RU = 0, ORC_CVAR_TCE = 1, ORC_VAR = 2, ORC_CHANCE = 3, ORC_MEAN = 4 };
 enum { ORC_R_DEV = 1, ORC_R_SPEED = 2, ORC_R_OBS = 4, ORC_R_BDRY = 8, ORC_R_LIN = 16 };
 
 typedef struct {
@@ -74,6 +74,7 @@ typedef struct {
   double track_straight, track_radius, track_half_width;
   double lam, alpha, A, B, C_u, eta;
   double band_delta;
+  double risk_threshold;
   uint64_t seed;
   uint64_t iteration;
   uint32_t instance_id;
@@ -193,13 +194,36 @@ static void process_noise_at(const orc_problem* p, uint64_t iteration, uint32_t 
     orc_box_muller(w[0], w[1], z);
     orc_box_muller(w[2], w[3], z + 2);
     for (int s = 0; s < ns; ++s) out[s] = p->w_scale[s] * z[s];
-  } else {
+  } else if (p->noise_type == ORC_LAPLACE_MIX) {
     uint32_t sel[4], val[4];
     noise_words(p, iteration, c1, c2, t, 0, sel);
     noise_words(p, iteration, c1, c2, t, 1, val);
     for (int s = 0; s < ns; ++s)
       out[s] = (p->w_scale[s] == 0.0) ? 0.0
                                       : orc_mix_value(sel[s], val[s], p->w_scale[s], p->mix_p, p->mix_scale);
+  } else if (p->noise_type == ORC_UNIFORM) {
+    /* w_s ~ U[-a_s, a_s] (the paper's uniform disturbance, Sec. V-B) */
+    uint32_t w[4];
+    noise_words(p, iteration, c1, c2, t, 0, w);
+    for (int s = 0; s < ns; ++s) out[s] = (2.0 * orc_uniform(w[s]) - 1.0) * p->w_scale[s];
+  } else {
+    /* impulse (Sec. V-B): with probability p a jump of per-slot size a_s
+     * along a direction uniform on the unit sphere of the slots with
+     * a_s != 0 (a normalised Gaussian vector), otherwise no disturbance */
+    uint32_t a[4], b[4];
+    noise_words(p, iteration, c1, c2, t, 0, a);
+    noise_words(p, iteration, c1, c2, t, 1, b);
+    double thr = floor(p->mix_p * 4294967296.0 > 4294967295.0 ? 4294967295.0 : p->mix_p * 4294967296.0);
+    if ((double)a[0] < thr) {
+      double z[4];
+      orc_box_muller(a[1], a[2], z);
+      orc_box_muller(a[3], b[0], z + 2);
+      double n2 = 0.0;
+      for (int s = 0; s < ns; ++s)
+        if (p->w_scale[s] != 0.0) n2 += z[s] * z[s];
+      double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+      for (int s = 0; s < ns; ++s) out[s] = p->w_scale[s] != 0.0 ? p->w_scale[s] * z[s] * inv : 0.0;
+    }
   }
 }
 
@@ -355,7 +379,17 @@ static int cmp_double(const void* a, const void* b) {
   return (x > y) - (x < y);
 }
 
+/* risk measure of M risk costs after the sensitivity scaling (Eqs. 18, 19):
+ * RU / TCE the two CVaR forms (Eqs. 10-13), VAR the quantile L_(j)
+ * (Eq. 11), CHANCE the fraction of scaled costs above `thr` (a chance
+ * constraint in place of CVaR, Sec. III-A), MEAN the risk-neutral mean */
+double orc_risk(const double* L, int32_t M, double alpha, double B, int32_t mode, double thr);
+
 double orc_cvar(const double* L, int32_t M, double alpha, double B, int32_t mode) {
+  return orc_risk(L, M, alpha, B, mode, 0.0);
+}
+
+double orc_risk(const double* L, int32_t M, double alpha, double B, int32_t mode, double thr) {
   /* a non-finite risk cost (NaN or inf) ranks as the worst outcome: the
    * sample's CVaR is +inf, so it receives zero weight in the update */
   for (int n = 0; n < M; ++n)
@@ -372,7 +406,16 @@ double orc_cvar(const double* L, int32_t M, double alpha, double B, int32_t mode
   if (j > M) j = M;
   double var = La[j - 1];
   double out;
-  if (mode == ORC_CVAR_RU) {
+  if (mode == ORC_VAR) {
+    out = var;
+  } else if (mode == ORC_CHANCE || mode == ORC_MEAN) {
+    double acc = 0.0;
+    for (int n = 0; n < M; ++n) {
+      double v = (B == 1.0) ? L[n] : B * (L[n] - mean) + mean; /* Eq. 18 with B = 1 is the identity */
+      acc += (mode == ORC_CHANCE) ? (v > thr ? 1.0 : 0.0) : v;
+    }
+    out = acc / (double)M;
+  } else if (mode == ORC_CVAR_RU) {
     double tail = ((double)j - aM) * var;
     for (int i = j; i < M; ++i) tail += La[i];
     out = tail / ((1.0 - alpha) * (double)M);
@@ -459,9 +502,9 @@ int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, con
       }
       Lm[m] = Lv; Lm[M + m] = Llo; Lm[2 * M + m] = Lhi;
     }
-    double cv = orc_cvar(Lm, M, p->alpha, p->B, p->cvar_mode);
-    double cv_lo = orc_cvar(Lm + M, M, p->alpha, p->B, p->cvar_mode);
-    double cv_hi = orc_cvar(Lm + 2 * M, M, p->alpha, p->B, p->cvar_mode);
+    double cv = orc_risk(Lm, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
+    double cv_lo = orc_risk(Lm + M, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
+    double cv_hi = orc_risk(Lm + 2 * M, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
     /* CVaR violation cost and modified trajectory cost (Eqs. 14-16) */
     double st = Sk + ((cv > p->C_u) ? p->A * cv : 0.0);
     if (U) memcpy(U + (size_t)i * T * nu, Uk, sizeof(double) * (size_t)T * nu);
@@ -748,7 +791,7 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
       }
       Lm[(size_t)k * M + m] = Lv;
     }
-    cv[k] = orc_cvar(Lm + (size_t)k * M, M, p->alpha, p->B, p->cvar_mode);
+    cv[k] = orc_risk(Lm + (size_t)k * M, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
     St[k] = S[k] + ((cv[k] > p->C_u) ? p->A * cv[k] : 0.0);
   }
   /* update and its weights */
@@ -805,8 +848,15 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
         double wa;
         if (p->cvar_mode == ORC_CVAR_RU)
           wa = La[m] > var ? 1.0 / denom : (La[m] == var ? ((double)(M - c_gt) - aM) / denom / c_eq : 0.0);
-        else
+        else if (p->cvar_mode == ORC_CVAR_TCE)
           wa = La[m] >= var ? 1.0 / (c_gt + c_eq) : 0.0;
+        else if (p->cvar_mode == ORC_VAR)
+          wa = La[m] == var ? 1.0 / c_eq : 0.0;
+        else if (p->cvar_mode == ORC_MEAN)
+          wa = 1.0 / M;
+        else
+          wa = 0.0; /* the chance measure is piecewise constant in L */
+        if (p->cvar_mode == ORC_CHANCE) continue;
         double lbar = cvbar * (p->B * wa + (1.0 - p->B) / M);
         if (lbar != 0.0)
           rollout_vjp(p, Xd + ((size_t)k * M + m) * (T + 1) * nx, Uk, obs, n_obs, p->risk_mask, 0, lbar, gU, gtheta);

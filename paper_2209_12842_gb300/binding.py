@@ -49,6 +49,7 @@ class ra_mppi_problem(ctypes.Structure):
         ("track_radius", ctypes.c_float), ("track_half_width", ctypes.c_float),
         ("lambda_", ctypes.c_float), ("alpha", ctypes.c_float), ("A", ctypes.c_float),
         ("B", ctypes.c_float), ("C_u", ctypes.c_float), ("eta", ctypes.c_float),
+        ("risk_threshold", ctypes.c_float),
         ("max_obstacles", ctypes.c_int32), ("instance_id", ctypes.c_uint32),
         ("seed", ctypes.c_uint64),
     ]
@@ -81,13 +82,13 @@ def _declare(L):
     L.ra_mppi_get_status.argtypes = [_VP]
     L.ra_mppi_last_error.argtypes = [_VP]
     L.ra_mppi_last_error.restype = ctypes.c_char_p
-    L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
+    L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.ra_mppi_set_timing_events.argtypes = [_VP, _VP, _VP]
     L.ra_mppi_set_diagnostics.argtypes = [_VP, _VP]
     L.ra_mppi_set_diagnostics.restype = ctypes.c_int
     L.ra_mppi_tune.argtypes = [_VP, _FP, _FP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     L.ra_mppi_tune.restype = ctypes.c_int
-    L.ra_mppi_get_launch.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.ra_mppi_get_launch.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 3
     L.ra_mppi_get_launch.restype = ctypes.c_int
     L.ra_mppi_set_cost_weights.argtypes = [_VP, ctypes.POINTER(ctypes.c_float)]
     L.ra_mppi_set_cost_weights.restype = ctypes.c_int
@@ -174,7 +175,7 @@ def ra_mppi_problem_from(p, flags=0, max_obstacles=None):
         pr.w_scale[i] = _f(p["w_scale"][i])
     for name in ("mix_p", "mix_scale", "w_dev", "w_speed", "v_target", "gamma", "w_obs", "w_bdry",
                  "c4", "c5", "c_lin", "kappa", "track_straight", "track_radius", "track_half_width",
-                 "alpha", "A", "B", "C_u", "eta"):
+                 "alpha", "A", "B", "C_u", "eta", "risk_threshold"):
         setattr(pr, name, _f(p[name]))
     pr.lambda_ = _f(p["lam"])
     n_obs = int(p.get("n_obs", 0))
@@ -235,9 +236,9 @@ def ra_mppi_tune(h, x0_ptr, V_ptr, replays=3):
 
 
 def ra_mppi_get_launch(h):
-    w, i = ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().ra_mppi_get_launch(h, ctypes.byref(w), ctypes.byref(i)), "ra_mppi_get_launch", h)
-    return w.value, i.value
+    w, i, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().ra_mppi_get_launch(h, ctypes.byref(w), ctypes.byref(i), ctypes.byref(g)), "ra_mppi_get_launch", h)
+    return w.value, i.value, g.value
 
 
 def ra_mppi_set_cost_weights(h, theta):
@@ -279,8 +280,9 @@ def ra_mppi_last_error(h):
     return msg.decode() if msg else ""
 
 
-def ra_mppi_set_launch(h, warps_per_block=0, ilp=0):
-    _check(lib().ra_mppi_set_launch(h, int(warps_per_block), int(ilp)), "ra_mppi_set_launch", h)
+def ra_mppi_set_launch(h, warps_per_block=0, ilp=0, warps_per_sample=0):
+    _check(lib().ra_mppi_set_launch(h, int(warps_per_block), int(ilp), int(warps_per_sample)),
+           "ra_mppi_set_launch", h)
 
 
 def ra_mppi_set_timing_events(h, begin_event_handle=None, end_event_handle=None):

@@ -107,8 +107,8 @@ class RaMppi:
     def status(self):
         return B.ra_mppi_get_status(self.h)
 
-    def set_launch(self, warps_per_block=0, ilp=0):
-        B.ra_mppi_set_launch(self.h, warps_per_block, ilp)
+    def set_launch(self, warps_per_block=0, ilp=0, warps_per_sample=0):
+        B.ra_mppi_set_launch(self.h, warps_per_block, ilp, warps_per_sample)
 
     def tune(self, x0, V, replays=3):
         """Pick the fastest launch shape on these inputs (results unchanged)."""

@@ -311,7 +311,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   for (int i = 0; i < NX; ++i) x0[i] = a.x0[i];
   const int R = (M + 31) >> 5;
   // pass 1: the risk costs (same arithmetic as the forward rollouts)
-  for (int r = 0; r < R; ++r) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r, ctl, Ls, obs_s, n_obs);
+  for (int r = 0; r < R; ++r) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r, 1, ctl, Ls, obs_s, n_obs);
   __syncwarp();
   // CVaR weights: VaR by radix select, then the tail
   constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
@@ -354,16 +354,27 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   }
   c_gt = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)c_gt);
   c_eq = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)c_eq);
-  const float w_gt = p.cvar_mode == 0 ? 1.0f / in.tail_denom : 1.0f / (float)(c_gt + c_eq);
-  const float w_eq = p.cvar_mode == 0 ? ((float)(M - in.j_var - c_gt) + in.frac_j) / in.tail_denom / (float)c_eq
-                                      : 1.0f / (float)(c_gt + c_eq);
-  const float base = (1.0f - p.B) / (float)M;
+  // weights of the risk measure in each scaled cost: above VaR, equal to VaR
+  float w_gt, w_eq, w_all = 0.0f;
+  if (p.cvar_mode == 0) {
+    w_gt = 1.0f / in.tail_denom;
+    w_eq = ((float)(M - in.j_var - c_gt) + in.frac_j) / in.tail_denom / (float)c_eq;
+  } else if (p.cvar_mode == 1) {
+    w_gt = w_eq = 1.0f / (float)(c_gt + c_eq);
+  } else if (p.cvar_mode == 2) {
+    w_gt = 0.0f;
+    w_eq = 1.0f / (float)c_eq;
+  } else {
+    w_gt = w_eq = 0.0f;  // chance: piecewise constant; mean: uniform weights below
+    if (p.cvar_mode == 4) w_all = 1.0f / (float)M;
+  }
+  const float base = p.cvar_mode == 3 ? 0.0f : (1.0f - p.B) / (float)M;
   // pass 2: reverse sweep of every rollout with a nonzero weight
   float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int r = 0; r < R; ++r) {
     const int m = lane + 32 * r;
     const float Lm = val[r];
-    const float wt = m < M ? (Lm > var ? w_gt : (Lm == var ? w_eq : 0.0f)) : 0.0f;
+    const float wt = m < M ? (Lm > var ? w_gt : (Lm == var ? w_eq : 0.0f)) + w_all : 0.0f;
     const float lbar = m < M ? cvbar * fmaf(p.B, wt, base) : 0.0f;
     if (!__any_sync(0xFFFFFFFFu, lbar != 0.0f)) continue;
     float ck[kMaxCk][NX];

@@ -19,7 +19,7 @@ struct ra_mppi {
   DevParams dp;
   int device = 0;
   int nx = 0, nu = 0;
-  int warps = 4, ilp = 1;
+  int warps = 4, ilp = 1, wps = 1;  // warps per block, rollouts interleaved, warps per sample
   int nb_upd = 1;
   int obs_cap = 0;
   size_t smem = 0;
@@ -86,12 +86,13 @@ bool finite_all(const float* v, int n) {
 std::string validate(const ra_mppi_problem& p) {
   if (p.model < 0 || p.model > 2) return "model must be 0 (kinematic), 1 (dynamic) or 2 (linear)";
   if (p.K < 1 || p.K > (1 << 24)) return "K must be in [1, 2^24]";
-  if (p.M < 1 || p.M > RA_MPPI_MAX_M) return "M must be in [1, 256]";
+  if (p.M < 1 || p.M > RA_MPPI_MAX_M) return "M must be in [1, 512]";
   if (p.T < 1 || p.T > RA_MPPI_MAX_T) return "T must be in [1, 256]";
   if (p.substeps < 1 || p.substeps > 64) return "substeps must be in [1, 64]";
-  if (p.noise_type != RA_MPPI_NOISE_GAUSS && p.noise_type != RA_MPPI_NOISE_LAPLACE_MIX) return "unknown noise_type";
+  if (p.noise_type < RA_MPPI_NOISE_GAUSS || p.noise_type > RA_MPPI_NOISE_IMPULSE) return "unknown noise_type";
   if (p.obs_mode != RA_MPPI_OBS_INDICATOR && p.obs_mode != RA_MPPI_OBS_SOFTPLUS) return "unknown obs_mode";
-  if (p.cvar_mode != RA_MPPI_CVAR_RU && p.cvar_mode != RA_MPPI_CVAR_TCE) return "unknown cvar_mode";
+  if (p.cvar_mode < RA_MPPI_CVAR_RU || p.cvar_mode > RA_MPPI_RISK_MEAN) return "unknown risk measure (cvar_mode)";
+  if (std::isnan(p.risk_threshold)) return "risk_threshold must not be NaN";
   if (p.max_obstacles < 0 || p.max_obstacles > RA_MPPI_MAX_OBSTACLES) return "max_obstacles must be in [0, 1024]";
   if (!(p.dt > 0.0f) || !std::isfinite(p.dt)) return "dt must be finite and > 0";
   if (!(p.lambda > 0.0f) || !std::isfinite(p.lambda)) return "lambda must be finite and > 0";
@@ -181,6 +182,7 @@ DevParams make_params(const ra_mppi_problem& p) {
   d.A = p.A;
   d.B = p.B;
   d.C_u = p.C_u;
+  d.risk_threshold = p.risk_threshold;
   d.seed_lo = (uint32_t)(p.seed & 0xFFFFFFFFull);
   d.seed_hi = (uint32_t)(p.seed >> 32);
   d.instance = p.instance_id;
@@ -226,8 +228,8 @@ std::mutex g_smem_mutex;
 size_t g_smem_limit[64][3] = {};  // per device, per model
 
 size_t rollout_smem(const ra_mppi* h) {
-  return (size_t)h->obs_cap * sizeof(float4) + (size_t)h->warps * h->prob.T * sizeof(float4) +
-         (size_t)h->warps * h->prob.M * sizeof(float);
+  const size_t spb = (size_t)(h->warps / h->wps);  // samples per disturbed block
+  return (size_t)h->obs_cap * sizeof(float4) + spb * h->prob.T * sizeof(float4) + spb * h->prob.M * sizeof(float);
 }
 
 cudaError_t prepare(ra_mppi* h) {
@@ -286,6 +288,14 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   h->obs_cap = p->max_obstacles;
   h->ilp = default_ilp(p->M, p->model);
   h->warps = 4;
+  // few samples with many rollouts: spread a sample over several warps so the
+  // grid still fills the GPU (about 32 warps per SM for 152 SMs)
+  {
+    const int R = (p->M + 31) / 32;
+    int g = 1;
+    while (g < 4 && (long long)p->K * g < 152LL * 24 && R >= 2 * g) g *= 2;
+    h->wps = g;
+  }
   cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaGetDevice(&h->device);
   const size_t K = (size_t)p->K, TN = (size_t)p->T * h->nu;
   h->nb_upd = (int)std::min<size_t>((K + ramppi::kUpdateThreads - 1) / ramppi::kUpdateThreads,
@@ -403,7 +413,9 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
   a.L = h->L;
   a.nb_nom = (p.K + 32 * h->warps - 1) / (32 * h->warps);
   a.obs_cap = h->obs_cap;
-  const int nb_dist = (p.K + h->warps - 1) / h->warps;
+  a.wps = h->wps;
+  const int spb = h->warps / h->wps;
+  const int nb_dist = (p.K + spb - 1) / spb;
   cudaError_t e;
   if (h->keep_x0 != nullptr) {
     e = cudaMemcpyAsync(h->keep_x0, x0, sizeof(float) * h->nx, cudaMemcpyDeviceToDevice, s);
@@ -528,26 +540,29 @@ int ra_mppi_get_status(ra_mppi_t* h) {
 
 const char* ra_mppi_last_error(const ra_mppi_t* h) { return h == nullptr ? "null handle" : h->err.c_str(); }
 
-int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp) {
+int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32_t warps_per_sample) {
   if (h == nullptr) return RA_MPPI_EINVAL;
   const int w = warps_per_block == 0 ? h->warps : warps_per_block;
   const int i = ilp == 0 ? h->ilp : ilp;
+  const int g = warps_per_sample == 0 ? h->wps : warps_per_sample;
   if (w < 1 || w > 8) return fail(h, RA_MPPI_EINVAL, "warps_per_block must be in [1, 8]");
   if (i != 1 && i != 2 && i != 4) return fail(h, RA_MPPI_EINVAL, "ilp must be 1, 2 or 4");
-  const int R = (h->prob.M + 31) / 32;
-  if (R % i != 0) return fail(h, RA_MPPI_EINVAL, "ilp must divide ceil(M / 32)");
-  const int old_w = h->warps, old_i = h->ilp;
+  if (g < 1 || g > w || w % g != 0) return fail(h, RA_MPPI_EINVAL, "warps_per_sample must divide warps_per_block");
+  const int old_w = h->warps, old_i = h->ilp, old_g = h->wps;
   h->warps = w;
   h->ilp = i;
+  h->wps = g;
   const cudaError_t e = prepare(h);
   if (e != cudaSuccess) {
     h->warps = old_w;
     h->ilp = old_i;
+    h->wps = old_g;
     prepare(h);
     return cuda_fail(h, e, "set_launch");
   }
   return RA_MPPI_OK;
 }
+
 
 int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays, float* best_ms) {
   if (h == nullptr || x0 == nullptr || V == nullptr) return RA_MPPI_EINVAL;
@@ -563,16 +578,20 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return cuda_fail(h, e, "tune");
   const int R = (h->prob.M + 31) / 32;
-  const int old_w = h->warps, old_i = h->ilp;
-  int bw = old_w, bi = old_i;
+  const int old_w = h->warps, old_i = h->ilp, old_g = h->wps;
+  int bw = old_w, bi = old_i, bg = old_g;
   float best = 1e30f;
   const int warps_c[] = {1, 2, 4, 8};
   const int ilp_c[] = {1, 2, 4};
+  const int wps_c[] = {1, 2, 4, 8};
   for (int w : warps_c) {
-    for (int il : ilp_c) {
-      if (R % il != 0) continue;
+    for (int il : ilp_c)
+    for (int g : wps_c) {
+      // shapes that leave a warp without a full set of interleaved rows add nothing
+      if (g > w || w % g != 0 || R < g * il) continue;
       h->warps = w;
       h->ilp = il;
+      h->wps = g;
       if (prepare(h) != cudaSuccess) continue;
       if (ra_mppi_step(h, x0, V, h->V_plus, nullptr, nullptr, s) != RA_MPPI_OK) continue;
       cudaEventRecord(e0, s);
@@ -586,6 +605,7 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
         best = ms;
         bw = w;
         bi = il;
+        bg = g;
       }
     }
   }
@@ -594,6 +614,7 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   cudaStreamDestroy(s);
   h->warps = bw;
   h->ilp = bi;
+  h->wps = bg;
   e = prepare(h);
   if (e == cudaSuccess) e = cudaMemcpy(&h->st->iteration, &saved_it, sizeof(saved_it), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(h, e, "tune");
@@ -601,10 +622,11 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   return RA_MPPI_OK;
 }
 
-int ra_mppi_get_launch(ra_mppi_t* h, int32_t* warps_per_block, int32_t* ilp) {
+int ra_mppi_get_launch(ra_mppi_t* h, int32_t* warps_per_block, int32_t* ilp, int32_t* warps_per_sample) {
   if (h == nullptr) return RA_MPPI_EINVAL;
   if (warps_per_block) *warps_per_block = h->warps;
   if (ilp) *ilp = h->ilp;
+  if (warps_per_sample) *warps_per_sample = h->wps;
   return RA_MPPI_OK;
 }
 

@@ -9,7 +9,7 @@
 namespace ramppi {
 
 constexpr float kPi = 3.14159265358979323846f;
-#define RA_MPPI_MAX_M_DEV 256
+#define RA_MPPI_MAX_M_DEV 512
 #define RA_MPPI_MAX_T_DEV 256
 
 // Constants of one problem, precomputed on the host (ra_api.cu) and passed to
@@ -33,6 +33,7 @@ struct DevParams {
   float w_dev, w_speed, v_target, gamma, w_obs, w_bdry, c4, c5, c_lin, kappa, inv_kappa;
   float track_S, track_R, track_hw;
   float inv_lambda, A, B, C_u;
+  float risk_threshold;  // level of the chance-constraint risk measure
   uint32_t seed_lo, seed_hi, instance;
   unsigned long long* diag;  // optional count of obstacle candidates tested (diagnostics)
 };
@@ -246,7 +247,7 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
       x[Md::slot_dim(2)] = fmaf(p.w_scale[2], z23.x, x[Md::slot_dim(2)]);
       if (Md::NS > 3) x[Md::slot_dim(3)] = fmaf(p.w_scale[3], z23.y, x[Md::slot_dim(3)]);
     }
-  } else {
+  } else if (p.noise_type == 1) {
     const uint4 sel = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
     const uint4 val = philox4x32_10(make_uint4(t | (1u << 16), m, k, instance), k0, k1);
     const uint32_t sw[4] = {sel.x, sel.y, sel.z, sel.w};
@@ -255,6 +256,31 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
     for (int s = 0; s < Md::NS; ++s) {
       if (p.w_scale[s] != 0.0f)
         x[Md::slot_dim(s)] += mix_value(sw[s], vw[s], p.w_scale[s], p.mix_gauss[s], p.mix_thresh);
+    }
+  } else if (p.noise_type == 2) {
+    // uniform on [-a_s, a_s]: (2u - 1) a_s
+    const uint4 w = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
+    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int s = 0; s < Md::NS; ++s)
+      x[Md::slot_dim(s)] += fmaf(2.0f * u01(ww[s]), p.w_scale[s], -p.w_scale[s]);
+  } else {
+    // impulse: with probability p a jump of per-slot size a_s along a
+    // direction uniform on the unit sphere of the active slots
+    const uint4 a = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
+    if (a.x < p.mix_thresh) {
+      const uint4 b = philox4x32_10(make_uint4(t | (1u << 16), m, k, instance), k0, k1);
+      const float2 z01 = box_muller(a.y, a.z);
+      const float2 z23 = box_muller(a.w, b.x);
+      const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+      float n2 = 0.0f;
+#pragma unroll
+      for (int s = 0; s < Md::NS; ++s)
+        if (p.w_scale[s] != 0.0f) n2 = fmaf(z[s], z[s], n2);
+      const float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+#pragma unroll
+      for (int s = 0; s < Md::NS; ++s)
+        if (p.w_scale[s] != 0.0f) x[Md::slot_dim(s)] = fmaf(p.w_scale[s] * z[s], inv, x[Md::slot_dim(s)]);
     }
   }
 }

@@ -56,6 +56,7 @@ struct RolloutArgs {
   float* L;            // [K][M] or nullptr
   int nb_nom;          // number of nominal blocks
   int obs_cap;
+  int wps;             // warps per sample in the disturbed blocks (divides the block's warps)
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -135,7 +136,7 @@ __device__ __forceinline__ void obstacle_hits_culled(const DevParams& p, float (
       cand = fmaf(dx, dx, dy * dy) <= fmaf(ob.w, 1.0001f, 1e-12f);
     }
     unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-    if (p.diag != nullptr && lane == 0 && m != 0u) atomicAdd(p.diag, (unsigned long long)__popc(m));
+    if (p.diag != nullptr && lane == 0 && m != 0u) atomicAdd(p.diag, (unsigned long long)(__popc(m) * ILP));
     while (m != 0u) {
       const int j = __ffs(m) - 1;
       m &= m - 1u;
@@ -171,18 +172,19 @@ __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP
   }
 }
 
-// ILP disturbed rollouts of one lane (rollouts lane + 32 (r0 + i)); risk costs to Ls
+// ILP disturbed rollouts of one lane: rollouts lane + 32 (r0 + i rstride),
+// i < ILP (rows r0, r0 + rstride, ... of the M rollouts); risk costs to Ls
 template <int MODEL, int ILP>
 __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in, const float* x0, int k, int lane,
-                                             int r0, const float4* ctl, float* Ls, const float4* obs_s,
-                                             int n_obs) {
+                                             int r0, int rstride, const float4* ctl, float* Ls,
+                                             const float4* obs_s, int n_obs) {
   using Md = Model<MODEL>;
   float x[ILP][Md::NX];
   float L[ILP];
   uint32_t m[ILP];
 #pragma unroll
   for (int i = 0; i < ILP; ++i) {
-    m[i] = (uint32_t)(lane + 32 * (r0 + i));
+    m[i] = (uint32_t)(lane + 32 * (r0 + i * rstride));
     L[i] = 0.0f;
 #pragma unroll
     for (int j = 0; j < Md::NX; ++j) x[i][j] = x0[j];
@@ -201,35 +203,41 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
     if ((int)m[i] < in.M) Ls[m[i]] = L[i];
 }
 
-// One warp: the M disturbed rollouts of sample k and CVaR_k (written to cvar[k]).
-// ctl [T] and Ls [M] are this warp's shared-memory scratch.
-template <int MODEL, int ILP>
-__device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst& in, const float* __restrict__ x0g,
-                                                 const float* __restrict__ V, int k, int lane, float4* ctl, float* Ls,
-                                                 const float4* obs_s, int n_obs, float* __restrict__ cvar,
-                                                 float* __restrict__ Lout, int* status) {
+// U^k into shared memory, steps t_first, t_first + t_stride, ... (the nominal
+// thread of sample k draws the same bits)
+template <int MODEL>
+__device__ __forceinline__ void fill_controls(const DevParams& p, const Inst& in, const float* __restrict__ V, int k,
+                                              int t_first, int t_stride, float4* ctl) {
   using Md = Model<MODEL>;
-  // U^k into shared memory (the nominal thread of sample k draws the same bits)
-  for (int t = lane; t < in.T; t += 32) {
+  for (int t = t_first; t < in.T; t += t_stride) {
     const float v0 = V[t * Md::NU];
     const float v1 = Md::NU > 1 ? V[t * Md::NU + 1] : 0.0f;
     const float2 u = control_sample(p, in.k0, in.k1, k, t, v0, v1, in.n_warm, in.instance);
     ctl[t] = Md::ctl(p, u.x, u.y);
   }
-  __syncwarp();
+}
 
+// the rollout rows r_first, r_first + r_stride, ... of sample k (one warp);
+// ILP rows interleaved, the rest one at a time
+template <int MODEL, int ILP>
+__device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in, const float* __restrict__ x0g, int k,
+                                             int lane, int r_first, int r_stride, const float4* ctl, float* Ls,
+                                             const float4* obs_s, int n_obs) {
+  using Md = Model<MODEL>;
   float x0[Md::NX];
 #pragma unroll
   for (int i = 0; i < Md::NX; ++i) x0[i] = x0g[i];
-
-  // disturbed rollouts and their risk costs (Eq. 9)
   const int R = (in.M + 31) >> 5;
-  int r0 = 0;
-  for (; r0 + ILP <= R; r0 += ILP) rollouts_ilp<MODEL, ILP>(p, in, x0, k, lane, r0, ctl, Ls, obs_s, n_obs);
+  int r = r_first;
+  for (; r + (ILP - 1) * r_stride < R; r += ILP * r_stride)
+    rollouts_ilp<MODEL, ILP>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs);
   if (ILP > 1)
-    for (; r0 < R; ++r0) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r0, ctl, Ls, obs_s, n_obs);
-  __syncwarp();
+    for (; r < R; r += r_stride) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs);
+}
 
+// CVaR_k (or the selected risk measure) of the M risk costs in Ls (one warp)
+__device__ __forceinline__ void risk_from_shared(const DevParams& p, const Inst& in, const float* Ls, int k, int lane,
+                                                 float* __restrict__ cvar, float* __restrict__ Lout, int* status) {
   // CVaR_k over the M risk costs (Eqs. 10-13, 18, 19)
   constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
   uint32_t key[RMAX];
@@ -298,14 +306,43 @@ __device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst&
     // statistic; ties with L_(j) beyond rank j count at full weight
     const float n_eq_tail = (float)(in.M - in.j_var - c_gt);
     cv = (s_gt + (n_eq_tail + in.frac_j) * var) / in.tail_denom;
-  } else {
+  } else if (p.cvar_mode == 1) {
     cv = (s_gt + (float)c_eq * var) / (float)(c_gt + c_eq);
+  } else if (p.cvar_mode == 2) {
+    cv = var;  // VaR_alpha (Eq. 11)
+  } else if (p.cvar_mode == 3) {
+    // chance measure: fraction of the scaled risk costs above the threshold
+    // (B = 1 compares the costs themselves, so no rounding enters the decision)
+    int over = 0;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const float v = p.B == 1.0f ? val[r] : fmaf(p.B, val[r] - mean, mean);
+      if (lane + 32 * r < in.M) over += v > p.risk_threshold ? 1 : 0;
+    }
+    cv = (float)__reduce_add_sync(0xFFFFFFFFu, (unsigned)over) / (float)in.M;
+  } else {
+    cv = mean;  // risk-neutral expected risk cost
   }
   // sensitivity scaling L_a = B (L - mean) + mean commutes with the tail
-  // average for B >= 0: CVaR(L_a) = B CVaR(L) + (1 - B) mean
-  if (p.B != 1.0f) cv = fmaf(p.B, cv, (1.0f - p.B) * mean);
+  // average and the quantile for B >= 0: rho(L_a) = B rho(L) + (1 - B) mean
+  if (p.B != 1.0f && p.cvar_mode <= 2) cv = fmaf(p.B, cv, (1.0f - p.B) * mean);
   if (lane == 0) cvar[k] = cv;
   __syncwarp();
+}
+
+// One warp: the M disturbed rollouts of sample k and CVaR_k (written to cvar[k]).
+// ctl [T] and Ls [M] are this warp's shared-memory scratch.
+template <int MODEL, int ILP>
+__device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst& in, const float* __restrict__ x0g,
+                                                 const float* __restrict__ V, int k, int lane, float4* ctl, float* Ls,
+                                                 const float4* obs_s, int n_obs, float* __restrict__ cvar,
+                                                 float* __restrict__ Lout, int* status) {
+  fill_controls<MODEL>(p, in, V, k, lane, 32, ctl);
+  __syncwarp();
+  // disturbed rollouts and their risk costs (Eq. 9)
+  run_rollouts<MODEL, ILP>(p, in, x0g, k, lane, 0, 1, ctl, Ls, obs_s, n_obs);
+  __syncwarp();
+  risk_from_shared(p, in, Ls, k, lane, cvar, Lout, status);
 }
 
 template <int MODEL, int ILP>
@@ -322,12 +359,25 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
     if (k < in.K) nominal_rollout<MODEL>(p, in, a.x0, a.V, a.U, a.S, k, obs_s, n_obs);
     return;
   }
+  // disturbed blocks: G = a.wps warps per sample, warps / G samples per block
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
-  if (k >= in.K) return;
-  float4* ctl = smem + a.obs_cap + w * in.T;
-  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * in.M;
-  disturbed_sample<MODEL, ILP>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L, &a.st->status);
+  const int G = a.wps, spb = warps / G, gi = w / G, g = w - gi * G;
+  const int k = ((int)blockIdx.x - a.nb_nom) * spb + gi;
+  float4* ctl = smem + a.obs_cap + gi * in.T;
+  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + spb * in.T) + gi * in.M;
+  if (G == 1) {
+    if (k >= in.K) return;
+    disturbed_sample<MODEL, ILP>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L, &a.st->status);
+    return;
+  }
+  // a sample's rollout rows split over its G warps; every warp of the block
+  // reaches both barriers
+  const bool valid = k < in.K;
+  if (valid) fill_controls<MODEL>(p, in, a.V, k, g * 32 + lane, 32 * G, ctl);
+  __syncthreads();
+  if (valid) run_rollouts<MODEL, ILP>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs);
+  __syncthreads();
+  if (valid && g == 0) risk_from_shared(p, in, Ls, k, lane, a.cvar, a.L, &a.st->status);
 }
 
 }  // namespace ramppi

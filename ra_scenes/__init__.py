@@ -20,10 +20,15 @@ from .presets import (  # noqa: F401
     MODEL_LINEAR_TEST,
     NOISE_GAUSS,
     NOISE_LAPLACE_MIX,
+    NOISE_UNIFORM,
+    NOISE_IMPULSE,
     OBS_INDICATOR,
     OBS_SOFTPLUS,
     CVAR_RU,
     CVAR_TCE,
+    RISK_VAR,
+    RISK_CHANCE,
+    RISK_MEAN,
     RISK_DEV,
     RISK_SPEED,
     RISK_OBS,
@@ -33,6 +38,8 @@ from .presets import (  # noqa: F401
 from .scene import (  # noqa: F401
     make_obstacles,
     obstacles_ahead,
+    scene_obstacles,
+    scene_initial_state,
     initial_state,
     zero_controls,
     random_controls,

@@ -18,12 +18,17 @@ MODEL_LINEAR_TEST = 2
 
 NOISE_GAUSS = 0
 NOISE_LAPLACE_MIX = 1
+NOISE_UNIFORM = 2
+NOISE_IMPULSE = 3
 
 OBS_INDICATOR = 0
 OBS_SOFTPLUS = 1
 
 CVAR_RU = 0
 CVAR_TCE = 1
+RISK_VAR = 2
+RISK_CHANCE = 3
+RISK_MEAN = 4
 
 # bits of risk_mask: which running-cost terms make up the risk cost l(x)
 RISK_DEV = 1
@@ -74,6 +79,7 @@ _COMMON = dict(
     C_u=0.0,
     eta=0.0,
     cvar_mode=CVAR_RU,
+    risk_threshold=0.0,
     seed=12842,
     instance_id=0,
     n_obs=10,
@@ -114,6 +120,19 @@ PRESETS = {
     "small_kin": dict(_COMMON, **_KIN, K=77, M=32, T=13, n_obs=10),
     "small_dyn": dict(_COMMON, **_DYN, K=45, M=64, T=11, n_obs=20,
                       obs_r=(0.2, 0.5)),
+    # the paper's simulation setting (Sec. V-A): K = 1024 samples, M = 300
+    # disturbed rollouts, T = 30, lambda = 0.35, eta = 0.2, A = 10, running
+    # cost 2 boundary + 1 obstacle + 0.1 deviation^2, terminal progress
+    # cost 0.6 - 2 s, risk cost l = q; alpha = 0.7, C_u = 0.6 (the loosened
+    # setting of Sec. V-B); a stadium of the paper's width (0.6 m),
+    # corner radius (0.3 m) and centreline length (10.9 m); 10 obstacles of
+    # radius 0.1 m; Gaussian disturbance 0.2 on the velocity states
+    "paper_sim": dict(_COMMON, **dict(_DYN, noise_type=NOISE_GAUSS, w_scale=(0.2, 0.2, 0.2, 0.0), mix_p=0.0),
+                      K=1024, M=300, T=30, w_dev=0.1, w_speed=0.0, w_obs=1.0, w_bdry=2.0, c4=0.6, c5=2.0,
+                      gamma=0.35, lam=0.35, eta=0.2, A=10.0, alpha=0.7, C_u=0.6,
+                      risk_mask=RISK_DEV | RISK_OBS | RISK_BDRY,
+                      track_straight=4.5075, track_radius=0.3, track_half_width=0.3, n_obs=10,
+                      obs_r=(0.1, 0.1)),
     # linear-Gaussian test system x+ = x + dt*u + w with cost c_lin * x
     "linear_test": dict(_COMMON, model=MODEL_LINEAR_TEST, dt=1.0,
                         model_params=(0,) * 8, noise_type=NOISE_GAUSS,

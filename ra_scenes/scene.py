@@ -66,6 +66,19 @@ def obstacles_ahead(seed, n, r_lo, r_hi, x_from=0.3, x_to=2.5, y_center=-4.0,
     return out
 
 
+def scene_obstacles(p, seed=None):
+    """The preset's obstacle field on its own track (seeded by the preset)."""
+    R = float(p["track_radius"])
+    return make_obstacles(p["seed"] if seed is None else seed, int(p["n_obs"]), *p["obs_r"],
+                          straight=float(p["track_straight"]), radius=R,
+                          half_width=float(p["track_half_width"]), start=(0.0, -R))
+
+
+def scene_initial_state(p):
+    """Start at the preset's track origin (0, -R) heading along +x."""
+    return initial_state(int(p["model"]), radius=float(p["track_radius"]))
+
+
 def initial_state(model, radius=4.0):
     """Start at the track origin (0, -R) heading along +x."""
     if model == MODEL_KIN_BICYCLE:

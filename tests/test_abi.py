@@ -55,7 +55,7 @@ def test_problem_struct_layout(pkg):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("K", 0), ("M", 257), ("T", 0), ("lam", 0.0), ("alpha", 1.0), ("alpha", 0.0),
+    ("K", 0), ("M", 513), ("T", 0), ("lam", 0.0), ("alpha", 1.0), ("alpha", 0.0),
     ("B", -1.0), ("eta", 1.0), ("substeps", 0), ("model", 7), ("cvar_mode", 5),
 ])
 def test_create_rejects_invalid_problems(pkg, field, value):
