@@ -45,7 +45,7 @@ def algorithmic_ops(p, tested_obstacles=None):
     """Formula count of ALU lane-operations per disturbed step and per nominal
     step: FP32 add/mul/FMA/min/max/compare/select and INT32 ops count 1 each,
     every special-function evaluation (sin, cos, tan, atan, atan2, log, exp,
-    sqrt, erfcinv, division) counts 1.  The indicator obstacle term of a
+    sqrt, rsqrt, division) counts 1.  The indicator obstacle term of a
     disturbed step counts the obstacles actually tested (`tested_obstacles`
     per rollout-step, after the kernel's exact bounding-box cull) when given,
     else all of them."""
@@ -58,7 +58,9 @@ def algorithmic_ops(p, tested_obstacles=None):
     if model == 1:
         deriv = 38  # slip angles 7, two tyres 10, sincos 2, six derivatives 19
         dyn = sub * (2 * deriv + 6 + 12)
-        noise = (2 * philox + 3 * 10) if int(p["noise_type"]) == 1 else (philox + 2 * 10 + 3)
+        # mixture: per slot the tail mass (3), ln, the Laplace value (1), the
+        # Gaussian radius and angle (sqrt, cos, 4), select and sign (2)
+        noise = (2 * philox + 3 * 12) if int(p["noise_type"]) == 1 else (philox + 2 * 10 + 3)
     elif model == 0:
         dyn = sub * 7
         noise = philox + 2 * 10 + 4
@@ -251,12 +253,14 @@ def run_ours(args, p, x0, V, obs):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select exactly these launches
     for i in range(args.steps):
         flush.fill_(float(i))
         ctl.set_timing_events(kv_b[i], kv_e[i])
         ev_b[i].record(stream)
         ctl.closed_loop_step(x_d, V_d, hits)
         ev_e[i].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()

@@ -96,11 +96,16 @@ enum { RA_MPPI_OBS_INDICATOR = 0, RA_MPPI_OBS_SOFTPLUS = 1 };
  *   TCE    CVaR in the literal Monte-Carlo form of Eqs. 12-13: mean of
  *          {L >= VaR}, VaR = L_(j) (Eq. 11)
  *   VAR    VaR_alpha = L_(j) itself (Eq. 11)
- *   CHANCE fraction of the M costs above risk_threshold (a chance constraint
- *          in place of CVaR; the paper names the block swappable, Sec. III-A)
- *   MEAN   the mean risk cost (risk neutral) */
+ *   CHANCE fraction of the M costs above risk_param (a chance constraint
+ *          in place of CVaR; the paper names chance constraints as a
+ *          replacement for its Monte-Carlo risk block, Secs. I and III-A)
+ *   MEAN   the mean risk cost (risk neutral)
+ *   MEANVAR mean-variance: mean + risk_param * (1/M) sum (L_a - mean)^2 of
+ *          the scaled costs L_a, risk_param >= 0 (the paper's risk block
+ *          admits other metrics, Secs. I and III-A; this classical one is
+ *          not among those it names) */
 enum { RA_MPPI_CVAR_RU = 0, RA_MPPI_CVAR_TCE = 1, RA_MPPI_RISK_VAR = 2, RA_MPPI_RISK_CHANCE = 3,
-       RA_MPPI_RISK_MEAN = 4 };
+       RA_MPPI_RISK_MEAN = 4, RA_MPPI_RISK_MEANVAR = 5 };
 
 /* Bits of risk_mask: the running-cost terms that form the risk cost l
  * (Eq. 9).  The paper's experiments use l = q (all terms). */
@@ -149,7 +154,7 @@ typedef struct ra_mppi_problem {
   float B;            /* risk sensitivity scale, >= 0 (Eq. 18)                */
   float C_u;          /* CVaR bound (Eq. 15)                                  */
   float eta;          /* zero-mean sample fraction in [0, 1) (Alg. 1)         */
-  float risk_threshold;  /* level of RA_MPPI_RISK_CHANCE                        */
+  float risk_param;   /* threshold of RISK_CHANCE; variance weight (>= 0) of RISK_MEANVAR */
   int32_t max_obstacles; /* capacity of the obstacle list, 0 .. RA_MPPI_MAX_OBSTACLES */
   uint32_t instance_id;  /* fourth Philox counter word                        */
   uint64_t seed;         /* Philox key                                        */

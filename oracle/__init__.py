@@ -57,7 +57,7 @@ class Problem(ctypes.Structure):
         ("track_half_width", ctypes.c_double),
         ("lam", ctypes.c_double), ("alpha", ctypes.c_double), ("A", ctypes.c_double),
         ("B", ctypes.c_double), ("C_u", ctypes.c_double), ("eta", ctypes.c_double),
-        ("band_delta", ctypes.c_double), ("risk_threshold", ctypes.c_double),
+        ("band_delta", ctypes.c_double), ("risk_param", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("iteration", ctypes.c_uint64),
         ("instance_id", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
     ]
@@ -78,8 +78,6 @@ def lib():
         L.orc_uniform.argtypes = [ctypes.c_uint32]
         L.orc_uniform.restype = ctypes.c_double
         L.orc_box_muller.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _D]
-        L.orc_erfcinv.argtypes = [ctypes.c_double]
-        L.orc_erfcinv.restype = ctypes.c_double
         L.orc_mix_value.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double]
         L.orc_mix_value.restype = ctypes.c_double
@@ -147,7 +145,7 @@ def make_problem(p, iteration=0, band_delta=1e-4, n_threads=1, exact=False):
         pr.w_scale[i] = _f32(p["w_scale"][i])
     for name in ("mix_p", "mix_scale", "w_dev", "w_speed", "v_target", "gamma", "w_obs",
                  "w_bdry", "c4", "c5", "c_lin", "kappa", "track_straight", "track_radius",
-                 "track_half_width", "lam", "alpha", "A", "B", "C_u", "eta", "risk_threshold"):
+                 "track_half_width", "lam", "alpha", "A", "B", "C_u", "eta", "risk_param"):
         setattr(pr, name, _f32(p[name]))
     pr.band_delta = float(band_delta)
     pr.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
@@ -179,10 +177,6 @@ def box_muller(a, b):
     out = np.zeros(2)
     lib().orc_box_muller(int(a), int(b), _ptr(out))
     return out
-
-
-def erfcinv(v):
-    return lib().orc_erfcinv(float(v))
 
 
 def mix_value(sel, word, b, p, mix_scale):

@@ -56,7 +56,7 @@
 enum { ORC_KIN = 0, ORC_DYN = 1, ORC_LIN = 2 };
 enum { ORC_GAUSS = 0, ORC_LAPLACE_MIX = 1, ORC_UNIFORM = 2, ORC_IMPULSE = 3 };
 enum { ORC_OBS_INDICATOR = 0, ORC_OBS_SOFTPLUS = 1 };
-enum { ORC_CVAR_RU = 0, ORC_CVAR_TCE = 1, ORC_VAR = 2, ORC_CHANCE = 3, ORC_MEAN = 4 };
+enum { ORC_CVAR_RU = 0, ORC_CVAR_TCE = 1, ORC_VAR = 2, ORC_CHANCE = 3, ORC_MEAN = 4, ORC_MEANVAR = 5 };
 enum { ORC_R_DEV = 1, ORC_R_SPEED = 2, ORC_R_OBS = 4, ORC_R_BDRY = 8, ORC_R_LIN = 16 };
 
 typedef struct {
@@ -74,7 +74,7 @@ typedef struct {
   double track_straight, track_radius, track_half_width;
   double lam, alpha, A, B, C_u, eta;
   double band_delta;
-  double risk_threshold;
+  double risk_param;
   uint64_t seed;
   uint64_t iteration;
   uint32_t instance_id;
@@ -121,38 +121,23 @@ void orc_box_muller(uint32_t a, uint32_t b, double out[2]) {
   out[1] = rad * sin(2.0 * ORC_PI * u2);
 }
 
-/* inverse of erfc on (0, 1]: the y >= 0 with erfc(y) = v.  Newton steps
- * safeguarded by a bisection bracket; stops at double-precision resolution. */
-double orc_erfcinv(double v) {
-  if (!(v > 0.0)) return INFINITY;
-  if (v >= 1.0) return 0.0;
-  double lo = 0.0, hi = 27.0; /* erfc(27) < 1e-300 */
-  double y = sqrt(-log(v));   /* start inside the bracket */
-  if (y > hi) y = hi;
-  for (int it = 0; it < 200; ++it) {
-    double f = erfc(y) - v; /* decreasing in y */
-    if (f > 0.0) lo = y; else hi = y;
-    double dfdy = -2.0 / sqrt(ORC_PI) * exp(-y * y);
-    double ny = (dfdy != 0.0) ? y - f / dfdy : 0.5 * (lo + hi);
-    if (!(ny > lo && ny < hi)) ny = 0.5 * (lo + hi);
-    if (fabs(ny - y) <= 1e-16 * (1.0 + y) || hi - lo <= 1e-16 * (1.0 + y)) return ny;
-    y = ny;
-  }
-  return y;
-}
-
-/* Heavy-tailed slot value: Laplace(0, b) by its inverse CDF, replaced with
- * probability p by N(0, (mix_scale b)^2) by the Gaussian inverse CDF.  Both
- * use the same uniform a = (x + 1/2) 2^-32 through the tail mass
- * v = 2 min(a, 1 - a) and the sign of a - 1/2; the branch is taken when the
- * selector word is below floor(p 2^32). */
+/* Heavy-tailed slot value (Eq. 6 with the mixture noise of the workload):
+ * Laplace(0, b) by its inverse CDF, replaced with probability p by
+ * N(0, (mix_scale b)^2).  The value word gives the tail mass
+ * v = 2 min(a, 1 - a) of a = (x + 1/2) 2^-32 and the sign of a - 1/2; the
+ * Gaussian branch is taken when the selector word is below floor(p 2^32). */
 double orc_mix_value(uint32_t sel, uint32_t word, double b, double p, double mix_scale) {
   uint32_t hi = word >> 31;
   uint32_t r = hi ? ~word : word;                 /* in [0, 2^31) */
   double v = ((double)r + 0.5) * (1.0 / 2147483648.0);
   double sgn = hi ? 1.0 : -1.0;
-  uint32_t thresh = (uint32_t)floor(p * 4294967296.0 > 4294967295.0 ? 4294967295.0 : p * 4294967296.0);
-  if (sel < thresh) return sgn * (mix_scale * b) * sqrt(2.0) * orc_erfcinv(v);
+  double thresh = floor(p * 4294967296.0 > 4294967295.0 ? 4294967295.0 : p * 4294967296.0);
+  if ((double)sel < thresh) {
+    /* Gaussian branch: Box-Muller with radius from v and angle from the
+     * selector, uniform on [0, thresh) given this branch */
+    double u2 = ((double)sel + 0.5) / thresh;
+    return sgn * (mix_scale * b) * sqrt(-2.0 * log(v)) * cos(2.0 * ORC_PI * u2);
+  }
   return sgn * (-b * log(v));
 }
 
@@ -382,7 +367,9 @@ static int cmp_double(const void* a, const void* b) {
 /* risk measure of M risk costs after the sensitivity scaling (Eqs. 18, 19):
  * RU / TCE the two CVaR forms (Eqs. 10-13), VAR the quantile L_(j)
  * (Eq. 11), CHANCE the fraction of scaled costs above `thr` (a chance
- * constraint in place of CVaR, Sec. III-A), MEAN the risk-neutral mean */
+ * constraint in place of CVaR, Sec. III-A), MEAN the risk-neutral mean,
+ * MEANVAR the mean plus `thr` times the population variance (a classical
+ * mean-variance measure; the risk block admits such metrics, Sec. III-A) */
 double orc_risk(const double* L, int32_t M, double alpha, double B, int32_t mode, double thr);
 
 double orc_cvar(const double* L, int32_t M, double alpha, double B, int32_t mode) {
@@ -415,6 +402,14 @@ double orc_risk(const double* L, int32_t M, double alpha, double B, int32_t mode
       acc += (mode == ORC_CHANCE) ? (v > thr ? 1.0 : 0.0) : v;
     }
     out = acc / (double)M;
+  } else if (mode == ORC_MEANVAR) {
+    /* mean + kappa * population variance of the scaled costs */
+    double m1 = 0.0;
+    for (int n = 0; n < M; ++n) m1 += La[n];
+    m1 /= (double)M;
+    double m2 = 0.0;
+    for (int n = 0; n < M; ++n) m2 += (La[n] - m1) * (La[n] - m1);
+    out = m1 + thr * (m2 / (double)M);
   } else if (mode == ORC_CVAR_RU) {
     double tail = ((double)j - aM) * var;
     for (int i = j; i < M; ++i) tail += La[i];
@@ -502,9 +497,9 @@ int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, con
       }
       Lm[m] = Lv; Lm[M + m] = Llo; Lm[2 * M + m] = Lhi;
     }
-    double cv = orc_risk(Lm, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
-    double cv_lo = orc_risk(Lm + M, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
-    double cv_hi = orc_risk(Lm + 2 * M, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
+    double cv = orc_risk(Lm, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
+    double cv_lo = orc_risk(Lm + M, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
+    double cv_hi = orc_risk(Lm + 2 * M, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
     /* CVaR violation cost and modified trajectory cost (Eqs. 14-16) */
     double st = Sk + ((cv > p->C_u) ? p->A * cv : 0.0);
     if (U) memcpy(U + (size_t)i * T * nu, Uk, sizeof(double) * (size_t)T * nu);
@@ -791,7 +786,7 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
       }
       Lm[(size_t)k * M + m] = Lv;
     }
-    cv[k] = orc_risk(Lm + (size_t)k * M, M, p->alpha, p->B, p->cvar_mode, p->risk_threshold);
+    cv[k] = orc_risk(Lm + (size_t)k * M, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
     St[k] = S[k] + ((cv[k] > p->C_u) ? p->A * cv[k] : 0.0);
   }
   /* update and its weights */
@@ -854,6 +849,8 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
           wa = La[m] == var ? 1.0 / c_eq : 0.0;
         else if (p->cvar_mode == ORC_MEAN)
           wa = 1.0 / M;
+        else if (p->cvar_mode == ORC_MEANVAR)
+          wa = (1.0 + 2.0 * p->risk_param * (La[m] - mean)) / M;
         else
           wa = 0.0; /* the chance measure is piecewise constant in L */
         if (p->cvar_mode == ORC_CHANCE) continue;

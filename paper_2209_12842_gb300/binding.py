@@ -49,7 +49,7 @@ class ra_mppi_problem(ctypes.Structure):
         ("track_radius", ctypes.c_float), ("track_half_width", ctypes.c_float),
         ("lambda_", ctypes.c_float), ("alpha", ctypes.c_float), ("A", ctypes.c_float),
         ("B", ctypes.c_float), ("C_u", ctypes.c_float), ("eta", ctypes.c_float),
-        ("risk_threshold", ctypes.c_float),
+        ("risk_param", ctypes.c_float),
         ("max_obstacles", ctypes.c_int32), ("instance_id", ctypes.c_uint32),
         ("seed", ctypes.c_uint64),
     ]
@@ -175,7 +175,7 @@ def ra_mppi_problem_from(p, flags=0, max_obstacles=None):
         pr.w_scale[i] = _f(p["w_scale"][i])
     for name in ("mix_p", "mix_scale", "w_dev", "w_speed", "v_target", "gamma", "w_obs", "w_bdry",
                  "c4", "c5", "c_lin", "kappa", "track_straight", "track_radius", "track_half_width",
-                 "alpha", "A", "B", "C_u", "eta", "risk_threshold"):
+                 "alpha", "A", "B", "C_u", "eta", "risk_param"):
         setattr(pr, name, _f(p[name]))
     pr.lambda_ = _f(p["lam"])
     n_obs = int(p.get("n_obs", 0))

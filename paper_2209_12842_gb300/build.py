@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libramppi.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
-              "--expt-relaxed-constexpr"]
+              "--expt-relaxed-constexpr", "-ftz=true"]
 
 
 def _nvcc():

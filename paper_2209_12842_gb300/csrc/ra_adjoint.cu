@@ -366,15 +366,19 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     w_eq = 1.0f / (float)c_eq;
   } else {
     w_gt = w_eq = 0.0f;  // chance: piecewise constant; mean: uniform weights below
-    if (p.cvar_mode == 4) w_all = 1.0f / (float)M;
+    if (p.cvar_mode >= 4) w_all = 1.0f / (float)M;
   }
+  // mean-variance: d rho / d L_a,n = (1 + 2 kappa (L_a,n - mean)) / M with
+  // L_a,n - mean = B (L_n - mean)
+  const float mean = warp_sum(sum) / (float)M;
+  const float w_dev = p.cvar_mode == 5 ? 2.0f * p.risk_param * p.B / (float)M : 0.0f;
   const float base = p.cvar_mode == 3 ? 0.0f : (1.0f - p.B) / (float)M;
   // pass 2: reverse sweep of every rollout with a nonzero weight
   float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int r = 0; r < R; ++r) {
     const int m = lane + 32 * r;
     const float Lm = val[r];
-    const float wt = m < M ? (Lm > var ? w_gt : (Lm == var ? w_eq : 0.0f)) + w_all : 0.0f;
+    const float wt = m < M ? (Lm > var ? w_gt : (Lm == var ? w_eq : 0.0f)) + fmaf(w_dev, Lm - mean, w_all) : 0.0f;
     const float lbar = m < M ? cvbar * fmaf(p.B, wt, base) : 0.0f;
     if (!__any_sync(0xFFFFFFFFu, lbar != 0.0f)) continue;
     float ck[kMaxCk][NX];

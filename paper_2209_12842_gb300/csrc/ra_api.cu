@@ -91,8 +91,10 @@ std::string validate(const ra_mppi_problem& p) {
   if (p.substeps < 1 || p.substeps > 64) return "substeps must be in [1, 64]";
   if (p.noise_type < RA_MPPI_NOISE_GAUSS || p.noise_type > RA_MPPI_NOISE_IMPULSE) return "unknown noise_type";
   if (p.obs_mode != RA_MPPI_OBS_INDICATOR && p.obs_mode != RA_MPPI_OBS_SOFTPLUS) return "unknown obs_mode";
-  if (p.cvar_mode < RA_MPPI_CVAR_RU || p.cvar_mode > RA_MPPI_RISK_MEAN) return "unknown risk measure (cvar_mode)";
-  if (std::isnan(p.risk_threshold)) return "risk_threshold must not be NaN";
+  if (p.cvar_mode < RA_MPPI_CVAR_RU || p.cvar_mode > RA_MPPI_RISK_MEANVAR) return "unknown risk measure (cvar_mode)";
+  if (std::isnan(p.risk_param)) return "risk_param must not be NaN";
+  if (p.cvar_mode == RA_MPPI_RISK_MEANVAR && !(p.risk_param >= 0.0f && std::isfinite(p.risk_param)))
+    return "the mean-variance weight risk_param must be finite and >= 0";
   if (p.max_obstacles < 0 || p.max_obstacles > RA_MPPI_MAX_OBSTACLES) return "max_obstacles must be in [0, 1024]";
   if (!(p.dt > 0.0f) || !std::isfinite(p.dt)) return "dt must be finite and > 0";
   if (!(p.lambda > 0.0f) || !std::isfinite(p.lambda)) return "lambda must be finite and > 0";
@@ -160,9 +162,10 @@ DevParams make_params(const ra_mppi_problem& p) {
   }
   const double thr = std::floor(std::fmin((double)p.mix_p * 4294967296.0, 4294967295.0));
   d.mix_thresh = (uint32_t)thr;
+  d.mix_inv_thresh = thr > 0.0 ? (float)(1.0 / thr) : 0.0f;
   for (int s = 0; s < 4; ++s) {
     d.w_scale[s] = p.w_scale[s];
-    d.mix_gauss[s] = (float)((double)p.mix_scale * (double)p.w_scale[s] * std::sqrt(2.0));
+    d.mix_gauss[s] = (float)((double)p.mix_scale * (double)p.w_scale[s]);
   }
   d.w_dev = p.w_dev;
   d.w_speed = p.w_speed;
@@ -182,7 +185,7 @@ DevParams make_params(const ra_mppi_problem& p) {
   d.A = p.A;
   d.B = p.B;
   d.C_u = p.C_u;
-  d.risk_threshold = p.risk_threshold;
+  d.risk_param = p.risk_param;
   d.seed_lo = (uint32_t)(p.seed & 0xFFFFFFFFull);
   d.seed_hi = (uint32_t)(p.seed >> 32);
   d.instance = p.instance_id;

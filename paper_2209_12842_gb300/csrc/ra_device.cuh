@@ -29,11 +29,12 @@ struct DevParams {
   float sigma_u[2], inv_sig2[2], u_lo[2], u_hi[2];
   float w_scale[4];
   uint32_t mix_thresh;    // floor(mix_p 2^32): Gaussian branch iff selector word < it
-  float mix_gauss[4];     // mix_scale * w_scale[s] * sqrt(2)
+  float mix_inv_thresh;   // 1 / floor(mix_p 2^32) (0 when the threshold is 0)
+  float mix_gauss[4];     // mix_scale * w_scale[s]: std of the Gaussian branch
   float w_dev, w_speed, v_target, gamma, w_obs, w_bdry, c4, c5, c_lin, kappa, inv_kappa;
   float track_S, track_R, track_hw;
   float inv_lambda, A, B, C_u;
-  float risk_threshold;  // level of the chance-constraint risk measure
+  float risk_param;  // threshold of the chance measure; variance weight of mean-variance
   uint32_t seed_lo, seed_hi, instance;
   unsigned long long* diag;  // optional count of obstacle candidates tested (diagnostics)
 };
@@ -80,19 +81,40 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
   return make_float2(__fmul_rn(rad, c), __fmul_rn(rad, s));
 }
 
-// Heavy-tailed slot value: Laplace(0, b) by its inverse CDF; with the
-// selector word below floor(p 2^32), N(0, (mix_scale b)^2) by the Gaussian
-// inverse CDF instead.  Both use the tail mass v = 2 min(a, 1 - a) of the
-// uniform a = (word + 1/2) 2^-32, computed from the integer so no precision
-// is lost near a = 1, and the sign of a - 1/2.
-__device__ __forceinline__ float mix_value(uint32_t sel, uint32_t word, float b, float gfac,
-                                           uint32_t thresh) {
+// The same pair for process noise, where an absolute error of a few 1e-7 in
+// the unit normal is far below the disturbance scale: the angle 2 pi u2 - pi
+// lies in (-pi, pi], where the hardware sine and cosine are accurate to about
+// 2^-21 absolute, and cos(2 pi u2) = -cos(2 pi u2 - pi) (likewise sin).  The
+// radius keeps the accurate logarithm (its error would be amplified by the
+// square root near u1 = 1) and takes the square root as x rsqrt(x).
+__device__ __forceinline__ float2 box_muller_process(uint32_t a, uint32_t b) {
+  const float e = -2.0f * logf(u01(a));
+  const float rad = e > 0.0f ? e * rsqrtf(e) : 0.0f;
+  float s, c;
+  __sincosf(fmaf(2.0f * kPi, u01(b), -kPi), &s, &c);
+  return make_float2(-rad * c, -rad * s);
+}
+
+// Heavy-tailed slot value from a selector word and a value word.  The value
+// word gives the tail mass v = 2 min(a, 1 - a) of the uniform
+// a = (word + 1/2) 2^-32, computed from the integer so no precision is lost
+// near a = 1, and the sign of a - 1/2.  With the selector at or above
+// floor(p 2^32): Laplace(0, b) by its inverse CDF, -b ln v.  Below it:
+// N(0, g^2) by Box-Muller from v and the selector itself, which is uniform
+// on [0, floor(p 2^32)) given the branch, as the angle
+// u2 = (sel + 1/2) / floor(p 2^32).  Both branches share ln v and neither
+// diverges within a warp.
+__device__ __forceinline__ float mix_value(uint32_t sel, uint32_t word, float b, float g,
+                                           uint32_t thresh, float inv_thresh) {
   const bool hi = (word >> 31) != 0u;
   const uint32_t r = hi ? ~word : word;
   const float v = __fmaf_rn(__uint2float_rn(r), 4.656612873077393e-10f, 2.3283064365386963e-10f);
-  float mag;
-  if (sel < thresh) mag = gfac * erfcinvf(v);
-  else mag = -b * logf(v);
+  const float lv = logf(v);
+  const float e = -2.0f * lv;
+  const float rad = e > 0.0f ? e * rsqrtf(e) : 0.0f;
+  const float u2 = (__uint2float_rn(sel) + 0.5f) * inv_thresh;
+  const float gauss = -g * rad * __cosf(fmaf(2.0f * kPi, u2, -kPi));
+  const float mag = sel < thresh ? gauss : -b * lv;
   return hi ? mag : -mag;
 }
 
@@ -113,7 +135,7 @@ __device__ __forceinline__ void heading_sincos(float a, float* s, float* c) {
 __device__ __forceinline__ float atan_poly(float z) {
   const float a = fabsf(z);
   const bool big = a > 1.0f;
-  const float t = big ? 1.0f / a : a;
+  const float t = big ? __fdividef(1.0f, a) : a;
   const float s = t * t;
   float q = -4.693589173e-03f;
   q = fmaf(q, s, 2.425358072e-02f);
@@ -171,11 +193,13 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
   // sin(C atan(z)) of the Pacejka lateral force.  For C = 3/2 it has the
   // closed form z (q + 2) / (q sqrt(2 q (q + 1))), q = sqrt(1 + z^2)
   // (half-angle identities with cos(atan z) = 1/q; no cancellation near 0),
-  // evaluated as z (q + 2) rsqrt(2 q^3 (q + 1)).
+  // evaluated with two reciprocal square roots as z (q + 2) (1/q) rsqrt(2 q (q + 1)).
   __device__ static __forceinline__ float pacejka_shape(const DevParams& p, float z) {
     if (p.pacejka_c15) {
-      const float q = sqrtf(fmaf(z, z, 1.0f));
-      return z * (q + 2.0f) * rsqrtf(2.0f * q * q * q * (q + 1.0f));
+      const float s = fmaf(z, z, 1.0f);
+      const float r1 = rsqrtf(s);  // 1 / q
+      const float q = s * r1;
+      return z * (q + 2.0f) * r1 * rsqrtf(2.0f * q * (q + 1.0f));
     }
     return sinf(p.mp[5] * atanf(z));
   }
@@ -184,7 +208,7 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], vfloor = p.mp[7];
     const float vx = x[3], vy = x[4], r = x[5];
     // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx)
-    const float inv_vx = 1.0f / fmaxf(vx, vfloor);
+    const float inv_vx = __fdividef(1.0f, fmaxf(vx, vfloor));
     const float af = c.x - atan_poly(fmaf(lf, r, vy) * inv_vx);
     const float ar = -atan_poly(fmaf(-lr, r, vy) * inv_vx);
     const float fyf = p.dfz_f * pacejka_shape(p, Bt * af);
@@ -239,11 +263,11 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
   using Md = Model<MODEL>;
   if (p.noise_type == 0) {
     const uint4 w = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
-    const float2 z01 = box_muller(w.x, w.y);
+    const float2 z01 = box_muller_process(w.x, w.y);
     x[Md::slot_dim(0)] = fmaf(p.w_scale[0], z01.x, x[Md::slot_dim(0)]);
     if (Md::NS > 1) {
       x[Md::slot_dim(1)] = fmaf(p.w_scale[1], z01.y, x[Md::slot_dim(1)]);
-      const float2 z23 = box_muller(w.z, w.w);
+      const float2 z23 = box_muller_process(w.z, w.w);
       x[Md::slot_dim(2)] = fmaf(p.w_scale[2], z23.x, x[Md::slot_dim(2)]);
       if (Md::NS > 3) x[Md::slot_dim(3)] = fmaf(p.w_scale[3], z23.y, x[Md::slot_dim(3)]);
     }
@@ -255,7 +279,7 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
 #pragma unroll
     for (int s = 0; s < Md::NS; ++s) {
       if (p.w_scale[s] != 0.0f)
-        x[Md::slot_dim(s)] += mix_value(sw[s], vw[s], p.w_scale[s], p.mix_gauss[s], p.mix_thresh);
+        x[Md::slot_dim(s)] += mix_value(sw[s], vw[s], p.w_scale[s], p.mix_gauss[s], p.mix_thresh, p.mix_inv_thresh);
     }
   } else if (p.noise_type == 2) {
     // uniform on [-a_s, a_s]: (2u - 1) a_s
@@ -270,8 +294,8 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
     const uint4 a = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
     if (a.x < p.mix_thresh) {
       const uint4 b = philox4x32_10(make_uint4(t | (1u << 16), m, k, instance), k0, k1);
-      const float2 z01 = box_muller(a.y, a.z);
-      const float2 z23 = box_muller(a.w, b.x);
+      const float2 z01 = box_muller_process(a.y, a.z);
+      const float2 z23 = box_muller_process(a.w, b.x);
       const float z[4] = {z01.x, z01.y, z23.x, z23.y};
       float n2 = 0.0f;
 #pragma unroll

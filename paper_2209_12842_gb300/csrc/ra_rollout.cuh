@@ -317,11 +317,20 @@ __device__ __forceinline__ void risk_from_shared(const DevParams& p, const Inst&
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) {
       const float v = p.B == 1.0f ? val[r] : fmaf(p.B, val[r] - mean, mean);
-      if (lane + 32 * r < in.M) over += v > p.risk_threshold ? 1 : 0;
+      if (lane + 32 * r < in.M) over += v > p.risk_param ? 1 : 0;
     }
     cv = (float)__reduce_add_sync(0xFFFFFFFFu, (unsigned)over) / (float)in.M;
-  } else {
+  } else if (p.cvar_mode == 4) {
     cv = mean;  // risk-neutral expected risk cost
+  } else {
+    // mean-variance: mean + kappa B^2 (1/M) sum (L - mean)^2, two-pass variance
+    float d2 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const float d = val[r] - mean;
+      if (lane + 32 * r < in.M) d2 = fmaf(d, d, d2);
+    }
+    cv = fmaf(p.risk_param * p.B * p.B, warp_sum(d2) / (float)in.M, mean);
   }
   // sensitivity scaling L_a = B (L - mean) + mean commutes with the tail
   // average and the quantile for B >= 0: rho(L_a) = B rho(L) + (1 - B) mean

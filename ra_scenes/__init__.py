@@ -29,6 +29,7 @@ from .presets import (  # noqa: F401
     RISK_VAR,
     RISK_CHANCE,
     RISK_MEAN,
+    RISK_MEANVAR,
     RISK_DEV,
     RISK_SPEED,
     RISK_OBS,

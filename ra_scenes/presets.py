@@ -29,6 +29,7 @@ CVAR_TCE = 1
 RISK_VAR = 2
 RISK_CHANCE = 3
 RISK_MEAN = 4
+RISK_MEANVAR = 5
 
 # bits of risk_mask: which running-cost terms make up the risk cost l(x)
 RISK_DEV = 1
@@ -79,7 +80,7 @@ _COMMON = dict(
     C_u=0.0,
     eta=0.0,
     cvar_mode=CVAR_RU,
-    risk_threshold=0.0,
+    risk_param=0.0,
     seed=12842,
     instance_id=0,
     n_obs=10,

@@ -53,7 +53,8 @@ def compare(p, g, ref, check_update=True):
         alpha = float(np.float32(p["alpha"]))
         Bs = float(np.float32(p["B"]))
         for i, k in enumerate(ks):
-            want = oracle.cvar(g["L"][k].astype(np.float64), alpha, Bs, p["cvar_mode"])
+            want = oracle.risk(g["L"][k].astype(np.float64), alpha, Bs, p["cvar_mode"],
+                               float(np.float32(p.get("risk_param", 0.0))))
             assert abs(g["cvar"][k] - want) <= 1e-5 * max(1.0, abs(want)), (k, g["cvar"][k], want)
     # 4. update stage on the GPU's S~ and U
     if check_update:

@@ -56,13 +56,21 @@ def test_problem_struct_layout(pkg):
 
 @pytest.mark.parametrize("field,value", [
     ("K", 0), ("M", 513), ("T", 0), ("lam", 0.0), ("alpha", 1.0), ("alpha", 0.0),
-    ("B", -1.0), ("eta", 1.0), ("substeps", 0), ("model", 7), ("cvar_mode", 5),
+    ("B", -1.0), ("eta", 1.0), ("substeps", 0), ("model", 7), ("cvar_mode", 6),
 ])
 def test_create_rejects_invalid_problems(pkg, field, value):
     p = rs.preset("c1_plain", **{field: value})
     prob = pkg.binding.ra_mppi_problem_from(p)
     with pytest.raises(pkg.binding.RaMppiError) as ei:
         pkg.binding.ra_mppi_create(prob)
+    assert ei.value.code == pkg.binding.RA_MPPI_EINVAL
+
+
+@pytest.mark.parametrize("kappa", [-1.0, float("inf"), float("nan")])
+def test_create_rejects_invalid_mean_variance_weight(pkg, kappa):
+    p = rs.preset("c1_plain", cvar_mode=rs.RISK_MEANVAR, risk_param=kappa)
+    with pytest.raises(pkg.binding.RaMppiError) as ei:
+        pkg.binding.ra_mppi_create(pkg.binding.ra_mppi_problem_from(p))
     assert ei.value.code == pkg.binding.RA_MPPI_EINVAL
 
 

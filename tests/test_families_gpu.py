@@ -66,11 +66,12 @@ def test_disturbance_families(name, noise):
     compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
 
 
-@pytest.mark.parametrize("mode", ["var", "chance", "mean"])
+@pytest.mark.parametrize("mode", ["var", "chance", "mean", "meanvar"])
 def test_risk_measures(mode):
-    m = {"var": rs.RISK_VAR, "chance": rs.RISK_CHANCE, "mean": rs.RISK_MEAN}[mode]
+    m = {"var": rs.RISK_VAR, "chance": rs.RISK_CHANCE, "mean": rs.RISK_MEAN, "meanvar": rs.RISK_MEANVAR}[mode]
+    param = 1e-3 if mode == "meanvar" else 500.0
     for B in (1.0, 2.0):
-        p = rs.preset("small_kin", cvar_mode=m, B=B, risk_threshold=500.0, K=96)
+        p = rs.preset("small_kin", cvar_mode=m, B=B, risk_param=param, K=96)
         obs = _scene(p)
         x0 = rs.initial_state(0)
         V = rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 5)
@@ -85,11 +86,11 @@ def test_risk_measures(mode):
             if m == rs.RISK_CHANCE and B != 1.0:
                 # the scaled cost is formed in float32 on the GPU: a cost within
                 # rounding of the threshold may fall on either side
-                lo = oracle.risk(Lk, a, B, m, 500.0 + 1e-3)
-                hi = oracle.risk(Lk, a, B, m, 500.0 - 1e-3)
+                lo = oracle.risk(Lk, a, B, m, param + 1e-3)
+                hi = oracle.risk(Lk, a, B, m, param - 1e-3)
                 assert lo - 1e-7 <= g["cvar"][k] <= hi + 1e-7, (mode, B, k, g["cvar"][k], lo, hi)
                 continue
-            want = oracle.risk(Lk, a, B, m, 500.0)
+            want = oracle.risk(Lk, a, B, m, float(np.float32(param)))
             assert abs(g["cvar"][k] - want) <= 1e-5 * max(1.0, abs(want)), (mode, B, k, g["cvar"][k], want)
 
 
@@ -119,12 +120,13 @@ def test_paper_preset():
     compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
 
 
-@pytest.mark.parametrize("mode", ["var", "mean"])
+@pytest.mark.parametrize("mode", ["var", "mean", "meanvar"])
 def test_adjoint_other_measures(mode):
     from paper_2209_12842_gb300 import RaMppi
 
-    m = {"var": rs.RISK_VAR, "mean": rs.RISK_MEAN}[mode]
-    p = rs.preset("c4_gradient", K=96, M=32, T=12, cvar_mode=m, risk_mask=rs.RISK_OBS | rs.RISK_DEV)
+    m = {"var": rs.RISK_VAR, "mean": rs.RISK_MEAN, "meanvar": rs.RISK_MEANVAR}[mode]
+    p = rs.preset("c4_gradient", K=96, M=32, T=12, cvar_mode=m, risk_param=0.05, B=1.5,
+                  risk_mask=rs.RISK_OBS | rs.RISK_DEV)
     obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4)
     x0 = np.array([0.0, -4.0, 0.0, 1.0], np.float32)
     V = rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 3)

@@ -41,9 +41,10 @@ def _fd_check(orc, p, x0, V, obs, gVp, gS, h=1e-6, rtol=1e-5):
     return gV, gth
 
 
-@pytest.mark.parametrize("mode,B", [(0, 1.0), (1, 1.0), (0, 2.0)])
+@pytest.mark.parametrize("mode,B", [(0, 1.0), (1, 1.0), (0, 2.0), (rs.RISK_VAR, 1.0), (rs.RISK_MEAN, 1.5),
+                                    (rs.RISK_MEANVAR, 1.0), (rs.RISK_MEANVAR, 2.0)])
 def test_p11_kinematic_softplus(orc, mode, B):
-    p = rs.preset("c4_gradient", K=12, M=8, T=6, cvar_mode=mode, B=B,
+    p = rs.preset("c4_gradient", K=12, M=8, T=6, cvar_mode=mode, B=B, risk_param=0.05,
                   risk_mask=rs.RISK_OBS | rs.RISK_DEV)
     obs = rs.obstacles_ahead(1, 6, 0.15, 0.3, x_from=0.05, x_to=0.6, lateral=0.3)
     x0 = np.array([0.0, -4.0, 0.0, 1.0])

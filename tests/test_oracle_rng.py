@@ -2,9 +2,9 @@
 
 - Philox4x32-10 words against an independent implementation run as a
   library (triton's CPU interpreter), on random counters and keys.
-- The uniform map, Box-Muller normals, the Laplace/Gaussian mixture and
-  the Gaussian inverse tail against scipy's distributions (KS tests,
-  moments) and scipy's erfcinv.
+- The uniform map, Box-Muller normals and the Laplace/Gaussian mixture
+  against scipy's distributions (KS tests, moments) and closed-form
+  values.
 """
 
 import json
@@ -14,7 +14,7 @@ import sys
 
 import numpy as np
 import pytest
-from scipy import special, stats
+from scipy import stats
 
 import ra_scenes as rs
 
@@ -101,14 +101,6 @@ def test_box_muller_normals(orc):
     assert abs(np.corrcoef(zz[:, 0], zz[:, 1])[0, 1]) < 4 / np.sqrt(len(zz))
 
 
-def test_erfcinv_against_scipy(orc):
-    for v in [1e-300, 1e-30, 1e-8, 1e-3, 0.01, 0.1, 0.3, 0.5, 0.77, 0.999, 1 - 1e-12]:
-        want = special.erfcinv(v)
-        got = orc.erfcinv(v)
-        assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (v, got, want)
-    assert orc.erfcinv(1.0) == 0.0
-
-
 def test_mix_laplace_branch(orc):
     b = 0.02
     w = _words(orc, 40000, seed=11)
@@ -125,13 +117,21 @@ def test_mix_laplace_branch(orc):
 
 
 def test_mix_gaussian_branch(orc):
+    # p = 1: every selector word below 2^32 - 1 takes the Gaussian branch, and
+    # the selector is the Box-Muller angle word
     b, s = 0.02, 5.0
     w = _words(orc, 40000, seed=12)
-    vals = np.array([orc.mix_value(0, int(x), b, 1.0, s) for x in w[:, 0]])
+    vals = np.array([orc.mix_value(int(a), int(x), b, 1.0, s) for a, x in w[:, :2]])
     assert stats.kstest(vals, stats.norm(scale=s * b).cdf).pvalue > 1e-3
-    x = 3000000000
-    a = (x + 0.5) / 2**32
-    assert abs(orc.mix_value(0, x, b, 1.0, s) - s * b * stats.norm.ppf(a)) < 1e-13
+    assert abs(vals.std() - s * b) < 0.02 * s * b
+    # the angle (sel + 1/2) / (2^32 - 1) is exactly 1/2 at sel = 2^31 - 1, so
+    # cos = -1 and the value is the Rayleigh radius sqrt(-2 ln v) (word < 2^31
+    # gives the negative sign, v = (word + 1/2) 2^-31)
+    for x in (0, 5, 123456789, 2**31 - 1):
+        v = (x + 0.5) / 2**31
+        assert orc.mix_value(2**31 - 1, x, b, 1.0, s) == pytest.approx(s * b * np.sqrt(-2 * np.log(v)), rel=1e-14, abs=1e-18)
+    # the radius does not depend on the sign word: words x and ~x mirror
+    assert orc.mix_value(77, 1000, b, 1.0, s) == -orc.mix_value(77, 0xFFFFFFFF - 1000, b, 1.0, s)
 
 
 def test_mixture_distribution(orc):
@@ -145,7 +145,9 @@ def test_mixture_distribution(orc):
     assert stats.kstest(vals, cdf).pvalue > 1e-3
     # the selector threshold is floor(p 2^32): an integer decision
     thr = int(np.floor(p * 2**32))
-    assert orc.mix_value(thr - 1, 5, b, p, s) == pytest.approx(-s * b * np.sqrt(2) * special.erfcinv((5 + 0.5) / 2**31), rel=1e-12)
+    v = (5 + 0.5) / 2**31
+    gauss = -s * b * np.sqrt(-2 * np.log(v)) * np.cos(2 * np.pi * (thr - 0.5) / thr)
+    assert orc.mix_value(thr - 1, 5, b, p, s) == pytest.approx(gauss, rel=1e-12)
     assert orc.mix_value(thr, 5, b, p, s) == pytest.approx(b * np.log((5 + 0.5) / 2**31), rel=1e-12)
 
 
