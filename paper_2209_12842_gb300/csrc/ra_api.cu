@@ -148,11 +148,14 @@ DevParams make_params(const ra_mppi_problem& p) {
   if (p.model == RA_MPPI_DYN_SINGLE_TRACK) {
     const double m = p.model_params[0], Iz = p.model_params[1], lf = p.model_params[2], lr = p.model_params[3];
     const double D = p.model_params[6], g = 9.81;
-    d.dfz_f = (float)(D * m * g * lr / (lf + lr));
-    d.dfz_r = (float)(D * m * g * lf / (lf + lr));
-    d.inv_m = (float)(1.0 / m);
-    d.inv_iz = (float)(1.0 / Iz);
     d.pacejka_c15 = p.model_params[5] == 1.5f ? 1 : 0;
+    // lateral accelerations per unit shape, with the 1/sqrt(2) of the C = 3/2
+    // closed form folded in; yaw arms l m / Iz
+    const double fold = d.pacejka_c15 ? std::sqrt(0.5) : 1.0;
+    d.acc_f = (float)(D * g * lr / (lf + lr) * fold);
+    d.acc_r = (float)(D * g * lf / (lf + lr) * fold);
+    d.yaw_f = (float)(lf * m / Iz);
+    d.yaw_r = (float)(lr * m / Iz);
   }
   for (int j2 = 0; j2 < 2; ++j2) {
     d.sigma_u[j2] = p.sigma_u[j2];

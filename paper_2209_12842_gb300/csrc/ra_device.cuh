@@ -24,8 +24,9 @@ struct DevParams {
   float tail_denom;   // (1 - alpha) M
   float h;            // integration step dt / substeps
   float mp[8];        // model parameters (see ra_mppi.h)
-  float dfz_f, dfz_r, inv_m, inv_iz;  // dynamic model: D Fz per axle, 1/m, 1/Iz
   int pacejka_c15;    // Pacejka shape factor C is exactly 3/2 (closed form below)
+  float acc_f, acc_r;  // D Fz / m per axle (times 1/sqrt(2) when pacejka_c15)
+  float yaw_f, yaw_r;  // l_f m / Iz, l_r m / Iz
   float sigma_u[2], inv_sig2[2], u_lo[2], u_hi[2];
   float w_scale[4];
   uint32_t mix_thresh;    // floor(mix_p 2^32): Gaussian branch iff selector word < it
@@ -132,10 +133,7 @@ __device__ __forceinline__ void heading_sincos(float a, float* s, float* c) {
 // z^2 (coefficients fitted here by iterated weighted least squares on
 // Chebyshev nodes for the relative error; max 2.5e-7 in float32), reflected
 // as pi/2 - atan(1/|z|) above 1, odd in z.
-__device__ __forceinline__ float atan_poly(float z) {
-  const float a = fabsf(z);
-  const bool big = a > 1.0f;
-  const float t = big ? __fdividef(1.0f, a) : a;
+__device__ __forceinline__ float atan_core(float t) {  // |t| <= 1
   const float s = t * t;
   float q = -4.693589173e-03f;
   q = fmaf(q, s, 2.425358072e-02f);
@@ -145,9 +143,28 @@ __device__ __forceinline__ float atan_poly(float z) {
   q = fmaf(q, s, 1.996973604e-01f);
   q = fmaf(q, s, -3.333199322e-01f);
   q = fmaf(q, s, 9.999998808e-01f);
-  float r = t * q;
+  return t * q;
+}
+__device__ __forceinline__ float atan_poly(float z) {
+  const float a = fabsf(z);
+  const bool big = a > 1.0f;
+  float r = atan_core(big ? __fdividef(1.0f, a) : a);
   r = big ? 1.57079632679489662f - r : r;
   return copysignf(r, z);
+}
+// Two arctangents at once.  When no active lane has an argument above 1 in
+// magnitude (the common case), the warp skips the reflection; z P(z^2) with
+// the odd z equals copysign(|z| P(z^2), z) bit for bit (P > 0), so both paths
+// give the same bits and the result does not depend on which lanes share a
+// warp.
+__device__ __forceinline__ void atan_pair(float za, float zb, float* ta, float* tb) {
+  if (__all_sync(__activemask(), fmaxf(fabsf(za), fabsf(zb)) <= 1.0f)) {
+    *ta = atan_core(za);
+    *tb = atan_core(zb);
+  } else {
+    *ta = atan_poly(za);
+    *tb = atan_poly(zb);
+  }
 }
 
 // ---------------------------------------------------------------- models
@@ -185,23 +202,26 @@ template <>
 struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heun
   static constexpr int NX = 6, NU = 2, NS = 3;
   __device__ static __forceinline__ int slot_dim(int s) { return 3 + s; }
+  // per-step control quantities: (B steer, accel, sin steer, cos steer)
   __device__ static __forceinline__ float4 ctl(const DevParams& p, float u0, float u1) {
     float s, c;
     sincosf(u0, &s, &c);
-    return make_float4(u0, u1, s, c);
+    return make_float4(p.mp[4] * u0, u1, s, c);
   }
-  // sin(C atan(z)) of the Pacejka lateral force.  For C = 3/2 it has the
-  // closed form z (q + 2) / (q sqrt(2 q (q + 1))), q = sqrt(1 + z^2)
-  // (half-angle identities with cos(atan z) = 1/q; no cancellation near 0),
-  // evaluated with two reciprocal square roots as z (q + 2) (1/q) rsqrt(2 q (q + 1)).
-  __device__ static __forceinline__ float pacejka_shape(const DevParams& p, float z) {
+  // lateral acceleration k sin(C atan z) of one axle (k = D Fz / m).  For
+  // C = 3/2 the shape has the closed form z (q + 2) / (q sqrt(2 q (q + 1))),
+  // q = sqrt(1 + z^2) (half-angle identities with cos(atan z) = 1/q; no
+  // cancellation near 0).  With s = 1 + z^2, 2 q (q + 1) = 2 (s + q), so it
+  // is z (q + 2) (1/q) rsqrt(s + q) / sqrt(2), the 1/sqrt(2) being folded
+  // into k on the host.
+  __device__ static __forceinline__ float pacejka(const DevParams& p, float z, float k) {
     if (p.pacejka_c15) {
       const float s = fmaf(z, z, 1.0f);
-      const float r1 = rsqrtf(s);  // 1 / q
-      const float q = s * r1;
-      return z * (q + 2.0f) * r1 * rsqrtf(2.0f * q * (q + 1.0f));
+      const float u = rsqrtf(s);  // 1 / q
+      const float q = s * u;
+      return (k * z) * (q + 2.0f) * u * rsqrtf(s + q);
     }
-    return sinf(p.mp[5] * atanf(z));
+    return k * sinf(p.mp[5] * atanf(z));
   }
   __device__ static __forceinline__ void deriv(const DevParams& p, const float* x, const float4 c,
                                                float* f) {
@@ -209,18 +229,20 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     const float vx = x[3], vy = x[4], r = x[5];
     // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx)
     const float inv_vx = __fdividef(1.0f, fmaxf(vx, vfloor));
-    const float af = c.x - atan_poly(fmaf(lf, r, vy) * inv_vx);
-    const float ar = -atan_poly(fmaf(-lr, r, vy) * inv_vx);
-    const float fyf = p.dfz_f * pacejka_shape(p, Bt * af);
-    const float fyr = p.dfz_r * pacejka_shape(p, Bt * ar);
+    float tf, tr;
+    atan_pair(fmaf(lf, r, vy) * inv_vx, fmaf(-lr, r, vy) * inv_vx, &tf, &tr);
+    // Pacejka arguments B alpha_f = B (steer - atan_f), B alpha_r = -B atan_r
+    const float ay_f = pacejka(p, fmaf(-Bt, tf, c.x), p.acc_f);
+    const float ay_r = pacejka(p, -Bt * tr, p.acc_r);
     float sp, cp;
     heading_sincos(x[2], &sp, &cp);
     f[0] = vx * cp - vy * sp;
     f[1] = vx * sp + vy * cp;
     f[2] = r;
-    f[3] = c.y - fyf * c.z * p.inv_m + r * vy;
-    f[4] = (fyf * c.w + fyr) * p.inv_m - r * vx;
-    f[5] = (lf * fyf * c.w - lr * fyr) * p.inv_iz;
+    const float g = ay_f * c.w;  // front force along the body y axis, per unit mass
+    f[3] = fmaf(r, vy, c.y) - ay_f * c.z;
+    f[4] = fmaf(-r, vx, g + ay_r);
+    f[5] = fmaf(p.yaw_f, g, -p.yaw_r * ay_r);
   }
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
     for (int s = 0; s < p.substeps; ++s) {

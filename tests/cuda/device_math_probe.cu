@@ -10,12 +10,24 @@ __global__ void probe(const float* z, int n, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float v = z[i];
-  out[4 * i + 0] = ramppi::atan_poly(v);
-  out[4 * i + 1] = atanf(v);
+  float* o = out + 8 * i;
+  o[0] = ramppi::atan_poly(v);
+  o[1] = atanf(v);
   ramppi::DevParams p{};
   p.pacejka_c15 = 1;
-  out[4 * i + 2] = ramppi::Model<1>::pacejka_shape(p, v);
-  out[4 * i + 3] = sinf(1.5f * atanf(v));
+  // k = 1/sqrt(2) undoes the factor the host folds into the axle constant
+  o[2] = ramppi::Model<1>::pacejka(p, v, 0.70710678118654752f);
+  o[3] = sinf(1.5f * atanf(v));
+  // the paired arctangent: the general path whenever a lane of the warp has
+  // an argument above 1, the fast one when the whole warp is within [-1, 1]
+  float a, b;
+  ramppi::atan_pair(v, 0.5f, &a, &b);
+  o[4] = a;
+  const float w = fminf(fmaxf(v, -1.0f), 1.0f);
+  ramppi::atan_pair(w, w, &a, &b);
+  o[5] = a;
+  o[6] = ramppi::atan_poly(w);
+  o[7] = b;
 }
 
 }  // namespace

@@ -1,7 +1,8 @@
 """The kernels' own device math against CUDA's functions and float64 (GPU).
 
 atan_poly (the slip-angle arctangent) must stay within 3e-7 relative of the
-true arctangent and within 4 float32 ulp of CUDA's atanf; the closed form of
+true arctangent and within 4 float32 ulp of CUDA's atanf, and the paired
+arctangent must give its bits on both of its paths; the closed form of
 sin(1.5 atan z) used by the Pacejka force must agree with CUDA's
 sinf(1.5f * atanf(z)) and with float64 to 1e-6 relative.
 """
@@ -25,7 +26,7 @@ def probe(tmp_path_factory):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     out = str(tmp_path_factory.mktemp("probe") / "libprobe.so")
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared",
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-ftz=true", "-shared",
                     "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "paper_2209_12842_gb300", "csrc"),
                     os.path.join(HERE, "cuda", "device_math_probe.cu"), "-o", out], check=True)
     lib = ctypes.CDLL(out)
@@ -35,7 +36,7 @@ def probe(tmp_path_factory):
 
 def _run(lib, z):
     zt = torch.from_numpy(z.astype(np.float32)).cuda()
-    out = torch.empty((z.size, 4), dtype=torch.float32, device="cuda")
+    out = torch.empty((z.size, 8), dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     assert lib.device_math_probe(zt.data_ptr(), z.size, out.data_ptr()) == 0
     return out.cpu().numpy().astype(np.float64)
@@ -61,3 +62,12 @@ def test_pacejka_closed_form(probe):
     nz = np.abs(exact) > 1e-30
     assert np.max(np.abs(r[nz, 2] - exact[nz]) / np.abs(exact[nz])) < 1e-6
     assert np.max(np.abs(r[nz, 2] - r[nz, 3]) / np.abs(exact[nz])) < 2e-6
+
+
+def test_atan_pair_paths_are_bitwise_equal(probe):
+    # mixed warps (some |z| > 1) take the general path; clamped warps the fast one
+    z = np.concatenate([np.linspace(-3, 3, 100001), np.linspace(-1, 1, 100001)]).astype(np.float32)
+    r = _run(probe, z).astype(np.float32)
+    np.testing.assert_array_equal(r[:, 4], r[:, 0])
+    np.testing.assert_array_equal(r[:, 5], r[:, 6])
+    np.testing.assert_array_equal(r[:, 7], r[:, 6])
