@@ -126,6 +126,10 @@ enum {
 #define RA_MPPI_MAX_M 512
 #define RA_MPPI_MAX_T 256
 #define RA_MPPI_MAX_OBSTACLES 1024
+/* Every obstacle disc must lie in the square |x|, |y| <= RA_MPPI_OBSTACLE_EXTENT
+ * metres (|centre| + r within it).  The kernels' obstacle cull is exact under
+ * this bound (float32 rounding of shifted coordinates stays below its pad). */
+#define RA_MPPI_OBSTACLE_EXTENT 500.0f
 
 /* Problem definition (the quantities of Sec. II-V).  All reals float32. */
 typedef struct ra_mppi_problem {
@@ -177,7 +181,8 @@ void ra_mppi_destroy(ra_mppi_t* h);
 /* Set the obstacle circles used by q and l (Eq. 22): xyr[n_obs][3] =
  * (centre x, centre y, radius), host or device pointer.  Synchronous: the
  * copy has completed when the call returns.  EINVAL if n_obs >
- * max_obstacles, a radius is negative or a centre is not finite. */
+ * max_obstacles, a radius is negative, a centre is not finite, or a disc
+ * leaves the square of side 2 RA_MPPI_OBSTACLE_EXTENT around the origin. */
 int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* stream);
 
 /* One RA-MPPI update on device buffers (steps 1-6 above).

@@ -270,6 +270,11 @@ int default_ilp(int M, int model) {
 
 // shared with the batched path (ra_batch.cu)
 namespace ramppi_api {
+// the disc (x, y, r) lies in |x|, |y| <= RA_MPPI_OBSTACLE_EXTENT
+bool obstacle_in_extent(float x, float y, float r) {
+  const double e = RA_MPPI_OBSTACLE_EXTENT;
+  return std::fabs((double)x) + r <= e && std::fabs((double)y) + r <= e;
+}
 std::string validate_problem(const ra_mppi_problem& p) { return validate(p); }
 DevParams make_params(const ra_mppi_problem& p) { return ::make_params(p); }
 }  // namespace ramppi_api
@@ -382,6 +387,11 @@ int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* s
         std::free(tmp);
         std::free(host);
         return fail(h, RA_MPPI_EINVAL, "obstacle radius must be >= 0 and centres finite");
+      }
+      if (!ramppi_api::obstacle_in_extent(tmp[3 * i], tmp[3 * i + 1], r)) {
+        std::free(tmp);
+        std::free(host);
+        return fail(h, RA_MPPI_EINVAL, "obstacle disc outside |x|, |y| <= RA_MPPI_OBSTACLE_EXTENT");
       }
       host[i] = make_float4(tmp[3 * i], tmp[3 * i + 1], r, r * r);
     }

@@ -24,6 +24,7 @@ using ramppi::InstDesc;
 namespace ramppi_api {
 std::string validate_problem(const ra_mppi_problem& p);
 DevParams make_params(const ra_mppi_problem& p);
+bool obstacle_in_extent(float x, float y, float r);
 }  // namespace ramppi_api
 
 struct ra_mppi_batch {
@@ -384,6 +385,8 @@ int ra_mppi_batch_set_obstacles(ra_mppi_batch_t* b, int32_t i, const float* xyr,
     const float r = tmp[3 * o + 2];
     if (!(r >= 0.0f) || !std::isfinite(tmp[3 * o]) || !std::isfinite(tmp[3 * o + 1]))
       return bfail(b, RA_MPPI_EINVAL, "obstacle radius must be >= 0 and centres finite");
+    if (!ramppi_api::obstacle_in_extent(tmp[3 * o], tmp[3 * o + 1], r))
+      return bfail(b, RA_MPPI_EINVAL, "obstacle disc outside |x|, |y| <= RA_MPPI_OBSTACLE_EXTENT");
     packed[o] = make_float4(tmp[3 * o], tmp[3 * o + 1], r, r * r);
   }
   if (n_obs > 0)

@@ -103,11 +103,21 @@ __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& 
 
 // Indicator obstacle count of the ILP states of every lane of the warp
 // (called by all 32 lanes together).  The warp first bounds its positions by
-// a box (order-preserving keys, warp min/max) and tests 32 obstacles at a
-// time against the box, the lane per obstacle; only obstacles whose disc can
-// reach the box (with a relative margin far above float32 rounding) get the
-// exact per-state test, in the original obstacle order.  A skipped obstacle
-// cannot contain any state, so the counts equal the full loop's.
+// a box and tests 32 obstacles at a time against the box, the lane per
+// obstacle; only obstacles whose disc can reach the box (with a relative
+// margin far above float32 rounding) get the exact per-state test, in the
+// original obstacle order.  A skipped obstacle cannot contain any state, so
+// the counts equal the full loop's.
+//
+// The box: coordinates shifted by kBoxShift are positive for every state
+// that can be inside an obstacle (obstacles lie within a few hundred metres
+// of the origin), so their bit patterns order like the values and one
+// integer warp min/max finds each bound.  The shift rounds by at most half
+// an ulp of 1024 (6.2e-5 m), so each bound is widened by kBoxPad.  A state
+// far below -1024 m turns a min bound very negative and leaves the max
+// bounds to the states that matter; a NaN (positive pattern, larger than any
+// finite value) makes its max bound NaN, which the candidate test treats as
+// unbounded.
 template <int MODEL, int ILP>
 __device__ __forceinline__ void obstacle_hits_culled(const DevParams& p, float (&x)[ILP][Model<MODEL>::NX],
                                                      float (&hits)[ILP], const float4* __restrict__ obs,
@@ -121,10 +131,17 @@ __device__ __forceinline__ void obstacle_hits_culled(const DevParams& p, float (
     ymn = fminf(ymn, x[i][1]);
     ymx = fmaxf(ymx, x[i][1]);
   }
-  xmn = fkey_inv(__reduce_min_sync(0xFFFFFFFFu, fkey(xmn)));
-  xmx = fkey_inv(__reduce_max_sync(0xFFFFFFFFu, fkey(xmx)));
-  ymn = fkey_inv(__reduce_min_sync(0xFFFFFFFFu, fkey(ymn)));
-  ymx = fkey_inv(__reduce_max_sync(0xFFFFFFFFu, fkey(ymx)));
+  constexpr float kBoxShift = 1024.0f, kBoxPad = 1.25e-4f;
+  const auto lo = [](float v) {
+    return __int_as_float(__reduce_min_sync(0xFFFFFFFFu, __float_as_int(v + kBoxShift))) - (kBoxShift + kBoxPad);
+  };
+  const auto hi = [](float v) {
+    return __int_as_float(__reduce_max_sync(0xFFFFFFFFu, __float_as_int(v + kBoxShift))) - (kBoxShift - kBoxPad);
+  };
+  xmn = lo(xmn);
+  xmx = hi(xmx);
+  ymn = lo(ymn);
+  ymx = hi(ymx);
   for (int base = 0; base < n_obs; base += 32) {
     const int o = base + lane;
     bool cand = false;

@@ -140,3 +140,14 @@ def test_adjoint_other_measures(mode):
     for got, want in ((gV.cpu().numpy(), rV), (gth.cpu().numpy(), rth)):
         got, want = np.asarray(got, np.float64).ravel(), np.asarray(want, np.float64).ravel()
         assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want), (mode, got, want)
+
+
+def test_obstacle_extent_is_enforced():
+    from paper_2209_12842_gb300 import RaMppi, RaMppiError
+
+    p = rs.preset("small_kin")
+    ctl = RaMppi(p, np.array([[499.0, -10.0, 1.0]], np.float32))  # on the boundary: accepted
+    for bad in ([[499.5, 0.0, 1.0]], [[0.0, -600.0, 0.3]], [[0.0, 0.0, 501.0]]):
+        with pytest.raises(RaMppiError):
+            ctl.set_obstacles(np.array(bad, np.float32))
+    ctl.close()
