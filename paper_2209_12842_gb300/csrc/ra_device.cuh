@@ -129,43 +129,77 @@ __device__ __forceinline__ void heading_sincos(float a, float* s, float* c) {
   __sincosf(r, s, c);
 }
 
+// ---------------------------------------------------------------- lanes x 2
+// The dynamic model is written once for T = float (one rollout) and
+// T = float2 (two rollouts of a lane side by side).  Every arithmetic step is
+// one IEEE operation with round-to-nearest: __fmaf_rn / __fmul_rn /
+// __fadd_rn for float, and the sm_100+ paired instructions __ffma2_rn /
+// __fmul2_rn / __fadd2_rn for float2, which round each half exactly like
+// the scalar ones.  So a pair gives the bits of two scalar evaluations, and
+// a launch that interleaves rollouts two by two matches one that does not,
+// while issuing one instruction for two FP32 operations.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+template <class T> __device__ __forceinline__ T bc(float c);
+template <> __device__ __forceinline__ float bc<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 bc<float2>(float c) { return make_float2(c, c); }
+// per-rollout application of a scalar function
+template <class F> __device__ __forceinline__ float vmap(float a, F f) { return f(a); }
+template <class F> __device__ __forceinline__ float2 vmap(float2 a, F f) { return make_float2(f(a.x), f(a.y)); }
+__device__ __forceinline__ float vmaxabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float vmaxabs(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ void vsincos(float a, float* s, float* c) { heading_sincos(a, s, c); }
+__device__ __forceinline__ void vsincos(float2 a, float2* s, float2* c) {
+  heading_sincos(a.x, &s->x, &c->x);
+  heading_sincos(a.y, &s->y, &c->y);
+}
+
 // arctangent for the slip angles: z P(z^2) on [0, 1] with P of degree 7 in
 // z^2 (coefficients fitted here by iterated weighted least squares on
 // Chebyshev nodes for the relative error; max 2.5e-7 in float32), reflected
 // as pi/2 - atan(1/|z|) above 1, odd in z.
-__device__ __forceinline__ float atan_core(float t) {  // |t| <= 1
-  const float s = t * t;
-  float q = -4.693589173e-03f;
-  q = fmaf(q, s, 2.425358072e-02f);
-  q = fmaf(q, s, -5.948816240e-02f);
-  q = fmaf(q, s, 9.914427996e-02f);
-  q = fmaf(q, s, -1.401953697e-01f);
-  q = fmaf(q, s, 1.996973604e-01f);
-  q = fmaf(q, s, -3.333199322e-01f);
-  q = fmaf(q, s, 9.999998808e-01f);
-  return t * q;
+template <class T>
+__device__ __forceinline__ T atan_core(T t) {  // |t| <= 1
+  const T s = vmul(t, t);
+  T q = bc<T>(-4.693589173e-03f);
+  q = vfma(q, s, bc<T>(2.425358072e-02f));
+  q = vfma(q, s, bc<T>(-5.948816240e-02f));
+  q = vfma(q, s, bc<T>(9.914427996e-02f));
+  q = vfma(q, s, bc<T>(-1.401953697e-01f));
+  q = vfma(q, s, bc<T>(1.996973604e-01f));
+  q = vfma(q, s, bc<T>(-3.333199322e-01f));
+  q = vfma(q, s, bc<T>(9.999998808e-01f));
+  return vmul(t, q);
 }
 __device__ __forceinline__ float atan_poly(float z) {
   const float a = fabsf(z);
   const bool big = a > 1.0f;
-  float r = atan_core(big ? __fdividef(1.0f, a) : a);
-  r = big ? 1.57079632679489662f - r : r;
+  float r = atan_core<float>(big ? __fdividef(1.0f, a) : a);
+  r = big ? __fadd_rn(1.57079632679489662f, -r) : r;
   return copysignf(r, z);
 }
-// Two arctangents at once.  When no active lane has an argument above 1 in
-// magnitude (the common case), the warp skips the reflection; z P(z^2) with
-// the odd z equals copysign(|z| P(z^2), z) bit for bit (P > 0), so both paths
-// give the same bits and the result does not depend on which lanes share a
-// warp.  (A shorter polynomial on |z| <= 1/2 was a few per cent faster at
-// small slip angles and slower under large disturbances, where few warps stay
-// below 1/2.)
-__device__ __forceinline__ void atan_pair(float za, float zb, float* ta, float* tb) {
-  if (__all_sync(__activemask(), fmaxf(fabsf(za), fabsf(zb)) <= 1.0f)) {
-    *ta = atan_core(za);
-    *tb = atan_core(zb);
+// Two arctangents at once (of T, so up to four rollouts' worth).  When no
+// active lane has an argument above 1 in magnitude (the common case), the
+// warp skips the reflection; z P(z^2) with the odd z equals
+// copysign(|z| P(z^2), z) bit for bit (P > 0), so both paths give the same
+// bits and the result does not depend on which lanes share a warp.  (A
+// shorter polynomial on |z| <= 1/2 was a few per cent faster at small slip
+// angles and slower under large disturbances, where few warps stay below
+// 1/2.)
+template <class T>
+__device__ __forceinline__ void atan_pair(T za, T zb, T* ta, T* tb) {
+  if (__all_sync(__activemask(), fmaxf(vmaxabs(za), vmaxabs(zb)) <= 1.0f)) {
+    *ta = atan_core<T>(za);
+    *tb = atan_core<T>(zb);
   } else {
-    *ta = atan_poly(za);
-    *tb = atan_poly(zb);
+    *ta = vmap(za, atan_poly);
+    *tb = vmap(zb, atan_poly);
   }
 }
 
@@ -216,47 +250,58 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
   // cancellation near 0).  With s = 1 + z^2, 2 q (q + 1) = 2 (s + q), so it
   // is z (q + 2) (1/q) rsqrt(s + q) / sqrt(2), the 1/sqrt(2) being folded
   // into k on the host.
-  __device__ static __forceinline__ float pacejka(const DevParams& p, float z, float k) {
+  template <class T>
+  __device__ static __forceinline__ T pacejka(const DevParams& p, T z, float k) {
     if (p.pacejka_c15) {
-      const float s = fmaf(z, z, 1.0f);
-      const float u = rsqrtf(s);  // 1 / q
-      const float q = s * u;
-      return (k * z) * (q + 2.0f) * u * rsqrtf(s + q);
+      const T s = vfma(z, z, bc<T>(1.0f));
+      const T u = vmap(s, [](float v) { return rsqrtf(v); });  // 1 / q
+      const T q = vmul(s, u);
+      const T w = vmap(vadd(s, q), [](float v) { return rsqrtf(v); });
+      return vmul(vmul(vmul(vmul(bc<T>(k), z), vadd(q, bc<T>(2.0f))), u), w);
     }
-    return k * sinf(p.mp[5] * atanf(z));
+    const float C = p.mp[5];
+    return vmul(bc<T>(k), vmap(z, [C](float v) { return sinf(C * atanf(v)); }));
   }
-  __device__ static __forceinline__ void deriv(const DevParams& p, const float* x, const float4 c,
-                                               float* f) {
+  template <class T>
+  __device__ static __forceinline__ void deriv(const DevParams& p, const T* x, const float4 c, T* f) {
     const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], vfloor = p.mp[7];
-    const float vx = x[3], vy = x[4], r = x[5];
+    const T vx = x[3], vy = x[4], r = x[5];
     // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx)
-    const float inv_vx = __fdividef(1.0f, fmaxf(vx, vfloor));
-    float tf, tr;
-    atan_pair(fmaf(lf, r, vy) * inv_vx, fmaf(-lr, r, vy) * inv_vx, &tf, &tr);
+    const T inv_vx = vmap(vx, [vfloor](float v) { return __fdividef(1.0f, fmaxf(v, vfloor)); });
+    T tf, tr;
+    atan_pair<T>(vmul(vfma(bc<T>(lf), r, vy), inv_vx), vmul(vfma(bc<T>(-lr), r, vy), inv_vx), &tf, &tr);
     // Pacejka arguments B alpha_f = B (steer - atan_f), B alpha_r = -B atan_r
-    const float ay_f = pacejka(p, fmaf(-Bt, tf, c.x), p.acc_f);
-    const float ay_r = pacejka(p, -Bt * tr, p.acc_r);
-    float sp, cp;
-    heading_sincos(x[2], &sp, &cp);
-    f[0] = vx * cp - vy * sp;
-    f[1] = vx * sp + vy * cp;
+    const T ay_f = pacejka<T>(p, vfma(bc<T>(-Bt), tf, bc<T>(c.x)), p.acc_f);
+    const T ay_r = pacejka<T>(p, vmul(bc<T>(-Bt), tr), p.acc_r);
+    T sp, cp;
+    vsincos(x[2], &sp, &cp);
+    f[0] = vfma(vx, cp, vneg(vmul(vy, sp)));
+    f[1] = vfma(vx, sp, vmul(vy, cp));
     f[2] = r;
-    const float g = ay_f * c.w;  // front force along the body y axis, per unit mass
-    f[3] = fmaf(r, vy, c.y) - ay_f * c.z;
-    f[4] = fmaf(-r, vx, g + ay_r);
-    f[5] = fmaf(p.yaw_f, g, -p.yaw_r * ay_r);
+    const T g = vmul(ay_f, bc<T>(c.w));  // front force along the body y axis, per unit mass
+    f[3] = vfma(vneg(ay_f), bc<T>(c.z), vfma(r, vy, bc<T>(c.y)));
+    f[4] = vfma(vneg(r), vx, vadd(g, ay_r));
+    f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(-p.yaw_r), ay_r));
   }
-  __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
+  template <class T>
+  __device__ static __forceinline__ void step_t(const DevParams& p, T* x, const float4 c) {
     for (int s = 0; s < p.substeps; ++s) {
-      float k1[6], k2[6], xp[6];
-      deriv(p, x, c, k1);
+      T k1[6], k2[6], xp[6];
+      deriv<T>(p, x, c, k1);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) xp[i] = fmaf(p.h, k1[i], x[i]);
-      deriv(p, xp, c, k2);
+      for (int i = 0; i < 6; ++i) xp[i] = vfma(bc<T>(p.h), k1[i], x[i]);
+      deriv<T>(p, xp, c, k2);
       const float hh = 0.5f * p.h;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) x[i] = fmaf(hh, k1[i] + k2[i], x[i]);
+      for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), vadd(k1[i], k2[i]), x[i]);
     }
+  }
+  __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
+    step_t<float>(p, x, c);
+  }
+  // two rollouts at once: x[i] = (state i of rollout a, state i of rollout b)
+  __device__ static __forceinline__ void step2(const DevParams& p, float2* x, const float4 c) {
+    step_t<float2>(p, x, c);
   }
   __device__ static __forceinline__ float speed(const float* x) { return x[3]; }
 };

@@ -209,8 +209,24 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
   for (int t = 0; t < in.T; ++t) {
     const float4 c = ctl[t];
     risk_cost_ilp<MODEL, ILP>(p, x, L, obs_s, n_obs);
+    if constexpr (MODEL == 1 && ILP % 2 == 0) {
+      // rollouts two by two in paired FP32 instructions (same bits as one by one)
 #pragma unroll
-    for (int i = 0; i < ILP; ++i) Md::step(p, x[i], c);
+      for (int i = 0; i < ILP; i += 2) {
+        float2 xx[Md::NX];
+#pragma unroll
+        for (int j = 0; j < Md::NX; ++j) xx[j] = make_float2(x[i][j], x[i + 1][j]);
+        Md::step2(p, xx, c);
+#pragma unroll
+        for (int j = 0; j < Md::NX; ++j) {
+          x[i][j] = xx[j].x;
+          x[i + 1][j] = xx[j].y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < ILP; ++i) Md::step(p, x[i], c);
+    }
 #pragma unroll
     for (int i = 0; i < ILP; ++i)
       add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, m[i], (uint32_t)k, in.instance, x[i]);
