@@ -123,9 +123,9 @@ __device__ __forceinline__ float mix_value(uint32_t sel, uint32_t word, float b,
 // split of 2 pi (Cody-Waite), then the hardware approximations, whose absolute
 // error is about 2^-21 on that interval.
 __device__ __forceinline__ void heading_sincos(float a, float* s, float* c) {
-  const float n = rintf(a * 0.15915494309189535f);  // a / (2 pi)
-  float r = fmaf(-n, 6.28318548202514648f, a);       // 2 pi rounded to float
-  r = fmaf(n, 1.7484556e-7f, r);                      // 2 pi - float(2 pi)
+  const float n = rintf(__fmul_rn(a, 0.15915494309189535f));  // a / (2 pi)
+  float r = __fmaf_rn(n, -6.28318548202514648f, a);            // 2 pi rounded to float
+  r = __fmaf_rn(n, 1.7484556e-7f, r);                           // 2 pi - float(2 pi)
   __sincosf(r, s, c);
 }
 
@@ -155,9 +155,14 @@ template <class F> __device__ __forceinline__ float2 vmap(float2 a, F f) { retur
 __device__ __forceinline__ float vmaxabs(float a) { return fabsf(a); }
 __device__ __forceinline__ float vmaxabs(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ void vsincos(float a, float* s, float* c) { heading_sincos(a, s, c); }
+// heading_sincos of two angles, the reduction in paired instructions
 __device__ __forceinline__ void vsincos(float2 a, float2* s, float2* c) {
-  heading_sincos(a.x, &s->x, &c->x);
-  heading_sincos(a.y, &s->y, &c->y);
+  const float2 y = vmul(a, bc<float2>(0.15915494309189535f));
+  const float2 n = make_float2(rintf(y.x), rintf(y.y));
+  float2 r = vfma(n, bc<float2>(-6.28318548202514648f), a);
+  r = vfma(n, bc<float2>(1.7484556e-7f), r);
+  __sincosf(r.x, &s->x, &c->x);
+  __sincosf(r.y, &s->y, &c->y);
 }
 
 // arctangent for the slip angles: z P(z^2) on [0, 1] with P of degree 7 in
@@ -275,12 +280,13 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     const T ay_r = pacejka<T>(p, vmul(bc<T>(-Bt), tr), p.acc_r);
     T sp, cp;
     vsincos(x[2], &sp, &cp);
-    f[0] = vfma(vx, cp, vneg(vmul(vy, sp)));
+    // (negated factors make the products exact negations: a (-b) = -(a b))
+    f[0] = vfma(vx, cp, vmul(vneg(vy), sp));
     f[1] = vfma(vx, sp, vmul(vy, cp));
     f[2] = r;
     const T g = vmul(ay_f, bc<T>(c.w));  // front force along the body y axis, per unit mass
-    f[3] = vfma(vneg(ay_f), bc<T>(c.z), vfma(r, vy, bc<T>(c.y)));
-    f[4] = vfma(vneg(r), vx, vadd(g, ay_r));
+    f[3] = vfma(ay_f, bc<T>(-c.z), vfma(r, vy, bc<T>(c.y)));
+    f[4] = vfma(r, vneg(vx), vadd(g, ay_r));
     f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(-p.yaw_r), ay_r));
   }
   template <class T>
