@@ -398,34 +398,40 @@ def ev_time(torch, fn, n, stream):
     return float(np.median(t)), float(np.percentile(t, 99))
 
 
-def closed_loop_study(torch, n_updates, alphas=(0.5, 0.9, 0.99)):
+def closed_loop_study(torch, n_updates, alphas=(0.5, 0.9, 0.99), seeds=(12842, 12843, 12844)):
     """Config 2's receding-horizon loop on the simulated plant: update rate
-    and plant collisions of RA-MPPI at each alpha and of plain MPPI (A = 0)."""
+    and plant collisions of RA-MPPI at each alpha and of plain MPPI (A = 0),
+    each over the same obstacle field with several noise seeds (the collision
+    count of one 1000-update run varies a lot with the noise)."""
     from paper_2209_12842_gb300 import RaMppi
 
     p0 = rs.preset("c2_closed_loop")
     obs = rs.make_obstacles(p0["seed"], p0["n_obs"], *p0["obs_r"])
-    out = {"updates": n_updates}
+    out = {"updates": n_updates, "seeds": list(seeds)}
     runs = [("mppi", dict(A=0.0))] + [(f"ra_alpha{a}", dict(alpha=a)) for a in alphas]
     for name, ov in runs:
-        p = rs.preset("c2_closed_loop", **ov)
-        ctl = RaMppi(p, obs)
-        x = torch.from_numpy(rs.initial_state(p["model"])).cuda()
-        V = torch.zeros((p["T"], 2), dtype=torch.float32, device="cuda")
-        hits = torch.zeros(1, dtype=torch.int32, device="cuda")
-        stream = torch.cuda.current_stream()
-        b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        b.record(stream)
-        for _ in range(n_updates):
-            ctl.closed_loop_step(x, V, hits)
-        e.record(stream)
-        torch.cuda.synchronize()
-        ms = b.elapsed_time(e)
-        xs = x.cpu().numpy()
-        out[name] = {"collisions": int(hits.item()), "update_hz": 1e3 * n_updates / ms,
-                     "final_state": [round(float(v), 3) for v in xs[:4]], "status": ctl.status()}
-        ctl.close()
+        hits_per_seed, hz, status = [], None, 0
+        for seed in seeds:
+            p = rs.preset("c2_closed_loop", seed=seed, **ov)
+            ctl = RaMppi(p, obs)
+            x = torch.from_numpy(rs.initial_state(p["model"])).cuda()
+            V = torch.zeros((p["T"], 2), dtype=torch.float32, device="cuda")
+            hits = torch.zeros(1, dtype=torch.int32, device="cuda")
+            stream = torch.cuda.current_stream()
+            b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            b.record(stream)
+            for _ in range(n_updates):
+                ctl.closed_loop_step(x, V, hits)
+            e.record(stream)
+            torch.cuda.synchronize()
+            if hz is None:
+                hz = 1e3 * n_updates / b.elapsed_time(e)
+            hits_per_seed.append(int(hits.item()))
+            status |= ctl.status()
+            ctl.close()
+        out[name] = {"collisions": hits_per_seed, "collisions_mean": float(np.mean(hits_per_seed)),
+                     "update_hz": hz, "status": status}
     return out
 
 

@@ -137,7 +137,11 @@ __device__ __forceinline__ void heading_sincos(float a, float* s, float* c) {
 // __fmul2_rn / __fadd2_rn for float2, which round each half exactly like
 // the scalar ones.  So a pair gives the bits of two scalar evaluations, and
 // a launch that interleaves rollouts two by two matches one that does not,
-// while issuing one instruction for two FP32 operations.
+// while issuing one instruction for two FP32 operations.  One rule keeps
+// this true: no product is ever added to something as a separate step.  The
+// compiler may fuse a paired multiply and a paired add into one FMA (the
+// scalar _rn forms are never fused), so every product-plus-term is written as
+// an explicit vfma.
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
@@ -145,6 +149,14 @@ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float vneg(float a) { return -a; }
+// the hardware reciprocal square root as one PTX instruction, so that no
+// compiler rewrite of an expression around it (s * rsqrt(s) as a square
+// root, say) can make the scalar and the paired paths differ
+__device__ __forceinline__ float rsqrt_hw(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
 template <class T> __device__ __forceinline__ T bc(float c);
 template <> __device__ __forceinline__ float bc<float>(float c) { return c; }
@@ -259,10 +271,9 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
   __device__ static __forceinline__ T pacejka(const DevParams& p, T z, float k) {
     if (p.pacejka_c15) {
       const T s = vfma(z, z, bc<T>(1.0f));
-      const T u = vmap(s, [](float v) { return rsqrtf(v); });  // 1 / q
-      const T q = vmul(s, u);
-      const T w = vmap(vadd(s, q), [](float v) { return rsqrtf(v); });
-      return vmul(vmul(vmul(vmul(bc<T>(k), z), vadd(q, bc<T>(2.0f))), u), w);
+      const T u = vmap(s, rsqrt_hw);  // 1 / q, and q = s u
+      const T w = vmap(vfma(s, u, s), rsqrt_hw);  // rsqrt(s + q)
+      return vmul(vmul(vmul(vmul(bc<T>(k), z), vfma(s, u, bc<T>(2.0f))), u), w);  // ... (q + 2) ...
     }
     const float C = p.mp[5];
     return vmul(bc<T>(k), vmap(z, [C](float v) { return sinf(C * atanf(v)); }));
@@ -286,7 +297,7 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     f[2] = r;
     const T g = vmul(ay_f, bc<T>(c.w));  // front force along the body y axis, per unit mass
     f[3] = vfma(ay_f, bc<T>(-c.z), vfma(r, vy, bc<T>(c.y)));
-    f[4] = vfma(r, vneg(vx), vadd(g, ay_r));
+    f[4] = vfma(r, vneg(vx), vfma(ay_f, bc<T>(c.w), ay_r));
     f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(-p.yaw_r), ay_r));
   }
   template <class T>

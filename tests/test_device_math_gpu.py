@@ -8,6 +8,7 @@ sinf(1.5f * atanf(z)) and with float64 to 1e-6 relative.
 """
 
 import ctypes
+import json
 import os
 import subprocess
 
@@ -71,3 +72,51 @@ def test_atan_pair_paths_are_bitwise_equal(probe):
     np.testing.assert_array_equal(r[:, 4], r[:, 0])
     np.testing.assert_array_equal(r[:, 5], r[:, 6])
     np.testing.assert_array_equal(r[:, 7], r[:, 6])
+
+
+@pytest.fixture(scope="module")
+def pair_probe(tmp_path_factory):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_12842_gb300 import binding, build
+
+    build.build()
+    pkg = os.path.dirname(binding.LIB_PATH)
+    out = str(tmp_path_factory.mktemp("pair") / "libpair.so")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-ftz=true", "-shared",
+                    "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"),
+                    "-I", os.path.join(ROOT, "paper_2209_12842_gb300", "csrc"),
+                    os.path.join(HERE, "cuda", "pair_probe.cu"), "-L", pkg, "-lramppi",
+                    "-Xlinker", "-rpath", "-Xlinker", pkg, "-o", out], check=True)
+    binding.lib()
+    lib = ctypes.CDLL(out)
+    lib.pair_probe_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    return lib, binding
+
+
+@pytest.mark.parametrize("C", [1.5, 1.3])
+def test_pairs_give_the_bits_of_two_scalars(pair_probe, C):
+    # one dynamic-model step (6 Heun sub-steps) on float2 pairs against two
+    # scalar steps, random states and controls; C = 1.5 takes the closed-form
+    # Pacejka shape, other C the library sin/atan
+    import ra_scenes as rs
+
+    lib, binding = pair_probe
+    mp = list(rs.preset("small_dyn")["model_params"])
+    mp[5] = C
+    p = rs.preset("small_dyn", model_params=tuple(mp))
+    prob = binding.ra_mppi_problem_from(p)
+    n = 20000
+    words = torch.from_numpy(np.random.default_rng(5).integers(0, 2**32, (n, 8), dtype=np.uint64)
+                             .astype(np.uint32).view(np.int32)).cuda()
+    out = torch.empty((n, 40), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    assert lib.pair_probe_run(words.data_ptr(), n, ctypes.addressof(prob), out.data_ptr()) == 0
+    o = out.cpu().numpy().view(np.uint32)
+    f = out.cpu().numpy()
+    checks = {"step rollout a": (slice(12, 18), slice(0, 6)), "step rollout b": (slice(18, 24), slice(6, 12)),
+              "pacejka": (slice(26, 28), slice(24, 26))}
+    bad = {k: float(np.mean(o[:, a] != o[:, b])) for k, (a, b) in checks.items()}
+    bad["derivative components"] = f[:, 32:38].mean(axis=0).tolist()
+    assert all(v == 0.0 for k, v in bad.items() if k != "derivative components") \
+        and not any(bad["derivative components"]), json.dumps(bad)
