@@ -242,10 +242,12 @@ int ra_mppi_get_status(ra_mppi_t* h);
 /* Human-readable reason of the last error on this handle ("" if none). */
 const char* ra_mppi_last_error(const ra_mppi_t* h);
 
-/* Launch-shape tuner: times every valid (warps per block, interleave) pair
- * on the given inputs (x0, V device; `replays` updates each), keeps the
- * fastest and restores the update counter, so later results are unchanged
- * (they never depend on the shape).  Synchronous. */
+/* Launch-shape tuner: times every valid (warps per block in {1..6, 8},
+ * interleave in {1, 2, 4}, warps per sample dividing the block) shape that
+ * gives each warp at least one full set of interleaved rows, on the given
+ * inputs (x0, V device; `replays` updates each), keeps the fastest and
+ * restores the update counter, so later results are unchanged (they never
+ * depend on the shape).  Synchronous. */
 int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays, float* best_ms);
 int ra_mppi_get_launch(ra_mppi_t* h, int32_t* warps_per_block, int32_t* ilp, int32_t* warps_per_sample);
 

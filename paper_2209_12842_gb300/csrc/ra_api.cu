@@ -597,9 +597,11 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   const int old_w = h->warps, old_i = h->ilp, old_g = h->wps;
   int bw = old_w, bi = old_i, bg = old_g;
   float best = 1e30f;
-  const int warps_c[] = {1, 2, 4, 8};
+  // warps per sample need not be a power of two: M = 300 has 10 rows of 32
+  // rollouts, which 5 warps split into one interleaved pair each
+  const int warps_c[] = {1, 2, 3, 4, 5, 6, 8};
   const int ilp_c[] = {1, 2, 4};
-  const int wps_c[] = {1, 2, 4, 8};
+  const int wps_c[] = {1, 2, 3, 4, 5, 6, 8};
   for (int w : warps_c) {
     for (int il : ilp_c)
     for (int g : wps_c) {

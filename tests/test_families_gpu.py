@@ -95,7 +95,8 @@ def test_risk_measures(mode):
 
 
 @pytest.mark.parametrize("M,launch", [(300, (4, 1, 4)), (300, (8, 2, 2)), (512, (8, 1, 8)), (512, (4, 4, 1)),
-                                      (100, (2, 1, 2))])
+                                      (100, (2, 1, 2)), (300, (5, 2, 5)), (300, (6, 2, 3)), (512, (3, 2, 3)),
+                                      (100, (6, 4, 1))])
 def test_large_M_and_warps_per_sample(M, launch):
     p = rs.preset("small_dyn", M=M, K=37)
     obs = _scene(p)
