@@ -309,8 +309,7 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   }
   cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaGetDevice(&h->device);
   const size_t K = (size_t)p->K, TN = (size_t)p->T * h->nu;
-  h->nb_upd = (int)std::min<size_t>((K + ramppi::kUpdateThreads - 1) / ramppi::kUpdateThreads,
-                                    (size_t)ramppi::kMaxUpdateBlocks);
+  h->nb_upd = ramppi::update_blocks((long long)K);
   if (e == cudaSuccess) e = dalloc(&h->U, K * TN);
   if (e == cudaSuccess) e = dalloc(&h->S, K);
   if (e == cudaSuccess) e = dalloc(&h->cvar, K);

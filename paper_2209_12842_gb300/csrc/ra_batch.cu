@@ -254,7 +254,7 @@ int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* 
     q.seed_lo = d.seed_lo;
     q.seed_hi = d.seed_hi;
     q.obs_cap = inst[i].max_obstacles;
-    q.nb_upd = std::min((q.K + ramppi::kUpdateThreads - 1) / ramppi::kUpdateThreads, ramppi::kMaxUpdateBlocks);
+    q.nb_upd = ramppi::update_blocks(q.K);
     q.upd_block_base = ub;
     q.x0_off = x0o;
     q.V_off = Vo;
