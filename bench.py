@@ -235,7 +235,7 @@ def run_ours(args, p, x0, V, obs):
     # execute v0+ on the simulated plant, warm start), from the state the loop
     # reaches after an untimed pre-roll, so the rollouts meet the obstacles.
     x_d = x0_d.clone()
-    hits = torch.zeros(1, dtype=torch.int32, device=dev)
+    hits = torch.zeros(2, dtype=torch.int32, device=dev)
     for i in range(args.preroll):
         ctl.closed_loop_step(x_d, V_d, hits)
     torch.cuda.synchronize()
@@ -338,6 +338,8 @@ def run_ours(args, p, x0, V, obs):
         }
         if world == 1 and not args.no_studies:
             line["closed_loop"] = closed_loop_study(torch, args.loop_updates)
+            line["closed_loop_paper_preset"] = closed_loop_study(
+                torch, args.loop_updates, "paper_sim", [("mppi", dict(A=0.0)), ("ra_alpha0.7", {})])
             line["batched"] = batched_study(torch, 10)
             line["adjoint"] = adjoint_study(torch, 10)
         if world == 1 and not args.no_cpu_baseline:
@@ -398,25 +400,29 @@ def ev_time(torch, fn, n, stream):
     return float(np.median(t)), float(np.percentile(t, 99))
 
 
-def closed_loop_study(torch, n_updates, alphas=(0.5, 0.9, 0.99), seeds=(12842, 12843, 12844)):
-    """Config 2's receding-horizon loop on the simulated plant: update rate
-    and plant collisions of RA-MPPI at each alpha and of plain MPPI (A = 0),
-    each over the same obstacle field with several noise seeds (the collision
-    count of one 1000-update run varies a lot with the noise)."""
+def closed_loop_study(torch, n_updates, preset="c2_closed_loop", runs=None, seeds=(12842, 12843, 12844)):
+    """Receding-horizon loop on the simulated plant (Alg. 1 outer loop): update
+    rate, plant steps inside an obstacle and steps off the track, for plain
+    MPPI (A = 0) and RA-MPPI, each over the same obstacle field with several
+    noise seeds (the counts of one 1000-update run vary a lot with the
+    noise).  Config 2 compares alpha in {0.5, 0.9, 0.99} with its risk cost
+    l = obstacle term; the paper's preset uses l = q (boundary, obstacles,
+    deviation) with A = 10, C_u = 0.6, alpha = 0.7."""
     from paper_2209_12842_gb300 import RaMppi
 
-    p0 = rs.preset("c2_closed_loop")
-    obs = rs.make_obstacles(p0["seed"], p0["n_obs"], *p0["obs_r"])
-    out = {"updates": n_updates, "seeds": list(seeds)}
-    runs = [("mppi", dict(A=0.0))] + [(f"ra_alpha{a}", dict(alpha=a)) for a in alphas]
+    p0 = rs.preset(preset)
+    obs = rs.scene_obstacles(p0)
+    out = {"preset": preset, "updates": n_updates, "seeds": list(seeds)}
+    if runs is None:
+        runs = [("mppi", dict(A=0.0))] + [(f"ra_alpha{a}", dict(alpha=a)) for a in (0.5, 0.9, 0.99)]
     for name, ov in runs:
-        hits_per_seed, hz, status = [], None, 0
+        hits_per_seed, exits_per_seed, hz, status = [], [], None, 0
         for seed in seeds:
-            p = rs.preset("c2_closed_loop", seed=seed, **ov)
+            p = rs.preset(preset, seed=seed, **ov)
             ctl = RaMppi(p, obs)
-            x = torch.from_numpy(rs.initial_state(p["model"])).cuda()
+            x = torch.from_numpy(rs.scene_initial_state(p)).cuda()
             V = torch.zeros((p["T"], 2), dtype=torch.float32, device="cuda")
-            hits = torch.zeros(1, dtype=torch.int32, device="cuda")
+            hits = torch.zeros(2, dtype=torch.int32, device="cuda")  # obstacle hits, track exits
             stream = torch.cuda.current_stream()
             b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -427,10 +433,13 @@ def closed_loop_study(torch, n_updates, alphas=(0.5, 0.9, 0.99), seeds=(12842, 1
             torch.cuda.synchronize()
             if hz is None:
                 hz = 1e3 * n_updates / b.elapsed_time(e)
-            hits_per_seed.append(int(hits.item()))
+            h2 = hits.cpu().numpy()
+            hits_per_seed.append(int(h2[0]))
+            exits_per_seed.append(int(h2[1]))
             status |= ctl.status()
             ctl.close()
-        out[name] = {"collisions": hits_per_seed, "collisions_mean": float(np.mean(hits_per_seed)),
+        out[name] = {"obstacle_hits": hits_per_seed, "obstacle_hits_mean": float(np.mean(hits_per_seed)),
+                     "track_exits": exits_per_seed, "track_exits_mean": float(np.mean(exits_per_seed)),
                      "update_hz": hz, "status": status}
     return out
 

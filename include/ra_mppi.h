@@ -212,8 +212,9 @@ int ra_mppi_step_host(ra_mppi_t* h, const float* x0_host, const float* V_in_host
  *   x          [nx]     device, in: plant state; out: next plant state
  *   V          [T][nu]  device, in: mean controls; out: next warm start
  *   S_tilde    [K]      device or NULL: receives the update's S~_k
- *   collisions [1]      device int32 or NULL: incremented when the new plant
- *                       state lies inside an obstacle or off the track
+ *   collisions [2]      device int32 or NULL: [0] incremented when the new
+ *                       plant state lies inside an obstacle (Eq. 22 with
+ *                       d < r), [1] when it is off the track (|e| > half width)
  * Enqueued on `stream` (three kernels), no synchronisation. */
 int ra_mppi_closed_loop_step(ra_mppi_t* h, float* x, float* V, float* S_tilde, int32_t* collisions,
                              int32_t shift, void* stream);

@@ -295,7 +295,7 @@ def plant_step(p, x, u, iteration, obs):
     xo = np.zeros(6)
     hit = lib().orc_plant_step(ctypes.byref(prob), int(iteration), _ptr(x), _ptr(u), _ptr(o),
                                int(len(o)), _ptr(xo))
-    return xo[: len(x)], int(hit)
+    return xo[: len(x)], np.array([hit & 1, (hit >> 1) & 1])
 
 
 def closed_loop(p, x0, V0, obs, n_updates, shift=True, iteration0=0, n_threads=1):
@@ -303,11 +303,13 @@ def closed_loop(p, x0, V0, obs, n_updates, shift=True, iteration0=0, n_threads=1
 
     Each iteration: update from the current plant state, apply v0+ to the
     plant (its own noise stream), then warm-start V from V+ (shifted left by
-    one step with the last control repeated when `shift`).
+    one step with the last control repeated when `shift`).  Returns the
+    states, the V+ sequence and the counts (steps inside an obstacle, steps
+    off the track).
     """
     x = np.asarray(x0, dtype=np.float64).copy()
     V = np.asarray(V0, dtype=np.float64).copy()
-    xs, Vs, hits = [x.copy()], [], 0
+    xs, Vs, hits = [x.copy()], [], np.zeros(2, dtype=np.int64)
     for n in range(n_updates):
         it = iteration0 + n
         out = step(p, x.astype(np.float32), V.astype(np.float32), obs, it, n_threads=n_threads)

@@ -552,7 +552,7 @@ int32_t orc_update(int32_t K, int32_t T, int32_t nu, double lam, const double* S
 /* Simulated plant for the receding-horizon loop (Alg. 1 outer loop)    */
 /* ------------------------------------------------------------------ */
 /* x_out = F(x, u) + w with the plant's own noise stream at `iteration`;
- * returns 1 when x_out is a collision (inside an obstacle or off track) */
+ * returns bit 0 when x_out is inside an obstacle, bit 1 when it is off the track */
 int32_t orc_plant_step(const orc_problem* p, uint64_t iteration, const double* x, const double* u,
                        const double* obs, int32_t n_obs, double* x_out) {
   int nx = nx_of(p->model);
@@ -564,10 +564,10 @@ int32_t orc_plant_step(const orc_problem* p, uint64_t iteration, const double* x
   if (p->model == ORC_LIN) return 0;
   double tr[3];
   orc_track(p, xn[0], xn[1], tr);
-  int hit = fabs(tr[0]) > p->track_half_width;
+  int hit = fabs(tr[0]) > p->track_half_width ? 2 : 0;
   for (int i = 0; i < n_obs; ++i) {
     double dx = xn[0] - obs[3 * i], dy = xn[1] - obs[3 * i + 1];
-    if (sqrt(dx * dx + dy * dy) < obs[3 * i + 2]) hit = 1;
+    if (sqrt(dx * dx + dy * dy) < obs[3 * i + 2]) hit |= 1;
   }
   return hit;
 }

@@ -69,8 +69,12 @@ class RaMppi:
 
     def closed_loop_step(self, x, V, collisions=None, shift=True, stream=None):
         """One receding-horizon iteration on a simulated plant; x and V are
-        device tensors updated in place (plant state, warm start)."""
+        device tensors updated in place (plant state, warm start).
+        `collisions`, if given, is an int32 device tensor of 2 counters:
+        steps inside an obstacle and steps off the track."""
         assert x.is_cuda and V.is_cuda and x.is_contiguous() and V.is_contiguous()
+        assert collisions is None or (collisions.is_cuda and collisions.dtype == torch.int32
+                                      and collisions.numel() >= 2)
         B.ra_mppi_closed_loop_step(self.h, x.data_ptr(), V.data_ptr(), self.S_tilde.data_ptr(),
                                    collisions.data_ptr() if collisions is not None else None,
                                    1 if shift else 0, _stream_ptr(stream))

@@ -241,26 +241,31 @@ size_t rollout_smem(const ra_mppi* h) {
 cudaError_t prepare(ra_mppi* h) {
   h->smem = rollout_smem(h);
   const int m = h->prob.model < 0 || h->prob.model > 2 ? 2 : h->prob.model;
-  std::lock_guard<std::mutex> lock(g_smem_mutex);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-  if (h->smem <= g_smem_limit[dev][m]) return cudaSuccess;
-  cudaError_t e;
-  switch (m) {
-    case 0: e = ramppi::prepare_rollout<0>(h->smem); break;
-    case 1: e = ramppi::prepare_rollout<1>(h->smem); break;
-    default: e = ramppi::prepare_rollout<2>(h->smem); break;
+  {
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    if (h->smem > g_smem_limit[dev][m]) {
+      cudaError_t e;
+      switch (m) {
+        case 0: e = ramppi::prepare_rollout<0>(h->smem); break;
+        case 1: e = ramppi::prepare_rollout<1>(h->smem); break;
+        default: e = ramppi::prepare_rollout<2>(h->smem); break;
+      }
+      if (e != cudaSuccess) return e;
+      g_smem_limit[dev][m] = h->smem;
+    }
   }
-  if (e == cudaSuccess) g_smem_limit[dev][m] = h->smem;
-  return e;
+  return cudaSuccess;
 }
 
-// largest interleave in {4, 2, 1} that divides the rollouts per lane
+// largest interleave in {2, 1} that divides the rollouts per lane
 int default_ilp(int M, int model) {
   const int R = (M + 31) / 32;
-  // measured on GB300: the dynamic model is register-bound (no interleave is
-  // fastest), the kinematic model gains from 2
-  const int cap = model == RA_MPPI_DYN_SINGLE_TRACK ? 1 : 2;
+  // measured on GB300: both models are fastest with 2 (the dynamic one steps
+  // the pair in paired FP32 instructions); 4 costs registers
+  (void)model;
+  const int cap = 2;
   for (int ilp = cap; ilp > 1; ilp >>= 1)
     if (R % ilp == 0) return ilp;
   return 1;
@@ -431,6 +436,7 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
   a.wps = h->wps;
   const int spb = h->warps / h->wps;
   const int nb_dist = (p.K + spb - 1) / spb;
+  const int grid = a.nb_nom + nb_dist;
   cudaError_t e;
   if (h->keep_x0 != nullptr) {
     e = cudaMemcpyAsync(h->keep_x0, x0, sizeof(float) * h->nx, cudaMemcpyDeviceToDevice, s);
@@ -443,9 +449,9 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
     if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
   }
   switch (p.model) {
-    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, h->smem, a.nb_nom + nb_dist, s); break;
-    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, h->smem, a.nb_nom + nb_dist, s); break;
-    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, h->smem, a.nb_nom + nb_dist, s); break;
+    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, h->smem, grid, s); break;
+    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, h->smem, grid, s); break;
+    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, h->smem, grid, s); break;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
   if (h->ev_end != nullptr) {

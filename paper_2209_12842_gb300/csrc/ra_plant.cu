@@ -1,7 +1,7 @@
 // Simulated plant of the receding-horizon loop (Algorithm 1, outer loop):
 // execute the first control of V+ on x~_{n+1} = F(x~_n, v0+) + w_n with the
-// plant's own noise stream, count a collision when the new state is inside an
-// obstacle or off the track, and warm-start the next update from V+ (shifted
+// plant's own noise stream, count the steps whose new state is inside an
+// obstacle and those off the track, and warm-start the next update from V+ (shifted
 // left by one step, the last control repeated, when `shift` is set).
 #include "ra_kernels.h"
 
@@ -11,8 +11,10 @@ template <int MODEL>
 __global__ void plant_step_kernel(const DevParams p, const float4* __restrict__ obs, DevState* st,
                                   float* __restrict__ x, const float* __restrict__ V_plus,
                                   float* __restrict__ V_next, int* __restrict__ collisions, int shift) {
+  // one warp: every lane steps the same state (no divergence, no broadcast
+  // needed), then the lanes split the obstacle test and the warm-start copy
   using Md = Model<MODEL>;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int lane = threadIdx.x;
   // the update that produced V+ has already advanced the counter: the plant
   // step belongs to the iteration before it
   const uint32_t iter = (uint32_t)(st->iteration - 1ull);
@@ -24,19 +26,28 @@ __global__ void plant_step_kernel(const DevParams p, const float4* __restrict__ 
   const float u1 = Md::NU > 1 ? V_plus[1] : 0.0f;
   Md::step(p, s, Md::ctl(p, u0, u1));
   add_process_noise<MODEL>(p, k0, k1, 0u, 0xFFFFFFFEu, 0xFFFFFFFFu, p.instance, s);
-#pragma unroll
-  for (int i = 0; i < Md::NX; ++i) x[i] = s[i];
   if (MODEL != 2 && collisions != nullptr) {
-    bool hit = fabsf(track_e(p, s[0], s[1])) > p.track_hw;
+    bool hit = false;
     const int n_obs = st->n_obs;
-    for (int i = 0; i < n_obs; ++i) {
-      const float dx = s[0] - obs[i].x, dy = s[1] - obs[i].y;
-      hit |= fmaf(dx, dx, dy * dy) < obs[i].w;
+    for (int i = lane; i < n_obs; i += 32) {
+      const float4 o = obs[i];
+      const float dx = s[0] - o.x, dy = s[1] - o.y;
+      hit |= fmaf(dx, dx, dy * dy) < o.w;
     }
-    if (hit) atomicAdd(collisions, 1);
+    hit = __any_sync(0xFFFFFFFFu, hit);
+    const bool off = fabsf(track_e(p, s[0], s[1])) > p.track_hw;
+    if (lane == 0) {
+      if (hit) atomicAdd(collisions, 1);      // inside an obstacle
+      if (off) atomicAdd(collisions + 1, 1);  // off the track
+    }
+  }
+  __syncwarp();  // every lane has read x before lane 0 overwrites it
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < Md::NX; ++i) x[i] = s[i];
   }
   const int TN = p.T * p.nu;
-  for (int c = 0; c < TN; ++c) {
+  for (int c = lane; c < TN; c += 32) {
     const int src = (shift && c + p.nu < TN) ? c + p.nu : c;
     V_next[c] = V_plus[src];
   }

@@ -402,6 +402,8 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
     return;
   }
   // disturbed blocks: G = a.wps warps per sample, warps / G samples per block
+  // (the hardware hands out blocks as SM slots free up; a persistent grid
+  // taking samples from a counter was slower: its per-unit barriers cost more)
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = a.wps, spb = warps / G, gi = w / G, g = w - gi * G;
   const int k = ((int)blockIdx.x - a.nb_nom) * spb + gi;

@@ -168,17 +168,20 @@ __device__ __forceinline__ void update_block(const DevParams& p, const UpdateArg
   if (!is_last) return;
   __threadfence();
 
-  // rescale each block's partials to the global minimum: exp(-(m_b - m) / lambda)
+  // rescale each block's partials to the global minimum: exp(-(m_b - m) / lambda).
+  // The other blocks' partials are read through L2 (ld.global.cg): they were
+  // stored before those blocks' fence and arrival, and L1 may hold nothing
+  // newer; unlike volatile loads these can be in flight together.
   const int nb = nblocks;
   const int stride = 2 + TN;
-  const volatile float* parts = a.partials;
+  const float* parts = a.partials;
   float m = __int_as_float(0x7F800000);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fminf(m, parts[(size_t)b * stride]);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fminf(m, __ldcg(parts + (size_t)b * stride));
   m = block_min(m, red);
   double s_loc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    const float mbb = parts[(size_t)b * stride];
-    const float sbb = parts[(size_t)b * stride + 1];
+    const float mbb = __ldcg(parts + (size_t)b * stride);
+    const float sbb = __ldcg(parts + (size_t)b * stride + 1);
     const float sc = (isfinite(mbb) && sbb > 0.0f) ? expf((m - mbb) * p.inv_lambda) : 0.0f;
     scale_s[b] = sc;
     s_loc += (double)sbb * (double)sc;
@@ -188,9 +191,11 @@ __device__ __forceinline__ void update_block(const DevParams& p, const UpdateArg
   const bool ok = isfinite(m) && s_tot > 0.0 && isfinite(s_tot);
   for (int col = threadIdx.x; col < TN; col += blockDim.x) {
     float y = 0.0f, yc = 0.0f;
+#pragma unroll 8
     for (int b = 0; b < nb; ++b) {
       const float sc = scale_s[b];
-      if (sc != 0.0f) neumaier_add(y, yc, parts[(size_t)b * stride + 2 + col] * sc);
+      const float v = __ldcg(parts + (size_t)b * stride + 2 + col);
+      if (sc != 0.0f) neumaier_add(y, yc, v * sc);
     }
     if (ok) a.V_out[col] = (float)(((double)y + (double)yc) / s_tot);
   }

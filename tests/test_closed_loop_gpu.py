@@ -38,7 +38,7 @@ def _run(name, n_updates, shift, obs, **ov):
     ctl = RaMppi(p, obs)
     x = torch.from_numpy(rs.initial_state(p["model"])).cuda()
     V = torch.from_numpy(rs.zero_controls(p["model"], p["T"])).cuda()
-    hits = torch.zeros(1, dtype=torch.int32, device="cuda")
+    hits = torch.zeros(2, dtype=torch.int32, device="cuda")  # obstacle hits, track exits
     rec = []
     for n in range(n_updates):
         x_n, V_n = x.cpu().numpy().copy(), V.cpu().numpy().copy()
@@ -49,7 +49,7 @@ def _run(name, n_updates, shift, obs, **ov):
                         S_tilde=ctl.S_tilde.cpu().numpy(), U=ws["U"].cpu().numpy()))
     status = ctl.status()
     ctl.close()
-    return p, rec, int(hits.item()), status
+    return p, rec, hits.cpu().numpy(), status
 
 
 @pytest.mark.parametrize("name,shift", [("small_kin", True), ("small_kin", False), ("small_dyn", True)])
@@ -60,7 +60,7 @@ def test_closed_loop_replayed_stagewise(name, shift):
     p, rec, hits, status = _run(name, 10, shift, obs, K=96, M=32)
     assert status == 0
     lam = float(np.float32(p["lam"]))
-    want_hits = 0
+    want_hits = np.zeros(2, dtype=np.int64)
     for n, r in enumerate(rec):
         ref = oracle.samples(p, r["x"], r["V"], obs, iteration=n, n_threads=8)
         check_banded("S_tilde", r["S_tilde"], ref["S_tilde"], ref["St_lo"], ref["St_hi"])
@@ -70,7 +70,7 @@ def test_closed_loop_replayed_stagewise(name, shift):
         x_ref, hit = oracle.plant_step(p, r["x"].astype(np.float64), Vp[0], n, obs)
         np.testing.assert_allclose(r["x_next"], x_ref, rtol=1e-4, atol=1e-5)
         want_hits += hit
-    assert hits == want_hits
+    np.testing.assert_array_equal(hits, want_hits)
     # the plant moved (with obstacles just ahead the controller may back off)
     assert np.linalg.norm(rec[-1]["x_next"][:2] - rec[0]["x"][:2]) > 0.01
 
@@ -84,7 +84,7 @@ def test_closed_loop_is_deterministic_and_resumable():
     for a, b in zip(rec_a, rec_b):
         np.testing.assert_array_equal(a["x_next"], b["x_next"])
         np.testing.assert_array_equal(a["V_next"], b["V_next"])
-    assert hits_a == hits_b
+    np.testing.assert_array_equal(hits_a, hits_b)
     # resume at iteration 3 from the recorded state and warm start
     ctl = RaMppi(p, obs)
     ctl.iteration = 3
