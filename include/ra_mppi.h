@@ -269,8 +269,8 @@ int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta);
  * 6, 9, 20-23; states recomputed from checkpoints every 8 steps), and of the
  * clip U = clip(V + eps) (Alg. 1).  The obstacle indicator (Eq. 22) has
  * zero derivative; use the softplus barrier to differentiate through
- * obstacles.  Needs RA_MPPI_DIFFERENTIABLE; the kinematic and linear models
- * only (EUNSUPPORTED for the dynamic model).  Enqueued on `stream`. */
+ * obstacles.  Needs RA_MPPI_DIFFERENTIABLE; all three models (the dynamic
+ * one through its Heun sub-steps).  Enqueued on `stream`. */
 int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, float* gV, float* gtheta,
                      void* stream);
 

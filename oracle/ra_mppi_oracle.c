@@ -601,8 +601,8 @@ int32_t orc_n_warm(const orc_problem* p) { return n_warm_of(p); }
 /*             for the samples drawn around V; the control cost            */
 /*             gamma v' Sigma^-1 u depends on V directly as well.          */
 /* The indicator obstacle term has zero derivative almost everywhere.    */
-/* Only the kinematic and linear models are differentiated (returns -6   */
-/* for the dynamic model).                                               */
+/* The dynamic model's Heun sub-steps are reversed with the analytic     */
+/* Jacobian of its derivative (slip angles, Pacejka forces, heading).    */
 /* ------------------------------------------------------------------ */
 
 /* gradient of the track deviation e and arc length s w.r.t. (px, py) */
@@ -675,12 +675,70 @@ static void state_cost_grad(const orc_problem* p, const double* x, const double*
   if (mask & ORC_R_LIN) gx[0] += c * p->c_lin;
 }
 
-/* one integration sub-step G of the kinematic / linear model and its
- * transposed Jacobians applied to lam: lam_out = (dG/ds)' lam, gu += (dG/du)' lam */
+/* transposed Jacobians of the dynamic model's derivative f(x, u) applied to
+ * fb: xb += (df/dx)' fb, ub += (df/du)' fb (the same formulas as dyn_deriv) */
+static void dyn_deriv_vjp(const double* mp, const double* x, const double* u, const double* fb, double* xb,
+                          double* ub) {
+  const double m = mp[0], Iz = mp[1], lf = mp[2], lr = mp[3];
+  const double Bt = mp[4], Ct = mp[5], Dt = mp[6], vfloor = mp[7];
+  const double g = 9.81;
+  const double psi = x[2], vx = x[3], vy = x[4], r = x[5];
+  const double delta = u[0];
+  const double Fzf = m * g * lr / (lf + lr), Fzr = m * g * lf / (lf + lr);
+  const double vxs = vx > vfloor ? vx : vfloor;
+  const double yf = vy + lf * r, yr = vy - lr * r;
+  const double af = delta - atan2(yf, vxs), ar = -atan2(yr, vxs);
+  const double Fyf = Dt * Fzf * sin(Ct * atan(Bt * af));
+  const double Fyr = Dt * Fzr * sin(Ct * atan(Bt * ar));
+  /* dF/dalpha = D Fz cos(C atan(B a)) C B / (1 + (B a)^2) */
+  const double dFf = Dt * Fzf * cos(Ct * atan(Bt * af)) * Ct * Bt / (1.0 + Bt * af * Bt * af);
+  const double dFr = Dt * Fzr * cos(Ct * atan(Bt * ar)) * Ct * Bt / (1.0 + Bt * ar * Bt * ar);
+  const double cp = cos(psi), sp = sin(psi), cd = cos(delta), sd = sin(delta);
+  /* f0 = vx cos psi - vy sin psi, f1 = vx sin psi + vy cos psi, f2 = r */
+  xb[2] += fb[0] * (-vx * sp - vy * cp) + fb[1] * (vx * cp - vy * sp);
+  xb[3] += fb[0] * cp + fb[1] * sp;
+  xb[4] += -fb[0] * sp + fb[1] * cp;
+  xb[5] += fb[2];
+  /* f3 = a - Fyf sin d / m + r vy */
+  ub[1] += fb[3];
+  xb[5] += fb[3] * vy;
+  xb[4] += fb[3] * r;
+  /* f4 = (Fyf cos d + Fyr) / m - r vx */
+  xb[5] += -fb[4] * vx;
+  xb[3] += -fb[4] * r;
+  /* forces and steer through f3, f4, f5 = (lf Fyf cos d - lr Fyr) / Iz */
+  const double Ffb = -fb[3] * sd / m + fb[4] * cd / m + fb[5] * lf * cd / Iz;
+  const double Frb = fb[4] / m - fb[5] * lr / Iz;
+  ub[0] += -fb[3] * Fyf * cd / m - fb[4] * Fyf * sd / m - fb[5] * lf * Fyf * sd / Iz;
+  const double afb = Ffb * dFf, arb = Frb * dFr;
+  ub[0] += afb;
+  /* alpha_f = d - atan2(yf, vxs), alpha_r = -atan2(yr, vxs) */
+  const double nf = vxs * vxs + yf * yf, nr = vxs * vxs + yr * yr;
+  const double yfb = afb * (-vxs / nf), yrb = arb * (-vxs / nr);
+  const double vxsb = afb * (yf / nf) + arb * (yr / nr);
+  xb[4] += yfb + yrb;
+  xb[5] += lf * yfb - lr * yrb;
+  if (vx > vfloor) xb[3] += vxsb;
+}
+
+/* one integration sub-step G and its transposed Jacobians applied to lam:
+ * lam_out = (dG/ds)' lam, gu += (dG/du)' lam */
 static void substep_vjp(const orc_problem* p, const double* s, const double* u, const double* lam,
                         double* lam_out, double* gu) {
   double h = p->dt / (p->substeps > 0 ? p->substeps : 1);
-  if (p->model == ORC_KIN) {
+  if (p->model == ORC_DYN) {
+    /* Heun: x1 = s + h f(s), G = s + h/2 (f(s) + f(x1)) */
+    double k1[6], x1[6];
+    dyn_deriv(p->model_params, s, u, k1);
+    for (int i = 0; i < 6; ++i) x1[i] = s[i] + h * k1[i];
+    double fb[6], x1b[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 6; ++i) fb[i] = 0.5 * h * lam[i];
+    dyn_deriv_vjp(p->model_params, x1, u, fb, x1b, gu);   /* through f(x1) */
+    double fa[6];
+    for (int i = 0; i < 6; ++i) fa[i] = 0.5 * h * lam[i] + h * x1b[i];
+    for (int i = 0; i < 6; ++i) lam_out[i] = lam[i] + x1b[i];
+    dyn_deriv_vjp(p->model_params, s, u, fa, lam_out, gu);  /* through f(s) */
+  } else if (p->model == ORC_KIN) {
     double L = p->model_params[0], psi = s[2], v = s[3];
     double cs = cos(psi), sn = sin(psi), tn = tan(u[0]), sec2 = 1.0 / (cos(u[0]) * cos(u[0]));
     lam_out[0] = lam[0];
@@ -736,7 +794,6 @@ static void rollout_vjp(const orc_problem* p, const double* xs, const double* Uk
 
 int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, const double* obs, int32_t n_obs,
                      const double* gVp, const double* gSt, double* gV, double* gtheta) {
-  if (p->model == ORC_DYN) return -6;
   if (p->substeps > 64) return -1;
   const int K = p->K, M = p->M, T = p->T, nx = nx_of(p->model), nu = nu_of(p->model);
   const int n_warm = n_warm_of(p);

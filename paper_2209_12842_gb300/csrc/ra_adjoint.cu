@@ -20,8 +20,9 @@
 //                depends on V directly as well.
 // Three launches: prep (d_k, w^_k, c), main (nominal blocks + one warp per
 // sample for the disturbed rollouts), reduce (sum over samples, clip mask).
-// The kinematic and linear models are differentiated; the indicator
-// obstacle term has zero derivative almost everywhere.
+// All three models are differentiated (the dynamic one through its Heun
+// sub-steps); the indicator obstacle term has zero derivative almost
+// everywhere.
 #include "ra_kernels.h"
 
 namespace ramppi {
@@ -121,6 +122,49 @@ __device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, un
   if (mask & 16u) g[0] = fmaf(c, p.c_lin, g[0]);
 }
 
+// Transposed Jacobians of the dynamic model's derivative f(x, u) at x
+// applied to fb: xb += (df/dx)' fb, gu += (df/du)' fb with u = (steer, accel).
+// The same formulas as the forward: slip angles atan(y / max(vx, floor)),
+// lateral accelerations k sin(C atan(B alpha)) (k = D Fz / m), yaw arms
+// l m / Iz; the derivative values use the library atan, sin and cos.
+__device__ __forceinline__ void dyn_deriv_vjp(const DevParams& p, const float* x, const float4 c, const float* fb,
+                                              float* xb, float* gu) {
+  const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], C = p.mp[5], vfloor = p.mp[7];
+  const float sq2 = p.pacejka_c15 ? 1.41421356237f : 1.0f;  // undo the fold of the closed form
+  const float kf = p.acc_f * sq2, kr = p.acc_r * sq2;
+  const float psi = x[2], vx = x[3], vy = x[4], r = x[5];
+  const float sd = c.z, cd = c.w;
+  const float vxs = fmaxf(vx, vfloor);
+  const float yf = fmaf(lf, r, vy), yr = fmaf(-lr, r, vy);
+  const float tf = atanf(yf / vxs), tr = atanf(yr / vxs);
+  const float zf = fmaf(-Bt, tf, c.x), zr = -Bt * tr;
+  const float qf = C * atanf(zf), qr = C * atanf(zr);
+  const float ayf = kf * sinf(qf), ayr = kr * sinf(qr);
+  const float dsf = C * cosf(qf) / fmaf(zf, zf, 1.0f), dsr = C * cosf(qr) / fmaf(zr, zr, 1.0f);
+  float sp, cp;
+  sincosf(psi, &sp, &cp);
+  // f0 = vx cos psi - vy sin psi, f1 = vx sin psi + vy cos psi, f2 = r
+  xb[2] += fb[0] * (-vx * sp - vy * cp) + fb[1] * (vx * cp - vy * sp);
+  xb[3] += fb[0] * cp + fb[1] * sp - fb[4] * r;
+  xb[4] += -fb[0] * sp + fb[1] * cp + fb[3] * r;
+  xb[5] += fb[2] + fb[3] * vy - fb[4] * vx;
+  // f3 = a - ayf sin d + r vy, f4 = ayf cos d + ayr - r vx, f5 = yaw_f ayf cos d - yaw_r ayr
+  gu[1] += fb[3];
+  const float ayfb = -fb[3] * sd + fb[4] * cd + fb[5] * p.yaw_f * cd;
+  const float ayrb = fb[4] - fb[5] * p.yaw_r;
+  gu[0] += -fb[3] * ayf * cd - fb[4] * ayf * sd - fb[5] * p.yaw_f * ayf * sd;
+  // z_f = B (steer - atan_f), z_r = -B atan_r
+  const float zfb = ayfb * kf * dsf, zrb = ayrb * kr * dsr;
+  gu[0] += Bt * zfb;
+  const float tfb = -Bt * zfb, trb = -Bt * zrb;
+  const float nf = fmaf(vxs, vxs, yf * yf), nr = fmaf(vxs, vxs, yr * yr);
+  const float yfb = tfb * vxs / nf, yrb = trb * vxs / nr;
+  const float vxsb = -tfb * yf / nf - trb * yr / nr;
+  xb[4] += yfb + yrb;
+  xb[5] += lf * yfb - lr * yrb;
+  if (vx > vfloor) xb[3] += vxsb;
+}
+
 // (dG/ds)' lam and (dG/du)' lam of one integration sub-step G at state s
 template <int MODEL>
 __device__ __forceinline__ void substep_vjp(const DevParams& p, const float* s, const float4 c, float* lam,
@@ -136,6 +180,23 @@ __device__ __forceinline__ void substep_vjp(const DevParams& p, const float* s, 
     lam[3] = l3 + h * (cp * l0 + sp * l1 + c.z * l2);
     gu[0] = fmaf(l2 * h * v, sec2_over_L, gu[0]);
     gu[1] = fmaf(l3, h, gu[1]);
+  } else if (MODEL == 1) {
+    // Heun: x1 = s + h f(s), G = s + h/2 (f(s) + f(x1)); x1 recomputed as the forward does
+    float k1[6], x1[6];
+    Model<1>::deriv<float>(p, s, c, k1);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x1[i] = __fmaf_rn(p.h, k1[i], s[i]);
+    float fb[6], x1b[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) fb[i] = 0.5f * p.h * lam[i];
+    dyn_deriv_vjp(p, x1, c, fb, x1b, gu);  // through f(x1)
+    float fa[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      fa[i] = fmaf(p.h, x1b[i], fb[i]);  // f(s) enters G with h/2 and x1 with h
+      lam[i] += x1b[i];
+    }
+    dyn_deriv_vjp(p, s, c, fa, lam, gu);  // through f(s)
   } else {
     gu[0] = fmaf(lam[0], p.h, gu[0]);
   }
@@ -501,6 +562,9 @@ cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int
   if (model == 0) {
     e = cudaFuncSetAttribute(bwd_main_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) bwd_main_kernel<0><<<grid, 128, smem, s>>>(p, a);
+  } else if (model == 1) {
+    e = cudaFuncSetAttribute(bwd_main_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) bwd_main_kernel<1><<<grid, 128, smem, s>>>(p, a);
   } else {
     e = cudaFuncSetAttribute(bwd_main_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) bwd_main_kernel<2><<<grid, 128, smem, s>>>(p, a);

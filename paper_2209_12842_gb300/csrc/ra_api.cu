@@ -670,8 +670,6 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   if (gV_plus == nullptr || gV == nullptr || gtheta == nullptr)
     return fail(h, RA_MPPI_EINVAL, "gV_plus, gV and gtheta are required");
   if (h->keep_x0 == nullptr) return fail(h, RA_MPPI_EINVAL, "the problem was created without RA_MPPI_DIFFERENTIABLE");
-  if (h->prob.model == RA_MPPI_DYN_SINGLE_TRACK)
-    return fail(h, RA_MPPI_EUNSUPPORTED, "the adjoint covers the kinematic and linear models");
   const ra_mppi_problem& p = h->prob;
   ramppi::BwdArgs a{};
   a.x0 = h->keep_x0;

@@ -300,18 +300,24 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     f[4] = vfma(r, vneg(vx), vfma(ay_f, bc<T>(c.w), ay_r));
     f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(-p.yaw_r), ay_r));
   }
+  // one Heun sub-step of size h
+  template <class T>
+  __device__ static __forceinline__ void substep_t(const DevParams& p, T* x, const float4 c) {
+    T k1[6], k2[6], xp[6];
+    deriv<T>(p, x, c, k1);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xp[i] = vfma(bc<T>(p.h), k1[i], x[i]);
+    deriv<T>(p, xp, c, k2);
+    const float hh = 0.5f * p.h;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), vadd(k1[i], k2[i]), x[i]);
+  }
   template <class T>
   __device__ static __forceinline__ void step_t(const DevParams& p, T* x, const float4 c) {
-    for (int s = 0; s < p.substeps; ++s) {
-      T k1[6], k2[6], xp[6];
-      deriv<T>(p, x, c, k1);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) xp[i] = vfma(bc<T>(p.h), k1[i], x[i]);
-      deriv<T>(p, xp, c, k2);
-      const float hh = 0.5f * p.h;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), vadd(k1[i], k2[i]), x[i]);
-    }
+    for (int s = 0; s < p.substeps; ++s) substep_t<T>(p, x, c);
+  }
+  __device__ static __forceinline__ void substep(const DevParams& p, float* x, const float4 c) {
+    substep_t<float>(p, x, c);
   }
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
     step_t<float>(p, x, c);

@@ -103,15 +103,32 @@ def test_autograd_function_matches_backward():
     ctl.close()
 
 
-def test_adjoint_rejects_dynamic_model_and_missing_flag():
+@pytest.mark.parametrize("case", ["mixture_C15", "gauss_C13", "all_terms"])
+def test_adjoint_dynamic_model(case):
+    # reverse sweeps through the Heun sub-steps of the dynamic single-track model
+    mp = list(rs.preset("small_dyn")["model_params"])
+    ov = dict(K=96, M=32, T=10, obs_mode=rs.OBS_SOFTPLUS, kappa=20.0, w_obs=5.0,
+              risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED)
+    if case == "gauss_C13":
+        mp[5] = 1.3
+        ov.update(noise_type=rs.NOISE_GAUSS, w_scale=(0.05, 0.05, 0.05, 0.0))
+    elif case == "all_terms":
+        ov.update(risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED | rs.RISK_BDRY, w_bdry=2.0, c4=0.6, c5=2.0,
+                  B=1.5, eta=0.2)
+    p = rs.preset("small_dyn", model_params=tuple(mp), **ov)
+    obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.1, x_to=1.2, lateral=0.4)
+    x0 = np.array([0.0, -4.0, 0.05, 2.0, 0.1, 0.3], np.float32)
+    V = rs.random_controls(1, p["T"], p["u_lo"], p["u_hi"], 3)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    gV, gth = _run(p, obs, x0, V, gVp, gS)
+    rV, rth = oracle.backward(p, x0, V, obs, gVp, gS)
+    _close("gV", gV, rV)
+    _close("gtheta", gth, rth)
+
+
+def test_adjoint_rejects_missing_flag():
     from paper_2209_12842_gb300 import RaMppi, RaMppiError
 
-    p = rs.preset("small_dyn")
-    ctl = RaMppi(p, rs.obstacles_ahead(1, 4, 0.2, 0.3), differentiable=True)
-    ctl.step(torch.from_numpy(rs.initial_state(1)).cuda(), torch.zeros(p["T"], 2, device="cuda"))
-    with pytest.raises(RaMppiError):
-        ctl.backward(torch.ones(p["T"], 2, device="cuda"))
-    ctl.close()
     q = rs.preset("small_kin")
     ctl = RaMppi(q, rs.obstacles_ahead(1, 4, 0.2, 0.3))
     ctl.step(torch.from_numpy(rs.initial_state(0)).cuda(), torch.zeros(q["T"], 2, device="cuda"))

@@ -1,6 +1,7 @@
 """Pins of the oracle's analytic adjoint (CPU only).
 
-P11: the vector-Jacobian product of one update (gradients of
+P11: the vector-Jacobian product of one update, for the kinematic, the
+dynamic single-track and the linear models (gradients of
 <gV+, V+> + <gS~, S~> w.r.t. the mean controls V and the cost weights
 theta = (w_dev, w_speed, gamma, w_obs)) against central finite differences
 of the oracle's own forward pass in float64.  A component is compared only
@@ -54,6 +55,22 @@ def test_p11_kinematic_softplus(orc, mode, B):
     assert np.all(np.isfinite(gV)) and np.any(gth != 0)
 
 
+@pytest.mark.parametrize("noise,C", [(rs.NOISE_LAPLACE_MIX, 1.5), (rs.NOISE_GAUSS, 1.3)])
+def test_p11_dynamic_single_track(orc, noise, C):
+    # the dynamic model's Heun sub-steps (slip angles, Pacejka forces,
+    # heading), softplus obstacles, deviation and speed in the risk cost
+    mp = list(rs.preset("small_dyn")["model_params"])
+    mp[5] = C
+    p = rs.preset("small_dyn", K=10, M=6, T=5, substeps=3, obs_mode=rs.OBS_SOFTPLUS, kappa=20.0, w_obs=5.0,
+                  noise_type=noise, model_params=tuple(mp), risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED)
+    obs = rs.obstacles_ahead(2, 6, 0.15, 0.3, x_from=0.05, x_to=0.6, lateral=0.3)
+    x0 = np.array([0.0, -4.0, 0.05, 2.0, 0.1, 0.3])
+    V = rs.random_controls(1, p["T"], p["u_lo"], p["u_hi"], 4).astype(np.float64)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 9)
+    gV, gth = _fd_check(orc, p, x0, V, obs, gVp, gS)
+    assert np.all(np.isfinite(gV)) and np.any(gV != 0)
+
+
 def test_p11_all_terms_and_zero_mean_samples(orc):
     p = rs.preset("c4_gradient", K=10, M=6, T=5, eta=0.3, w_bdry=2.0, c4=0.6, c5=2.0, A=2.0, C_u=10.0,
                   risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED | rs.RISK_BDRY)
@@ -75,7 +92,8 @@ def test_p11_linear_closed_form(orc):
     np.testing.assert_allclose(gV, gVp, rtol=1e-12)
 
 
-def test_dynamic_model_is_reported_unsupported(orc):
-    p = rs.preset("small_dyn", K=2, M=2, T=2)
+def test_too_many_substeps_is_reported(orc):
+    # the reverse sweep keeps at most 64 sub-step states per control step
+    p = rs.preset("small_dyn", K=2, M=2, T=2, substeps=65)
     with pytest.raises(RuntimeError):
         orc.backward(p, rs.initial_state(1), rs.zero_controls(1, 2), np.zeros((0, 3)), np.ones((2, 2)))
