@@ -6,12 +6,14 @@
 //   - nominal: one thread per sample k draws its control sequence, writes
 //     U^k to HBM and rolls it out on the nominal dynamics with the full
 //     running cost q, giving S_k (Eq. 3);
-//   - disturbed: one warp per sample k; the lanes redraw U^k into shared
-//     memory (same counter, same bits), then each lane runs the rollouts
-//     m = lane + 32 r on x~_{t+1} = F(x~_t, u_t) + w_t, ILP of them
-//     interleaved, with states and noise in registers, and stores the M risk
-//     costs L_{k,m} (Eq. 9) in shared memory; the warp then forms CVaR_k by a
-//     radix select of VaR = L_(j) and warp reductions of the tail.
+//   - disturbed: G warps per sample k (G = 1 by default); the lanes redraw
+//     U^k into shared memory (same counter, same bits), then each lane runs
+//     the rollouts m = lane + 32 r of its warp's rows r on
+//     x~_{t+1} = F(x~_t, u_t) + w_t, ILP of them interleaved (two by two in
+//     paired FP32 instructions for the dynamic model), with states and noise
+//     in registers, and stores the M risk costs L_{k,m} (Eq. 9) in shared
+//     memory; one warp then forms CVaR_k by a radix select of VaR = L_(j)
+//     and warp reductions of the tail.
 // The single-problem kernel below puts nominal blocks first and disturbed
 // blocks after them in one launch, so the nominal work (1/M of the total)
 // overlaps the disturbed work; the batched kernel (ra_batch.cu) pulls the
