@@ -245,7 +245,9 @@ const char* ra_mppi_last_error(const ra_mppi_t* h);
 
 /* Launch-shape tuner: times every valid (warps per block in {1..6, 8},
  * interleave in {1, 2, 4}, warps per sample dividing the block) shape that
- * gives each warp at least one full set of interleaved rows, on the given
+ * gives each warp at least one full set of interleaved rows (or, dynamic
+ * model with M <= 32, interleave 2 and one warp per sample: two samples per
+ * warp, stepped as pairs), on the given
  * inputs (x0, V device; `replays` updates each), keeps the fastest and
  * restores the update counter, so later results are unchanged (they never
  * depend on the shape).  Synchronous. */
@@ -277,7 +279,8 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
 /* Kernel launch tuning: disturbed-rollout warps per block (1..8), rollouts
  * each lane interleaves (1, 2 or 4) and warps sharing one sample's M
  * rollouts (1..8, dividing warps_per_block); 0 keeps the current value.
- * Results never depend on the shape. */
+ * Dynamic model, M <= 32, interleave 2 and one warp per sample: each warp
+ * takes two samples (the default there).  Results never depend on the shape. */
 int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32_t warps_per_sample);
 
 /* Diagnostics: when `candidates` (device uint64) is set, the disturbed

@@ -233,8 +233,18 @@ void release(ra_mppi* h) {
 std::mutex g_smem_mutex;
 size_t g_smem_limit[64][3] = {};  // per device, per model
 
+// one row of rollouts per sample and two interleaved, dynamic model: each
+// warp takes two samples (one rollout of each per lane, a paired-instruction
+// pair; see disturbed_sample_pair)
+bool pairs_samples(const ra_mppi* h) {
+  return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->ilp == 2 && h->wps == 1 && h->prob.M <= 32;
+}
+
+// samples per disturbed block
+int samples_per_block(const ra_mppi* h) { return (h->warps / h->wps) * (pairs_samples(h) ? 2 : 1); }
+
 size_t rollout_smem(const ra_mppi* h) {
-  const size_t spb = (size_t)(h->warps / h->wps);  // samples per disturbed block
+  const size_t spb = (size_t)samples_per_block(h);
   return (size_t)h->obs_cap * sizeof(float4) + spb * h->prob.T * sizeof(float4) + spb * h->prob.M * sizeof(float);
 }
 
@@ -264,7 +274,8 @@ int default_ilp(int M, int model) {
   const int R = (M + 31) / 32;
   // measured on GB300: both models are fastest with 2 (the dynamic one steps
   // the pair in paired FP32 instructions); 4 costs registers
-  (void)model;
+  // one row per sample: the dynamic model pairs two samples per warp
+  if (model == RA_MPPI_DYN_SINGLE_TRACK && R == 1) return 2;
   const int cap = 2;
   for (int ilp = cap; ilp > 1; ilp >>= 1)
     if (R % ilp == 0) return ilp;
@@ -434,7 +445,7 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
   a.nb_nom = (p.K + 32 * h->warps - 1) / (32 * h->warps);
   a.obs_cap = h->obs_cap;
   a.wps = h->wps;
-  const int spb = h->warps / h->wps;
+  const int spb = samples_per_block(h);
   const int nb_dist = (p.K + spb - 1) / spb;
   const int grid = a.nb_nom + nb_dist;
   cudaError_t e;
@@ -449,9 +460,9 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
     if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
   }
   switch (p.model) {
-    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, h->smem, grid, s); break;
-    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, h->smem, grid, s); break;
-    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, h->smem, grid, s); break;
+    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, pairs_samples(h), h->smem, grid, s); break;
+    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, pairs_samples(h), h->smem, grid, s); break;
+    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, pairs_samples(h), h->smem, grid, s); break;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
   if (h->ev_end != nullptr) {
@@ -610,8 +621,10 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   for (int w : warps_c) {
     for (int il : ilp_c)
     for (int g : wps_c) {
-      // shapes that leave a warp without a full set of interleaved rows add nothing
-      if (g > w || w % g != 0 || R < g * il) continue;
+      // shapes that leave a warp without a full set of interleaved rows add
+      // nothing, except one row per sample, which two samples share (dynamic model)
+      const bool sample_pairs = h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && R == 1 && il == 2 && g == 1;
+      if (g > w || w % g != 0 || (R < g * il && !sample_pairs)) continue;
       h->warps = w;
       h->ilp = il;
       h->wps = g;

@@ -177,6 +177,23 @@ __device__ __forceinline__ void vsincos(float2 a, float2* s, float2* c) {
   __sincosf(r.y, &s->y, &c->y);
 }
 
+// The per-step control quantities of the dynamic model in the lane type T:
+// B steer, accel, sin steer, -sin steer, cos steer.  For T = float2 they are
+// either the same for both halves (two rollouts of one sample) or the two
+// samples' own (one rollout each of two samples).
+template <class T>
+struct CtlT {
+  T bd, a, sd, nsd, cd;
+};
+__device__ __forceinline__ CtlT<float> ctl_of(const float4 c, float) { return {c.x, c.y, c.z, -c.z, c.w}; }
+__device__ __forceinline__ CtlT<float2> ctl_of(const float4 c, float2) {
+  return {bc<float2>(c.x), bc<float2>(c.y), bc<float2>(c.z), bc<float2>(-c.z), bc<float2>(c.w)};
+}
+__device__ __forceinline__ CtlT<float2> ctl_pair(const float4 ca, const float4 cb) {
+  return {make_float2(ca.x, cb.x), make_float2(ca.y, cb.y), make_float2(ca.z, cb.z), make_float2(-ca.z, -cb.z),
+          make_float2(ca.w, cb.w)};
+}
+
 // arctangent for the slip angles: z P(z^2) on [0, 1] with P of degree 7 in
 // z^2 (coefficients fitted here by iterated weighted least squares on
 // Chebyshev nodes for the relative error; max 2.5e-7 in float32), reflected
@@ -279,7 +296,7 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     return vmul(bc<T>(k), vmap(z, [C](float v) { return sinf(C * atanf(v)); }));
   }
   template <class T>
-  __device__ static __forceinline__ void deriv(const DevParams& p, const T* x, const float4 c, T* f) {
+  __device__ static __forceinline__ void deriv(const DevParams& p, const T* x, const CtlT<T>& c, T* f) {
     const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], vfloor = p.mp[7];
     const T vx = x[3], vy = x[4], r = x[5];
     // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx)
@@ -287,7 +304,7 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     T tf, tr;
     atan_pair<T>(vmul(vfma(bc<T>(lf), r, vy), inv_vx), vmul(vfma(bc<T>(-lr), r, vy), inv_vx), &tf, &tr);
     // Pacejka arguments B alpha_f = B (steer - atan_f), B alpha_r = -B atan_r
-    const T ay_f = pacejka<T>(p, vfma(bc<T>(-Bt), tf, bc<T>(c.x)), p.acc_f);
+    const T ay_f = pacejka<T>(p, vfma(bc<T>(-Bt), tf, c.bd), p.acc_f);
     const T ay_r = pacejka<T>(p, vmul(bc<T>(-Bt), tr), p.acc_r);
     T sp, cp;
     vsincos(x[2], &sp, &cp);
@@ -295,14 +312,14 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     f[0] = vfma(vx, cp, vmul(vneg(vy), sp));
     f[1] = vfma(vx, sp, vmul(vy, cp));
     f[2] = r;
-    const T g = vmul(ay_f, bc<T>(c.w));  // front force along the body y axis, per unit mass
-    f[3] = vfma(ay_f, bc<T>(-c.z), vfma(r, vy, bc<T>(c.y)));
-    f[4] = vfma(r, vneg(vx), vfma(ay_f, bc<T>(c.w), ay_r));
+    const T g = vmul(ay_f, c.cd);  // front force along the body y axis, per unit mass
+    f[3] = vfma(ay_f, c.nsd, vfma(r, vy, c.a));
+    f[4] = vfma(r, vneg(vx), vfma(ay_f, c.cd, ay_r));
     f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(-p.yaw_r), ay_r));
   }
   // one Heun sub-step of size h
   template <class T>
-  __device__ static __forceinline__ void substep_t(const DevParams& p, T* x, const float4 c) {
+  __device__ static __forceinline__ void substep_t(const DevParams& p, T* x, const CtlT<T>& c) {
     T k1[6], k2[6], xp[6];
     deriv<T>(p, x, c, k1);
 #pragma unroll
@@ -313,18 +330,27 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), vadd(k1[i], k2[i]), x[i]);
   }
   template <class T>
-  __device__ static __forceinline__ void step_t(const DevParams& p, T* x, const float4 c) {
+  __device__ static __forceinline__ void step_t(const DevParams& p, T* x, const CtlT<T>& c) {
     for (int s = 0; s < p.substeps; ++s) substep_t<T>(p, x, c);
   }
+  // the derivative with one sample's control quantities
+  template <class T>
+  __device__ static __forceinline__ void deriv(const DevParams& p, const T* x, const float4 c, T* f) {
+    deriv<T>(p, x, ctl_of(c, T{}), f);
+  }
   __device__ static __forceinline__ void substep(const DevParams& p, float* x, const float4 c) {
-    substep_t<float>(p, x, c);
+    substep_t<float>(p, x, ctl_of(c, 0.0f));
   }
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
-    step_t<float>(p, x, c);
+    step_t<float>(p, x, ctl_of(c, 0.0f));
   }
   // two rollouts at once: x[i] = (state i of rollout a, state i of rollout b)
   __device__ static __forceinline__ void step2(const DevParams& p, float2* x, const float4 c) {
-    step_t<float2>(p, x, c);
+    step_t<float2>(p, x, ctl_of(c, float2{}));
+  }
+  // one rollout each of two samples: x[i] = (state i under ca, state i under cb)
+  __device__ static __forceinline__ void step2x(const DevParams& p, float2* x, const float4 ca, const float4 cb) {
+    step_t<float2>(p, x, ctl_pair(ca, cb));
   }
   __device__ static __forceinline__ float speed(const float* x) { return x[3]; }
 };

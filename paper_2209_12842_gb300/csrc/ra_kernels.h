@@ -19,9 +19,10 @@ struct UpdateArgs {
   DevState* st;
 };
 
-// Rollout kernel launch for one model; ilp in {1, 2, 4}.
+// Rollout kernel launch for one model; ilp in {1, 2, 4}; `pairs`: two
+// samples per warp (dynamic model, ilp 2, at most 32 rollouts per sample).
 template <int MODEL>
-cudaError_t launch_rollout(const DevParams& p, const RolloutArgs& a, int warps, int ilp,
+cudaError_t launch_rollout(const DevParams& p, const RolloutArgs& a, int warps, int ilp, bool pairs,
                            size_t smem, int grid, cudaStream_t s);
 // Raise the dynamic shared memory limit of every instance of a model.
 template <int MODEL>

@@ -389,7 +389,53 @@ __device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst&
   risk_from_shared(p, in, Ls, k, lane, cvar, Lout, status);
 }
 
-template <int MODEL, int ILP>
+// One warp, two samples ka, kb of at most 32 rollouts each (the dynamic
+// model, interleave 2): lane l steps rollout l of ka and rollout l of kb as
+// one pair in paired FP32 instructions, each under its own sample's controls
+// (the same bits as one sample per warp).  kb may be past the last sample;
+// then its results are not stored.
+template <int MODEL>
+__device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const Inst& in, const float* __restrict__ x0g,
+                                                      const float* __restrict__ V, int ka, int kb, int lane,
+                                                      float4* ctl_a, float4* ctl_b, float* Ls_a, float* Ls_b,
+                                                      const float4* obs_s, int n_obs, float* __restrict__ cvar,
+                                                      float* __restrict__ Lout, int* status) {
+  using Md = Model<MODEL>;
+  fill_controls<MODEL>(p, in, V, ka, lane, 32, ctl_a);
+  fill_controls<MODEL>(p, in, V, kb, lane, 32, ctl_b);
+  __syncwarp();
+  float x[2][Md::NX];
+  float L[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int j = 0; j < Md::NX; ++j) x[0][j] = x[1][j] = x0g[j];
+  const uint32_t m = (uint32_t)lane;
+  for (int t = 0; t < in.T; ++t) {
+    risk_cost_ilp<MODEL, 2>(p, x, L, obs_s, n_obs);
+    float2 xx[Md::NX];
+#pragma unroll
+    for (int j = 0; j < Md::NX; ++j) xx[j] = make_float2(x[0][j], x[1][j]);
+    Md::step2x(p, xx, ctl_a[t], ctl_b[t]);
+#pragma unroll
+    for (int j = 0; j < Md::NX; ++j) {
+      x[0][j] = xx[j].x;
+      x[1][j] = xx[j].y;
+    }
+    add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, m, (uint32_t)ka, in.instance, x[0]);
+    add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, m, (uint32_t)kb, in.instance, x[1]);
+  }
+  if ((int)m < in.M) {
+    Ls_a[m] = L[0];
+    Ls_b[m] = L[1];
+  }
+  __syncwarp();
+  risk_from_shared(p, in, Ls_a, ka, lane, cvar, Lout, status);
+  if (kb < in.K) risk_from_shared(p, in, Ls_b, kb, lane, cvar, Lout, status);
+}
+
+// PAIRS: the instantiation that takes two samples per warp (dynamic model,
+// interleave 2, one row per sample); a separate kernel so that its code does
+// not raise the register count of the others
+template <int MODEL, int ILP, bool PAIRS = false>
 __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
   extern __shared__ float4 smem[];
   float4* obs_s = smem;
@@ -411,6 +457,16 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   const int k = ((int)blockIdx.x - a.nb_nom) * spb + gi;
   float4* ctl = smem + a.obs_cap + gi * in.T;
   float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + spb * in.T) + gi * in.M;
+  if constexpr (PAIRS) {
+    // two samples per warp: slots 2w and 2w + 1 of the block's controls and costs
+    const int ka = ((int)blockIdx.x - a.nb_nom) * 2 * warps + 2 * w, kb = ka + 1;
+    if (ka >= in.K) return;
+    float4* ctl_a = smem + a.obs_cap + (2 * w) * in.T;
+    float* Ls_a = reinterpret_cast<float*>(smem + a.obs_cap + 2 * warps * in.T) + (2 * w) * in.M;
+    disturbed_sample_pair<MODEL>(p, in, a.x0, a.V, ka, kb, lane, ctl_a, ctl_a + in.T, Ls_a, Ls_a + in.M, obs_s,
+                                 n_obs, a.cvar, a.L, &a.st->status);
+    return;
+  } else {
   if (G == 1) {
     if (k >= in.K) return;
     disturbed_sample<MODEL, ILP>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L, &a.st->status);
@@ -424,6 +480,7 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   if (valid) run_rollouts<MODEL, ILP>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs);
   __syncthreads();
   if (valid && g == 0) risk_from_shared(p, in, Ls, k, lane, a.cvar, a.L, &a.st->status);
+  }
 }
 
 }  // namespace ramppi

@@ -109,6 +109,32 @@ def test_large_M_and_warps_per_sample(M, launch):
     compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
 
 
+@pytest.mark.parametrize("M", [32, 17, 5])
+@pytest.mark.parametrize("launch", [(4, 2, 1), (1, 2, 1), (7, 2, 1)])
+def test_two_samples_per_warp(M, launch):
+    """At most 32 rollouts per sample, dynamic model, interleave 2: each warp
+    steps two samples at once; an odd K leaves the last warp's second sample
+    empty. Same bits as one sample per warp, and the oracle's results."""
+    p = rs.preset("small_dyn", M=M, K=37)
+    obs = _scene(p)
+    x0 = rs.initial_state(1)
+    V = rs.random_controls(1, p["T"], p["u_lo"], p["u_hi"], 9)
+    base = _gpu(p, obs, x0, V, launch=(4, 1, 1))
+    g = _gpu(p, obs, x0, V, launch=launch)
+    for key in ("U", "S", "cvar", "S_tilde", "L", "V_plus"):
+        np.testing.assert_array_equal(g[key], base[key], err_msg=f"{launch} {key}")
+    compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
+
+
+def test_two_samples_per_warp_is_the_default():
+    from paper_2209_12842_gb300 import RaMppi
+
+    p = rs.preset("small_dyn", M=32, K=64)
+    ctl = RaMppi(p, _scene(p))
+    assert ctl.get_launch()[1] == 2
+    ctl.close()
+
+
 def test_paper_preset():
     p = rs.preset("paper_sim", K=96)
     obs = rs.scene_obstacles(p)
