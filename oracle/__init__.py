@@ -60,6 +60,7 @@ class Problem(ctypes.Structure):
         ("band_delta", ctypes.c_double), ("risk_param", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("iteration", ctypes.c_uint64),
         ("instance_id", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
+        ("is_scale", ctypes.c_double), ("is_frac", ctypes.c_double),
     ]
 
 
@@ -90,6 +91,11 @@ def lib():
         L.orc_risk.argtypes = [_D, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                ctypes.c_double]
         L.orc_risk.restype = ctypes.c_double
+        L.orc_risk_w.argtypes = [_D, _D, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                 ctypes.c_double]
+        L.orc_risk_w.restype = ctypes.c_double
+        L.orc_is_weights.argtypes = [_P, ctypes.c_int32, _D]
+        L.orc_is_weights.restype = ctypes.c_int32
         L.orc_samples.argtypes = [_P, _D, _D, _D, ctypes.c_int32, _I32, ctypes.c_int32] + [_D] * 11
         L.orc_samples.restype = ctypes.c_int32
         L.orc_update.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -151,6 +157,8 @@ def make_problem(p, iteration=0, band_delta=1e-4, n_threads=1, exact=False):
     pr.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
     pr.iteration = int(iteration)
     pr.instance_id = int(p["instance_id"]) & 0xFFFFFFFF
+    pr.is_scale = _f32(p.get("is_scale", 1.0))
+    pr.is_frac = _f32(p.get("is_frac", 0.0))
     return pr
 
 
@@ -229,6 +237,25 @@ def risk(L, alpha, B=1.0, mode=0, threshold=0.0):
     """Risk measure of a set of risk costs (CVaR forms, VaR, chance, mean)."""
     L = _arr(L)
     return lib().orc_risk(_ptr(L), int(L.size), float(alpha), float(B), int(mode), float(threshold))
+
+
+def risk_w(L, w, alpha, B=1.0, mode=0, threshold=0.0):
+    """Risk measure of the weighted empirical distribution of the risk costs
+    L with weights w (None: all equal)."""
+    L = _arr(L)
+    w = None if w is None else _arr(w)
+    return lib().orc_risk_w(_ptr(L), _ptr(w), int(L.size), float(alpha), float(B), int(mode), float(threshold))
+
+
+def is_weights(p, k, iteration=0):
+    """Importance weights of the M disturbed rollouts of sample k (all 1 when
+    importance sampling is off)."""
+    prob = make_problem(p, iteration)
+    w = np.zeros(int(p["M"]))
+    rc = lib().orc_is_weights(ctypes.byref(prob), int(k), _ptr(w))
+    if rc != 0:
+        raise RuntimeError(f"orc_is_weights failed: {rc}")
+    return w
 
 
 def n_warm(prob):

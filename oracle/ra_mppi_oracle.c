@@ -33,6 +33,9 @@
  *   - q and l are charged on x_0 .. x_{T-1}; phi on x_T
  *   - controls are clipped to the box after the noise is added
  *   - the control-cost weight uses 1/sigma^2 and is 0 where sigma = 0
+ *   - importance sampling of the process noise (the paper leaves it out,
+ *     Sec. III-A, pointing to importance sampling for alpha near 1): the
+ *     deterministic-mixture form with a scaled proposal, see orc_is_weights
  *   - the random numbers come from Philox4x32-10 (Salmon, Moraes, Dror,
  *     Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11), keyed by
  *     (seed, iteration) with counter (t | draw << 16, m, k, instance);
@@ -79,6 +82,8 @@ typedef struct {
   uint64_t iteration;
   uint32_t instance_id;
   uint32_t pad_;
+  double is_scale; /* proposal scale s >= 1 of the importance-sampled rollouts */
+  double is_frac;  /* fraction of the M rollouts drawn from the proposal, in [0, 1) */
 } orc_problem;
 
 /* ------------------------------------------------------------------ */
@@ -126,13 +131,14 @@ void orc_box_muller(uint32_t a, uint32_t b, double out[2]) {
  * N(0, (mix_scale b)^2).  The value word gives the tail mass
  * v = 2 min(a, 1 - a) of a = (x + 1/2) 2^-32 and the sign of a - 1/2; the
  * Gaussian branch is taken when the selector word is below floor(p 2^32). */
-double orc_mix_value(uint32_t sel, uint32_t word, double b, double p, double mix_scale) {
+static double mix_value_branch(uint32_t sel, uint32_t word, double b, double p, double mix_scale, int* gauss) {
   uint32_t hi = word >> 31;
   uint32_t r = hi ? ~word : word;                 /* in [0, 2^31) */
   double v = ((double)r + 0.5) * (1.0 / 2147483648.0);
   double sgn = hi ? 1.0 : -1.0;
   double thresh = floor(p * 4294967296.0 > 4294967295.0 ? 4294967295.0 : p * 4294967296.0);
-  if ((double)sel < thresh) {
+  *gauss = (double)sel < thresh;
+  if (*gauss) {
     /* Gaussian branch: Box-Muller with radius from v and angle from the
      * selector, uniform on [0, thresh) given this branch */
     double u2 = ((double)sel + 0.5) / thresh;
@@ -140,6 +146,15 @@ double orc_mix_value(uint32_t sel, uint32_t word, double b, double p, double mix
   }
   return sgn * (-b * log(v));
 }
+
+double orc_mix_value(uint32_t sel, uint32_t word, double b, double p, double mix_scale) {
+  int gauss;
+  return mix_value_branch(sel, word, b, p, mix_scale, &gauss);
+}
+
+/* log densities of one noise value */
+static double log_gauss(double w, double sd) { return -log(sd) - 0.5 * log(2.0 * ORC_PI) - w * w / (2.0 * sd * sd); }
+static double log_laplace(double w, double b) { return -log(2.0 * b) - fabs(w) / b; }
 
 static int nx_of(int model) { return model == ORC_KIN ? 4 : model == ORC_DYN ? 6 : 1; }
 static int nu_of(int model) { return model == ORC_LIN ? 1 : 2; }
@@ -168,8 +183,14 @@ static void noise_words(const orc_problem* p, uint64_t iteration, uint32_t c1, u
   orc_philox(ctr, key, w);
 }
 
+/* the process noise of step t, each value multiplied by g (1, or the
+ * proposal scale s for an importance-sampled rollout).  With log_ratio
+ * non-NULL (Gaussian and mixture noise only) it adds, for every value w
+ * drawn, ln q(w) - ln p(w): p the value's nominal density, q(w) = p(w/s)/s
+ * the proposal's (for the mixture, the densities given the branch drawn,
+ * whose probabilities the proposal keeps) */
 static void process_noise_at(const orc_problem* p, uint64_t iteration, uint32_t c1, uint32_t c2,
-                             int32_t t, double out[4]) {
+                             int32_t t, double g, double* log_ratio, double out[4]) {
   int ns = nslots_of(p->model);
   for (int s = 0; s < 4; ++s) out[s] = 0.0;
   if (p->noise_type == ORC_GAUSS) {
@@ -178,14 +199,31 @@ static void process_noise_at(const orc_problem* p, uint64_t iteration, uint32_t 
     double z[4];
     orc_box_muller(w[0], w[1], z);
     orc_box_muller(w[2], w[3], z + 2);
-    for (int s = 0; s < ns; ++s) out[s] = p->w_scale[s] * z[s];
+    for (int s = 0; s < ns; ++s) {
+      out[s] = g * (p->w_scale[s] * z[s]);
+      if (log_ratio && p->w_scale[s] != 0.0)
+        *log_ratio += log_gauss(out[s], p->is_scale * p->w_scale[s]) - log_gauss(out[s], p->w_scale[s]);
+    }
   } else if (p->noise_type == ORC_LAPLACE_MIX) {
     uint32_t sel[4], val[4];
     noise_words(p, iteration, c1, c2, t, 0, sel);
     noise_words(p, iteration, c1, c2, t, 1, val);
-    for (int s = 0; s < ns; ++s)
-      out[s] = (p->w_scale[s] == 0.0) ? 0.0
-                                      : orc_mix_value(sel[s], val[s], p->w_scale[s], p->mix_p, p->mix_scale);
+    for (int s = 0; s < ns; ++s) {
+      if (p->w_scale[s] == 0.0) {
+        out[s] = 0.0;
+        continue;
+      }
+      int gauss;
+      out[s] = g * mix_value_branch(sel[s], val[s], p->w_scale[s], p->mix_p, p->mix_scale, &gauss);
+      if (log_ratio) {
+        if (gauss) {
+          const double sd = p->mix_scale * p->w_scale[s];
+          *log_ratio += log_gauss(out[s], p->is_scale * sd) - log_gauss(out[s], sd);
+        } else {
+          *log_ratio += log_laplace(out[s], p->is_scale * p->w_scale[s]) - log_laplace(out[s], p->w_scale[s]);
+        }
+      }
+    }
   } else if (p->noise_type == ORC_UNIFORM) {
     /* w_s ~ U[-a_s, a_s] (the paper's uniform disturbance, Sec. V-B) */
     uint32_t w[4];
@@ -213,7 +251,53 @@ static void process_noise_at(const orc_problem* p, uint64_t iteration, uint32_t 
 }
 
 void orc_process_noise(const orc_problem* p, int32_t k, int32_t m, int32_t t, double out[4]) {
-  process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, out);
+  process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, 1.0, NULL, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Importance-sampled rollouts (the paper leaves importance sampling out,  */
+/* Sec. III-A, naming it as the remedy when alpha is near 1).  The last    */
+/* M_s = floor(is_frac M) rollouts of every sample draw each process-noise */
+/* value at is_scale times its nominal size; the others are unchanged.     */
+/* With b = M_s / M, rollout m's noise path W_m gets the balance-heuristic */
+/* (deterministic-mixture) weight                                          */
+/*   w_m = p(W_m) / ((1 - b) p(W_m) + b q(W_m)) = 1 / ((1 - b) + b e^G_m), */
+/* G_m = ln q(W_m) - ln p(W_m) summed over the path's values, so that      */
+/* sum_m w_m f(W_m) / M is an unbiased estimate of E_p f.  The risk        */
+/* measures are then those of the weighted empirical distribution of the   */
+/* risk costs.  Off (all weights 1) when M_s = 0 or is_scale = 1.          */
+/* ------------------------------------------------------------------ */
+static int is_count(const orc_problem* p) {
+  if (p->is_scale == 1.0 || p->is_frac <= 0.0) return 0;
+  return (int)floor(p->is_frac * (double)p->M);
+}
+
+/* proposal factor of rollout m: s for the last M_s rollouts, else 1 */
+static double is_factor(const orc_problem* p, int m, int M_s) {
+  return m >= p->M - M_s ? p->is_scale : 1.0;
+}
+
+static double is_weight(const orc_problem* p, int M_s, double log_ratio) {
+  const double b = (double)M_s / (double)p->M;
+  return 1.0 / ((1.0 - b) + b * exp(log_ratio));
+}
+
+/* the M weights of sample k (noise only: no dynamics); all 1 when off.
+ * Returns -6 for noise types without a density ratio (uniform, impulse). */
+int32_t orc_is_weights(const orc_problem* p, int32_t k, double* w) {
+  const int M_s = is_count(p);
+  if (M_s > 0 && p->noise_type != ORC_GAUSS && p->noise_type != ORC_LAPLACE_MIX) return -6;
+  for (int m = 0; m < p->M; ++m) {
+    if (M_s == 0) {
+      w[m] = 1.0;
+      continue;
+    }
+    double G = 0.0, out[4];
+    for (int t = 0; t < p->T; ++t)
+      process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, is_factor(p, m, M_s), &G, out);
+    w[m] = is_weight(p, M_s, G);
+  }
+  return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -425,6 +509,74 @@ double orc_risk(const double* L, int32_t M, double alpha, double B, int32_t mode
   return out;
 }
 
+/* Risk measure of M risk costs with positive weights w (NULL: all 1), the
+ * measure of the weighted empirical distribution sum_m (w_m / W) at L_m,
+ * W = sum w.  The costs are scaled first, La = B (L - mean) + mean with the
+ * weighted mean (Eqs. 18, 19).  With tau = (1 - alpha) W:
+ *   VAR     the smallest La_m whose strictly larger weight W(La > La_m)
+ *           is at most tau (with equal weights: L_(ceil(alpha M)))
+ *   RU      VaR + sum_m w_m (La_m - VaR)+ / tau, the Rockafellar-Uryasev
+ *           objective c + sum w (La - c)+ / tau at its minimiser c = VaR
+ *   TCE     the weighted mean of the La_m >= VaR
+ *   CHANCE  the weight fraction of La_m above thr; MEAN the weighted mean;
+ *   MEANVAR the weighted mean plus thr times the weighted variance.
+ * VaR is found by its definition, one weight sum per candidate (O(M^2)). */
+double orc_risk_w(const double* L, const double* w, int32_t M, double alpha, double B, int32_t mode, double thr) {
+  if (w == NULL) return orc_risk(L, M, alpha, B, mode, thr);
+  for (int n = 0; n < M; ++n)
+    if (!isfinite(L[n])) return INFINITY;
+  double W = 0.0, mean = 0.0;
+  for (int n = 0; n < M; ++n) {
+    W += w[n];
+    mean += w[n] * L[n];
+  }
+  mean /= W;
+  double* La = (double*)malloc(sizeof(double) * (size_t)M);
+  for (int n = 0; n < M; ++n) La[n] = B * (L[n] - mean) + mean;
+  const double tau = (1.0 - alpha) * W;
+  double var = INFINITY;
+  for (int c = 0; c < M; ++c) {
+    double above = 0.0;
+    for (int n = 0; n < M; ++n)
+      if (La[n] > La[c]) above += w[n];
+    if (above <= tau && La[c] < var) var = La[c];
+  }
+  double out;
+  if (mode == ORC_VAR) {
+    out = var;
+  } else if (mode == ORC_CVAR_RU) {
+    double tail = 0.0;
+    for (int n = 0; n < M; ++n)
+      if (La[n] > var) tail += w[n] * (La[n] - var);
+    out = var + tail / tau;
+  } else if (mode == ORC_CVAR_TCE) {
+    double s = 0.0, ws = 0.0;
+    for (int n = 0; n < M; ++n)
+      if (La[n] >= var) { s += w[n] * La[n]; ws += w[n]; }
+    out = s / ws;
+  } else if (mode == ORC_CHANCE) {
+    double over = 0.0;
+    for (int n = 0; n < M; ++n) {
+      double v = (B == 1.0) ? L[n] : La[n];
+      if (v > thr) over += w[n];
+    }
+    out = over / W;
+  } else if (mode == ORC_MEAN) {
+    double acc = 0.0;
+    for (int n = 0; n < M; ++n) acc += w[n] * La[n];
+    out = acc / W;
+  } else {
+    double m1 = 0.0;
+    for (int n = 0; n < M; ++n) m1 += w[n] * La[n];
+    m1 /= W;
+    double m2 = 0.0;
+    for (int n = 0; n < M; ++n) m2 += w[n] * (La[n] - m1) * (La[n] - m1);
+    out = m1 + thr * (m2 / W);
+  }
+  free(La);
+  return out;
+}
+
 /* ------------------------------------------------------------------ */
 /* Per-sample stage (Alg. 1 loop body for sample k)                     */
 /* ------------------------------------------------------------------ */
@@ -445,6 +597,8 @@ int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, con
                     double* cvar_hi, double* St_lo, double* St_hi) {
   const int nx = nx_of(p->model), nu = nu_of(p->model), T = p->T, M = p->M;
   const int n_warm = n_warm_of(p);
+  const int M_s = is_count(p);
+  if (M_s > 0 && p->noise_type != ORC_GAUSS && p->noise_type != ORC_LAPLACE_MIX) return -6;
   double inv_sig2[2];
   for (int j = 0; j < 2; ++j) inv_sig2[j] = p->sigma_u[j] > 0.0 ? 1.0 / (p->sigma_u[j] * p->sigma_u[j]) : 0.0;
   int nthreads = p->n_threads > 0 ? p->n_threads : 1;
@@ -454,6 +608,7 @@ int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, con
     const int k = ks[i];
     double* Uk = (double*)malloc(sizeof(double) * (size_t)T * nu);
     double* Lm = (double*)malloc(sizeof(double) * (size_t)M * 3);
+    double* Wm = (double*)malloc(sizeof(double) * (size_t)M);
     /* sample the control sequence */
     for (int t = 0; t < T; ++t) {
       double eps[2];
@@ -480,26 +635,30 @@ int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, con
     }
     double phi = terminal_cost(p, x);
     Sk += phi; Sk_lo += phi; Sk_hi += phi;
-    /* disturbed rollouts and their risk costs (Eq. 9) */
+    /* disturbed rollouts and their risk costs (Eq. 9); importance weights
+     * of the rollouts when some draw from the scaled proposal */
     for (int m = 0; m < M; ++m) {
       double xt[6];
       for (int a = 0; a < nx; ++a) xt[a] = x0[a];
-      double Lv = 0.0, Llo = 0.0, Lhi = 0.0;
+      double Lv = 0.0, Llo = 0.0, Lhi = 0.0, G = 0.0;
       for (int t = 0; t < T; ++t) {
         Lv += state_cost(p, xt, obs, n_obs, p->risk_mask, 0.0);
         Llo += state_cost(p, xt, obs, n_obs, p->risk_mask, -p->band_delta);
         Lhi += state_cost(p, xt, obs, n_obs, p->risk_mask, p->band_delta);
         double w[4];
-        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, w);
+        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, is_factor(p, m, M_s),
+                         M_s > 0 ? &G : NULL, w);
         orc_dynamics(p, xt, Uk + t * nu, xn);
         for (int a = 0; a < nx; ++a) xt[a] = xn[a];
         for (int s = 0; s < nslots_of(p->model); ++s) xt[slot_dim(p->model, s)] += w[s];
       }
       Lm[m] = Lv; Lm[M + m] = Llo; Lm[2 * M + m] = Lhi;
+      Wm[m] = M_s > 0 ? is_weight(p, M_s, G) : 1.0;
     }
-    double cv = orc_risk(Lm, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
-    double cv_lo = orc_risk(Lm + M, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
-    double cv_hi = orc_risk(Lm + 2 * M, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
+    const double* wts = M_s > 0 ? Wm : NULL;
+    double cv = orc_risk_w(Lm, wts, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
+    double cv_lo = orc_risk_w(Lm + M, wts, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
+    double cv_hi = orc_risk_w(Lm + 2 * M, wts, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
     /* CVaR violation cost and modified trajectory cost (Eqs. 14-16) */
     double st = Sk + ((cv > p->C_u) ? p->A * cv : 0.0);
     if (U) memcpy(U + (size_t)i * T * nu, Uk, sizeof(double) * (size_t)T * nu);
@@ -515,6 +674,7 @@ int32_t orc_samples(const orc_problem* p, const double* x0, const double* V, con
     if (cvar_hi) cvar_hi[i] = cv_hi;
     free(Uk);
     free(Lm);
+    free(Wm);
   }
   return 0;
 }
@@ -558,7 +718,7 @@ int32_t orc_plant_step(const orc_problem* p, uint64_t iteration, const double* x
   int nx = nx_of(p->model);
   double xn[6], w[4];
   orc_dynamics(p, x, u, xn);
-  process_noise_at(p, iteration, 0xFFFFFFFEu, 0xFFFFFFFFu, 0, w);
+  process_noise_at(p, iteration, 0xFFFFFFFEu, 0xFFFFFFFFu, 0, 1.0, NULL, w);
   for (int s = 0; s < nslots_of(p->model); ++s) xn[slot_dim(p->model, s)] += w[s];
   for (int a = 0; a < nx; ++a) x_out[a] = xn[a];
   if (p->model == ORC_LIN) return 0;
@@ -795,6 +955,7 @@ static void rollout_vjp(const orc_problem* p, const double* xs, const double* Uk
 int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, const double* obs, int32_t n_obs,
                      const double* gVp, const double* gSt, double* gV, double* gtheta) {
   if (p->substeps > 64) return -1;
+  if (is_count(p) > 0) return -6; /* importance-sampled rollouts: forward only */
   const int K = p->K, M = p->M, T = p->T, nx = nx_of(p->model), nu = nu_of(p->model);
   const int n_warm = n_warm_of(p);
   double inv_sig2[2];
@@ -837,7 +998,7 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
       for (int t = 0; t < T; ++t) {
         Lv += state_cost(p, xd + (size_t)t * nx, obs, n_obs, p->risk_mask, 0.0);
         double w[4];
-        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, w);
+        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, 1.0, NULL, w);
         orc_dynamics(p, xd + (size_t)t * nx, Uk + t * nu, xd + (size_t)(t + 1) * nx);
         for (int s = 0; s < nslots_of(p->model); ++s) xd[(size_t)(t + 1) * nx + slot_dim(p->model, s)] += w[s];
       }

@@ -81,6 +81,10 @@ _COMMON = dict(
     eta=0.0,
     cvar_mode=CVAR_RU,
     risk_param=0.0,
+    # importance-sampled rollouts: the last floor(is_frac M) rollouts draw
+    # their process noise at is_scale times its size (off: 1.0 / 0.0)
+    is_scale=1.0,
+    is_frac=0.0,
     seed=12842,
     instance_id=0,
     n_obs=10,
