@@ -162,6 +162,22 @@ typedef struct ra_mppi_problem {
   int32_t max_obstacles; /* capacity of the obstacle list, 0 .. RA_MPPI_MAX_OBSTACLES */
   uint32_t instance_id;  /* fourth Philox counter word                        */
   uint64_t seed;         /* Philox key                                        */
+  /* Importance-sampled rollouts (the paper names importance sampling for
+   * alpha near 1 but leaves it out, Sec. III-A).  The last
+   * M_s = floor(is_frac M) rollouts of every sample draw each process-noise
+   * value at is_scale times its size; with b = M_s / M, rollout m gets the
+   * deterministic-mixture weight w_m = 1 / ((1 - b) + b q(W_m)/p(W_m)) of
+   * its noise path W_m (p the nominal density, q(w) = p(w/s)/s per value;
+   * for the mixture noise the density given the branch drawn), and every
+   * risk measure becomes that of the weighted empirical distribution of the
+   * M risk costs (VaR: the smallest cost whose strictly larger weight is at
+   * most (1 - alpha) sum w; RU CVaR: VaR + sum w (L - VaR)+ / ((1 - alpha)
+   * sum w); the others the weighted tail mean, fraction or moments).
+   * Off when is_frac = 0 or is_scale = 1 (or M_s = 0).  is_scale in
+   * [1, 16], is_frac in [0, 1); Gaussian and mixture noise only; not with
+   * ra_mppi_backward or the batched path (EUNSUPPORTED there). */
+  float is_scale;
+  float is_frac;
 } ra_mppi_problem;
 
 typedef struct ra_mppi ra_mppi_t;
@@ -230,6 +246,12 @@ int ra_mppi_workspace(ra_mppi_t* h, const float** U, const float** S, const floa
  * any may be NULL): U [K][T][nu], S [K], cvar [K], L [K][M] (EINVAL if L is
  * requested without RA_MPPI_KEEP_RISK_COSTS).  Enqueued on `stream`. */
 int ra_mppi_copy_workspace(ra_mppi_t* h, float* U, float* S, float* cvar, float* L, void* stream);
+
+/* Copy the last update's importance weights W [K][M] (the deterministic-
+ * mixture weight of every disturbed rollout; see is_scale) into a caller
+ * buffer (host or device).  EINVAL unless the problem had
+ * RA_MPPI_KEEP_RISK_COSTS and importance sampling on.  Enqueued on `stream`. */
+int ra_mppi_copy_weights(ra_mppi_t* h, float* W, void* stream);
 
 /* Update counter that keys the noise.  get waits for the device. */
 int ra_mppi_get_iteration(ra_mppi_t* h, uint64_t* iteration);

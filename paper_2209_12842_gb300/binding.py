@@ -52,6 +52,7 @@ class ra_mppi_problem(ctypes.Structure):
         ("risk_param", ctypes.c_float),
         ("max_obstacles", ctypes.c_int32), ("instance_id", ctypes.c_uint32),
         ("seed", ctypes.c_uint64),
+        ("is_scale", ctypes.c_float), ("is_frac", ctypes.c_float),
     ]
 
 
@@ -77,6 +78,7 @@ def _declare(L):
     L.ra_mppi_step_host.argtypes = [_VP, _FP, _FP, _FP, _FP, _VP]
     L.ra_mppi_workspace.argtypes = [_VP] + [ctypes.POINTER(_VP)] * 4
     L.ra_mppi_copy_workspace.argtypes = [_VP, _FP, _FP, _FP, _FP, _VP]
+    L.ra_mppi_copy_weights.argtypes = [_VP, _FP, _VP]
     L.ra_mppi_get_iteration.argtypes = [_VP, ctypes.POINTER(ctypes.c_uint64)]
     L.ra_mppi_set_iteration.argtypes = [_VP, ctypes.c_uint64]
     L.ra_mppi_get_status.argtypes = [_VP]
@@ -127,8 +129,8 @@ def _declare(L):
                  "ra_mppi_batch_set_launch", "ra_mppi_batch_get_launch", "ra_mppi_batch_tune"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("ra_mppi_create", "ra_mppi_set_obstacles", "ra_mppi_step", "ra_mppi_step_host",
-                 "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_get_iteration", "ra_mppi_set_iteration",
-                 "ra_mppi_get_status", "ra_mppi_set_launch", "ra_mppi_set_timing_events"):
+                 "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_copy_weights", "ra_mppi_get_iteration",
+                 "ra_mppi_set_iteration", "ra_mppi_get_status", "ra_mppi_set_launch", "ra_mppi_set_timing_events"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -182,6 +184,8 @@ def ra_mppi_problem_from(p, flags=0, max_obstacles=None):
     pr.max_obstacles = int(max_obstacles if max_obstacles is not None else max(n_obs, 1))
     pr.instance_id = int(p["instance_id"]) & 0xFFFFFFFF
     pr.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
+    pr.is_scale = _f(p.get("is_scale", 1.0))
+    pr.is_frac = _f(p.get("is_frac", 0.0))
     return pr
 
 
@@ -254,6 +258,10 @@ def ra_mppi_workspace(h):
     ptrs = [_VP() for _ in range(4)]
     _check(lib().ra_mppi_workspace(h, *[ctypes.byref(p) for p in ptrs]), "ra_mppi_workspace", h)
     return [p.value for p in ptrs]
+
+
+def ra_mppi_copy_weights(h, W_ptr, stream=0):
+    _check(lib().ra_mppi_copy_weights(h, W_ptr, stream), "ra_mppi_copy_weights", h)
 
 
 def ra_mppi_copy_workspace(h, U_ptr=None, S_ptr=None, cvar_ptr=None, L_ptr=None, stream=0):

@@ -100,6 +100,13 @@ class RaMppi:
                                  L.data_ptr() if L is not None else None, _stream_ptr(stream))
         return dict(U=U, S=S, cvar=cv, L=L)
 
+    def importance_weights(self, stream=None):
+        """Copy of the last update's importance weights W [K, M] (needs
+        keep_risk_costs and importance sampling on)."""
+        W = torch.empty((self.K, self.M), dtype=torch.float32, device=self.S_tilde.device)
+        B.ra_mppi_copy_weights(self.h, W.data_ptr(), _stream_ptr(stream))
+        return W
+
     @property
     def iteration(self):
         return B.ra_mppi_get_iteration(self.h)

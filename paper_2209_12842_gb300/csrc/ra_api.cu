@@ -75,6 +75,7 @@ bool fault(const char* what) {
 
 int model_nx(int model) { return model == RA_MPPI_KIN_BICYCLE ? 4 : model == RA_MPPI_DYN_SINGLE_TRACK ? 6 : 1; }
 int model_nu(int model) { return model == RA_MPPI_LINEAR_TEST ? 1 : 2; }
+int model_slots(int model) { return model == RA_MPPI_KIN_BICYCLE ? 4 : model == RA_MPPI_DYN_SINGLE_TRACK ? 3 : 1; }
 
 bool finite_all(const float* v, int n) {
   for (int i = 0; i < n; ++i)
@@ -83,6 +84,12 @@ bool finite_all(const float* v, int n) {
 }
 
 // returns "" when valid, otherwise the reason
+// number of importance-sampled (proposal) rollouts per sample, 0 when off
+int is_count(const ra_mppi_problem& p) {
+  if (p.is_scale == 1.0f || !(p.is_frac > 0.0f)) return 0;
+  return (int)std::floor((double)p.is_frac * (double)p.M);
+}
+
 std::string validate(const ra_mppi_problem& p) {
   if (p.model < 0 || p.model > 2) return "model must be 0 (kinematic), 1 (dynamic) or 2 (linear)";
   if (p.K < 1 || p.K > (1 << 24)) return "K must be in [1, 2^24]";
@@ -120,6 +127,10 @@ std::string validate(const ra_mppi_problem& p) {
                      p.track_straight, p.track_radius, p.track_half_width, p.A, p.C_u, p.mix_scale};
   for (float v : w)
     if (std::isnan(v)) return "cost and track parameters must not be NaN";
+  if (!(p.is_scale >= 1.0f && p.is_scale <= 16.0f)) return "is_scale must be in [1, 16]";
+  if (!(p.is_frac >= 0.0f && p.is_frac < 1.0f)) return "is_frac must be in [0, 1)";
+  if (is_count(p) > 0 && p.noise_type != RA_MPPI_NOISE_GAUSS && p.noise_type != RA_MPPI_NOISE_LAPLACE_MIX)
+    return "importance sampling needs Gaussian or mixture process noise";
   return "";
 }
 
@@ -189,6 +200,22 @@ DevParams make_params(const ra_mppi_problem& p) {
   d.B = p.B;
   d.C_u = p.C_u;
   d.risk_param = p.risk_param;
+  d.one_m_alpha = (float)(1.0 - (double)p.alpha);
+  {
+    // importance sampling: per rollout ln q/p = -(draws) ln s + (1 - 1/s) A_L
+    // + (1 - 1/s^2)/2 A_G over its unit-scale Laplace magnitudes A_L and
+    // squared normals A_G (q(w) = p(w/s)/s for both densities)
+    const int M_s = is_count(p);
+    const double s = p.is_scale;
+    int slots = 0;
+    for (int i = 0; i < model_slots(p.model); ++i) slots += p.w_scale[i] != 0.0f ? 1 : 0;
+    d.is_m0 = p.M - M_s;
+    d.is_s = p.is_scale;
+    d.is_b = (float)((double)M_s / (double)p.M);
+    d.is_base = (float)(-(double)p.T * slots * std::log(s));
+    d.is_cl = (float)(1.0 - 1.0 / s);
+    d.is_cg = (float)(0.5 * (1.0 - 1.0 / (s * s)));
+  }
   d.seed_lo = (uint32_t)(p.seed & 0xFFFFFFFFull);
   d.seed_hi = (uint32_t)(p.seed >> 32);
   d.instance = p.instance_id;
@@ -236,8 +263,11 @@ size_t g_smem_limit[64][3] = {};  // per device, per model
 // one row of rollouts per sample and two interleaved, dynamic model: each
 // warp takes two samples (one rollout of each per lane, a paired-instruction
 // pair; see disturbed_sample_pair)
+bool importance(const ra_mppi* h) { return is_count(h->prob) > 0; }
+
 bool pairs_samples(const ra_mppi* h) {
-  return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->ilp == 2 && h->wps == 1 && h->prob.M <= 32;
+  return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->ilp == 2 && h->wps == 1 && h->prob.M <= 32 &&
+         !importance(h);
 }
 
 // samples per disturbed block
@@ -245,7 +275,9 @@ int samples_per_block(const ra_mppi* h) { return (h->warps / h->wps) * (pairs_sa
 
 size_t rollout_smem(const ra_mppi* h) {
   const size_t spb = (size_t)samples_per_block(h);
-  return (size_t)h->obs_cap * sizeof(float4) + spb * h->prob.T * sizeof(float4) + spb * h->prob.M * sizeof(float);
+  // obstacles, controls, risk costs (and importance weights) per sample
+  return (size_t)h->obs_cap * sizeof(float4) + spb * h->prob.T * sizeof(float4) +
+         spb * h->prob.M * sizeof(float) * (importance(h) ? 2 : 1);
 }
 
 cudaError_t prepare(ra_mppi* h) {
@@ -331,7 +363,9 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   if (e == cudaSuccess) e = dalloc(&h->cvar, K);
   if (e == cudaSuccess) e = dalloc(&h->S_tilde, K);
   if (e == cudaSuccess) e = dalloc(&h->partials, (size_t)h->nb_upd * (2 + TN));
-  if (e == cudaSuccess && (p->flags & RA_MPPI_KEEP_RISK_COSTS)) e = dalloc(&h->L, K * (size_t)p->M);
+  // kept risk costs [K][M], followed by the importance weights [K][M] when on
+  if (e == cudaSuccess && (p->flags & RA_MPPI_KEEP_RISK_COSTS))
+    e = dalloc(&h->L, K * (size_t)p->M * (is_count(*p) > 0 ? 2 : 1));
   if (e == cudaSuccess) e = dalloc(&h->obs, (size_t)h->obs_cap);
   if (e == cudaSuccess) e = dalloc(&h->st, 1);
   if (e == cudaSuccess) e = dalloc(&h->x0_dev, 8);
@@ -460,9 +494,9 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
     if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
   }
   switch (p.model) {
-    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, pairs_samples(h), h->smem, grid, s); break;
-    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, pairs_samples(h), h->smem, grid, s); break;
-    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, pairs_samples(h), h->smem, grid, s); break;
+    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), h->smem, grid, s); break;
+    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), h->smem, grid, s); break;
+    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), h->smem, grid, s); break;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
   if (h->ev_end != nullptr) {
@@ -541,6 +575,17 @@ int ra_mppi_copy_workspace(ra_mppi_t* h, float* U, float* S, float* cvar, float*
   return RA_MPPI_OK;
 }
 
+int ra_mppi_copy_weights(ra_mppi_t* h, float* W, void* stream) {
+  if (h == nullptr || W == nullptr) return RA_MPPI_EINVAL;
+  if (h->L == nullptr || !importance(h))
+    return fail(h, RA_MPPI_EINVAL, "weights are kept only with RA_MPPI_KEEP_RISK_COSTS and importance sampling");
+  const size_t KM = (size_t)h->prob.K * h->prob.M;
+  const cudaError_t e = cudaMemcpyAsync(W, h->L + KM, sizeof(float) * KM, cudaMemcpyDefault,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy_weights");
+  return RA_MPPI_OK;
+}
+
 int ra_mppi_get_iteration(ra_mppi_t* h, uint64_t* iteration) {
   if (h == nullptr || iteration == nullptr) return RA_MPPI_EINVAL;
   unsigned long long it = 0;
@@ -579,6 +624,7 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32
   const int g = warps_per_sample == 0 ? h->wps : warps_per_sample;
   if (w < 1 || w > 8) return fail(h, RA_MPPI_EINVAL, "warps_per_block must be in [1, 8]");
   if (i != 1 && i != 2 && i != 4) return fail(h, RA_MPPI_EINVAL, "ilp must be 1, 2 or 4");
+  if (i == 4 && importance(h)) return fail(h, RA_MPPI_EINVAL, "importance-sampled rollouts interleave 1 or 2");
   if (g < 1 || g > w || w % g != 0) return fail(h, RA_MPPI_EINVAL, "warps_per_sample must divide warps_per_block");
   const int old_w = h->warps, old_i = h->ilp, old_g = h->wps;
   h->warps = w;
@@ -621,6 +667,7 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   for (int w : warps_c) {
     for (int il : ilp_c)
     for (int g : wps_c) {
+      if (il == 4 && importance(h)) continue;
       // shapes that leave a warp without a full set of interleaved rows add
       // nothing, except one row per sample, which two samples share (dynamic model)
       const bool sample_pairs = h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && R == 1 && il == 2 && g == 1;
@@ -683,6 +730,7 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   if (gV_plus == nullptr || gV == nullptr || gtheta == nullptr)
     return fail(h, RA_MPPI_EINVAL, "gV_plus, gV and gtheta are required");
   if (h->keep_x0 == nullptr) return fail(h, RA_MPPI_EINVAL, "the problem was created without RA_MPPI_DIFFERENTIABLE");
+  if (importance(h)) return fail(h, RA_MPPI_EUNSUPPORTED, "backward of importance-sampled rollouts is not supported");
   const ra_mppi_problem& p = h->prob;
   ramppi::BwdArgs a{};
   a.x0 = h->keep_x0;

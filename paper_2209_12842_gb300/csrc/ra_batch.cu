@@ -209,6 +209,10 @@ extern "C" {
 int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* inst, int32_t B,
                          ra_mppi_batch_t** out) {
   if (common == nullptr || inst == nullptr || out == nullptr || B < 1 || B > 65536) return RA_MPPI_EINVAL;
+  if (common->is_scale != 1.0f && common->is_frac > 0.0f) {
+    std::fprintf(stderr, "ra_mppi_batch_create: importance-sampled rollouts are not supported by the batched path\n");
+    return RA_MPPI_EUNSUPPORTED;
+  }
   // every problem must be valid as a single problem
   for (int i = 0; i < B; ++i) {
     ra_mppi_problem p = *common;

@@ -36,6 +36,15 @@ struct DevParams {
   float track_S, track_R, track_hw;
   float inv_lambda, A, B, C_u;
   float risk_param;  // threshold of the chance measure; variance weight of mean-variance
+  float one_m_alpha;  // 1 - alpha
+  // importance-sampled rollouts (see add_process_noise): rollouts m >= is_m0
+  // draw their noise at is_s times its size; a rollout's log density ratio
+  // is is_base + is_cl f A_L + is_cg f^2 A_G (f its factor, A_L the sum of
+  // the unit Laplace magnitudes, A_G of the squared unit normals it drew)
+  int is_m0;
+  float is_s, is_b;         // proposal scale s, proposal fraction b = (M - is_m0) / M
+  float is_base;            // -(draws per rollout) ln s
+  float is_cl, is_cg;       // 1 - 1/s, (1 - 1/s^2) / 2
   uint32_t seed_lo, seed_hi, instance;
   unsigned long long* diag;  // optional count of obstacle candidates tested (diagnostics)
 };
@@ -116,6 +125,29 @@ __device__ __forceinline__ float mix_value(uint32_t sel, uint32_t word, float b,
   const float u2 = (__uint2float_rn(sel) + 0.5f) * inv_thresh;
   const float gauss = -g * rad * __cosf(fmaf(2.0f * kPi, u2, -kPi));
   const float mag = sel < thresh ? gauss : -b * lv;
+  return hi ? mag : -mag;
+}
+
+// mix_value with the unit-scale draw reported for the importance weights:
+// adds |u| of a Laplace draw (-ln v) to *aL, or u^2 of a Gaussian one to
+// *aG (u the value over its branch's scale).  The returned value has the bits
+// of mix_value.
+__device__ __forceinline__ float mix_value_is(uint32_t sel, uint32_t word, float b, float g,
+                                              uint32_t thresh, float inv_thresh, float* aL, float* aG) {
+  const bool hi = (word >> 31) != 0u;
+  const uint32_t r = hi ? ~word : word;
+  const float v = __fmaf_rn(__uint2float_rn(r), 4.656612873077393e-10f, 2.3283064365386963e-10f);
+  const float lv = logf(v);
+  const float e = -2.0f * lv;
+  const float rad = e > 0.0f ? e * rsqrtf(e) : 0.0f;
+  const float u2 = (__uint2float_rn(sel) + 0.5f) * inv_thresh;
+  const float c = __cosf(fmaf(2.0f * kPi, u2, -kPi));
+  const float gauss = -g * rad * c;
+  const bool is_gauss = sel < thresh;
+  const float zc = rad * c;
+  if (is_gauss) *aG = fmaf(zc, zc, *aG);
+  else *aL -= lv;
+  const float mag = is_gauss ? gauss : -b * lv;
   return hi ? mag : -mag;
 }
 
@@ -373,12 +405,41 @@ struct Model<2> {  // linear test system x+ = x + h u
 
 // ---------------------------------------------------------------- noise
 // Process noise of rollout m of sample k at step t, added to the state:
-// counter (t | draw << 16, m, k, instance).
-template <int MODEL>
+// counter (t | draw << 16, m, k, instance).  IS: every value is multiplied by
+// f (the rollout's proposal factor, 1 or s; f = 1 keeps the bits) and the
+// unit-scale draws are summed into *aL (Laplace magnitudes) and *aG (squared
+// normals) for the importance weight (Gaussian and mixture noise only).
+template <int MODEL, bool IS = false>
 __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k0, uint32_t k1,
                                                   uint32_t t, uint32_t m, uint32_t k, uint32_t instance,
-                                                  float* x) {
+                                                  float* x, float f = 1.0f, float* aL = nullptr,
+                                                  float* aG = nullptr) {
   using Md = Model<MODEL>;
+  if constexpr (IS) {
+    if (p.noise_type == 0) {
+      const uint4 w = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
+      const float2 z01 = box_muller_process(w.x, w.y);
+      const float2 z23 = Md::NS > 2 ? box_muller_process(w.z, w.w) : make_float2(0.0f, 0.0f);
+      const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+#pragma unroll
+      for (int s = 0; s < Md::NS; ++s) {
+        x[Md::slot_dim(s)] = fmaf(p.w_scale[s] * f, z[s], x[Md::slot_dim(s)]);
+        if (p.w_scale[s] != 0.0f) *aG = fmaf(z[s], z[s], *aG);
+      }
+    } else {
+      const uint4 sel = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
+      const uint4 val = philox4x32_10(make_uint4(t | (1u << 16), m, k, instance), k0, k1);
+      const uint32_t sw[4] = {sel.x, sel.y, sel.z, sel.w};
+      const uint32_t vw[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+      for (int s = 0; s < Md::NS; ++s) {
+        if (p.w_scale[s] != 0.0f)
+          x[Md::slot_dim(s)] += f * mix_value_is(sw[s], vw[s], p.w_scale[s], p.mix_gauss[s], p.mix_thresh,
+                                                 p.mix_inv_thresh, aL, aG);
+      }
+    }
+    return;
+  }
   if (p.noise_type == 0) {
     const uint4 w = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
     const float2 z01 = box_muller_process(w.x, w.y);

@@ -20,9 +20,10 @@ struct UpdateArgs {
 };
 
 // Rollout kernel launch for one model; ilp in {1, 2, 4}; `pairs`: two
-// samples per warp (dynamic model, ilp 2, at most 32 rollouts per sample).
+// samples per warp (dynamic model, ilp 2, at most 32 rollouts per sample);
+// `is`: importance-sampled rollouts (ilp 1 or 2, not with pairs).
 template <int MODEL>
-cudaError_t launch_rollout(const DevParams& p, const RolloutArgs& a, int warps, int ilp, bool pairs,
+cudaError_t launch_rollout(const DevParams& p, const RolloutArgs& a, int warps, int ilp, bool pairs, bool is,
                            size_t smem, int grid, cudaStream_t s);
 // Raise the dynamic shared memory limit of every instance of a model.
 template <int MODEL>

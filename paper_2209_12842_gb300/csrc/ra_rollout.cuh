@@ -191,20 +191,32 @@ __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP
   }
 }
 
+// Importance weight of one rollout from its proposal factor f and its draw
+// sums: the balance-heuristic weight 1 / ((1 - b) + b q/p) with
+// ln q/p = base + cl f A_L + cg f^2 A_G (an overflowing ratio gives 0)
+__device__ __forceinline__ float is_weight(const DevParams& p, float f, float aL, float aG) {
+  const float lr = fmaf(p.is_cg * f * f, aG, fmaf(p.is_cl * f, aL, p.is_base));
+  return 1.0f / fmaf(p.is_b, expf(lr), 1.0f - p.is_b);
+}
+
 // ILP disturbed rollouts of one lane: rollouts lane + 32 (r0 + i rstride),
 // i < ILP (rows r0, r0 + rstride, ... of the M rollouts); risk costs to Ls
-template <int MODEL, int ILP>
+// (IS: and importance weights to Ws)
+template <int MODEL, int ILP, bool IS = false>
 __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in, const float* x0, int k, int lane,
                                              int r0, int rstride, const float4* ctl, float* Ls,
-                                             const float4* obs_s, int n_obs) {
+                                             const float4* obs_s, int n_obs, float* Ws = nullptr) {
   using Md = Model<MODEL>;
   float x[ILP][Md::NX];
   float L[ILP];
   uint32_t m[ILP];
+  float fis[ILP], aL[ILP], aG[ILP];
 #pragma unroll
   for (int i = 0; i < ILP; ++i) {
     m[i] = (uint32_t)(lane + 32 * (r0 + i * rstride));
     L[i] = 0.0f;
+    fis[i] = IS && (int)m[i] >= p.is_m0 ? p.is_s : 1.0f;
+    aL[i] = aG[i] = 0.0f;
 #pragma unroll
     for (int j = 0; j < Md::NX; ++j) x[i][j] = x0[j];
   }
@@ -231,11 +243,15 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
     }
 #pragma unroll
     for (int i = 0; i < ILP; ++i)
-      add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, m[i], (uint32_t)k, in.instance, x[i]);
+      add_process_noise<MODEL, IS>(p, in.k0, in.k1, (uint32_t)t, m[i], (uint32_t)k, in.instance, x[i], fis[i],
+                                   &aL[i], &aG[i]);
   }
 #pragma unroll
   for (int i = 0; i < ILP; ++i)
-    if ((int)m[i] < in.M) Ls[m[i]] = L[i];
+    if ((int)m[i] < in.M) {
+      Ls[m[i]] = L[i];
+      if constexpr (IS) Ws[m[i]] = is_weight(p, fis[i], aL[i], aG[i]);
+    }
 }
 
 // U^k into shared memory, steps t_first, t_first + t_stride, ... (the nominal
@@ -254,10 +270,10 @@ __device__ __forceinline__ void fill_controls(const DevParams& p, const Inst& in
 
 // the rollout rows r_first, r_first + r_stride, ... of sample k (one warp);
 // ILP rows interleaved, the rest one at a time
-template <int MODEL, int ILP>
+template <int MODEL, int ILP, bool IS = false>
 __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in, const float* __restrict__ x0g, int k,
                                              int lane, int r_first, int r_stride, const float4* ctl, float* Ls,
-                                             const float4* obs_s, int n_obs) {
+                                             const float4* obs_s, int n_obs, float* Ws = nullptr) {
   using Md = Model<MODEL>;
   float x0[Md::NX];
 #pragma unroll
@@ -265,9 +281,10 @@ __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in,
   const int R = (in.M + 31) >> 5;
   int r = r_first;
   for (; r + (ILP - 1) * r_stride < R; r += ILP * r_stride)
-    rollouts_ilp<MODEL, ILP>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs);
+    rollouts_ilp<MODEL, ILP, IS>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
   if (ILP > 1)
-    for (; r < R; r += r_stride) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs);
+    for (; r < R; r += r_stride)
+      rollouts_ilp<MODEL, 1, IS>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
 }
 
 // CVaR_k (or the selected risk measure) of the M risk costs in Ls (one warp)
@@ -374,19 +391,141 @@ __device__ __forceinline__ void risk_from_shared(const DevParams& p, const Inst&
   __syncwarp();
 }
 
+// The risk measure of the weighted empirical distribution of the M risk
+// costs in Ls with the importance weights in Ws (one warp).  With
+// W = sum w and tau = (1 - alpha) W: VaR is the smallest cost whose strictly
+// larger weight is at most tau (a radix select on the order-preserving keys
+// that sums weights instead of counting), RU CVaR = VaR + sum w (L - VaR)+ /
+// tau, TCE the weighted mean of the costs >= VaR, the chance measure the
+// weight fraction above the threshold, the mean and mean-variance the
+// weighted moments.  Fixed summation order: the bits do not depend on the
+// launch shape.
+__device__ __forceinline__ void risk_from_shared_w(const DevParams& p, const Inst& in, const float* Ls,
+                                                   const float* Ws, int k, int lane, float* __restrict__ cvar,
+                                                   float* __restrict__ Lout, int* status) {
+  constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
+  uint32_t key[RMAX];
+  float val[RMAX], wt[RMAX];
+  bool bad = false;
+  float sw = 0.0f, swl = 0.0f;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const int idx = lane + 32 * r;
+    const bool valid = idx < in.M;
+    const float v = valid ? Ls[idx] : 0.0f;
+    const float w = valid ? Ws[idx] : 0.0f;
+    val[r] = v;
+    wt[r] = w;
+    bad |= valid && !isfinite(v);
+    sw += w;
+    swl = fmaf(w, v, swl);
+    key[r] = valid ? fkey(v) : 0xFFFFFFFFu;
+  }
+  if (Lout != nullptr) {
+    // kept costs, then the weights after all K x M costs
+    float* Wout = Lout + (size_t)in.K * in.M;
+    for (int idx = lane; idx < in.M; idx += 32) {
+      Lout[(size_t)k * in.M + idx] = Ls[idx];
+      Wout[(size_t)k * in.M + idx] = Ws[idx];
+    }
+  }
+  if (__any_sync(0xFFFFFFFFu, bad)) {
+    if (lane == 0) {
+      cvar[k] = __int_as_float(0x7F800000);
+      atomicOr(status, kStatusNonFinite);
+    }
+    __syncwarp();
+    return;
+  }
+  const float W = warp_sum(sw);
+  const float mean = warp_sum(swl) / W;
+  const float tau = p.one_m_alpha * W;
+  // VaR: bit by bit from the top, keep the upper half while the weight above
+  // it plus its own stays at most tau
+  uint32_t prefix = 0u;
+  float above = 0.0f;
+#pragma unroll 1
+  for (int b = 31; b >= 0; --b) {
+    const uint32_t hi_mask = (b == 31) ? 0u : (0xFFFFFFFFu << (b + 1));
+    float s1 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const uint32_t kk = key[r];
+      if ((kk & hi_mask) == prefix && ((kk >> b) & 1u) != 0u && (lane + 32 * r) < in.M) s1 += wt[r];
+    }
+    s1 = warp_sum(s1);
+    if (above + s1 > tau) prefix |= (1u << b);
+    else above += s1;
+  }
+  // the weight sums round: should a near-tie have left the search below
+  // every cost of the bucket it skipped, take the smallest cost at or above
+  // the key found (in exact arithmetic, the key itself)
+  uint32_t kmin = 0xFFFFFFFFu;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r)
+    if (lane + 32 * r < in.M && key[r] >= prefix) kmin = min(kmin, key[r]);
+  kmin = __reduce_min_sync(0xFFFFFFFFu, kmin);
+  const float var = fkey_inv(kmin != 0xFFFFFFFFu ? kmin : prefix);
+  float w_gt = 0.0f, w_eq = 0.0f, tail = 0.0f, wl_ge = 0.0f;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    if (lane + 32 * r < in.M) {
+      const float v = val[r], w = wt[r];
+      if (v > var) {
+        w_gt += w;
+        tail = fmaf(w, v - var, tail);
+        wl_ge = fmaf(w, v, wl_ge);
+      } else if (v == var) {
+        w_eq += w;
+        wl_ge = fmaf(w, v, wl_ge);
+      }
+    }
+  }
+  float cv;
+  if (p.cvar_mode == 0) {
+    cv = var + warp_sum(tail) / tau;
+  } else if (p.cvar_mode == 1) {
+    cv = warp_sum(wl_ge) / (warp_sum(w_gt) + warp_sum(w_eq));
+  } else if (p.cvar_mode == 2) {
+    cv = var;
+  } else if (p.cvar_mode == 3) {
+    float over = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const float v = p.B == 1.0f ? val[r] : fmaf(p.B, val[r] - mean, mean);
+      if (lane + 32 * r < in.M && v > p.risk_param) over += wt[r];
+    }
+    cv = warp_sum(over) / W;
+  } else if (p.cvar_mode == 4) {
+    cv = mean;
+  } else {
+    float d2 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const float d = val[r] - mean;
+      if (lane + 32 * r < in.M) d2 = fmaf(wt[r] * d, d, d2);
+    }
+    cv = fmaf(p.risk_param * p.B * p.B, warp_sum(d2) / W, mean);
+  }
+  if (p.B != 1.0f && p.cvar_mode <= 2) cv = fmaf(p.B, cv, (1.0f - p.B) * mean);
+  if (lane == 0) cvar[k] = cv;
+  __syncwarp();
+}
+
 // One warp: the M disturbed rollouts of sample k and CVaR_k (written to cvar[k]).
 // ctl [T] and Ls [M] are this warp's shared-memory scratch.
-template <int MODEL, int ILP>
+template <int MODEL, int ILP, bool IS = false>
 __device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst& in, const float* __restrict__ x0g,
                                                  const float* __restrict__ V, int k, int lane, float4* ctl, float* Ls,
                                                  const float4* obs_s, int n_obs, float* __restrict__ cvar,
-                                                 float* __restrict__ Lout, int* status) {
+                                                 float* __restrict__ Lout, int* status, float* Ws = nullptr) {
   fill_controls<MODEL>(p, in, V, k, lane, 32, ctl);
   __syncwarp();
   // disturbed rollouts and their risk costs (Eq. 9)
-  run_rollouts<MODEL, ILP>(p, in, x0g, k, lane, 0, 1, ctl, Ls, obs_s, n_obs);
+  run_rollouts<MODEL, ILP, IS>(p, in, x0g, k, lane, 0, 1, ctl, Ls, obs_s, n_obs, Ws);
   __syncwarp();
-  risk_from_shared(p, in, Ls, k, lane, cvar, Lout, status);
+  if constexpr (IS) risk_from_shared_w(p, in, Ls, Ws, k, lane, cvar, Lout, status);
+  else risk_from_shared(p, in, Ls, k, lane, cvar, Lout, status);
 }
 
 // One warp, two samples ka, kb of at most 32 rollouts each (the dynamic
@@ -435,7 +574,9 @@ __device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const 
 // PAIRS: the instantiation that takes two samples per warp (dynamic model,
 // interleave 2, one row per sample); a separate kernel so that its code does
 // not raise the register count of the others
-template <int MODEL, int ILP, bool PAIRS = false>
+// IS: importance-sampled rollouts with weights in shared memory after the
+// costs (a separate instantiation; never with PAIRS)
+template <int MODEL, int ILP, bool PAIRS = false, bool IS = false>
 __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
   extern __shared__ float4 smem[];
   float4* obs_s = smem;
@@ -457,6 +598,7 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   const int k = ((int)blockIdx.x - a.nb_nom) * spb + gi;
   float4* ctl = smem + a.obs_cap + gi * in.T;
   float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + spb * in.T) + gi * in.M;
+  float* Ws = IS ? Ls + spb * in.M : nullptr;
   if constexpr (PAIRS) {
     // two samples per warp: slots 2w and 2w + 1 of the block's controls and costs
     const int ka = ((int)blockIdx.x - a.nb_nom) * 2 * warps + 2 * w, kb = ka + 1;
@@ -469,7 +611,8 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   } else {
   if (G == 1) {
     if (k >= in.K) return;
-    disturbed_sample<MODEL, ILP>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L, &a.st->status);
+    disturbed_sample<MODEL, ILP, IS>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L,
+                                     &a.st->status, Ws);
     return;
   }
   // a sample's rollout rows split over its G warps; every warp of the block
@@ -477,9 +620,12 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   const bool valid = k < in.K;
   if (valid) fill_controls<MODEL>(p, in, a.V, k, g * 32 + lane, 32 * G, ctl);
   __syncthreads();
-  if (valid) run_rollouts<MODEL, ILP>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs);
+  if (valid) run_rollouts<MODEL, ILP, IS>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs, Ws);
   __syncthreads();
-  if (valid && g == 0) risk_from_shared(p, in, Ls, k, lane, a.cvar, a.L, &a.st->status);
+  if (valid && g == 0) {
+    if constexpr (IS) risk_from_shared_w(p, in, Ls, Ws, k, lane, a.cvar, a.L, &a.st->status);
+    else risk_from_shared(p, in, Ls, k, lane, a.cvar, a.L, &a.st->status);
+  }
   }
 }
 

@@ -19,6 +19,13 @@ import oracle
 RTOL = 1e-4
 
 
+def importance_on(p):
+    """Whether a preset draws importance-sampled rollouts (at least one)."""
+    s = float(np.float32(p.get("is_scale", 1.0)))
+    f = float(np.float32(p.get("is_frac", 0.0)))
+    return s != 1.0 and f > 0.0 and int(np.floor(f * int(p["M"]))) > 0
+
+
 def abs_floor(ref):
     return 1e-4 * max(1.0, float(np.median(np.abs(ref))))
 
@@ -48,13 +55,24 @@ def compare(p, g, ref, check_update=True):
     nC = check_banded("CVaR", g["cvar"][ks], ref["cvar"], ref["cvar_lo"], ref["cvar_hi"],
                       floor=1e-4 * max(1.0, float(np.median(np.abs(ref["S_tilde"])))))
     nT = check_banded("S_tilde", g["S_tilde"][ks], ref["S_tilde"], ref["St_lo"], ref["St_hi"])
-    # 3. CVaR on the GPU's own risk costs
+    # 3. CVaR on the GPU's own risk costs (and its own importance weights,
+    # which must match the oracle's within the float32 error of their log
+    # density ratio: about 1e-6 per draw from the Box-Muller transcendentals,
+    # bounded here by 4e-6 per draw)
     if g["L"] is not None:
         alpha = float(np.float32(p["alpha"]))
         Bs = float(np.float32(p["B"]))
+        weighted = importance_on(p)
         for i, k in enumerate(ks):
-            want = oracle.risk(g["L"][k].astype(np.float64), alpha, Bs, p["cvar_mode"],
-                               float(np.float32(p.get("risk_param", 0.0))))
+            w = None
+            if weighted:
+                w = g["W"][k].astype(np.float64)
+                w_ref = oracle.is_weights(p, k)
+                n_draws = int(p["T"]) * int(np.count_nonzero(np.asarray(p["w_scale"], np.float32)))
+                np.testing.assert_allclose(np.log(w), np.log(w_ref), rtol=0, atol=4e-6 * n_draws,
+                                           err_msg=f"importance weights of sample {k}")
+            want = oracle.risk_w(g["L"][k].astype(np.float64), w, alpha, Bs, p["cvar_mode"],
+                                 float(np.float32(p.get("risk_param", 0.0))))
             assert abs(g["cvar"][k] - want) <= 1e-5 * max(1.0, abs(want)), (k, g["cvar"][k], want)
     # 4. update stage on the GPU's S~ and U
     if check_update:

@@ -74,6 +74,26 @@ def test_create_rejects_invalid_mean_variance_weight(pkg, kappa):
     assert ei.value.code == pkg.binding.RA_MPPI_EINVAL
 
 
+@pytest.mark.parametrize("ov", [dict(is_scale=0.5, is_frac=0.5), dict(is_scale=17.0, is_frac=0.5),
+                                dict(is_scale=float("nan"), is_frac=0.5), dict(is_scale=2.0, is_frac=1.0),
+                                dict(is_scale=2.0, is_frac=-0.1),
+                                dict(is_scale=2.0, is_frac=0.5, noise_type=rs.NOISE_UNIFORM),
+                                dict(is_scale=2.0, is_frac=0.5, noise_type=rs.NOISE_IMPULSE)])
+def test_create_rejects_invalid_importance_sampling(pkg, ov):
+    p = rs.preset("c1_plain", **ov)
+    with pytest.raises(pkg.binding.RaMppiError) as ei:
+        pkg.binding.ra_mppi_create(pkg.binding.ra_mppi_problem_from(p))
+    assert ei.value.code == pkg.binding.RA_MPPI_EINVAL
+
+
+def test_batched_path_refuses_importance_sampling(pkg):
+    p = rs.preset("c1_plain", is_scale=1.5, is_frac=0.5)
+    inst = [pkg.binding.ra_mppi_instance(K=64, M=32, T=10, max_obstacles=4, seed=1, instance_id=0, reserved=0)]
+    with pytest.raises(pkg.binding.RaMppiError) as ei:
+        pkg.binding.ra_mppi_batch_create(pkg.binding.ra_mppi_problem_from(p), inst)
+    assert ei.value.code == pkg.binding.RA_MPPI_EUNSUPPORTED
+
+
 def test_null_arguments(pkg):
     L = pkg.lib()
     assert L.ra_mppi_create(None, None) == pkg.binding.RA_MPPI_EINVAL
