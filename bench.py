@@ -513,7 +513,7 @@ def adjoint_study(torch, steps):
             "backward_rollout_steps_per_s": units / b50 * 1e3}
 
 
-def importance_study(torch, is_scale=1.5, is_frac=0.5, alpha=0.99):
+def importance_study(torch, scales=((1.5, 0.5), (1.1, 0.5)), alpha=0.99):
     """Importance-sampled CVaR at alpha = 0.99: the spread of the estimate
     over K independent samples with identical controls (sigma_u = 0), plain
     Monte Carlo against the scaled-proposal, deterministic-mixture weights at
@@ -536,7 +536,7 @@ def importance_study(torch, is_scale=1.5, is_frac=0.5, alpha=0.99):
         ctl.close()
         return cv, ms
 
-    out = {"alpha": alpha, "is_scale": is_scale, "is_frac": is_frac}
+    out = {"alpha": alpha}
     T, sw = 10, float(np.float32(0.5))
     a32 = float(np.float32(alpha))
     V = (np.arange(T) * 0.1 - 0.3).astype(np.float32).reshape(T, 1)
@@ -545,8 +545,8 @@ def importance_study(torch, is_scale=1.5, is_frac=0.5, alpha=0.99):
     sd = sw * np.sqrt((T - 1) * T * (2 * T - 1) / 6.0)
     truth = xs.sum() + sd * NormalDist().pdf(NormalDist().inv_cdf(a32)) / (1 - a32)
     p = rs.preset("linear_test", K=4096, M=128, T=T, w_scale=(sw, 0, 0, 0), alpha=alpha)
-    lin = {"closed_form": truth, "M": 128, "K": 4096}
-    for name, ov in (("plain", {}), ("importance", dict(is_scale=is_scale, is_frac=is_frac))):
+    lin = {"closed_form": truth, "M": 128, "K": 4096, "is_scale": scales[0][0], "is_frac": scales[0][1]}
+    for name, ov in (("plain", {}), ("importance", dict(is_scale=scales[0][0], is_frac=scales[0][1]))):
         cv, ms = estimates(dict(p, **ov), np.zeros((0, 3), np.float32), x0, V)
         lin[name] = {"mean": float(cv.mean()), "sd": float(cv.std()),
                      "rmse": float(np.sqrt(np.mean((cv - truth) ** 2))), "update_ms": ms}
@@ -557,8 +557,9 @@ def importance_study(torch, is_scale=1.5, is_frac=0.5, alpha=0.99):
     obs = np.array([[0.8, x0[1] + 0.21, 0.2], [1.2, x0[1] - 0.21, 0.2]], np.float32)
     V = np.tile(np.array([[0.0, 1.0]], np.float32), (p["T"], 1))  # straight, accelerating
     ref, _ = estimates(dict(p, M=512), obs, x0, V)
-    dyn = {"reference_mean_M512": float(ref.mean()), "M": p["M"], "K": p["K"]}
-    for name, ov in (("plain", {}), ("importance", dict(is_scale=is_scale, is_frac=is_frac))):
+    dyn = {"reference_mean_M512": float(ref.mean()), "M": p["M"], "K": p["K"], "is_scale": scales[1][0],
+           "is_frac": scales[1][1]}
+    for name, ov in (("plain", {}), ("importance", dict(is_scale=scales[1][0], is_frac=scales[1][1]))):
         cv, ms = estimates(dict(p, **ov), obs, x0, V)
         dyn[name] = {"mean": float(cv.mean()), "sd": float(cv.std()), "update_ms": ms}
     dyn["variance_ratio"] = (dyn["plain"]["sd"] / dyn["importance"]["sd"]) ** 2 if dyn["importance"]["sd"] > 0 else None
