@@ -955,7 +955,8 @@ static void rollout_vjp(const orc_problem* p, const double* xs, const double* Uk
 int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, const double* obs, int32_t n_obs,
                      const double* gVp, const double* gSt, double* gV, double* gtheta) {
   if (p->substeps > 64) return -1;
-  if (is_count(p) > 0) return -6; /* importance-sampled rollouts: forward only */
+  const int M_s = is_count(p);
+  if (M_s > 0 && p->noise_type != ORC_GAUSS && p->noise_type != ORC_LAPLACE_MIX) return -6;
   const int K = p->K, M = p->M, T = p->T, nx = nx_of(p->model), nu = nu_of(p->model);
   const int n_warm = n_warm_of(p);
   double inv_sig2[2];
@@ -968,6 +969,7 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
   double* Xn = (double*)calloc((size_t)K * (T + 1) * nx, sizeof(double));
   double* Xd = (double*)calloc((size_t)K * M * (T + 1) * nx, sizeof(double));
   double* Lm = (double*)calloc((size_t)K * M, sizeof(double));
+  double* Wm = (double*)calloc((size_t)K * M, sizeof(double)); /* importance weights (1 when off) */
   /* forward with stored states (same steps as orc_samples) */
   for (int k = 0; k < K; ++k) {
     double* Uk = U + (size_t)k * T * nu;
@@ -994,17 +996,19 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
     for (int m = 0; m < M; ++m) {
       double* xd = Xd + ((size_t)k * M + m) * (T + 1) * nx;
       for (int a = 0; a < nx; ++a) xd[a] = x0[a];
-      double Lv = 0.0;
+      double Lv = 0.0, G = 0.0;
       for (int t = 0; t < T; ++t) {
         Lv += state_cost(p, xd + (size_t)t * nx, obs, n_obs, p->risk_mask, 0.0);
         double w[4];
-        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, 1.0, NULL, w);
+        process_noise_at(p, p->iteration, (uint32_t)m, (uint32_t)k, t, is_factor(p, m, M_s), M_s > 0 ? &G : NULL, w);
         orc_dynamics(p, xd + (size_t)t * nx, Uk + t * nu, xd + (size_t)(t + 1) * nx);
         for (int s = 0; s < nslots_of(p->model); ++s) xd[(size_t)(t + 1) * nx + slot_dim(p->model, s)] += w[s];
       }
       Lm[(size_t)k * M + m] = Lv;
+      Wm[(size_t)k * M + m] = M_s > 0 ? is_weight(p, M_s, G) : 1.0;
     }
-    cv[k] = orc_risk(Lm + (size_t)k * M, M, p->alpha, p->B, p->cvar_mode, p->risk_param);
+    cv[k] = orc_risk_w(Lm + (size_t)k * M, M_s > 0 ? Wm + (size_t)k * M : NULL, M, p->alpha, p->B, p->cvar_mode,
+                       p->risk_param);
     St[k] = S[k] + ((cv[k] > p->C_u) ? p->A * cv[k] : 0.0);
   }
   /* update and its weights */
@@ -1021,7 +1025,6 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
   for (int i = 0; i < 4; ++i) gtheta[i] = 0.0;
   double* gU = (double*)calloc((size_t)T * nu, sizeof(double));
   double* La = (double*)calloc((size_t)M, sizeof(double));
-  double* srt = (double*)calloc((size_t)M, sizeof(double));
   for (int k = 0; k < K; ++k) {
     const double* Uk = U + (size_t)k * T * nu;
     /* cotangent of S~_k */
@@ -1041,38 +1044,43 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
       }
       gtheta[2] += sbar * ctrl;
     }
-    /* disturbed: weights of CVaR in each L_{k,m} */
+    /* disturbed: weights of CVaR in each L_{k,m}.  With importance weights
+     * w (all 1 when off) every count becomes a weight sum: the measure of
+     * the weighted empirical distribution, W = sum w in place of M */
     if (cvbar != 0.0) {
       const double* Lk = Lm + (size_t)k * M;
-      double mean = 0.0;
-      for (int m = 0; m < M; ++m) mean += Lk[m];
-      mean /= M;
-      for (int m = 0; m < M; ++m) { La[m] = p->B * (Lk[m] - mean) + mean; srt[m] = La[m]; }
-      qsort(srt, (size_t)M, sizeof(double), cmp_double);
-      double aM = p->alpha * M;
-      int j = (int)ceil(aM);
-      if (j < 1) j = 1;
-      if (j > M) j = M;
-      double var = srt[j - 1];
-      int c_gt = 0, c_eq = 0;
-      for (int m = 0; m < M; ++m) { if (La[m] > var) ++c_gt; else if (La[m] == var) ++c_eq; }
-      double denom = (1.0 - p->alpha) * M;
+      const double* wk = Wm + (size_t)k * M;
+      double W = 0.0, mean = 0.0;
+      for (int m = 0; m < M; ++m) { W += wk[m]; mean += wk[m] * Lk[m]; }
+      mean /= W;
+      for (int m = 0; m < M; ++m) La[m] = p->B * (Lk[m] - mean) + mean;
+      /* VaR: the smallest La_m whose strictly larger weight is at most (1 - alpha) W */
+      const double tau = (1.0 - p->alpha) * W;
+      double var = INFINITY;
+      for (int c = 0; c < M; ++c) {
+        double above = 0.0;
+        for (int n = 0; n < M; ++n)
+          if (La[n] > La[c]) above += wk[n];
+        if (above <= tau && La[c] < var) var = La[c];
+      }
+      double w_gt = 0.0, w_eq = 0.0;
+      for (int m = 0; m < M; ++m) { if (La[m] > var) w_gt += wk[m]; else if (La[m] == var) w_eq += wk[m]; }
       for (int m = 0; m < M; ++m) {
         double wa;
         if (p->cvar_mode == ORC_CVAR_RU)
-          wa = La[m] > var ? 1.0 / denom : (La[m] == var ? ((double)(M - c_gt) - aM) / denom / c_eq : 0.0);
+          wa = La[m] > var ? wk[m] / tau : (La[m] == var ? (1.0 - w_gt / tau) * wk[m] / w_eq : 0.0);
         else if (p->cvar_mode == ORC_CVAR_TCE)
-          wa = La[m] >= var ? 1.0 / (c_gt + c_eq) : 0.0;
+          wa = La[m] >= var ? wk[m] / (w_gt + w_eq) : 0.0;
         else if (p->cvar_mode == ORC_VAR)
-          wa = La[m] == var ? 1.0 / c_eq : 0.0;
+          wa = La[m] == var ? wk[m] / w_eq : 0.0;
         else if (p->cvar_mode == ORC_MEAN)
-          wa = 1.0 / M;
+          wa = wk[m] / W;
         else if (p->cvar_mode == ORC_MEANVAR)
-          wa = (1.0 + 2.0 * p->risk_param * (La[m] - mean)) / M;
+          wa = wk[m] * (1.0 + 2.0 * p->risk_param * (La[m] - mean)) / W;
         else
           wa = 0.0; /* the chance measure is piecewise constant in L */
         if (p->cvar_mode == ORC_CHANCE) continue;
-        double lbar = cvbar * (p->B * wa + (1.0 - p->B) / M);
+        double lbar = cvbar * (p->B * wa + (1.0 - p->B) * wk[m] / W);
         if (lbar != 0.0)
           rollout_vjp(p, Xd + ((size_t)k * M + m) * (T + 1) * nx, Uk, obs, n_obs, p->risk_mask, 0, lbar, gU, gtheta);
       }
@@ -1080,8 +1088,8 @@ int32_t orc_backward(const orc_problem* p, const double* x0, const double* V, co
     /* through U = clip(V + eps) to V */
     for (int c = 0; c < T * nu; ++c) gV[c] += gU[c] * inside[(size_t)k * T * nu + c];
   }
-  free(U); free(inside); free(S); free(cv); free(St); free(Xn); free(Xd); free(Lm);
-  free(wh); free(Vp); free(gU); free(La); free(srt);
+  free(U); free(inside); free(S); free(cv); free(St); free(Xn); free(Xd); free(Lm); free(Wm);
+  free(wh); free(Vp); free(gU); free(La);
   return 0;
 }
 

@@ -71,6 +71,29 @@ def test_p11_dynamic_single_track(orc, noise, C):
     assert np.all(np.isfinite(gV)) and np.any(gV != 0)
 
 
+@pytest.mark.parametrize("name,mode", [("c4_gradient", 0), ("c4_gradient", rs.RISK_MEANVAR), ("small_dyn", 0),
+                                       ("small_dyn", rs.CVAR_TCE)])
+def test_p11_importance_sampled(orc, name, mode):
+    # importance weights depend on the noise only, so the risk measure of the
+    # weighted costs differentiates like the plain one with weights in it
+    if name == "small_dyn":
+        p = rs.preset(name, K=8, M=12, T=4, substeps=2, obs_mode=rs.OBS_SOFTPLUS, kappa=20.0, w_obs=5.0,
+                      risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED, mix_p=0.3)
+        x0 = np.array([0.0, -4.0, 0.05, 2.0, 0.1, 0.3])
+    else:
+        p = rs.preset(name, K=10, M=12, T=5, risk_mask=rs.RISK_OBS | rs.RISK_DEV)
+        x0 = np.array([0.0, -4.0, 0.0, 1.0])
+    p = dict(p, cvar_mode=mode, B=1.5, risk_param=0.05, alpha=0.8, is_scale=1.4, is_frac=0.5)
+    obs = rs.obstacles_ahead(3, 6, 0.15, 0.3, x_from=0.05, x_to=0.6, lateral=0.3)
+    V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 6).astype(np.float64)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 12)
+    gV, gth = _fd_check(orc, p, x0, V, obs, gVp, gS)
+    assert np.all(np.isfinite(gV)) and np.any(gV != 0)
+    # and it differs from the unweighted gradient
+    gV0, _ = orc.backward(dict(p, is_frac=0.0), x0, V, obs, gVp, gS, exact=True)
+    assert np.max(np.abs(gV - gV0)) > 1e-6 * max(1.0, np.max(np.abs(gV0)))
+
+
 def test_p11_all_terms_and_zero_mean_samples(orc):
     p = rs.preset("c4_gradient", K=10, M=6, T=5, eta=0.3, w_bdry=2.0, c4=0.6, c5=2.0, A=2.0, C_u=10.0,
                   risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED | rs.RISK_BDRY)
