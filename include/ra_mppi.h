@@ -174,8 +174,9 @@ typedef struct ra_mppi_problem {
    * most (1 - alpha) sum w; RU CVaR: VaR + sum w (L - VaR)+ / ((1 - alpha)
    * sum w); the others the weighted tail mean, fraction or moments).
    * Off when is_frac = 0 or is_scale = 1 (or M_s = 0).  is_scale in
-   * [1, 16], is_frac in [0, 1); Gaussian and mixture noise only; not with
-   * ra_mppi_backward or the batched path (EUNSUPPORTED there). */
+   * [1, 16], is_frac in [0, 1); Gaussian and mixture noise only; not on the
+   * batched path (EUNSUPPORTED there).  ra_mppi_backward differentiates the
+   * weighted measure (the weights depend on the noise only). */
   float is_scale;
   float is_frac;
 } ra_mppi_problem;
@@ -288,7 +289,8 @@ int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta);
  * from gV_plus [T][nu] (device) and gS_tilde [K] (device, or NULL for 0):
  * the derivative of the softmin update (Eqs. 4, 5, 17), of the violation
  * cost (Eqs. 14-16: A where CVaR > C_u, else 0), of the fractional-tail or
- * literal CVaR (Eqs. 10-13: the tail weights; Eqs. 18, 19: the scaling), of
+ * literal CVaR (Eqs. 10-13: the tail weights, times the importance weights
+ * when importance sampling is on; Eqs. 18, 19: the scaling), of
  * the costs and dynamics along every nominal and disturbed rollout (Eqs. 3,
  * 6, 9, 20-23; states recomputed from checkpoints every 8 steps), and of the
  * clip U = clip(V + eps) (Alg. 1).  The obstacle indicator (Eq. 22) has

@@ -345,11 +345,26 @@ __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a
   for (int i = 0; i < 4; ++i) a.thn[(size_t)k * 4 + i] = gth[i];
 }
 
+// process noise of rollout m at step t as the forward added it: scaled by
+// the rollout's proposal factor when importance sampling is on
+template <int MODEL, bool IS>
+__device__ __forceinline__ void replay_noise(const DevParams& p, const Inst& in, int t, int m, int k, float* x) {
+  if constexpr (IS) {
+    float aL = 0.0f, aG = 0.0f;
+    add_process_noise<MODEL, true>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance, x,
+                                   m >= p.is_m0 ? p.is_s : 1.0f, &aL, &aG);
+  } else {
+    add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance, x);
+  }
+}
+
 // disturbed rollouts of sample k (one warp): cotangents of U_k through the
-// CVaR term; theta partials of the risk costs
-template <int MODEL>
+// CVaR term; theta partials of the risk costs.  With importance sampling the
+// importance weights Ws (beside Ls) enter every weight of the risk measure
+// (a separate instantiation, so the plain adjoint keeps its registers).
+template <int MODEL, bool IS>
 __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs& a, int k, int lane, float4* ctl,
-                              float* Ls, float* gus, const float4* obs_s, int n_obs) {
+                              float* Ls, float* Ws, float* gus, const float4* obs_s, int n_obs) {
   using Md = Model<MODEL>;
   constexpr int NX = Md::NX, NU = Md::NU;
   const int T = in.T, TN = T * NU, M = in.M;
@@ -372,7 +387,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   for (int i = 0; i < NX; ++i) x0[i] = a.x0[i];
   const int R = (M + 31) >> 5;
   // pass 1: the risk costs (same arithmetic as the forward rollouts)
-  for (int r = 0; r < R; ++r) rollouts_ilp<MODEL, 1>(p, in, x0, k, lane, r, 1, ctl, Ls, obs_s, n_obs);
+  for (int r = 0; r < R; ++r) rollouts_ilp<MODEL, 1, IS>(p, in, x0, k, lane, r, 1, ctl, Ls, obs_s, n_obs, Ws);
   __syncwarp();
   // CVaR weights: VaR by radix select, then the tail
   constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
@@ -431,16 +446,61 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   }
   // mean-variance: d rho / d L_a,n = (1 + 2 kappa (L_a,n - mean)) / M with
   // L_a,n - mean = B (L_n - mean)
-  const float mean = warp_sum(sum) / (float)M;
-  const float w_dev = p.cvar_mode == 5 ? 2.0f * p.risk_param * p.B / (float)M : 0.0f;
-  const float base = p.cvar_mode == 3 ? 0.0f : (1.0f - p.B) / (float)M;
+  float mean = warp_sum(sum) / (float)M;
+  float w_dev = p.cvar_mode == 5 ? 2.0f * p.risk_param * p.B / (float)M : 0.0f;
+  float base = p.cvar_mode == 3 ? 0.0f : (1.0f - p.B) / (float)M;
+  float wts[IS ? RMAX : 1];
+  float vw = var;
+  if constexpr (IS) {
+    // the weighted empirical distribution: every count becomes a weight sum
+    // (W in place of M, (1 - alpha) W in place of (1 - alpha) M), and each
+    // rollout's weight multiplies its share
+    float sw = 0.0f, swl = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const bool valid = lane + 32 * r < M;
+      wts[r] = valid ? Ws[lane + 32 * r] : 0.0f;
+      sw += wts[r];
+      swl = fmaf(wts[r], val[r], swl);
+    }
+    const float W = warp_sum(sw);
+    mean = warp_sum(swl) / W;
+    const float tau = p.one_m_alpha * W;
+    vw = weighted_var<RMAX>(key, wts, M, lane, tau);
+    float wgt = 0.0f, weq = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (lane + 32 * r < M) {
+        if (val[r] > vw) wgt += wts[r];
+        else if (val[r] == vw) weq += wts[r];
+      }
+    }
+    wgt = warp_sum(wgt);
+    weq = warp_sum(weq);
+    w_all = 0.0f;
+    if (p.cvar_mode == 0) {
+      w_gt = 1.0f / tau;
+      w_eq = (1.0f - wgt / tau) / weq;
+    } else if (p.cvar_mode == 1) {
+      w_gt = w_eq = 1.0f / (wgt + weq);
+    } else if (p.cvar_mode == 2) {
+      w_gt = 0.0f;
+      w_eq = 1.0f / weq;
+    } else {
+      w_gt = w_eq = 0.0f;
+      if (p.cvar_mode >= 4) w_all = 1.0f / W;
+    }
+    w_dev = p.cvar_mode == 5 ? 2.0f * p.risk_param * p.B / W : 0.0f;
+    base = p.cvar_mode == 3 ? 0.0f : (1.0f - p.B) / W;
+  }
   // pass 2: reverse sweep of every rollout with a nonzero weight
   float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int r = 0; r < R; ++r) {
     const int m = lane + 32 * r;
     const float Lm = val[r];
-    const float wt = m < M ? (Lm > var ? w_gt : (Lm == var ? w_eq : 0.0f)) + fmaf(w_dev, Lm - mean, w_all) : 0.0f;
-    const float lbar = m < M ? cvbar * fmaf(p.B, wt, base) : 0.0f;
+    const float wt = m < M ? (Lm > vw ? w_gt : (Lm == vw ? w_eq : 0.0f)) + fmaf(w_dev, Lm - mean, w_all) : 0.0f;
+    float lbar = m < M ? cvbar * fmaf(p.B, wt, base) : 0.0f;
+    if constexpr (IS) lbar *= wts[r];
     if (!__any_sync(0xFFFFFFFFu, lbar != 0.0f)) continue;
     float ck[kMaxCk][NX];
     float x[NX];
@@ -452,7 +512,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
         for (int i = 0; i < NX; ++i) ck[t / kSeg][i] = x[i];
       }
       Md::step(p, x, ctl[t]);
-      add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance, x);
+      replay_noise<MODEL, IS>(p, in, t, m, k, x);
     }
     float lam[NX];
 #pragma unroll
@@ -467,8 +527,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
 #pragma unroll
         for (int i = 0; i < NX; ++i) xs[t + 1 - t0][i] = xs[t - t0][i];
         Md::step(p, xs[t + 1 - t0], ctl[t]);
-        add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance,
-                                 xs[t + 1 - t0]);
+        replay_noise<MODEL, IS>(p, in, t, m, k, xs[t + 1 - t0]);
       }
       for (int t = t1 - 1; t >= t0; --t) {
         float gu[2] = {0.0f, 0.0f};
@@ -491,7 +550,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   }
 }
 
-template <int MODEL>
+template <int MODEL, bool IS>
 __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const BwdArgs a) {
   extern __shared__ float4 smem[];
   float4* obs_s = smem;
@@ -509,9 +568,12 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
   const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
   if (k >= in.K) return;
   float4* ctl = smem + a.obs_cap + w * in.T;
-  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * (in.M + in.T * p.nu);
-  float* gus = Ls + in.M;
-  bwd_disturbed<MODEL>(p, in, a, k, lane, ctl, Ls, gus, obs_s, n_obs);
+  // per warp: risk costs [M], importance weights [M] (when on), U cotangents [T nu]
+  const int wcap = IS ? in.M : 0;
+  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * (in.M + wcap + in.T * p.nu);
+  float* Ws = Ls + in.M;
+  float* gus = Ws + wcap;
+  bwd_disturbed<MODEL, IS>(p, in, a, k, lane, ctl, Ls, Ws, gus, obs_s, n_obs);
 }
 
 // gV[c] = sum_k Gnom[k][c] + mask[k][c] gUd[k][c]; gtheta[i] = sum_k thn + thd
@@ -553,22 +615,29 @@ __global__ void __launch_bounds__(256) bwd_reduce_kernel(const DevParams p, cons
   if (threadIdx.x == 0) a.arrive[1] = 0u;
 }
 
+template <int MODEL>
+cudaError_t launch_bwd_main(const DevParams& p, const BwdArgs& a, bool is, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e;
+  if (is) {
+    e = cudaFuncSetAttribute(bwd_main_kernel<MODEL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) bwd_main_kernel<MODEL, true><<<grid, 128, smem, s>>>(p, a);
+  } else {
+    e = cudaFuncSetAttribute(bwd_main_kernel<MODEL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) bwd_main_kernel<MODEL, false><<<grid, 128, smem, s>>>(p, a);
+  }
+  return e;
+}
+
 cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
                             size_t smem, int nb_red, cudaStream_t s) {
   bwd_prep_kernel<<<nb_prep, 256, 0, s>>>(p, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int grid = a.nb_nom + nb_dist;
-  if (model == 0) {
-    e = cudaFuncSetAttribute(bwd_main_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) bwd_main_kernel<0><<<grid, 128, smem, s>>>(p, a);
-  } else if (model == 1) {
-    e = cudaFuncSetAttribute(bwd_main_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) bwd_main_kernel<1><<<grid, 128, smem, s>>>(p, a);
-  } else {
-    e = cudaFuncSetAttribute(bwd_main_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) bwd_main_kernel<2><<<grid, 128, smem, s>>>(p, a);
-  }
+  const bool is = p.is_b > 0.0f;
+  if (model == 0) e = launch_bwd_main<0>(p, a, is, grid, smem, s);
+  else if (model == 1) e = launch_bwd_main<1>(p, a, is, grid, smem, s);
+  else e = launch_bwd_main<2>(p, a, is, grid, smem, s);
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

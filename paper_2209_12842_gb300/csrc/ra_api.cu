@@ -730,7 +730,6 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   if (gV_plus == nullptr || gV == nullptr || gtheta == nullptr)
     return fail(h, RA_MPPI_EINVAL, "gV_plus, gV and gtheta are required");
   if (h->keep_x0 == nullptr) return fail(h, RA_MPPI_EINVAL, "the problem was created without RA_MPPI_DIFFERENTIABLE");
-  if (importance(h)) return fail(h, RA_MPPI_EUNSUPPORTED, "backward of importance-sampled rollouts is not supported");
   const ra_mppi_problem& p = h->prob;
   ramppi::BwdArgs a{};
   a.x0 = h->keep_x0;
@@ -759,8 +758,9 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.nb_nom = (p.K + 32 * kBwdWarps - 1) / (32 * kBwdWarps);
   a.obs_cap = h->obs_cap;
   const int nb_dist = (p.K + kBwdWarps - 1) / kBwdWarps;
+  // per warp: controls, risk costs, importance weights (when on), U cotangents
   const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * p.T * sizeof(float4) +
-                      (size_t)kBwdWarps * (p.M + (size_t)p.T * h->nu) * sizeof(float);
+                      (size_t)kBwdWarps * (p.M * (importance(h) ? 2 : 1) + (size_t)p.T * h->nu) * sizeof(float);
   const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, h->nb_prep, nb_dist, smem, h->nb_red,
                                                 static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");

@@ -391,12 +391,43 @@ __device__ __forceinline__ void risk_from_shared(const DevParams& p, const Inst&
   __syncwarp();
 }
 
+// VaR of the weighted empirical distribution of M costs held by one warp
+// (key, wt: rows lane + 32 r): the smallest cost whose strictly larger weight
+// is at most tau.  A radix select on the order-preserving keys that sums
+// weights instead of counting: bit by bit from the top, keep the upper half
+// while the weight above it plus its own exceeds tau.  The weight sums
+// round: should a near-tie have left the search below every cost of the
+// bucket it skipped, the smallest cost at or above the key found is taken
+// (in exact arithmetic, the key itself).
+template <int RMAX>
+__device__ __forceinline__ float weighted_var(const uint32_t* key, const float* wt, int M, int lane, float tau) {
+  uint32_t prefix = 0u;
+  float above = 0.0f;
+#pragma unroll 1
+  for (int b = 31; b >= 0; --b) {
+    const uint32_t hi_mask = (b == 31) ? 0u : (0xFFFFFFFFu << (b + 1));
+    float s1 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const uint32_t kk = key[r];
+      if ((kk & hi_mask) == prefix && ((kk >> b) & 1u) != 0u && (lane + 32 * r) < M) s1 += wt[r];
+    }
+    s1 = warp_sum(s1);
+    if (above + s1 > tau) prefix |= (1u << b);
+    else above += s1;
+  }
+  uint32_t kmin = 0xFFFFFFFFu;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r)
+    if (lane + 32 * r < M && key[r] >= prefix) kmin = min(kmin, key[r]);
+  kmin = __reduce_min_sync(0xFFFFFFFFu, kmin);
+  return fkey_inv(kmin != 0xFFFFFFFFu ? kmin : prefix);
+}
+
 // The risk measure of the weighted empirical distribution of the M risk
 // costs in Ls with the importance weights in Ws (one warp).  With
-// W = sum w and tau = (1 - alpha) W: VaR is the smallest cost whose strictly
-// larger weight is at most tau (a radix select on the order-preserving keys
-// that sums weights instead of counting), RU CVaR = VaR + sum w (L - VaR)+ /
-// tau, TCE the weighted mean of the costs >= VaR, the chance measure the
+// W = sum w and tau = (1 - alpha) W: VaR from weighted_var, RU CVaR =
+// VaR + sum w (L - VaR)+ / tau, TCE the weighted mean of the costs >= VaR, the chance measure the
 // weight fraction above the threshold, the mean and mean-variance the
 // weighted moments.  Fixed summation order: the bits do not depend on the
 // launch shape.
@@ -440,32 +471,7 @@ __device__ __forceinline__ void risk_from_shared_w(const DevParams& p, const Ins
   const float W = warp_sum(sw);
   const float mean = warp_sum(swl) / W;
   const float tau = p.one_m_alpha * W;
-  // VaR: bit by bit from the top, keep the upper half while the weight above
-  // it plus its own stays at most tau
-  uint32_t prefix = 0u;
-  float above = 0.0f;
-#pragma unroll 1
-  for (int b = 31; b >= 0; --b) {
-    const uint32_t hi_mask = (b == 31) ? 0u : (0xFFFFFFFFu << (b + 1));
-    float s1 = 0.0f;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      const uint32_t kk = key[r];
-      if ((kk & hi_mask) == prefix && ((kk >> b) & 1u) != 0u && (lane + 32 * r) < in.M) s1 += wt[r];
-    }
-    s1 = warp_sum(s1);
-    if (above + s1 > tau) prefix |= (1u << b);
-    else above += s1;
-  }
-  // the weight sums round: should a near-tie have left the search below
-  // every cost of the bucket it skipped, take the smallest cost at or above
-  // the key found (in exact arithmetic, the key itself)
-  uint32_t kmin = 0xFFFFFFFFu;
-#pragma unroll
-  for (int r = 0; r < RMAX; ++r)
-    if (lane + 32 * r < in.M && key[r] >= prefix) kmin = min(kmin, key[r]);
-  kmin = __reduce_min_sync(0xFFFFFFFFu, kmin);
-  const float var = fkey_inv(kmin != 0xFFFFFFFFu ? kmin : prefix);
+  const float var = weighted_var<RMAX>(key, wt, in.M, lane, tau);
   float w_gt = 0.0f, w_eq = 0.0f, tail = 0.0f, wl_ge = 0.0f;
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) {

@@ -126,6 +126,29 @@ def test_adjoint_dynamic_model(case):
     _close("gtheta", gth, rth)
 
 
+@pytest.mark.parametrize("case", ["kin_ru", "kin_meanvar", "dyn_ru", "dyn_tce"])
+def test_adjoint_importance_sampled(case):
+    # importance weights depend on the noise only: the adjoint of the weighted
+    # risk measure, through the scaled noise of the proposal rollouts
+    if case.startswith("kin"):
+        p = rs.preset("c4_gradient", K=96, M=40, T=12, is_scale=1.4, is_frac=0.5, alpha=0.8, B=1.5,
+                      cvar_mode=rs.CVAR_RU if case == "kin_ru" else rs.RISK_MEANVAR, risk_param=0.05)
+        x0 = np.array([0.0, -4.0, 0.0, 1.0], np.float32)
+        obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4)
+    else:
+        p = rs.preset("small_dyn", K=64, M=40, T=8, obs_mode=rs.OBS_SOFTPLUS, kappa=20.0, w_obs=5.0,
+                      risk_mask=rs.RISK_OBS | rs.RISK_DEV | rs.RISK_SPEED, is_scale=1.3, is_frac=0.5, alpha=0.8,
+                      cvar_mode=rs.CVAR_RU if case == "dyn_ru" else rs.CVAR_TCE, mix_p=0.3)
+        x0 = np.array([0.0, -4.0, 0.05, 2.0, 0.1, 0.3], np.float32)
+        obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.1, x_to=1.2, lateral=0.4)
+    V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 3)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    gV, gth = _run(p, obs, x0, V, gVp, gS)
+    rV, rth = oracle.backward(p, x0, V, obs, gVp, gS)
+    _close("gV", gV, rV)
+    _close("gtheta", gth, rth)
+
+
 def test_adjoint_rejects_missing_flag():
     from paper_2209_12842_gb300 import RaMppi, RaMppiError
 

@@ -131,10 +131,12 @@ def test_importance_is_refused_where_unsupported():
     from paper_2209_12842_gb300.binding import RaMppiError
 
     p, obs, x0, V = _case("small_kin")
-    ctl = RaMppi(p, obs, differentiable=True)
-    ctl.step(torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda())
+    ctl = RaMppi(p, obs)
     with pytest.raises(RaMppiError):
-        ctl.backward(torch.zeros(p["T"], 2, device="cuda"))
-    with pytest.raises(RaMppiError):
-        ctl.set_launch(4, 4, 1)
+        ctl.set_launch(4, 4, 1)  # importance-sampled rollouts interleave 1 or 2
     ctl.close()
+    plain = RaMppi(dict(p, is_frac=0.0), obs, keep_risk_costs=True)
+    plain.step(torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda())
+    with pytest.raises(RaMppiError):
+        plain.importance_weights()  # no weights without importance sampling
+    plain.close()
