@@ -95,6 +95,28 @@ def test_importance_launch_shapes(launch):
     compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
 
 
+@pytest.mark.parametrize("M,launch", [(512, (8, 2, 8)), (512, (4, 1, 4)), (33, (2, 1, 1)), (300, (6, 2, 3)),
+                                      (2, (4, 2, 1))])
+def test_importance_sizes(M, launch):
+    # large, ragged and tiny M (M = 2 with f = 1/2: one proposal rollout)
+    p, obs, x0, V = _case("small_kin", M=M, K=21)
+    base = _gpu(p, obs, x0, V, launch=(4, 1, 1))
+    g = _gpu(p, obs, x0, V, launch=launch)
+    for key in ("L", "W", "cvar", "S_tilde", "V_plus"):
+        np.testing.assert_array_equal(g[key], base[key], err_msg=f"{M} {launch} {key}")
+    compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
+
+
+def test_importance_single_rollout_is_plain():
+    # M = 1: floor(f M) = 0 proposal rollouts, so importance sampling is off
+    p, obs, x0, V = _case("small_dyn", M=1)
+    g = _gpu(p, obs, x0, V)
+    plain = _gpu(dict(p, is_frac=0.0), obs, x0, V)
+    for key in ("L", "cvar", "S_tilde", "V_plus"):
+        np.testing.assert_array_equal(g[key], plain[key], err_msg=key)
+    assert "W" not in g
+
+
 @pytest.mark.parametrize("mode", [rs.RISK_VAR, rs.CVAR_TCE])
 def test_importance_var_and_tail_mean_are_valid(mode):
     """VaR must be a risk cost v with W(L > v) <= tau <= W(L >= v) up to
