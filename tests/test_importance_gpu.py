@@ -107,6 +107,25 @@ def test_importance_sizes(M, launch):
     compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
 
 
+def test_importance_config2_full_size_sampled():
+    # config 2 at full size (K = 4096, M = 128, T = 40, mixture noise) with
+    # importance sampling, on sampled k, in the tuned launch
+    from paper_2209_12842_gb300 import RaMppi
+
+    p = rs.preset("c2_closed_loop", is_scale=1.1, is_frac=0.5, alpha=0.99)
+    obs = rs.obstacles_ahead(5, int(p["n_obs"]), *p["obs_r"], x_from=0.1, x_to=1.2)
+    x0 = rs.initial_state(1)
+    V = rs.random_controls(1, p["T"], p["u_lo"], p["u_hi"], 4)
+    ctl = RaMppi(p, obs)
+    ctl.tune(torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda(), 2)
+    launch = ctl.get_launch()
+    ctl.close()
+    g = _gpu(p, obs, x0, V, launch=launch)
+    K = int(p["K"])
+    ks = np.unique(np.concatenate([[0, K // 2, K - 1], np.random.default_rng(3).integers(0, K, 13)])).astype(np.int32)
+    compare(p, g, oracle.samples(p, x0, V, obs, ks=ks, n_threads=8))
+
+
 def test_importance_single_rollout_is_plain():
     # M = 1: floor(f M) = 0 proposal rollouts, so importance sampling is off
     p, obs, x0, V = _case("small_dyn", M=1)
