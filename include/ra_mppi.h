@@ -57,7 +57,7 @@ typedef enum {
   RA_MPPI_ECUDA = -3,        /* a CUDA runtime call or launch failed        */
   RA_MPPI_ETIMEOUT = -4,     /* a bounded device wait gave up               */
   RA_MPPI_ENONFINITE = -5,   /* a cost was NaN/inf or all weights vanished  */
-  RA_MPPI_EUNSUPPORTED = -6  /* valid request that this build does not do   */
+  RA_MPPI_EUNSUPPORTED = -6  /* valid request the library does not support  */
 } ra_mppi_status;
 
 /* Dynamics F (Eq. 1).  The paper does not give its vehicle model; these are
