@@ -174,9 +174,10 @@ typedef struct ra_mppi_problem {
    * most (1 - alpha) sum w; RU CVaR: VaR + sum w (L - VaR)+ / ((1 - alpha)
    * sum w); the others the weighted tail mean, fraction or moments).
    * Off when is_frac = 0 or is_scale = 1 (or M_s = 0).  is_scale in
-   * [1, 16], is_frac in [0, 1); Gaussian and mixture noise only; not on the
-   * batched path (EUNSUPPORTED there).  ra_mppi_backward differentiates the
-   * weighted measure (the weights depend on the noise only). */
+   * [1, 16], is_frac in [0, 1); Gaussian and mixture noise only.  The
+   * batched path applies it per problem (M_s from each problem's M);
+   * ra_mppi_backward differentiates the weighted measure (the weights depend
+   * on the noise only). */
   float is_scale;
   float is_frac;
 } ra_mppi_problem;

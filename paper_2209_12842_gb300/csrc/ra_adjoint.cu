@@ -352,7 +352,7 @@ __device__ __forceinline__ void replay_noise(const DevParams& p, const Inst& in,
   if constexpr (IS) {
     float aL = 0.0f, aG = 0.0f;
     add_process_noise<MODEL, true>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance, x,
-                                   m >= p.is_m0 ? p.is_s : 1.0f, &aL, &aG);
+                                   m >= in.is_m0 ? p.is_s : 1.0f, &aL, &aG);
   } else {
     add_process_noise<MODEL>(p, in.k0, in.k1, (uint32_t)t, (uint32_t)m, (uint32_t)k, in.instance, x);
   }

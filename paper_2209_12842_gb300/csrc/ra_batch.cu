@@ -49,6 +49,7 @@ struct ra_mppi_batch {
   long long n_items = 0, n_x0 = 0, n_V = 0, n_U = 0, n_k = 0, n_obs = 0, n_part = 0;
   int obs_cap_max = 0, T_max = 0, M_max = 0, upd_blocks = 0;
   int warps = 4, ilp = 1, blocks_per_sm = 1, n_sms = 1;
+  bool is = false;  // importance-sampled rollouts
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -92,7 +93,7 @@ void release(ra_mppi_batch* b) {
 }
 
 size_t batch_smem(const ra_mppi_batch* b) {
-  return (size_t)b->warps * ramppi::batch_warp_f4(b->obs_cap_max, b->T_max, b->M_max) * sizeof(float4);
+  return (size_t)b->warps * ramppi::batch_warp_f4(b->obs_cap_max, b->T_max, b->M_max, b->is) * sizeof(float4);
 }
 
 // per-kernel dynamic shared-memory limit, shared by all batches: only raised
@@ -122,13 +123,13 @@ cudaError_t prepare(ra_mppi_batch* b) {
   int bps = 0;
   switch (b->common.model) {
     case 0:
-      e = ramppi::batch_rollout_occupancy<0>(b->warps, b->ilp, smem, &bps);
+      e = ramppi::batch_rollout_occupancy<0>(b->warps, b->ilp, b->is, smem, &bps);
       break;
     case 1:
-      e = ramppi::batch_rollout_occupancy<1>(b->warps, b->ilp, smem, &bps);
+      e = ramppi::batch_rollout_occupancy<1>(b->warps, b->ilp, b->is, smem, &bps);
       break;
     default:
-      e = ramppi::batch_rollout_occupancy<2>(b->warps, b->ilp, smem, &bps);
+      e = ramppi::batch_rollout_occupancy<2>(b->warps, b->ilp, b->is, smem, &bps);
       break;
   }
   if (e != cudaSuccess) return e;
@@ -166,9 +167,9 @@ cudaError_t enqueue(ra_mppi_batch* b, cudaStream_t s) {
   const size_t smem = batch_smem(b);
   const int grid = b->blocks_per_sm * b->n_sms;
   switch (b->common.model) {
-    case 0: e = ramppi::launch_batch_rollout<0>(b->dp, a, b->warps, b->ilp, smem, grid, s); break;
-    case 1: e = ramppi::launch_batch_rollout<1>(b->dp, a, b->warps, b->ilp, smem, grid, s); break;
-    default: e = ramppi::launch_batch_rollout<2>(b->dp, a, b->warps, b->ilp, smem, grid, s); break;
+    case 0: e = ramppi::launch_batch_rollout<0>(b->dp, a, b->warps, b->ilp, b->is, smem, grid, s); break;
+    case 1: e = ramppi::launch_batch_rollout<1>(b->dp, a, b->warps, b->ilp, b->is, smem, grid, s); break;
+    default: e = ramppi::launch_batch_rollout<2>(b->dp, a, b->warps, b->ilp, b->is, smem, grid, s); break;
   }
   if (e != cudaSuccess) return e;
   BatchUpdateArgs u{};
@@ -209,10 +210,6 @@ extern "C" {
 int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* inst, int32_t B,
                          ra_mppi_batch_t** out) {
   if (common == nullptr || inst == nullptr || out == nullptr || B < 1 || B > 65536) return RA_MPPI_EINVAL;
-  if (common->is_scale != 1.0f && common->is_frac > 0.0f) {
-    std::fprintf(stderr, "ra_mppi_batch_create: importance-sampled rollouts are not supported by the batched path\n");
-    return RA_MPPI_EUNSUPPORTED;
-  }
   // every problem must be valid as a single problem
   for (int i = 0; i < B; ++i) {
     ra_mppi_problem p = *common;
@@ -230,6 +227,7 @@ int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* 
   if (b == nullptr) return RA_MPPI_ENOMEM;
   b->common = *common;
   b->dp = ramppi_api::make_params(*common);
+  b->is = common->is_scale != 1.0f && common->is_frac > 0.0f;
   b->B = B;
   b->nx = common->model == RA_MPPI_KIN_BICYCLE ? 4 : common->model == RA_MPPI_DYN_SINGLE_TRACK ? 6 : 1;
   b->nu = common->model == RA_MPPI_LINEAR_TEST ? 1 : 2;
@@ -258,6 +256,9 @@ int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* 
     q.seed_lo = d.seed_lo;
     q.seed_hi = d.seed_hi;
     q.obs_cap = inst[i].max_obstacles;
+    q.is_m0 = d.is_m0;
+    q.is_b = d.is_b;
+    q.is_base = d.is_base;
     q.nb_upd = ramppi::update_blocks(q.K);
     q.upd_block_base = ub;
     q.x0_off = x0o;

@@ -19,6 +19,8 @@ struct InstDesc {
   int obs_cap;          // obstacle capacity of this problem
   int nb_upd;           // update blocks of this problem
   int upd_block_base;   // first update block of this problem
+  int is_m0;            // importance sampling: first proposal rollout,
+  float is_b, is_base;  // proposal fraction, -(draws per rollout) ln s
   int pad_;
   long long x0_off, V_off, U_off, k_off, obs_off, part_off;
 };
@@ -40,18 +42,22 @@ struct BatchArgs {
   int obs_cap_max, T_max, M_max;
 };
 
-__host__ __device__ inline int batch_warp_f4(int obs_cap_max, int T_max, int M_max) {
-  return obs_cap_max + T_max + (M_max + 3) / 4;
+// float4 slots of one warp's shared memory: obstacles, controls, risk costs
+// (and importance weights)
+__host__ __device__ inline int batch_warp_f4(int obs_cap_max, int T_max, int M_max, bool is = false) {
+  return obs_cap_max + T_max + (M_max + 3) / 4 * (is ? 2 : 1);
 }
 
-template <int MODEL, int ILP>
+// IS: importance-sampled rollouts (a separate instantiation)
+template <int MODEL, int ILP, bool IS = false>
 __global__ void __launch_bounds__(256) batch_rollout_kernel(const DevParams p, const BatchArgs a) {
   extern __shared__ float4 smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* base = smem + (size_t)w * batch_warp_f4(a.obs_cap_max, a.T_max, a.M_max);
+  float4* base = smem + (size_t)w * batch_warp_f4(a.obs_cap_max, a.T_max, a.M_max, IS);
   float4* obs_s = base;
   float4* ctl = base + a.obs_cap_max;
   float* Ls = reinterpret_cast<float*>(base + a.obs_cap_max + a.T_max);
+  float* Ws = IS ? reinterpret_cast<float*>(base + a.obs_cap_max + a.T_max + (a.M_max + 3) / 4) : nullptr;
   int cur = -1, n_obs = 0;
   Inst in{};
   const InstDesc* d = nullptr;
@@ -84,6 +90,9 @@ __global__ void __launch_bounds__(256) batch_rollout_kernel(const DevParams p, c
       in.instance = d->instance;
       in.k0 = d->seed_lo;
       in.k1 = d->seed_hi ^ (uint32_t)a.st[i].iteration;
+      in.is_m0 = d->is_m0;
+      in.is_b = d->is_b;
+      in.is_base = d->is_base;
       cur = i;
       __syncwarp();
     }
@@ -93,8 +102,14 @@ __global__ void __launch_bounds__(256) batch_rollout_kernel(const DevParams p, c
         nominal_rollout<MODEL>(p, in, a.x0 + d->x0_off, a.V + d->V_off, a.U + d->U_off, a.S + d->k_off, k, obs_s,
                                n_obs);
     } else {
-      disturbed_sample<MODEL, ILP>(p, in, a.x0 + d->x0_off, a.V + d->V_off, (int)local, lane, ctl, Ls, obs_s, n_obs,
-                                   a.cvar + d->k_off, nullptr, &a.st[i].status);
+      // a problem too small for a proposal rollout (floor(f M) = 0) takes
+      // the plain path, as a single-problem handle does
+      if (IS && in.is_b > 0.0f)
+        disturbed_sample<MODEL, ILP, true>(p, in, a.x0 + d->x0_off, a.V + d->V_off, (int)local, lane, ctl, Ls, obs_s,
+                                           n_obs, a.cvar + d->k_off, nullptr, &a.st[i].status, Ws);
+      else
+        disturbed_sample<MODEL, ILP, false>(p, in, a.x0 + d->x0_off, a.V + d->V_off, (int)local, lane, ctl, Ls,
+                                            obs_s, n_obs, a.cvar + d->k_off, nullptr, &a.st[i].status);
     }
     __syncwarp();
   }

@@ -61,14 +61,15 @@ cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int
                             size_t smem, int nb_red, cudaStream_t s);
 
 // Batched path (ra_batch.cuh, ra_batch.cu): persistent rollout kernel of one
-// model, its shared-memory limit and occupancy, and the batched update.
+// model, its shared-memory limit and occupancy, and the batched update
+// (`is`: importance-sampled rollouts).
 template <int MODEL>
-cudaError_t launch_batch_rollout(const DevParams& p, const BatchArgs& a, int warps, int ilp, size_t smem,
+cudaError_t launch_batch_rollout(const DevParams& p, const BatchArgs& a, int warps, int ilp, bool is, size_t smem,
                                  int grid, cudaStream_t s);
 template <int MODEL>
 cudaError_t prepare_batch_rollout(size_t smem);
 template <int MODEL>
-cudaError_t batch_rollout_occupancy(int warps, int ilp, size_t smem, int* blocks_per_sm);
+cudaError_t batch_rollout_occupancy(int warps, int ilp, bool is, size_t smem, int* blocks_per_sm);
 
 struct BatchUpdateArgs {
   const InstDesc* desc;

@@ -30,6 +30,10 @@ struct Inst {
   int K, M, T, n_warm, j_var;
   float frac_j, tail_denom;
   uint32_t instance, k0, k1;  // Philox counter word 3 and key
+  // importance sampling: first proposal rollout, proposal fraction b and
+  // -(draws per rollout) ln s (they depend on M and T)
+  int is_m0;
+  float is_b, is_base;
 };
 
 __device__ __forceinline__ Inst inst_of(const DevParams& p, uint32_t iteration) {
@@ -44,6 +48,9 @@ __device__ __forceinline__ Inst inst_of(const DevParams& p, uint32_t iteration) 
   in.instance = p.instance;
   in.k0 = p.seed_lo;
   in.k1 = p.seed_hi ^ iteration;
+  in.is_m0 = p.is_m0;
+  in.is_b = p.is_b;
+  in.is_base = p.is_base;
   return in;
 }
 
@@ -194,9 +201,9 @@ __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP
 // Importance weight of one rollout from its proposal factor f and its draw
 // sums: the balance-heuristic weight 1 / ((1 - b) + b q/p) with
 // ln q/p = base + cl f A_L + cg f^2 A_G (an overflowing ratio gives 0)
-__device__ __forceinline__ float is_weight(const DevParams& p, float f, float aL, float aG) {
-  const float lr = fmaf(p.is_cg * f * f, aG, fmaf(p.is_cl * f, aL, p.is_base));
-  return 1.0f / fmaf(p.is_b, expf(lr), 1.0f - p.is_b);
+__device__ __forceinline__ float is_weight(const DevParams& p, const Inst& in, float f, float aL, float aG) {
+  const float lr = fmaf(p.is_cg * f * f, aG, fmaf(p.is_cl * f, aL, in.is_base));
+  return 1.0f / fmaf(in.is_b, expf(lr), 1.0f - in.is_b);
 }
 
 // ILP disturbed rollouts of one lane: rollouts lane + 32 (r0 + i rstride),
@@ -215,7 +222,7 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
   for (int i = 0; i < ILP; ++i) {
     m[i] = (uint32_t)(lane + 32 * (r0 + i * rstride));
     L[i] = 0.0f;
-    fis[i] = IS && (int)m[i] >= p.is_m0 ? p.is_s : 1.0f;
+    fis[i] = IS && (int)m[i] >= in.is_m0 ? p.is_s : 1.0f;
     aL[i] = aG[i] = 0.0f;
 #pragma unroll
     for (int j = 0; j < Md::NX; ++j) x[i][j] = x0[j];
@@ -250,7 +257,7 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
   for (int i = 0; i < ILP; ++i)
     if ((int)m[i] < in.M) {
       Ls[m[i]] = L[i];
-      if constexpr (IS) Ws[m[i]] = is_weight(p, fis[i], aL[i], aG[i]);
+      if constexpr (IS) Ws[m[i]] = is_weight(p, in, fis[i], aL[i], aG[i]);
     }
 }
 

@@ -86,12 +86,12 @@ def test_create_rejects_invalid_importance_sampling(pkg, ov):
     assert ei.value.code == pkg.binding.RA_MPPI_EINVAL
 
 
-def test_batched_path_refuses_importance_sampling(pkg):
-    p = rs.preset("c1_plain", is_scale=1.5, is_frac=0.5)
+def test_batched_path_validates_importance_sampling(pkg):
+    p = rs.preset("c1_plain", is_scale=1.5, is_frac=0.5, noise_type=rs.NOISE_UNIFORM)
     inst = [pkg.binding.ra_mppi_instance(K=64, M=32, T=10, max_obstacles=4, seed=1, instance_id=0, reserved=0)]
     with pytest.raises(pkg.binding.RaMppiError) as ei:
         pkg.binding.ra_mppi_batch_create(pkg.binding.ra_mppi_problem_from(p), inst)
-    assert ei.value.code == pkg.binding.RA_MPPI_EUNSUPPORTED
+    assert ei.value.code == pkg.binding.RA_MPPI_EINVAL
 
 
 def test_null_arguments(pkg):

@@ -42,10 +42,10 @@ def _uneven(n, seed, model):
     return out
 
 
-def _setup(name, insts):
+def _setup(name, insts, **ov):
     from paper_2209_12842_gb300.controller import RaMppiBatch
 
-    p = rs.preset(name)
+    p = rs.preset(name, **ov)
     model = p["model"]
     batch = RaMppiBatch(p, insts)
     obs, x0s, Vs = [], [], []
@@ -81,10 +81,13 @@ def _batch_results(batch):
     return [dict(V_plus=Vs[i], S_tilde=Ss[i], **ws[i]) for i in range(batch.B)]
 
 
-@pytest.mark.parametrize("name", ["small_kin", "small_dyn"])
-def test_batched_equals_single_problems(name):
+@pytest.mark.parametrize("name,ov", [("small_kin", {}), ("small_dyn", {}),
+                                     ("small_kin", dict(is_scale=1.3, is_frac=0.5)),
+                                     ("small_dyn", dict(is_scale=1.2, is_frac=0.25))])
+def test_batched_equals_single_problems(name, ov):
+    # (with importance sampling: per-problem proposal counts and weights)
     insts = _uneven(10, 5, rs.preset(name)["model"])
-    p, batch, obs, x0s, Vs = _setup(name, insts)
+    p, batch, obs, x0s, Vs = _setup(name, insts, **ov)
     batch.set_iteration(4)
     batch.step()
     res = _batch_results(batch)
