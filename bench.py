@@ -664,13 +664,16 @@ def main():
     ap.add_argument("--preroll", type=int, default=200,
                     help="untimed receding-horizon iterations before timing (the state leaves the start area)")
     ap.add_argument("--sweep", action="store_true", help="config 5 stress sweep over M and alpha")
+    ap.add_argument("--K", type=int, default=0,
+                    help="run the workload with this many samples instead (a smaller case for ncu captures; "
+                         "not a bench line of the named workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.sweep:
         stress_sweep(args)
         return
-    p = rs.preset(WORKLOADS[args.workload])
+    p = rs.preset(WORKLOADS[args.workload], **({"K": args.K} if args.K > 0 else {}))
     obs = rs.scene_obstacles(p)
     x0 = rs.scene_initial_state(p)
     V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 3)
