@@ -348,13 +348,15 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   h->ilp = default_ilp(p->M, p->model);
   h->warps = 4;
   // few samples with many rollouts: spread a sample over several warps until
-  // the sample warps fill two waves of the GPU (24 resident warps per SM at
-  // 80 registers, 152 SMs), so the last partial wave is short; measured on
-  // config 2 (K = 4096, M = 128): 2 warps per sample 0.845 ms, 1 warp 0.893
+  // the sample warps fill the GPU (24 resident warps per SM at 80 registers,
+  // 152 SMs).  The dynamic model's long rollouts gain from two waves, so the
+  // last partial wave is short (config 2, K = 4096, M = 128: 2 warps per
+  // sample 0.845 ms, 1 warp 0.893); the cheaper kinematic rollouts from one.
   {
     const int R = (p->M + 31) / 32;
+    const long long waves = p->model == RA_MPPI_DYN_SINGLE_TRACK ? 2 : 1;
     int g = 1;
-    while (g < 4 && (long long)p->K * g < 2LL * 152 * 24 && R >= 2 * g) g *= 2;
+    while (g < 4 && (long long)p->K * g < waves * 152 * 24 && R >= 2 * g) g *= 2;
     h->wps = g;
   }
   cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaGetDevice(&h->device);
