@@ -294,11 +294,13 @@ __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in,
       rollouts_ilp<MODEL, 1, IS>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
 }
 
-// CVaR_k (or the selected risk measure) of the M risk costs in Ls (one warp)
-__device__ __forceinline__ void risk_from_shared(const DevParams& p, const Inst& in, const float* Ls, int k, int lane,
-                                                 float* __restrict__ cvar, float* __restrict__ Lout, int* status) {
+// CVaR_k (or the selected risk measure) of the M risk costs in Ls (one warp),
+// with RMAX >= ceil(M / 32) rows of costs per lane in registers
+template <int RMAX>
+__device__ __forceinline__ void risk_from_shared_rows(const DevParams& p, const Inst& in, const float* Ls, int k,
+                                                      int lane, float* __restrict__ cvar, float* __restrict__ Lout,
+                                                      int* status) {
   // CVaR_k over the M risk costs (Eqs. 10-13, 18, 19)
-  constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
   uint32_t key[RMAX];
   float val[RMAX];
   bool bad = false;
@@ -398,6 +400,19 @@ __device__ __forceinline__ void risk_from_shared(const DevParams& p, const Inst&
   __syncwarp();
 }
 
+// The row count sized to M, so that the 32 select passes loop over the rows
+// that hold costs only (rows past M add nothing: the same bits for every
+// size class)
+__device__ __forceinline__ void risk_from_shared(const DevParams& p, const Inst& in, const float* Ls, int k, int lane,
+                                                 float* __restrict__ cvar, float* __restrict__ Lout, int* status) {
+  constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
+  if (in.M <= 32) risk_from_shared_rows<1>(p, in, Ls, k, lane, cvar, Lout, status);
+  else if (in.M <= 64) risk_from_shared_rows<2>(p, in, Ls, k, lane, cvar, Lout, status);
+  else if (in.M <= 128) risk_from_shared_rows<4>(p, in, Ls, k, lane, cvar, Lout, status);
+  else if (in.M <= 256) risk_from_shared_rows<8>(p, in, Ls, k, lane, cvar, Lout, status);
+  else risk_from_shared_rows<RMAX>(p, in, Ls, k, lane, cvar, Lout, status);
+}
+
 // VaR of the weighted empirical distribution of M costs held by one warp
 // (key, wt: rows lane + 32 r): the smallest cost whose strictly larger weight
 // is at most tau.  A radix select on the order-preserving keys that sums
@@ -438,10 +453,10 @@ __device__ __forceinline__ float weighted_var(const uint32_t* key, const float* 
 // weight fraction above the threshold, the mean and mean-variance the
 // weighted moments.  Fixed summation order: the bits do not depend on the
 // launch shape.
-__device__ __forceinline__ void risk_from_shared_w(const DevParams& p, const Inst& in, const float* Ls,
-                                                   const float* Ws, int k, int lane, float* __restrict__ cvar,
-                                                   float* __restrict__ Lout, int* status) {
-  constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
+template <int RMAX>
+__device__ __forceinline__ void risk_from_shared_w_rows(const DevParams& p, const Inst& in, const float* Ls,
+                                                        const float* Ws, int k, int lane, float* __restrict__ cvar,
+                                                        float* __restrict__ Lout, int* status) {
   uint32_t key[RMAX];
   float val[RMAX], wt[RMAX];
   bool bad = false;
@@ -523,6 +538,15 @@ __device__ __forceinline__ void risk_from_shared_w(const DevParams& p, const Ins
   if (p.B != 1.0f && p.cvar_mode <= 2) cv = fmaf(p.B, cv, (1.0f - p.B) * mean);
   if (lane == 0) cvar[k] = cv;
   __syncwarp();
+}
+
+__device__ __forceinline__ void risk_from_shared_w(const DevParams& p, const Inst& in, const float* Ls,
+                                                   const float* Ws, int k, int lane, float* __restrict__ cvar,
+                                                   float* __restrict__ Lout, int* status) {
+  constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
+  if (in.M <= 64) risk_from_shared_w_rows<2>(p, in, Ls, Ws, k, lane, cvar, Lout, status);
+  else if (in.M <= 256) risk_from_shared_w_rows<8>(p, in, Ls, Ws, k, lane, cvar, Lout, status);
+  else risk_from_shared_w_rows<RMAX>(p, in, Ls, Ws, k, lane, cvar, Lout, status);
 }
 
 // One warp: the M disturbed rollouts of sample k and CVaR_k (written to cvar[k]).
