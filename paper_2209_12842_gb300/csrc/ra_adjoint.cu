@@ -364,7 +364,7 @@ __device__ __forceinline__ void replay_noise(const DevParams& p, const Inst& in,
 // (a separate instantiation, so the plain adjoint keeps its registers).
 template <int MODEL, bool IS>
 __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs& a, int k, int lane, float4* ctl,
-                              float* Ls, float* Ws, float* gus, const float4* obs_s, int n_obs) {
+                              float* Ls, float* Ws, int* act, float* gus, const float4* obs_s, int n_obs) {
   using Md = Model<MODEL>;
   constexpr int NX = Md::NX, NU = Md::NU;
   const int T = in.T, TN = T * NU, M = in.M;
@@ -493,15 +493,34 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     w_dev = p.cvar_mode == 5 ? 2.0f * p.risk_param * p.B / W : 0.0f;
     base = p.cvar_mode == 3 ? 0.0f : (1.0f - p.B) / W;
   }
-  // pass 2: reverse sweep of every rollout with a nonzero weight
-  float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  for (int r = 0; r < R; ++r) {
+  // the rollouts with a nonzero cotangent, packed: (index, cotangent) pairs
+  // in act[] and Ls[] (the costs are in registers now).  A CVaR tail holds
+  // about (1 - alpha) M of them, so the reverse sweeps below take
+  // ceil(n / 32) rows instead of all ceil(M / 32).
+  int n_act = 0;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    if (r >= R) break;
     const int m = lane + 32 * r;
     const float Lm = val[r];
     const float wt = m < M ? (Lm > vw ? w_gt : (Lm == vw ? w_eq : 0.0f)) + fmaf(w_dev, Lm - mean, w_all) : 0.0f;
-    float lbar = m < M ? cvbar * fmaf(p.B, wt, base) : 0.0f;
-    if constexpr (IS) lbar *= wts[r];
-    if (!__any_sync(0xFFFFFFFFu, lbar != 0.0f)) continue;
+    float lb = m < M ? cvbar * fmaf(p.B, wt, base) : 0.0f;
+    if constexpr (IS) lb *= wts[r];
+    const unsigned nz = __ballot_sync(0xFFFFFFFFu, lb != 0.0f);
+    if (lb != 0.0f) {
+      const int pos = n_act + __popc(nz & ((1u << lane) - 1u));
+      act[pos] = m;
+      Ls[pos] = lb;
+    }
+    n_act += __popc(nz);
+  }
+  __syncwarp();
+  // pass 2: reverse sweep of every rollout with a nonzero weight, 32 at a time
+  float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int c0 = 0; c0 < n_act; c0 += 32) {
+    const bool has = c0 + lane < n_act;
+    const int m = has ? act[c0 + lane] : 0;  // an idle lane replays rollout 0 with no cotangent
+    const float lbar = has ? Ls[c0 + lane] : 0.0f;
     float ck[kMaxCk][NX];
     float x[NX];
 #pragma unroll
@@ -568,12 +587,14 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
   const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
   if (k >= in.K) return;
   float4* ctl = smem + a.obs_cap + w * in.T;
-  // per warp: risk costs [M], importance weights [M] (when on), U cotangents [T nu]
+  // per warp: risk costs [M], importance weights [M] (when on), packed
+  // rollout indices [M], U cotangents [T nu]
   const int wcap = IS ? in.M : 0;
-  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * (in.M + wcap + in.T * p.nu);
+  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * (2 * in.M + wcap + in.T * p.nu);
   float* Ws = Ls + in.M;
-  float* gus = Ws + wcap;
-  bwd_disturbed<MODEL, IS>(p, in, a, k, lane, ctl, Ls, Ws, gus, obs_s, n_obs);
+  int* act = reinterpret_cast<int*>(Ws + wcap);
+  float* gus = reinterpret_cast<float*>(act + in.M);
+  bwd_disturbed<MODEL, IS>(p, in, a, k, lane, ctl, Ls, Ws, act, gus, obs_s, n_obs);
 }
 
 // gV[c] = sum_k Gnom[k][c] + mask[k][c] gUd[k][c]; gtheta[i] = sum_k thn + thd

@@ -762,9 +762,10 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.nb_nom = (p.K + 32 * kBwdWarps - 1) / (32 * kBwdWarps);
   a.obs_cap = h->obs_cap;
   const int nb_dist = (p.K + kBwdWarps - 1) / kBwdWarps;
-  // per warp: controls, risk costs, importance weights (when on), U cotangents
+  // per warp: controls, risk costs, importance weights (when on), packed
+  // rollout indices, U cotangents
   const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * p.T * sizeof(float4) +
-                      (size_t)kBwdWarps * (p.M * (importance(h) ? 2 : 1) + (size_t)p.T * h->nu) * sizeof(float);
+                      (size_t)kBwdWarps * (p.M * (importance(h) ? 3 : 2) + (size_t)p.T * h->nu) * sizeof(float);
   const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, h->nb_prep, nb_dist, smem, h->nb_red,
                                                 static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
