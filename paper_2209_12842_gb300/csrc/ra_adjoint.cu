@@ -386,8 +386,9 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
 #pragma unroll
   for (int i = 0; i < NX; ++i) x0[i] = a.x0[i];
   const int R = (M + 31) >> 5;
-  // pass 1: the risk costs (same arithmetic as the forward rollouts)
-  for (int r = 0; r < R; ++r) rollouts_ilp<MODEL, 1, IS>(p, in, x0, k, lane, r, 1, ctl, Ls, obs_s, n_obs, Ws);
+  // pass 1: the risk costs (the forward rollouts' arithmetic and bits, two
+  // rows at a time)
+  run_rollouts<MODEL, 2, IS>(p, in, a.x0, k, lane, 0, 1, ctl, Ls, obs_s, n_obs, Ws);
   __syncwarp();
   // CVaR weights: VaR by radix select, then the tail
   constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
