@@ -200,7 +200,10 @@ void ra_mppi_destroy(ra_mppi_t* h);
  * (centre x, centre y, radius), host or device pointer.  Synchronous: the
  * copy has completed when the call returns.  EINVAL if n_obs >
  * max_obstacles, a radius is negative, a centre is not finite, or a disc
- * leaves the square of side 2 RA_MPPI_OBSTACLE_EXTENT around the origin. */
+ * leaves the square of side 2 RA_MPPI_OBSTACLE_EXTENT around the origin.
+ * The library keeps them sorted by x (the obstacle cull narrows to an x
+ * window); the costs do not depend on the order, except for the rounding of
+ * the softplus barrier's sum. */
 int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* stream);
 
 /* One RA-MPPI update on device buffers (steps 1-6 above).

@@ -574,11 +574,13 @@ template <int MODEL, bool IS>
 __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const BwdArgs a) {
   extern __shared__ float4 smem[];
   float4* obs_s = smem;
+  float4* const scratch = obs_s + a.obs_cap;  // the warps' scratch after the obstacles
   const int n_obs = a.st->n_obs;
   // the differentiated update already advanced the counter
   const Inst in = inst_of(p, (uint32_t)(a.st->iteration - 1ull));
   for (int i = threadIdx.x; i < n_obs; i += blockDim.x) obs_s[i] = a.obs[i];
   __syncthreads();
+
   if ((int)blockIdx.x < a.nb_nom) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < in.K) bwd_nominal<MODEL>(p, in, a, k, obs_s, n_obs);
@@ -587,11 +589,11 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
   if (k >= in.K) return;
-  float4* ctl = smem + a.obs_cap + w * in.T;
+  float4* ctl = scratch + w * in.T;
   // per warp: risk costs [M], importance weights [M] (when on), packed
   // rollout indices [M], U cotangents [T nu]
   const int wcap = IS ? in.M : 0;
-  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + warps * in.T) + w * (2 * in.M + wcap + in.T * p.nu);
+  float* Ls = reinterpret_cast<float*>(scratch + warps * in.T) + w * (2 * in.M + wcap + in.T * p.nu);
   float* Ws = Ls + in.M;
   int* act = reinterpret_cast<int*>(Ws + wcap);
   float* gus = reinterpret_cast<float*>(act + in.M);

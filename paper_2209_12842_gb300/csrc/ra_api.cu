@@ -1,6 +1,7 @@
 // C ABI of the RA-MPPI update library (declarations and contracts in
 // include/ra_mppi.h).  Host side only: validation, workspace, constants and
 // kernel launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -20,6 +21,7 @@ struct ra_mppi {
   int device = 0;
   int nx = 0, nu = 0;
   int warps = 4, ilp = 1, wps = 1;  // warps per block, rollouts interleaved, warps per sample
+  int n_obs_host = 0;                // obstacle count of the last set_obstacles
   int nb_upd = 1;
   int obs_cap = 0;
   size_t smem = 0;
@@ -265,6 +267,10 @@ size_t g_smem_limit[64][3] = {};  // per device, per model
 // pair; see disturbed_sample_pair)
 bool importance(const ra_mppi* h) { return is_count(h->prob) > 0; }
 
+// the obstacle cull's x window: dynamic model with more than 64 obstacles
+// (below that the box test takes two rounds at most)
+bool windowed(const ra_mppi* h) { return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->n_obs_host > 64; }
+
 bool pairs_samples(const ra_mppi* h) {
   return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->ilp == 2 && h->wps == 1 && h->prob.M <= 32 &&
          !importance(h);
@@ -275,8 +281,9 @@ int samples_per_block(const ra_mppi* h) { return (h->warps / h->wps) * (pairs_sa
 
 size_t rollout_smem(const ra_mppi* h) {
   const size_t spb = (size_t)samples_per_block(h);
-  // obstacles, controls, risk costs (and importance weights) per sample
-  return (size_t)h->obs_cap * sizeof(float4) + spb * h->prob.T * sizeof(float4) +
+  // the largest obstacle radius (read by the windowed cull only), obstacles,
+  // then controls, risk costs (and importance weights) per sample
+  return (1 + (size_t)h->obs_cap) * sizeof(float4) + spb * h->prob.T * sizeof(float4) +
          spb * h->prob.M * sizeof(float) * (importance(h) ? 2 : 1);
 }
 
@@ -449,6 +456,8 @@ int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* s
       host[i] = make_float4(tmp[3 * i], tmp[3 * i + 1], r, r * r);
     }
     std::free(tmp);
+    // stored sorted by x: the kernels' obstacle cull narrows to an x window
+    std::stable_sort(host, host + n_obs, [](const float4& u, const float4& v) { return u.x < v.x; });
     e = cudaMemcpyAsync(h->obs, host, sizeof(float4) * n_obs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     std::free(host);
@@ -461,6 +470,7 @@ int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* s
   } else {
     return cuda_fail(h, e, "set_obstacles count");
   }
+  h->n_obs_host = n_obs;
   return RA_MPPI_OK;
 }
 
@@ -498,9 +508,9 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
     if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
   }
   switch (p.model) {
-    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), h->smem, grid, s); break;
-    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), h->smem, grid, s); break;
-    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), h->smem, grid, s); break;
+    case 0: e = ramppi::launch_rollout<0>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), windowed(h), h->smem, grid, s); break;
+    case 1: e = ramppi::launch_rollout<1>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), windowed(h), h->smem, grid, s); break;
+    default: e = ramppi::launch_rollout<2>(h->dp, a, h->warps, h->ilp, pairs_samples(h), importance(h), windowed(h), h->smem, grid, s); break;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
   if (h->ev_end != nullptr) {

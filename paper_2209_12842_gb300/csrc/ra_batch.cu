@@ -394,6 +394,8 @@ int ra_mppi_batch_set_obstacles(ra_mppi_batch_t* b, int32_t i, const float* xyr,
       return bfail(b, RA_MPPI_EINVAL, "obstacle disc outside |x|, |y| <= RA_MPPI_OBSTACLE_EXTENT");
     packed[o] = make_float4(tmp[3 * o], tmp[3 * o + 1], r, r * r);
   }
+  // stored sorted by x: the kernels' obstacle cull narrows to an x window
+  std::stable_sort(packed.begin(), packed.end(), [](const float4& u, const float4& v) { return u.x < v.x; });
   if (n_obs > 0)
     e = cudaMemcpyAsync(b->obs + q.obs_off, packed.data(), sizeof(float4) * n_obs, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&b->st[i].n_obs, &n_obs, sizeof(int32_t), cudaMemcpyHostToDevice, s);

@@ -55,9 +55,9 @@ __global__ void __launch_bounds__(256) batch_rollout_kernel(const DevParams p, c
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4* base = smem + (size_t)w * batch_warp_f4(a.obs_cap_max, a.T_max, a.M_max, IS);
   float4* obs_s = base;
-  float4* ctl = base + a.obs_cap_max;
-  float* Ls = reinterpret_cast<float*>(base + a.obs_cap_max + a.T_max);
-  float* Ws = IS ? reinterpret_cast<float*>(base + a.obs_cap_max + a.T_max + (a.M_max + 3) / 4) : nullptr;
+  float4* ctl = obs_s + a.obs_cap_max;
+  float* Ls = reinterpret_cast<float*>(ctl + a.T_max);
+  float* Ws = IS ? Ls + (a.M_max + 3) / 4 * 4 : nullptr;
   int cur = -1, n_obs = 0;
   Inst in{};
   const InstDesc* d = nullptr;

@@ -21,10 +21,12 @@ struct UpdateArgs {
 
 // Rollout kernel launch for one model; ilp in {1, 2, 4}; `pairs`: two
 // samples per warp (dynamic model, ilp 2, at most 32 rollouts per sample);
-// `is`: importance-sampled rollouts (ilp 1 or 2, not with pairs).
+// `is`: importance-sampled rollouts (ilp 1 or 2, not with pairs); `win`: the
+// obstacle cull's x window (dynamic model, neither pairs nor is; ignored
+// otherwise).
 template <int MODEL>
 cudaError_t launch_rollout(const DevParams& p, const RolloutArgs& a, int warps, int ilp, bool pairs, bool is,
-                           size_t smem, int grid, cudaStream_t s);
+                           bool win, size_t smem, int grid, cudaStream_t s);
 // Raise the dynamic shared memory limit of every instance of a model.
 template <int MODEL>
 cudaError_t prepare_rollout(size_t smem);

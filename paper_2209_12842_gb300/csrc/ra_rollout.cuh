@@ -74,6 +74,12 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+
 // order-preserving map of finite floats to unsigned keys
 __device__ __forceinline__ uint32_t fkey(float f) {
   const uint32_t b = __float_as_uint(f);
@@ -110,6 +116,24 @@ __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& 
   S_out[k] = S;
 }
 
+// Number of obstacles (sorted by x, at most 1024) with x < v (or x <= v when
+// `le`), by two ballots: 32 evenly spaced samples locate the stretch that
+// holds the boundary, then its (at most 32) entries give the exact count.
+// Warp-collective; every lane returns the same count.
+constexpr int kWindowMin = 64;  // fewer obstacles: two rounds of the box test at most
+
+__device__ __forceinline__ int sorted_count(const float4* __restrict__ obs, int n, int lane, float v, bool le) {
+  const int stride = (n + 31) >> 5;
+  const int j1 = lane * stride;
+  const bool p1 = j1 < n && (le ? obs[j1].x <= v : obs[j1].x < v);
+  const int c1 = __popc(__ballot_sync(0xFFFFFFFFu, p1));
+  if (c1 == 0) return 0;
+  const int start = (c1 - 1) * stride;
+  const int j2 = start + lane;
+  const bool p2 = lane < stride && j2 < n && (le ? obs[j2].x <= v : obs[j2].x < v);
+  return start + __popc(__ballot_sync(0xFFFFFFFFu, p2));
+}
+
 // Indicator obstacle count of the ILP states of every lane of the warp
 // (called by all 32 lanes together).  The warp first bounds its positions by
 // a box and tests 32 obstacles at a time against the box, the lane per
@@ -117,6 +141,13 @@ __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& 
 // margin far above float32 rounding) get the exact per-state test, in the
 // original obstacle order.  A skipped obstacle cannot contain any state, so
 // the counts equal the full loop's.
+//
+// Obstacles are stored sorted by x, and obs[-1].x holds the largest radius.
+// WIN (the dynamic model's kernels for more than kWindowMin obstacles, where
+// it pays): the warp first narrows the candidates
+// to those with x within that radius (plus a margin far above the rounding of
+// the bounds) of the box, found by two ballots over the sorted x; any other
+// obstacle would fail the box test below anyway, so the counts stay exact.
 //
 // The box: coordinates shifted by kBoxShift are positive for every state
 // that can be inside an obstacle (obstacles lie within a few hundred metres
@@ -127,7 +158,7 @@ __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& 
 // bounds to the states that matter; a NaN (positive pattern, larger than any
 // finite value) makes its max bound NaN, which the candidate test treats as
 // unbounded.
-template <int MODEL, int ILP>
+template <int MODEL, int ILP, bool WIN = false>
 __device__ __forceinline__ void obstacle_hits_culled(const DevParams& p, float (&x)[ILP][Model<MODEL>::NX],
                                                      float (&hits)[ILP], const float4* __restrict__ obs,
                                                      int n_obs) {
@@ -151,10 +182,19 @@ __device__ __forceinline__ void obstacle_hits_culled(const DevParams& p, float (
   xmx = hi(xmx);
   ymn = lo(ymn);
   ymx = hi(ymx);
-  for (int base = 0; base < n_obs; base += 32) {
+  int o_begin = 0, o_end = n_obs;
+  if (WIN && n_obs > kWindowMin) {
+    const float rm = fmaf(obs[-1].x, 1.001f, 2e-4f);
+    const float wlo = xmn - rm, whi = xmx + rm;
+    if (wlo == wlo && whi == whi) {  // a NaN bound keeps every obstacle
+      o_begin = sorted_count(obs, n_obs, lane, wlo, false);
+      o_end = sorted_count(obs, n_obs, lane, whi, true);
+    }
+  }
+  for (int base = o_begin; base < o_end; base += 32) {
     const int o = base + lane;
     bool cand = false;
-    if (o < n_obs) {
+    if (o < o_end) {
       const float4 ob = obs[o];
       // distance from the centre to the box; a NaN bound acts as unbounded
       const float dx = fmaxf(fmaxf(xmn - ob.x, ob.x - xmx), 0.0f);
@@ -177,7 +217,7 @@ __device__ __forceinline__ void obstacle_hits_culled(const DevParams& p, float (
 }
 
 // risk cost l of ILP states of every lane (warp-collective for the indicator term)
-template <int MODEL, int ILP>
+template <int MODEL, int ILP, bool WIN = false>
 __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP][Model<MODEL>::NX],
                                               float (&L)[ILP], const float4* __restrict__ obs,
                                               int n_obs) {
@@ -186,7 +226,7 @@ __device__ __forceinline__ void risk_cost_ilp(const DevParams& p, float (&x)[ILP
     float hits[ILP];
 #pragma unroll
     for (int i = 0; i < ILP; ++i) hits[i] = 0.0f;
-    obstacle_hits_culled<MODEL, ILP>(p, x, hits, obs, n_obs);
+    obstacle_hits_culled<MODEL, ILP, WIN>(p, x, hits, obs, n_obs);
 #pragma unroll
     for (int i = 0; i < ILP; ++i) {
       L[i] = fmaf(p.w_obs, hits[i], L[i]);
@@ -209,7 +249,7 @@ __device__ __forceinline__ float is_weight(const DevParams& p, const Inst& in, f
 // ILP disturbed rollouts of one lane: rollouts lane + 32 (r0 + i rstride),
 // i < ILP (rows r0, r0 + rstride, ... of the M rollouts); risk costs to Ls
 // (IS: and importance weights to Ws)
-template <int MODEL, int ILP, bool IS = false>
+template <int MODEL, int ILP, bool IS = false, bool WIN = false>
 __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in, const float* x0, int k, int lane,
                                              int r0, int rstride, const float4* ctl, float* Ls,
                                              const float4* obs_s, int n_obs, float* Ws = nullptr) {
@@ -229,7 +269,7 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
   }
   for (int t = 0; t < in.T; ++t) {
     const float4 c = ctl[t];
-    risk_cost_ilp<MODEL, ILP>(p, x, L, obs_s, n_obs);
+    risk_cost_ilp<MODEL, ILP, WIN>(p, x, L, obs_s, n_obs);
     if constexpr (MODEL == 1 && ILP % 2 == 0) {
       // rollouts two by two in paired FP32 instructions (same bits as one by one)
 #pragma unroll
@@ -277,7 +317,7 @@ __device__ __forceinline__ void fill_controls(const DevParams& p, const Inst& in
 
 // the rollout rows r_first, r_first + r_stride, ... of sample k (one warp);
 // ILP rows interleaved, the rest one at a time
-template <int MODEL, int ILP, bool IS = false>
+template <int MODEL, int ILP, bool IS = false, bool WIN = false>
 __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in, const float* __restrict__ x0g, int k,
                                              int lane, int r_first, int r_stride, const float4* ctl, float* Ls,
                                              const float4* obs_s, int n_obs, float* Ws = nullptr) {
@@ -288,10 +328,10 @@ __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in,
   const int R = (in.M + 31) >> 5;
   int r = r_first;
   for (; r + (ILP - 1) * r_stride < R; r += ILP * r_stride)
-    rollouts_ilp<MODEL, ILP, IS>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
+    rollouts_ilp<MODEL, ILP, IS, WIN>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
   if (ILP > 1)
     for (; r < R; r += r_stride)
-      rollouts_ilp<MODEL, 1, IS>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
+      rollouts_ilp<MODEL, 1, IS, WIN>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
 }
 
 // CVaR_k (or the selected risk measure) of the M risk costs in Ls (one warp),
@@ -551,7 +591,7 @@ __device__ __forceinline__ void risk_from_shared_w(const DevParams& p, const Ins
 
 // One warp: the M disturbed rollouts of sample k and CVaR_k (written to cvar[k]).
 // ctl [T] and Ls [M] are this warp's shared-memory scratch.
-template <int MODEL, int ILP, bool IS = false>
+template <int MODEL, int ILP, bool IS = false, bool WIN = false>
 __device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst& in, const float* __restrict__ x0g,
                                                  const float* __restrict__ V, int k, int lane, float4* ctl, float* Ls,
                                                  const float4* obs_s, int n_obs, float* __restrict__ cvar,
@@ -559,7 +599,7 @@ __device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst&
   fill_controls<MODEL>(p, in, V, k, lane, 32, ctl);
   __syncwarp();
   // disturbed rollouts and their risk costs (Eq. 9)
-  run_rollouts<MODEL, ILP, IS>(p, in, x0g, k, lane, 0, 1, ctl, Ls, obs_s, n_obs, Ws);
+  run_rollouts<MODEL, ILP, IS, WIN>(p, in, x0g, k, lane, 0, 1, ctl, Ls, obs_s, n_obs, Ws);
   __syncwarp();
   if constexpr (IS) risk_from_shared_w(p, in, Ls, Ws, k, lane, cvar, Lout, status);
   else risk_from_shared(p, in, Ls, k, lane, cvar, Lout, status);
@@ -613,14 +653,29 @@ __device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const 
 // not raise the register count of the others
 // IS: importance-sampled rollouts with weights in shared memory after the
 // costs (a separate instantiation; never with PAIRS)
-template <int MODEL, int ILP, bool PAIRS = false, bool IS = false>
+// WIN: the obstacle cull's x window (dynamic model, more than kWindowMin
+// obstacles; a separate instantiation so the others keep their code)
+template <int MODEL, int ILP, bool PAIRS = false, bool IS = false, bool WIN = false>
 __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
   extern __shared__ float4 smem[];
-  float4* obs_s = smem;
+  // WIN: smem[0].x holds the largest obstacle radius and the obstacles start
+  // at smem[1]; otherwise at smem[0].  The samples' controls, costs (and
+  // weights) follow the obstacles.
+  float4* obs_s = smem + (WIN ? 1 : 0);
+  float4* const scratch = obs_s + a.obs_cap;
   const int n_obs = a.st->n_obs;
   const Inst in = inst_of(p, (uint32_t)a.st->iteration);
   for (int i = threadIdx.x; i < n_obs; i += blockDim.x) obs_s[i] = a.obs[i];
   __syncthreads();
+  if (WIN && n_obs > kWindowMin) {  // only the windowed cull reads it
+    if (threadIdx.x < 32) {
+      float r = 0.0f;
+      for (int i = threadIdx.x; i < n_obs; i += 32) r = fmaxf(r, obs_s[i].z);
+      r = warp_max(r);
+      if (threadIdx.x == 0) smem[0] = make_float4(r, 0.0f, 0.0f, 0.0f);
+    }
+    __syncthreads();
+  }
 
   if ((int)blockIdx.x < a.nb_nom) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -633,22 +688,22 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = a.wps, spb = warps / G, gi = w / G, g = w - gi * G;
   const int k = ((int)blockIdx.x - a.nb_nom) * spb + gi;
-  float4* ctl = smem + a.obs_cap + gi * in.T;
-  float* Ls = reinterpret_cast<float*>(smem + a.obs_cap + spb * in.T) + gi * in.M;
+  float4* ctl = scratch + gi * in.T;
+  float* Ls = reinterpret_cast<float*>(scratch + spb * in.T) + gi * in.M;
   float* Ws = IS ? Ls + spb * in.M : nullptr;
   if constexpr (PAIRS) {
     // two samples per warp: slots 2w and 2w + 1 of the block's controls and costs
     const int ka = ((int)blockIdx.x - a.nb_nom) * 2 * warps + 2 * w, kb = ka + 1;
     if (ka >= in.K) return;
-    float4* ctl_a = smem + a.obs_cap + (2 * w) * in.T;
-    float* Ls_a = reinterpret_cast<float*>(smem + a.obs_cap + 2 * warps * in.T) + (2 * w) * in.M;
+    float4* ctl_a = scratch + (2 * w) * in.T;
+    float* Ls_a = reinterpret_cast<float*>(scratch + 2 * warps * in.T) + (2 * w) * in.M;
     disturbed_sample_pair<MODEL>(p, in, a.x0, a.V, ka, kb, lane, ctl_a, ctl_a + in.T, Ls_a, Ls_a + in.M, obs_s,
                                  n_obs, a.cvar, a.L, &a.st->status);
     return;
   } else {
   if (G == 1) {
     if (k >= in.K) return;
-    disturbed_sample<MODEL, ILP, IS>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L,
+    disturbed_sample<MODEL, ILP, IS, WIN>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L,
                                      &a.st->status, Ws);
     return;
   }
@@ -657,7 +712,7 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   const bool valid = k < in.K;
   if (valid) fill_controls<MODEL>(p, in, a.V, k, g * 32 + lane, 32 * G, ctl);
   __syncthreads();
-  if (valid) run_rollouts<MODEL, ILP, IS>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs, Ws);
+  if (valid) run_rollouts<MODEL, ILP, IS, WIN>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs, Ws);
   __syncthreads();
   if (valid && g == 0) {
     if constexpr (IS) risk_from_shared_w(p, in, Ls, Ws, k, lane, a.cvar, a.L, &a.st->status);
