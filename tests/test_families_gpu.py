@@ -135,6 +135,28 @@ def test_two_samples_per_warp_is_the_default():
     ctl.close()
 
 
+@pytest.mark.parametrize("launch", [(4, 1, 1), (4, 2, 2), (8, 2, 1), (3, 1, 3)])
+def test_obstacle_x_window(launch):
+    """More than 64 obstacles on the dynamic model: the cull first narrows to
+    the obstacles within the largest radius of the warp's box in x (stored
+    sorted by x).  Small obstacles along the path, a few large ones (the
+    largest radius sets the window) and far-away ones on both sides; counts
+    must equal the oracle's, with the same bits for every launch shape."""
+    p = rs.preset("small_dyn", K=37, M=64, n_obs=120)
+    near = rs.obstacles_ahead(11, 100, 0.02, 0.08, x_from=-0.5, x_to=1.5, lateral=0.5)
+    big = np.array([[0.9, -3.2, 0.6], [-3.0, -4.0, 0.9]], np.float32)
+    far = rs.obstacles_ahead(12, 18, 0.1, 0.3, x_from=-40.0, x_to=40.0, lateral=20.0)
+    obs = np.concatenate([near, big, far])
+    x0 = rs.initial_state(1)
+    V = rs.random_controls(1, p["T"], p["u_lo"], p["u_hi"], 5)
+    base = _gpu(p, obs, x0, V, launch=(4, 1, 1))
+    g = _gpu(p, obs, x0, V, launch=launch)
+    for key in ("U", "S", "cvar", "S_tilde", "L"):
+        np.testing.assert_array_equal(g[key], base[key], err_msg=f"{launch} {key}")
+    assert np.any(g["L"] > 0)
+    compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
+
+
 def test_paper_preset():
     p = rs.preset("paper_sim", K=96)
     obs = rs.scene_obstacles(p)
