@@ -138,16 +138,15 @@ __device__ __forceinline__ int sorted_count(const float4* __restrict__ obs, int 
 // (called by all 32 lanes together).  The warp first bounds its positions by
 // a box and tests 32 obstacles at a time against the box, the lane per
 // obstacle; only obstacles whose disc can reach the box (with a relative
-// margin far above float32 rounding) get the exact per-state test, in the
-// original obstacle order.  A skipped obstacle cannot contain any state, so
-// the counts equal the full loop's.
+// margin far above float32 rounding) get the exact per-state test.  A skipped
+// obstacle cannot contain any state, so the counts equal the full loop's.
 //
-// Obstacles are stored sorted by x, and obs[-1].x holds the largest radius.
-// WIN (the dynamic model's kernels for more than kWindowMin obstacles, where
-// it pays): the warp first narrows the candidates
-// to those with x within that radius (plus a margin far above the rounding of
-// the bounds) of the box, found by two ballots over the sorted x; any other
-// obstacle would fail the box test below anyway, so the counts stay exact.
+// Obstacles are stored sorted by x.  WIN (the dynamic model's kernels for
+// more than kWindowMin obstacles, where it pays; obs[-1].x then holds the
+// largest radius): the warp first narrows the candidates to those with x
+// within that radius (plus a margin far above the rounding of the bounds) of
+// the box, found by two ballots over the sorted x; any other obstacle would
+// fail the box test below anyway, so the counts stay exact.
 //
 // The box: coordinates shifted by kBoxShift are positive for every state
 // that can be inside an obstacle (obstacles lie within a few hundred metres
