@@ -131,6 +131,21 @@ def test_edge_sizes(K, M, T):
         np.testing.assert_array_equal(g["V_plus"], g["U"][0])
 
 
+@pytest.mark.parametrize("name", ["small_kin", "small_dyn"])
+def test_maximum_horizon_and_obstacle_count(name):
+    # the largest T (256) and obstacle capacity (1024, the window's largest
+    # sorted search for the dynamic model), with M = 512
+    p = rs.preset(name, K=5, M=512, T=256, n_obs=1024)
+    x0 = rs.initial_state(p["model"])
+    near = rs.obstacles_ahead(3, 600, 0.02, 0.1, x_from=-1.0, x_to=6.0, lateral=1.0)
+    far = rs.obstacles_ahead(4, 424, 0.1, 0.4, x_from=-200.0, x_to=200.0, lateral=150.0)
+    obs = np.concatenate([near, far])
+    V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 8)
+    g = run_gpu(p, obs, x0, V)
+    assert g["status"] == 0
+    compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
+
+
 def test_no_obstacles_and_options():
     p = rs.preset("small_kin", eta=0.3, B=2.5, A=3.0, C_u=50.0, gamma=0.7,
                   risk_mask=rs.RISK_DEV | rs.RISK_SPEED | rs.RISK_OBS | rs.RISK_BDRY,
