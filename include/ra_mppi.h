@@ -296,7 +296,8 @@ int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta);
  * literal CVaR (Eqs. 10-13: the tail weights, times the importance weights
  * when importance sampling is on; Eqs. 18, 19: the scaling), of
  * the costs and dynamics along every nominal and disturbed rollout (Eqs. 3,
- * 6, 9, 20-23; states recomputed from checkpoints every 8 steps), and of the
+ * 6, 9, 20-23; the risk costs kept by the update, states recomputed from
+ * checkpoints every 8 steps), and of the
  * clip U = clip(V + eps) (Alg. 1).  The obstacle indicator (Eq. 22) has
  * zero derivative; use the softplus barrier to differentiate through
  * obstacles.  Needs RA_MPPI_DIFFERENTIABLE; all three models (the dynamic

@@ -386,9 +386,11 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
 #pragma unroll
   for (int i = 0; i < NX; ++i) x0[i] = a.x0[i];
   const int R = (M + 31) >> 5;
-  // pass 1: the risk costs (the forward rollouts' arithmetic and bits, two
-  // rows at a time)
-  run_rollouts<MODEL, 2, IS>(p, in, a.x0, k, lane, 0, 1, ctl, Ls, obs_s, n_obs, Ws);
+  // the risk costs (and importance weights) the update kept
+  for (int m = lane; m < M; m += 32) {
+    Ls[m] = a.L[(size_t)k * M + m];
+    if constexpr (IS) Ws[m] = a.L[(size_t)in.K * M + (size_t)k * M + m];
+  }
   __syncwarp();
   // CVaR weights: VaR by radix select, then the tail
   constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;

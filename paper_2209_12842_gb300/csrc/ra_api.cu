@@ -375,7 +375,8 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   if (e == cudaSuccess) e = dalloc(&h->S_tilde, K);
   if (e == cudaSuccess) e = dalloc(&h->partials, (size_t)h->nb_upd * (2 + TN));
   // kept risk costs [K][M], followed by the importance weights [K][M] when on
-  if (e == cudaSuccess && (p->flags & RA_MPPI_KEEP_RISK_COSTS))
+  // (also for the adjoint, which reads them instead of recomputing them)
+  if (e == cudaSuccess && (p->flags & (RA_MPPI_KEEP_RISK_COSTS | RA_MPPI_DIFFERENTIABLE)))
     e = dalloc(&h->L, K * (size_t)p->M * (is_count(*p) > 0 ? 2 : 1));
   if (e == cudaSuccess) e = dalloc(&h->obs, (size_t)h->obs_cap);
   if (e == cudaSuccess) e = dalloc(&h->st, 1);
@@ -751,6 +752,7 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.U = h->U;
   a.S = h->S;
   a.cvar = h->cvar;
+  a.L = h->L;
   a.obs = h->obs;
   a.st = h->st;
   a.gVp = gV_plus;

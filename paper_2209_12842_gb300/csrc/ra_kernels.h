@@ -40,6 +40,7 @@ struct BwdArgs {
   const float* U;       // [K][T][nu] its samples
   const float* S;       // [K]
   const float* cvar;    // [K]
+  const float* L;       // [K][M] risk costs of the update (then [K][M] importance weights)
   const float4* obs;
   DevState* st;
   const float* gVp;     // [T][nu]
