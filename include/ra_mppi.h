@@ -120,7 +120,7 @@ enum {
 /* flags */
 enum {
   RA_MPPI_KEEP_RISK_COSTS = 1, /* keep the K x M risk costs L for inspection              */
-  RA_MPPI_DIFFERENTIABLE = 2   /* keep what ra_mppi_backward needs (x0, V of each update) */
+  RA_MPPI_DIFFERENTIABLE = 2   /* keep what ra_mppi_backward needs (x0, V and the risk costs of each update) */
 };
 
 #define RA_MPPI_MAX_M 512
