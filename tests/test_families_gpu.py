@@ -157,6 +157,20 @@ def test_obstacle_x_window(launch):
     compare(p, g, oracle.samples(p, x0, V, obs, n_threads=8))
 
 
+@pytest.mark.parametrize("name,n_obs", [("small_dyn", 120), ("small_kin", 40)])
+def test_obstacle_order_does_not_matter(name, n_obs):
+    """The library keeps the obstacles sorted by x; with the indicator cost the
+    results are the same bits for any order of the input list."""
+    p = rs.preset(name, K=37, M=64, n_obs=n_obs)
+    obs = rs.obstacles_ahead(13, n_obs, 0.05, 0.2, x_from=-0.5, x_to=2.0, lateral=0.5)
+    x0 = rs.initial_state(p["model"])
+    V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 6)
+    a = _gpu(p, obs, x0, V)
+    b = _gpu(p, obs[np.random.default_rng(0).permutation(n_obs)], x0, V)
+    for key in ("U", "S", "cvar", "S_tilde", "L", "V_plus"):
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
 def test_paper_preset():
     p = rs.preset("paper_sim", K=96)
     obs = rs.scene_obstacles(p)
