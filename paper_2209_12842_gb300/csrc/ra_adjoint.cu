@@ -96,25 +96,32 @@ __device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, un
   }
   if (mask & 4u) {
     float val = 0.0f, g0 = 0.0f, g1 = 0.0f;
-    for (int i = 0; i < n_obs; ++i) {
-      const float4 o = obs[i];
-      const float dx = x[0] - o.x, dy = x[1] - o.y;
-      const float d2 = fmaf(dx, dx, dy * dy);
-      if (p.obs_mode == 0) {
-        val += d2 < o.w ? 1.0f : 0.0f;
-      } else {
-        const float d = sqrtf(d2);
-        const float z = p.kappa * (o.z - d);
-        const float sp = z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
-        val += sp;
-        const float sig = 1.0f / (1.0f + expf(-z));
-        if (d > 0.0f) {
-          g0 -= sig * dx / d;
-          g1 -= sig * dy / d;
-        }
+    if (p.obs_mode == 0) {
+      for (int i = 0; i < n_obs; ++i) {  // indicator: a value, no gradient
+        const float4 o = obs[i];
+        const float dx = x[0] - o.x, dy = x[1] - o.y;
+        val += fmaf(dx, dx, dy * dy) < o.w ? 1.0f : 0.0f;
       }
+    } else {
+      // softplus(z) = max(z, 0) + log(1 + e) and sigmoid(z) = 1 / (1 + e)
+      // or e / (1 + e), both from e = exp(-|z|); no direction at the centre.
+      // The obstacles are independent: unrolled, a lone thread overlaps them
+#pragma unroll 4
+      for (int i = 0; i < n_obs; ++i) {
+        const float4 o = obs[i];
+        const float dx = x[0] - o.x, dy = x[1] - o.y;
+        const float d2 = fmaf(dx, dx, dy * dy);
+        const float rd = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+        const float z = p.kappa * (o.z - d2 * rd);
+        const float e = expf(-fabsf(z));
+        val += fmaxf(z, 0.0f) + log1pf(e);
+        const float r = 1.0f / (1.0f + e);
+        const float k = (z > 0.0f ? r : e * r) * rd;
+        g0 = fmaf(-k, dx, g0);
+        g1 = fmaf(-k, dy, g1);
+      }
+      val *= p.inv_kappa;
     }
-    if (p.obs_mode != 0) val *= p.inv_kappa;
     g[0] = fmaf(c * p.w_obs, g0, g[0]);
     g[1] = fmaf(c * p.w_obs, g1, g[1]);
     gth[3] = fmaf(c, val, gth[3]);
