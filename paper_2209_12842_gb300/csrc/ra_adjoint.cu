@@ -233,44 +233,55 @@ __device__ __forceinline__ float s_tilde_of(const DevParams& p, float S, float c
 
 }  // namespace
 
-// d_k = <gV+, U_k>, w^_k, and c = sum_k w^_k d_k (last block merges, FP64)
+// d_k = <gV+, U_k>, w^_k, and c = sum_k w^_k d_k.  One warp per sample (the
+// lanes read U_k's row together and sum in a fixed shuffle tree), eight
+// samples per block; the FP64 block partials are summed by the last block to
+// arrive, all its threads at once, in an order fixed by K: deterministic
+constexpr int kPrepSamples = 8;  // warps of a 256-thread block
 __global__ void __launch_bounds__(256) bwd_prep_kernel(const DevParams p, const BwdArgs a) {
-  __shared__ double red[8];
+  __shared__ double red[kPrepSamples];
   __shared__ unsigned int is_last;
   const int TN = p.T * p.nu;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const float m = a.st->last_min;
-  const double s_tot = a.st->last_sum;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * kPrepSamples + w;
   double part = 0.0;
   if (k < p.K) {
-    float d = 0.0f;
     const float* Uk = a.U + (size_t)k * TN;
-    for (int c = 0; c < TN; ++c) d = fmaf(a.gVp[c], Uk[c], d);
+    float d = 0.0f;
+    for (int c = lane; c < TN; c += 32) d = fmaf(a.gVp[c], Uk[c], d);
+    d = warp_sum(d);
+    const float m = a.st->last_min;
+    const double s_tot = a.st->last_sum;
     const float st = s_tilde_of(p, a.S[k], a.cvar[k]);
-    const float w = (isfinite(st) && s_tot > 0.0) ? (float)((double)expf((m - st) * p.inv_lambda) / s_tot) : 0.0f;
-    a.dk[k] = d;
-    a.wk[k] = w;
-    part = (double)w * (double)d;
+    const float wt = (isfinite(st) && s_tot > 0.0) ? (float)((double)expf((m - st) * p.inv_lambda) / s_tot) : 0.0f;
+    if (lane == 0) {
+      a.dk[k] = d;
+      a.wk[k] = wt;
+    }
+    part = (double)wt * (double)d;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  if (lane == 0) red[w] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int i = 0; i < kPrepSamples; ++i) t += red[i];
     a.prep_part[blockIdx.x] = t;
     __threadfence();
-    const unsigned int ticket = atomicAdd(&a.arrive[0], 1u);
-    is_last = ticket == gridDim.x - 1 ? 1u : 0u;
+    is_last = atomicAdd(&a.arrive[0], 1u) == gridDim.x - 1 ? 1u : 0u;
   }
   __syncthreads();
-  if (is_last && threadIdx.x == 0) {
-    __threadfence();
-    const volatile double* pp = a.prep_part;
-    double c = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) c += pp[b];
-    *a.c_out = c;
+  if (!is_last) return;
+  __threadfence();
+  double c = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) c += __ldcg(&a.prep_part[b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  if (lane == 0) red[w] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kPrepSamples; ++i) t += red[i];
+    *a.c_out = t;
     a.arrive[0] = 0u;
   }
 }
@@ -609,28 +620,39 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
   bwd_disturbed<MODEL, IS>(p, in, a, k, lane, ctl, Ls, Ws, act, gus, obs_s, n_obs);
 }
 
-// gV[c] = sum_k Gnom[k][c] + mask[k][c] gUd[k][c]; gtheta[i] = sum_k thn + thd
-__global__ void __launch_bounds__(256) bwd_reduce_kernel(const DevParams p, const BwdArgs a) {
+// gV and gtheta: column sums over the K samples of the U cotangents (the
+// nominal part plus the clip-masked disturbed part) and of the theta
+// partials.  A block sums a slice of the samples, kRedRows row lanes per
+// column in FP64, combined in a fixed order; the last block to arrive merges
+// the slices the same way.  The order depends on K and the grid only.
+constexpr int kRedCols = 64, kRedRows = 4;  // 256 threads
+__global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const DevParams p, const BwdArgs a) {
+  __shared__ double acc[kRedRows][kRedCols];
   __shared__ unsigned int is_last;
   const int TN = p.T * p.nu, NC = TN + 4;
   const int per = (p.K + gridDim.x - 1) / gridDim.x;
   const int kb = blockIdx.x * per, ke = min(p.K, kb + per);
+  const int cl = threadIdx.x % kRedCols, rl = threadIdx.x / kRedCols;
   float* part = a.red_part + (size_t)blockIdx.x * NC;
-  for (int c = threadIdx.x; c < NC; c += blockDim.x) {
-    float s = 0.0f, comp = 0.0f;
-    for (int k = kb; k < ke; ++k) {
-      float v;
-      if (c < TN) {
-        const size_t idx = (size_t)k * TN + c;
-        v = a.Gnom[idx] + a.mask[idx] * a.gUd[idx];
-      } else {
-        v = a.thn[(size_t)k * 4 + (c - TN)] + a.thd[(size_t)k * 4 + (c - TN)];
+  for (int c0 = 0; c0 < NC; c0 += kRedCols) {
+    const int c = c0 + cl;
+    double s = 0.0;
+    if (c < NC) {
+      for (int k = kb + rl; k < ke; k += kRedRows) {
+        float v;
+        if (c < TN) {
+          const size_t idx = (size_t)k * TN + c;
+          v = a.Gnom[idx] + a.mask[idx] * a.gUd[idx];
+        } else {
+          v = a.thn[(size_t)k * 4 + (c - TN)] + a.thd[(size_t)k * 4 + (c - TN)];
+        }
+        s += (double)v;
       }
-      const float t = s + v;
-      comp += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
-      s = t;
     }
-    part[c] = s + comp;
+    acc[rl][cl] = s;
+    __syncthreads();
+    if (rl == 0 && c < NC) part[c] = (float)(((acc[0][cl] + acc[1][cl]) + acc[2][cl]) + acc[3][cl]);
+    __syncthreads();
   }
   __threadfence();
   __syncthreads();
@@ -638,12 +660,20 @@ __global__ void __launch_bounds__(256) bwd_reduce_kernel(const DevParams p, cons
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const volatile float* pp = a.red_part;
-  for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+  for (int c0 = 0; c0 < NC; c0 += kRedCols) {
+    const int c = c0 + cl;
     double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += (double)pp[(size_t)b * NC + c];
-    if (c < TN) a.gV[c] = (float)s;
-    else a.gtheta[c - TN] = (float)s;
+    if (c < NC) {
+      for (int b = rl; b < (int)gridDim.x; b += kRedRows) s += (double)__ldcg(&a.red_part[(size_t)b * NC + c]);
+    }
+    acc[rl][cl] = s;
+    __syncthreads();
+    if (rl == 0 && c < NC) {
+      const double t = ((acc[0][cl] + acc[1][cl]) + acc[2][cl]) + acc[3][cl];
+      if (c < TN) a.gV[c] = (float)t;
+      else a.gtheta[c - TN] = (float)t;
+    }
+    __syncthreads();
   }
   if (threadIdx.x == 0) a.arrive[1] = 0u;
 }

@@ -384,8 +384,10 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   if (e == cudaSuccess) e = dalloc(&h->V_dev, TN);
   if (e == cudaSuccess) e = dalloc(&h->V_plus, TN);
   if (e == cudaSuccess && (p->flags & RA_MPPI_DIFFERENTIABLE)) {
-    h->nb_prep = (int)((K + 255) / 256);
-    h->nb_red = (int)std::min<size_t>((K + 255) / 256, 256);
+    // adjoint grids: one warp per sample in the prep (8 per block); the
+    // column reduction takes slices of 32 samples, at most 256 slices
+    h->nb_prep = (int)((K + 7) / 8);
+    h->nb_red = (int)std::min<size_t>((K + 31) / 32, 256);
     e = dalloc(&h->keep_x0, 8);
     if (e == cudaSuccess) e = dalloc(&h->keep_V, TN);
     if (e == cudaSuccess) e = dalloc(&h->b_dk, K);

@@ -68,6 +68,24 @@ def test_adjoint_matches_oracle_small(case):
     _close("gtheta", gth, rth)
 
 
+@pytest.mark.parametrize("n_obs", [0, 1, 3, 4, 5, 7, 13])
+def test_adjoint_obstacle_counts(n_obs):
+    # the softplus gradient's obstacle loop is unrolled four times: counts
+    # below, at and between multiples of four, and none; the obstacles lie on
+    # and beside the path, so states inside (z > 0) and outside both occur
+    p = rs.preset("c4_gradient", K=64, M=32, T=12)
+    obs = (rs.obstacles_ahead(3, n_obs, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4) if n_obs
+           else np.zeros((0, 3), np.float32))
+    p["n_obs"] = max(n_obs, 1)
+    x0 = np.array([0.0, -4.0, 0.0, 1.0], np.float32)
+    V = rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 3)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    gV, gth = _run(p, obs, x0, V, gVp, gS)
+    rV, rth = oracle.backward(p, x0, V, obs, gVp, gS)
+    _close("gV", gV, rV)
+    _close("gtheta", gth, rth)
+
+
 def test_adjoint_config4_full_size():
     p = rs.preset("c4_gradient")
     obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
