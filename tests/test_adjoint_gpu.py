@@ -167,6 +167,28 @@ def test_adjoint_importance_sampled(case):
     _close("gtheta", gth, rth)
 
 
+@pytest.mark.parametrize("K", [1, 33, 1024, 9000])
+def test_adjoint_is_deterministic(K):
+    # the prep and column reductions sum in an order fixed by K: repeated
+    # backward passes give the same bits (one sample, ragged and many slices)
+    p = rs.preset("c4_gradient", K=K, M=32, T=12)
+    obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4)
+    from paper_2209_12842_gb300 import RaMppi
+
+    ctl = RaMppi(p, obs, differentiable=True)
+    ctl.step(torch.tensor([0.0, -4.0, 0.0, 1.0], device="cuda"),
+             torch.from_numpy(rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 3)).cuda())
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    gVp, gS = torch.from_numpy(gVp).cuda(), torch.from_numpy(gS).cuda()
+    runs = [tuple(t.cpu().numpy() for t in ctl.backward(gVp, gS)) for _ in range(3)]
+    assert ctl.status() == 0
+    ctl.close()
+    for gV, gth in runs[1:]:
+        np.testing.assert_array_equal(gV, runs[0][0])
+        np.testing.assert_array_equal(gth, runs[0][1])
+    assert np.all(np.isfinite(runs[0][0])) and np.all(np.isfinite(runs[0][1]))
+
+
 def test_adjoint_rejects_missing_flag():
     from paper_2209_12842_gb300 import RaMppi, RaMppiError
 
