@@ -64,6 +64,41 @@ __device__ __forceinline__ void track_s_grad(const DevParams& p, float px, float
   ds[1] = r2 > 0.0f ? p.track_R * dx / r2 : 0.0f;
 }
 
+// The obstacle term at x over the obstacles first, first + stride, ...:
+// sums of its values (softplus or indicator, before 1/kappa) and of the
+// slopes d/dx, d/dy (before w_obs).
+// softplus(z) = max(z, 0) + log(1 + e) and sigmoid(z) = 1 / (1 + e) or
+// e / (1 + e), both from e = exp(-|z|); no direction at the centre.  The
+// obstacles are independent: unrolled, a lone thread overlaps them.
+// Hardware exponential, logarithm and reciprocal: a gradient needs no more
+// (the log of 1 + e is off by at most about 1e-7 absolute)
+__device__ __forceinline__ void obstacle_grad_part(const DevParams& p, const float* x, const float4* __restrict__ obs,
+                                                   int n_obs, int first, int stride, float& val, float& g0,
+                                                   float& g1) {
+  if (p.obs_mode == 0) {
+    for (int i = first; i < n_obs; i += stride) {  // indicator: a value, no gradient
+      const float4 o = obs[i];
+      const float dx = x[0] - o.x, dy = x[1] - o.y;
+      val += fmaf(dx, dx, dy * dy) < o.w ? 1.0f : 0.0f;
+    }
+    return;
+  }
+#pragma unroll 4
+  for (int i = first; i < n_obs; i += stride) {
+    const float4 o = obs[i];
+    const float dx = x[0] - o.x, dy = x[1] - o.y;
+    const float d2 = fmaf(dx, dx, dy * dy);
+    const float rd = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+    const float z = p.kappa * (o.z - d2 * rd);
+    const float e = __expf(-fabsf(z));
+    val += fmaxf(z, 0.0f) + __logf(1.0f + e);
+    const float r = __frcp_rn(1.0f + e);
+    const float kk = (z > 0.0f ? r : e * r) * rd;
+    g0 = fmaf(-kk, dx, g0);
+    g1 = fmaf(-kk, dy, g1);
+  }
+}
+
 // c * d(cost terms in mask)/dx added to g; c * d(cost)/d(w_dev, w_speed, -, w_obs) added to gth
 template <int MODEL>
 __device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, unsigned mask, float c,
@@ -96,39 +131,46 @@ __device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, un
   }
   if (mask & 4u) {
     float val = 0.0f, g0 = 0.0f, g1 = 0.0f;
-    if (p.obs_mode == 0) {
-      for (int i = 0; i < n_obs; ++i) {  // indicator: a value, no gradient
-        const float4 o = obs[i];
-        const float dx = x[0] - o.x, dy = x[1] - o.y;
-        val += fmaf(dx, dx, dy * dy) < o.w ? 1.0f : 0.0f;
-      }
-    } else {
-      // softplus(z) = max(z, 0) + log(1 + e) and sigmoid(z) = 1 / (1 + e)
-      // or e / (1 + e), both from e = exp(-|z|); no direction at the centre.
-      // The obstacles are independent: unrolled, a lone thread overlaps them.
-      // Hardware exponential, logarithm and reciprocal: a gradient needs no
-      // more (the log of 1 + e is off by at most about 1e-7 absolute)
-#pragma unroll 4
-      for (int i = 0; i < n_obs; ++i) {
-        const float4 o = obs[i];
-        const float dx = x[0] - o.x, dy = x[1] - o.y;
-        const float d2 = fmaf(dx, dx, dy * dy);
-        const float rd = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
-        const float z = p.kappa * (o.z - d2 * rd);
-        const float e = __expf(-fabsf(z));
-        val += fmaxf(z, 0.0f) + __logf(1.0f + e);
-        const float r = __frcp_rn(1.0f + e);
-        const float k = (z > 0.0f ? r : e * r) * rd;
-        g0 = fmaf(-k, dx, g0);
-        g1 = fmaf(-k, dy, g1);
-      }
-      val *= p.inv_kappa;
-    }
+    obstacle_grad_part(p, x, obs, n_obs, 0, 1, val, g0, g1);
+    if (p.obs_mode != 0) val *= p.inv_kappa;
     g[0] = fmaf(c * p.w_obs, g0, g[0]);
     g[1] = fmaf(c * p.w_obs, g1, g[1]);
     gth[3] = fmaf(c, val, gth[3]);
   }
   if (mask & 16u) g[0] = fmaf(c, p.c_lin, g[0]);
+}
+
+// cost_grad for one state held by `lpr` lanes (an aligned group of the warp,
+// sub = 0 .. lpr - 1; every lane of the warp calls it with the same lpr):
+// the obstacles split over the group and their slopes summed by shuffles, so
+// g stays the same on every lane of the group; the other terms on every lane,
+// their theta partials kept on sub = 0 only, and each lane keeps its share of
+// the obstacle values (a sum over the group adds them up)
+template <int MODEL>
+__device__ __forceinline__ void cost_grad_split(const DevParams& p, const float* x, unsigned mask, float c,
+                                                const float4* __restrict__ obs, int n_obs, int sub, int lpr,
+                                                float* g, float* gth) {
+  if (lpr == 1) {
+    cost_grad<MODEL>(p, x, mask, c, obs, n_obs, g, gth);
+    return;
+  }
+  float gt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  cost_grad<MODEL>(p, x, mask & ~4u, c, obs, n_obs, g, gt);
+  const float keep = sub == 0 ? 1.0f : 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) gth[i] = fmaf(keep, gt[i], gth[i]);
+  if (MODEL != 2 && (mask & 4u)) {
+    float val = 0.0f, g0 = 0.0f, g1 = 0.0f;
+    obstacle_grad_part(p, x, obs, n_obs, sub, lpr, val, g0, g1);
+    for (int o = 1; o < lpr; o <<= 1) {
+      g0 += __shfl_xor_sync(0xFFFFFFFFu, g0, o);
+      g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, o);
+    }
+    if (p.obs_mode != 0) val *= p.inv_kappa;
+    g[0] = fmaf(c * p.w_obs, g0, g[0]);
+    g[1] = fmaf(c * p.w_obs, g1, g[1]);
+    gth[3] = fmaf(c, val, gth[3]);
+  }
 }
 
 // Transposed Jacobians of the dynamic model's derivative f(x, u) at x
@@ -295,11 +337,22 @@ __device__ __forceinline__ float sbar_of(const DevParams& p, const BwdArgs& a, i
   return g - a.wk[k] * p.inv_lambda * (a.dk[k] - c);
 }
 
-// nominal sample k (one thread): cotangents of U_k from V+, the nominal cost
-// and the control cost, masked by the clip; theta partials of S_k
+// lanes per nominal rollout in the adjoint: they carry the same state and
+// cotangent and split the obstacles of the cost gradient (with one lane per
+// rollout, K = 1024 samples leave 32 warps, each on a long serial chain).
+// The dynamic model keeps one lane: its Heun sub-steps, repeated on every
+// lane of a group, cost more than the split saves
+constexpr int kNomLanes = 4;
 template <int MODEL>
-__device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a, int k, const float4* obs_s,
-                            int n_obs) {
+constexpr int nom_lanes() { return MODEL == 1 ? 1 : kNomLanes; }
+
+// nominal sample k, reversed by nom_lanes lanes (sub = 0 .. nom_lanes - 1;
+// all 32 lanes of the warp take part, a lane past K on a copy of sample
+// K - 1 that writes nothing): cotangents of U_k from V+, the nominal cost and
+// the control cost, masked by the clip; theta partials of S_k
+template <int MODEL>
+__device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a, int k, int sub, bool writes,
+                            const float4* obs_s, int n_obs) {
   using Md = Model<MODEL>;
   constexpr int NX = Md::NX, NU = Md::NU;
   const int T = in.T, TN = T * NU;
@@ -342,7 +395,7 @@ __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a
       const float u0 = Uk[t * NU], u1 = NU > 1 ? Uk[t * NU + 1] : 0.0f;
       float gu[2] = {0.0f, 0.0f};
       step_vjp<MODEL>(p, xs[t - t0], Md::ctl(p, u0, u1), lam, gu);
-      cost_grad<MODEL>(p, xs[t - t0], 0xFFFFFFFFu, sbar, obs_s, n_obs, lam, gth);
+      cost_grad_split<MODEL>(p, xs[t - t0], 0xFFFFFFFFu, sbar, obs_s, n_obs, sub, nom_lanes<MODEL>(), lam, gth);
       // control cost gamma v_t' S^-1 u_t and the clip of U = clip(V + eps)
       const float v0 = a.V[t * NU], v1 = NU > 1 ? a.V[t * NU + 1] : 0.0f;
       const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0xFFFFFFFFu, (uint32_t)k, in.instance), in.k0, in.k1);
@@ -356,13 +409,20 @@ __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a
         const float msk = (warm && raw > p.u_lo[j] && raw < p.u_hi[j]) ? 1.0f : 0.0f;
         const float gc = p.gamma * p.inv_sig2[j];
         const size_t idx = (size_t)k * TN + t * NU + j;
-        a.mask[idx] = msk;
-        a.Gnom[idx] = msk * (wk * a.gVp[t * NU + j] + gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
+        if (writes && sub == 0) {
+          a.mask[idx] = msk;
+          a.Gnom[idx] = msk * (wk * a.gVp[t * NU + j] + gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
+        }
       }
     }
   }
+  // the obstacle values are split over the group; the other partials are whole on sub = 0
 #pragma unroll
-  for (int i = 0; i < 4; ++i) a.thn[(size_t)k * 4 + i] = gth[i];
+  for (int o = 1; o < nom_lanes<MODEL>(); o <<= 1) gth[3] += __shfl_xor_sync(0xFFFFFFFFu, gth[3], o);
+  if (writes && sub == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.thn[(size_t)k * 4 + i] = gth[i];
+  }
 }
 
 // process noise of rollout m at step t as the forward added it: scaled by
@@ -538,12 +598,16 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     n_act += __popc(nz);
   }
   __syncwarp();
-  // pass 2: reverse sweep of every rollout with a nonzero weight, 32 at a time
+  // pass 2: reverse sweep of every rollout with a nonzero weight.  A short
+  // list (a CVaR tail) would leave lanes idle, so each rollout gets lpr
+  // lanes that split its obstacle terms: 32 / lpr rollouts per pass
+  const int lpr = MODEL == 1 ? 1 : (n_act <= 8 ? 4 : (n_act <= 16 ? 2 : 1));  // as nom_lanes
+  const int slots = 32 / lpr, slot = lane / lpr, sub = lane % lpr;
   float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  for (int c0 = 0; c0 < n_act; c0 += 32) {
-    const bool has = c0 + lane < n_act;
-    const int m = has ? act[c0 + lane] : 0;  // an idle lane replays rollout 0 with no cotangent
-    const float lbar = has ? Ls[c0 + lane] : 0.0f;
+  for (int c0 = 0; c0 < n_act; c0 += slots) {
+    const bool has = c0 + slot < n_act;
+    const int m = has ? act[c0 + slot] : 0;  // an idle group replays rollout 0 with no cotangent
+    const float lbar = has ? Ls[c0 + slot] : 0.0f;
     float ck[kMaxCk][NX];
     float x[NX];
 #pragma unroll
@@ -574,10 +638,10 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
       for (int t = t1 - 1; t >= t0; --t) {
         float gu[2] = {0.0f, 0.0f};
         step_vjp<MODEL>(p, xs[t - t0], ctl[t], lam, gu);
-        cost_grad<MODEL>(p, xs[t - t0], p.risk_mask, lbar, obs_s, n_obs, lam, gth);
+        cost_grad_split<MODEL>(p, xs[t - t0], p.risk_mask, lbar, obs_s, n_obs, sub, lpr, lam, gth);
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
-          const float s = warp_sum(gu[j]);
+          const float s = warp_sum(sub == 0 ? gu[j] : 0.0f);  // one copy per rollout
           if (lane == 0) gus[t * NU + j] += s;
         }
       }
@@ -604,8 +668,13 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
   __syncthreads();
 
   if ((int)blockIdx.x < a.nb_nom) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < in.K) bwd_nominal<MODEL>(p, in, a, k, obs_s, n_obs);
+    // nom_lanes lanes per nominal rollout; every lane of a warp with a sample
+    // in range takes part in the group shuffles
+    constexpr int NL = nom_lanes<MODEL>();
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = gt / NL, sub = gt % NL;
+    const int k_warp0 = (gt & ~31) / NL;
+    if (k_warp0 < in.K) bwd_nominal<MODEL>(p, in, a, min(k, in.K - 1), sub, k < in.K, obs_s, n_obs);
     return;
   }
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -698,11 +767,16 @@ cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int
   bwd_prep_kernel<<<nb_prep, 256, 0, s>>>(p, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int grid = a.nb_nom + nb_dist;
+  // a.nb_nom counts blocks at one lane per nominal rollout
+  BwdArgs b = a;
+  if (model == 0) b.nb_nom = a.nb_nom * nom_lanes<0>();
+  else if (model == 1) b.nb_nom = a.nb_nom * nom_lanes<1>();
+  else b.nb_nom = a.nb_nom * nom_lanes<2>();
+  const int grid = b.nb_nom + nb_dist;
   const bool is = p.is_b > 0.0f;
-  if (model == 0) e = launch_bwd_main<0>(p, a, is, grid, smem, s);
-  else if (model == 1) e = launch_bwd_main<1>(p, a, is, grid, smem, s);
-  else e = launch_bwd_main<2>(p, a, is, grid, smem, s);
+  if (model == 0) e = launch_bwd_main<0>(p, b, is, grid, smem, s);
+  else if (model == 1) e = launch_bwd_main<1>(p, b, is, grid, smem, s);
+  else e = launch_bwd_main<2>(p, b, is, grid, smem, s);
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

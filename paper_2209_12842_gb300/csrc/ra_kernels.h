@@ -58,7 +58,7 @@ struct BwdArgs {
   float* red_part;      // [nb_red][T nu + 4]
   float* gV;            // [T][nu] out
   float* gtheta;        // [4] out
-  int nb_nom, obs_cap;
+  int nb_nom, obs_cap;  // nb_nom: 128-thread blocks at one lane per nominal rollout
 };
 cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
                             size_t smem, int nb_red, cudaStream_t s);
