@@ -301,10 +301,10 @@ int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta);
  * clip U = clip(V + eps) (Alg. 1).  The obstacle indicator (Eq. 22) has
  * zero derivative; use the softplus barrier to differentiate through
  * obstacles.  Needs RA_MPPI_DIFFERENTIABLE; all three models (the dynamic
- * one through its Heun sub-steps).  FP32, with the sums over samples taken
- * in FP64 in an order fixed by K, so repeated calls give the same bits; the
- * barrier's slope uses the hardware exponential and logarithm.  Enqueued on
- * `stream`. */
+ * one through its Heun sub-steps).  FP32; the sums over samples accumulate
+ * in FP64 (partials over slices of samples stored as FP32) in an order fixed
+ * by K, so repeated calls give the same bits; the barrier's slope uses the
+ * hardware exponential and logarithm.  Enqueued on `stream`. */
 int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, float* gV, float* gtheta,
                      void* stream);
 
