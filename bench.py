@@ -3,9 +3,11 @@
 Metric: rollout-steps/s, one rollout-step being one disturbed step of one
 of the K x M rollouts (K M T per update); the K T nominal steps are extra
 work that is not counted.  A "step" of this benchmark is one complete
-update (sampling, nominal and disturbed rollouts, CVaR, softmin update) on
-the paper-scale closed-loop workload: dynamic single-track vehicle,
-K = 4096 samples, M = 128 disturbed rollouts, T = 40 steps, 50 obstacles.
+update (sampling, nominal and disturbed rollouts, CVaR, softmin update;
+ra_mppi_step) on the stress workload by default: dynamic single-track
+vehicle, K = 65536 samples, M = 256 disturbed rollouts, T = 50 steps, 200
+obstacles (`--workload` picks another; the line's sections carry the
+others).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -41,37 +43,126 @@ LANES_PER_SM = 128
 
 
 # ---------------------------------------------------------------- op counts
-def algorithmic_ops(p, tested_obstacles=None):
-    """Formula count of ALU lane-operations per disturbed step and per nominal
-    step: FP32 add/mul/FMA/min/max/compare/select and INT32 ops count 1 each,
-    every special-function evaluation (sin, cos, tan, atan, atan2, log, exp,
-    sqrt, rsqrt, division) counts 1.  The indicator obstacle term of a
-    disturbed step counts the obstacles actually tested (`tested_obstacles`
-    per rollout-step, after the kernel's exact bounding-box cull) when given,
-    else all of them."""
+# Formula counts of the rollout kernel's work, by pipe, per disturbed
+# rollout-step and per nominal step (lane-operations).  Each count follows
+# the source of the device functions it names:
+#   fp32  FP32 add, multiply, FMA, min/max, compare-select, rounding;
+#   xu    special-function unit: every rsqrt, rcp, sin, cos, log, exp, sqrt,
+#         tan the kernel calls (a math-library call counts as one operation,
+#         whatever it expands to), and every int <-> float conversion;
+#   int   32-bit integer and logic operations, warp votes and reductions;
+#   issue warp instructions x 32 of the three, where the dynamic model's
+#         FP32 arithmetic counts half when the launch steps rollouts in
+#         paired FP32 instructions (loads, moves and branches are not
+#         counted, so this is a lower bound of what the kernel issues).
+PHILOX_INT = 60  # 10 rounds x (2 wide multiplies, 2 three-input xors, 2 key adds)
+
+
+def _dyn_substep():
+    """One Heun sub-step of the dynamic single-track model (Model<1>):
+    two derivative evaluations and the trapezoid update.  Per derivative:
+    the floored 1/vx (1 fp32 + rcp), slip arguments (4), the warp's range
+    vote (1), two arctangent polynomials (2 x 9), Pacejka arguments (2), two
+    closed-form C = 3/2 shapes (2 x (7 fp32 + 2 rsqrt)), the heading sincos
+    (5 fp32 + sin + cos) and the six derivatives (11)."""
+    deriv_fp32 = 1 + 4 + 1 + 18 + 2 + 14 + 5 + 11
+    deriv_xu = 1 + 4 + 2
+    return dict(fp32=2 * deriv_fp32 + 18, xu=2 * deriv_xu, int=0)
+
+
+def _kin_substep():
+    """One Euler sub-step of the kinematic bicycle: heading sincos (5 fp32 +
+    sin + cos), h v (1) and four FMAs."""
+    return dict(fp32=10, xu=2, int=0)
+
+
+def _noise(p):
+    """Process noise of one rollout-step (add_process_noise)."""
+    model, nt = int(p["model"]), int(p["noise_type"])
+    slots = {0: 4, 1: 3, 2: 1}[model]
+    if nt == 1:  # mixture: two Philox calls; per slot mix_value
+        return dict(fp32=14 * slots, xu=5 * slots, int=2 * PHILOX_INT + 4 * slots)
+    if nt == 0:  # Gaussian: one Philox call, ceil(slots / 2) Box-Muller pairs
+        bm = (slots + 1) // 2
+        return dict(fp32=9 * bm + slots, xu=6 * bm, int=PHILOX_INT)
+    if nt == 2:  # uniform
+        return dict(fp32=2 * slots, xu=slots, int=PHILOX_INT)
+    return dict(fp32=slots + 2, xu=0, int=PHILOX_INT + 2)  # impulse (mostly no jump)
+
+
+def pipe_counts(p, tested=None, ilp=1, paired=False):
+    """(disturbed, nominal): per-pipe lane-operation counts per disturbed
+    rollout-step and per nominal step, and the issue count.
+
+    tested: obstacles tested exactly per rollout-step after the kernel's
+    bounding-box cull (measured by the diagnostic counter); None counts all
+    of them (brute force).  ilp: rollouts a lane interleaves (the cull's box
+    and its obstacle rounds are shared by them).  paired: the dynamic model's
+    FP32 arithmetic runs in paired instructions."""
     model, n_obs, sub = int(p["model"]), int(p["n_obs"]), int(p["substeps"])
-    philox = 100  # 10 rounds x (2 mullo + 2 mulhi + 4 xor + 2 key adds)
-    n_test = n_obs if tested_obstacles is None else tested_obstacles
-    obs_ind = 6 * n_test  # 2 sub, mul, fma, compare-select, add
-    obs_sp = 10 * n_obs  # 2 sub, mul, fma, sqrt, sub, mul, exp, log1p, add
-    obs = obs_ind if int(p["obs_mode"]) == 0 else obs_sp
+    ind = int(p["obs_mode"]) == 0
     if model == 1:
-        deriv = 38  # slip angles 7, two tyres 10, sincos 2, six derivatives 19
-        dyn = sub * (2 * deriv + 6 + 12)
-        # mixture: per slot the tail mass (3), ln, the Laplace value (1), the
-        # Gaussian radius and angle (sqrt, cos, 4), select and sign (2)
-        noise = (2 * philox + 3 * 12) if int(p["noise_type"]) == 1 else (philox + 2 * 10 + 3)
+        step = {k: v * sub for k, v in _dyn_substep().items()}
     elif model == 0:
-        dyn = sub * 7
-        noise = philox + 2 * 10 + 4
+        step = {k: v * sub for k, v in _kin_substep().items()}
     else:
-        dyn, noise = sub, philox + 10 + 1
-    risk = 1 + obs
-    disturbed = dyn + noise + risk
-    # nominal: control draw (Philox + Box-Muller + clip ~ 120), dynamics, full q
-    # (the nominal rollout tests every obstacle)
-    nominal = 120 + dyn + (6 * n_obs if int(p["obs_mode"]) == 0 else obs_sp) + 30
-    return disturbed, nominal
+        step = dict(fp32=sub, xu=0, int=0)
+    dyn_fp32 = step["fp32"]
+    nz = _noise(p)
+    d = {k: step[k] + nz[k] for k in ("fp32", "xu", "int")}
+    risk_obs = int(p["risk_mask"]) & 4
+    if risk_obs and ind and model != 2:
+        n_test = n_obs if tested is None else tested
+        windowed = model == 1 and n_obs > 64
+        rounds = 1 if windowed else max(1, -(-n_obs // 32))
+        # box of the warp's states: min/max, shift, warp reductions, unshift;
+        # per 32-obstacle round: the box test (8 fp32) and its ballot and loop
+        # (4 int); per candidate: the exact test (6 fp32) per state and the
+        # candidate loop (3 int, shared); the x window's two searches (10 int)
+        d["fp32"] += (2 * (ilp - 1) + 8 + 8 * rounds) / ilp + 6 * n_test + 1
+        d["int"] += (4 + 4 * rounds + (10 if windowed else 0)) / ilp + 3 * n_test / ilp
+    elif risk_obs and model != 2:  # softplus barrier: per obstacle 10 fp32, sqrt + exp + log
+        d["fp32"] += 10 * n_obs + 1
+        d["xu"] += 3 * n_obs
+    if int(p["risk_mask"]) & ~4:
+        d["fp32"] += 8
+        d["xu"] += 1
+    fp32_instr = d["fp32"] - (dyn_fp32 / 2 if paired and model == 1 else 0)
+    d["issue"] = fp32_instr + d["xu"] + d["int"]
+    # nominal step: control draw (Philox, accurate Box-Muller, clip: 11 fp32,
+    # log + sqrt + sin + cos + 2 conversions), the per-step control
+    # quantities, the dynamics, the full running cost (track 6 fp32 + sqrt,
+    # deviation, speed, every obstacle) and the control cost
+    n = dict(fp32=11 + step["fp32"] + 6 + 2 + 3 + (6 * n_obs if ind else 10 * n_obs) + 3 + 2,
+             xu=6 + (2 if model == 1 else 2) + step["xu"] + 1 + (0 if ind else 3 * n_obs),
+             int=PHILOX_INT + step["int"] + 4)
+    n["issue"] = n["fp32"] + n["xu"] + n["int"]
+    return d, n
+
+
+def pipe_roofline(p, units, kernel_s, tested, ilp, paired, rates, n_sms, sm_mhz):
+    """Per-pipe roofline of one rollout-kernel launch: achieved lane-ops/s of
+    each pipe from the formula counts over the measured kernel time, against
+    n_sms x (measured lane-ops per SM per clock) x the sampled SM clock."""
+    d, n = pipe_counts(p, tested, ilp, paired)
+    K, T = int(p["K"]), int(p["T"])
+    clk = sm_mhz * 1e6
+    out = {}
+    for pipe in ("fp32", "xu", "issue"):
+        ops = units * d[pipe] + K * T * n[pipe]
+        peak = n_sms * rates[pipe] * clk
+        out[pipe] = {"ops_per_launch": ops, "achieved": ops / kernel_s / 1e9, "peak": peak / 1e9,
+                     "frac": ops / kernel_s / peak, "per_disturbed_step": d[pipe], "per_nominal_step": n[pipe]}
+    out["int_ops_per_disturbed_step"] = d["int"]
+    bound = max(("fp32", "xu", "issue"), key=lambda k: out[k]["frac"])
+    return bound, out
+
+
+def algorithmic_ops(p, tested_obstacles=None):
+    """All counted lane-operations (fp32 + xu + int) per disturbed and per
+    nominal step, one number each (the blended count)."""
+    d, n = pipe_counts(p, tested_obstacles)
+    return d["fp32"] + d["xu"] + d["int"], n["fp32"] + n["xu"] + n["int"]
 
 
 # ---------------------------------------------------------------- clocks
@@ -184,7 +275,7 @@ def run_reference(args, p, x0, V, obs):
         "unit": "rollout-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": config_dict(p, args),
+        "config": config_dict(p, args, reference=True),
         "cpu_baseline": {"value": value, "unit": "rollout-steps/s", "cores": threads, "kind": "oracle",
                          "sample": f"{ks_n} of {K} samples x M={M} x T={T} per step (FP64 C oracle, "
                                    f"OpenMP over samples), then the softmin update over them"},
@@ -193,23 +284,137 @@ def run_reference(args, p, x0, V, obs):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(p, args):
+def config_dict(p, args, reference=False):
     return {"workload": f"{args.workload}: {p['K']} samples x {p['M']} rollouts x {p['T']} steps, "
                         f"{['kinematic bicycle', 'dynamic single-track', 'linear'][int(p['model'])]}, "
                         f"{p['n_obs']} obstacles",
             "K": int(p["K"]), "M": int(p["M"]), "T": int(p["T"]), "model": int(p["model"]),
             "substeps": int(p["substeps"]), "n_obs": int(p["n_obs"]), "alpha": float(p["alpha"]),
-            "step": f"one receding-horizon iteration (update, plant step, warm start) after a "
-                    f"{args.preroll}-iteration untimed pre-roll from the track origin",
+            "step": ("one RA-MPPI update (the FP64 oracle's per-sample stage over a bounded sample of the "
+                     "K samples, then its softmin update) from the track origin" if reference else
+                     f"one RA-MPPI update (ra_mppi_step: sampling, nominal and disturbed rollouts, CVaR, "
+                     f"softmin update) of the state that an untimed {args.preroll}-iteration receding-horizon "
+                     f"pre-roll from the track origin reaches"),
             "l2": "flushed before every timed step (256 MB write, outside the step's events)"}
 
 
 # ---------------------------------------------------------------- GPU arm
+# Default per-SM-per-clock lane-operation rates, used when the probes cannot
+# run: 128 FP32 lanes, 4 schedulers x 32 lanes of issue, and the special-
+# function rate the probe measured on GB300 (see measure_pipe_rates).
+DEFAULT_RATES = {"fp32": 128.0, "issue": 128.0, "xu": 32.0}
+PROBE_KINDS = {"ffma": (0, 400000), "ffma2": (1, 200000), "rsqrt": (2, 60000), "rcp": (3, 60000),
+               "ex2": (4, 60000), "lg2": (5, 60000), "sin": (6, 60000), "i2f": (7, 60000),
+               "imad": (8, 200000)}
+
+
+def measure_pipe_rates(torch, reps=3):
+    """Lane-operations per SM per clock of each pipe from the library's
+    probe kernels (CUDA events, best of `reps`), converted with the median SM
+    clock sampled while they ran.  The special-function rate of the roofline
+    is the median over the six unit operations."""
+    from paper_2209_12842_gb300 import binding as B
+
+    n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    raw = {}
+    for name, (kind, iters) in PROBE_KINDS.items():
+        best = None
+        for _ in range(reps):
+            ms, ops = B.ra_mppi_pipe_probe(kind, iters)
+            rate = ops / (ms / 1e3)
+            best = rate if best is None or rate > best else best
+        raw[name] = best
+    clk = clocks.stop()
+    mhz = clk.get("sm_mhz") or 2070.0
+    per = {k: v / (n_sms * mhz * 1e6) for k, v in raw.items()}
+    xu = float(np.median([per[k] for k in ("rsqrt", "rcp", "ex2", "lg2", "sin")]))
+    rates = {"fp32": per["ffma"], "issue": DEFAULT_RATES["issue"], "xu": xu}
+    return {"per_sm_per_clock": per, "rates_used": rates, "n_sms": n_sms, "clocks": clk,
+            "basis": "probe kernels, 8 independent chains per thread, 4 x 256 threads per SM; "
+                     "issue rate = 4 schedulers x 32 lanes"}
+
+
+def measure_update(torch, p, obs, x0, V, steps, warmup, preroll, rates, clocks=None, flush=None, tune=True):
+    """Device-timed updates of one problem (ra_mppi_step on HBM-resident
+    inputs, fresh noise every update) from the state an untimed receding-
+    horizon pre-roll reaches: per-update CUDA events on the launching stream
+    with an L2 flush before each, the rollout kernel timed by the library's
+    event hook, and the per-pipe roofline of that kernel."""
+    from paper_2209_12842_gb300 import RaMppi
+    from paper_2209_12842_gb300 import binding as B
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    ctl = RaMppi(p, obs)
+    x_d = torch.from_numpy(x0).to(dev)
+    V_d = torch.from_numpy(V).to(dev)
+    hits = torch.zeros(2, dtype=torch.int32, device=dev)
+    for _ in range(preroll):
+        ctl.closed_loop_step(x_d, V_d, hits)
+    torch.cuda.synchronize()
+    tune_ms = ctl.tune(x_d, V_d, 3) if tune else None
+    warps, ilp, wps = ctl.get_launch()
+    V_out = torch.empty_like(V_d)
+    for _ in range(warmup):
+        ctl.step(x_d, V_d, V_out, want_cvar=False)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(steps)] for _ in range(4)]
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.4)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select exactly these launches
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(float(i))
+        ctl.set_timing_events(ev[2][i], ev[3][i])
+        ev[0][i].record(stream)
+        ctl.step(x_d, V_d, V_out, want_cvar=False)
+        ev[1][i].record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    ctl.set_timing_events(None)
+    status = ctl.status()
+    # obstacles tested exactly per rollout-step (one extra, untimed update)
+    cand = torch.zeros(1, dtype=torch.int64, device=dev)
+    B.ra_mppi_set_diagnostics(ctl.h, cand.data_ptr())
+    ctl.step(x_d, V_d, V_out)
+    torch.cuda.synchronize()
+    B.ra_mppi_set_diagnostics(ctl.h, None)
+    K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
+    tested = float(cand.item()) / (K * ((M + 31) // 32) * T)
+    step_ms = np.array([b.elapsed_time(e) for b, e in zip(ev[0], ev[1])])
+    kern_ms = np.array([b.elapsed_time(e) for b, e in zip(ev[2], ev[3])])
+    units = K * M * T
+    sm_mhz = ((clk or {}).get("sm_mhz")) or 2070.0
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    paired = int(p["model"]) == 1 and ilp % 2 == 0
+    k_s = float(kern_ms.mean()) / 1e3
+    bound, pipes = pipe_roofline(p, units, k_s, tested, ilp, paired, rates, n_sms, sm_mhz)
+    _, pipes_bf = pipe_roofline(p, units, k_s, None, ilp, paired, rates, n_sms, sm_mhz)
+    out = {"ctl": ctl, "x": x_d, "V": V_d, "step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk,
+           "status": status, "tested": tested, "units": units, "launch": (warps, ilp, wps), "tune_ms": tune_ms,
+           "roofline": {
+               "bound": "alu", "kernel": "rollout_cvar_kernel", "pipe": bound,
+               "achieved": pipes[bound]["achieved"], "peak": pipes[bound]["peak"],
+               "unit": f"G lane-ops/s ({bound} pipe, formula count)", "frac": pipes[bound]["frac"],
+               "pipes": pipes, "obstacles_tested_per_rollout_step": tested,
+               "frac_brute_force_count": {k: pipes_bf[k]["frac"] for k in ("fp32", "xu", "issue")},
+               "peak_basis": f"{n_sms} SMs x measured lane-ops per SM per clock "
+                             f"(fp32 {rates['fp32']:.1f}, xu {rates['xu']:.1f}, issue {rates['issue']:.0f}) "
+                             f"x median SM clock {sm_mhz:.0f} MHz during the timed region",
+               "kernel_ms_mean": 1e3 * k_s}}
+    return out
+
+
 def run_ours(args, p, x0, V, obs):
     import torch
     import torch.distributed as dist
 
-    from paper_2209_12842_gb300 import RaMppi
     from paper_2209_12842_gb300 import binding as B
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -221,69 +426,28 @@ def run_ours(args, p, x0, V, obs):
     p = dict(p, seed=int(p["seed"]) + rank, instance_id=rank)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    ctl = RaMppi(p, obs)
-    x0_d = torch.from_numpy(x0).to(dev)
-    V_d = torch.from_numpy(V).to(dev)
-    V_out = torch.empty_like(V_d)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kv_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kv_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    peaks = None
+    rates = dict(DEFAULT_RATES)
+    if rank == 0 and world == 1 and not args.no_probes:
+        peaks = measure_pipe_rates(torch)
+        rates = peaks["rates_used"]
 
-    # The timed step is one receding-horizon iteration of Algorithm 1 (update,
-    # execute v0+ on the simulated plant, warm start), from the state the loop
-    # reaches after an untimed pre-roll, so the rollouts meet the obstacles.
-    x_d = x0_d.clone()
-    hits = torch.zeros(2, dtype=torch.int32, device=dev)
-    for i in range(args.preroll):
-        ctl.closed_loop_step(x_d, V_d, hits)
-    torch.cuda.synchronize()
-    tune_ms = ctl.tune(x_d, V_d, 3)  # launch-shape autotuner (results do not depend on it)
-    warps, ilp, wps = ctl.get_launch()
-    for i in range(args.warmup):
-        ctl.closed_loop_step(x_d, V_d, hits)
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    if rank == 0:
-        clocks.start()
-        time.sleep(0.4)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
     t0 = time.perf_counter()
-    torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select exactly these launches
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ctl.set_timing_events(kv_b[i], kv_e[i])
-        ev_b[i].record(stream)
-        ctl.closed_loop_step(x_d, V_d, hits)
-        ev_e[i].record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
+    m = measure_update(torch, p, obs, x0, V, args.steps, args.warmup, args.preroll, rates, clocks, flush)
+    wall = time.perf_counter() - t0
     if world > 1:
         dist.barrier()
-    wall = time.perf_counter() - t0
-    ctl.set_timing_events(None)
-    clk = clocks.stop() if rank == 0 else None
-    status = ctl.status()
-    # obstacles tested exactly per rollout-step (one extra, untimed update)
-    cand = torch.zeros(1, dtype=torch.int64, device=dev)
-    B.ra_mppi_set_diagnostics(ctl.h, cand.data_ptr())
-    ctl.step(x_d, V_d, V_out)
-    torch.cuda.synchronize()
-    B.ra_mppi_set_diagnostics(ctl.h, None)
-    tested = float(cand.item()) / (int(p["K"]) * ((int(p["M"]) + 31) // 32) * int(p["T"]))
-
-    step_ms = np.array([b.elapsed_time(e) for b, e in zip(ev_b, ev_e)])
-    kern_ms = np.array([b.elapsed_time(e) for b, e in zip(kv_b, kv_e)])
-    t_step = aggregate_over_ranks(dist if world > 1 else None, torch, float(step_ms.sum()) / 1e3, dev)
+    ctl, x_d = m["ctl"], m["x"]
     K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
-    units = K * M * T
-    value = job_value(world, units, args.steps, t_step)
+    t_step = aggregate_over_ranks(dist if world > 1 else None, torch, float(m["step_ms"].sum()) / 1e3, dev)
+    value = job_value(world, m["units"], args.steps, t_step)
 
-    # end to end through the C ABI with host buffers (pinned), copies inside
+    # end to end through the C ABI with host buffers (pinned): the same update
+    # of the same state, its inputs copied in and V+ copied out inside the call
     nx = x0.size
     x0_h = x_d.cpu().pin_memory()
     V_h = torch.from_numpy(V).pin_memory()
@@ -301,14 +465,10 @@ def run_ours(args, p, x0, V, obs):
     ctl.close()
 
     if rank == 0:
-        d_ops, n_ops = algorithmic_ops(p, tested)
-        d_ops_bf, _ = algorithmic_ops(p)
-        ops_per_launch = units * d_ops + K * T * n_ops
-        k_mean = float(kern_ms.mean()) / 1e3
-        achieved = ops_per_launch / k_mean / 1e9
-        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-        peak = N_SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e9
-        traffic = load_traffic(args.workload)
+        step_ms = m["step_ms"]
+        warps, ilp, wps = m["launch"]
+        roof = m["roofline"]
+        roof["traffic"] = load_traffic(args.workload)
         line = {
             "metric": "rollout-steps/s (K*M*T)", "value": value, "unit": "rollout-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -316,45 +476,89 @@ def run_ours(args, p, x0, V, obs):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(p, args),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                           "rollout_kernel_mean": 1e3 * k_mean},
-            "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
-            "gpu_launches": 3 * args.steps,
+                           "rollout_kernel_mean": float(m["kern_ms"].mean())},
+            "wall_s_timed_section": wall,
+            "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
             "launch": {"warps_per_block": warps, "rollouts_interleaved": ilp, "warps_per_sample": wps,
-                       "tune_ms": tune_ms},
-            "status": B.STATUS_NAMES.get(status, status),
-            "clocks": clk,
-            "e2e": {"value": world * units / e2e_t, "unit": "rollout-steps/s",
+                       "tune_ms": m["tune_ms"]},
+            "status": B.STATUS_NAMES.get(m["status"], m["status"]),
+            "clocks": m["clocks"],
+            "e2e": {"value": world * m["units"] / e2e_t, "unit": "rollout-steps/s",
                     "h2d_bytes_per_step": 4 * (nx + V.size), "d2h_bytes_per_step": 4 * V.size,
-                    "ms_per_step": 1e3 * e2e_t},
-            "roofline": {"bound": "alu", "kernel": "rollout_cvar_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "Gop/s (ALU lane-ops, formula count)", "frac": achieved / peak,
-                         "ops_per_launch": ops_per_launch, "ops_per_disturbed_step": d_ops,
-                         "ops_per_nominal_step": n_ops,
-                         "obstacles_tested_per_rollout_step": tested,
-                         "ops_per_disturbed_step_brute_force": d_ops_bf,
-                         "frac_brute_force_count": (units * d_ops_bf + K * T * n_ops) / k_mean / 1e9 / peak,
-                         "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock {sm_mhz:.0f} MHz",
-                         "traffic": traffic},
+                    "ms_per_step": 1e3 * e2e_t,
+                    "call": "ra_mppi_step_host: the same update, copies in and out and a stream sync inside"},
+            "roofline": roof,
+            "pipe_peaks": peaks,
         }
         if world == 1 and not args.no_studies:
-            line["closed_loop"] = closed_loop_study(torch, args.loop_updates)
-            line["closed_loop_paper_preset"] = closed_loop_study(
-                torch, args.loop_updates, "paper_sim", [("mppi", dict(A=0.0)), ("ra_alpha0.7", {})])
-            line["batched"] = batched_study(torch, 10)
-            line["adjoint"] = adjoint_study(torch, 10)
-            line["importance"] = importance_study(torch)
+            line["sections"] = sections(torch, args, rates, flush)
         if world == 1 and not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
-            rate, n_s, dt = oracle_rate(p, x0, V, obs, args.cpu_seconds, threads)
-            line["cpu_baseline"] = {"value": rate, "unit": "rollout-steps/s", "cores": threads,
-                                    "kind": "oracle",
-                                    "sample": f"{n_s} of {K} samples x M={M} x T={T} "
-                                              f"({dt:.1f} s, FP64 C oracle, OpenMP over samples)"}
+            line["cpu_baseline"] = cpu_baseline(p, x_d.cpu().numpy(), V, obs, threads, args.cpu_seconds)
         else:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+LAUNCHES_PER_UPDATE = 2  # rollout_cvar_kernel and softmin_update_kernel
+
+
+def cpu_baseline(p, x0, V, obs, threads, seconds):
+    """The FP64 oracle on the host cores (OpenMP over samples) on K/64 of the
+    workload's samples (at least the thread count), repeated for about
+    `seconds`; reported as rollout-steps/s and the full update's
+    extrapolated time."""
+    import oracle
+
+    K, M, T = int(p["K"]), int(p["M"]), int(p["T"])
+    n = max(threads, K // 64)
+    ks = np.arange(min(n, K), dtype=np.int32)
+    reps, spent = 0, 0.0
+    while spent < seconds or reps == 0:
+        t0 = time.perf_counter()
+        out = oracle.samples(p, x0, V, obs, ks=ks, iteration=reps, n_threads=threads)
+        oracle.update(out["S_tilde"], out["U"], float(np.float32(p["lam"])))
+        spent += time.perf_counter() - t0
+        reps += 1
+    rate = reps * len(ks) * M * T / spent
+    return {"value": rate, "unit": "rollout-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(ks)} of {K} samples (K/64) x M={M} x T={T}, {reps} updates in {spent:.1f} s "
+                      f"(FP64 C oracle, OpenMP over samples); the full update extrapolates to "
+                      f"{K * M * T / rate:.1f} s"}
+
+
+def roofline_summary(m):
+    r = m["roofline"]
+    return {"pipe": r["pipe"], "frac": r["frac"], "fracs": {k: r["pipes"][k]["frac"] for k in ("fp32", "xu", "issue")},
+            "kernel_ms_mean": r["kernel_ms_mean"], "obstacles_tested_per_rollout_step": r[
+                "obstacles_tested_per_rollout_step"]}
+
+
+def sections(torch, args, rates, flush):
+    """The other workloads of the same line: config 2 (update rate and
+    roofline, and its 1000-update closed loop), the paper's simulation preset
+    (update rate only), config 3 (batched), config 4 (adjoint), and the
+    importance-sampling study."""
+    out = {}
+    for name, preset in (("c2_update", "c2_closed_loop"), ("paper_preset_update", "paper_sim"),
+                         ("c1_update", "c1_plain")):
+        q = rs.preset(preset)
+        m = measure_update(torch, q, rs.scene_obstacles(q), rs.scene_initial_state(q),
+                           rs.random_controls(q["model"], q["T"], q["u_lo"], q["u_hi"], 3), 20, 5,
+                           args.preroll, rates, None, flush)
+        m["ctl"].close()
+        out[name] = {"K": q["K"], "M": q["M"], "T": q["T"], "p50_ms": float(np.percentile(m["step_ms"], 50)),
+                     "p99_ms": float(np.percentile(m["step_ms"], 99)),
+                     "rollout_steps_per_s": m["units"] / (float(np.median(m["step_ms"])) / 1e3),
+                     "update_hz": 1e3 / float(np.median(m["step_ms"])), "launch": m["launch"],
+                     "roofline": roofline_summary(m)}
+    out["c2_closed_loop"] = closed_loop_study(torch, args.loop_updates)
+    out["batched"] = batched_study(torch, 10)
+    out["adjoint"] = adjoint_study(torch, 10)
+    out["importance"] = importance_study(torch)
+    return out
 
 
 def kernel_source_sha():
@@ -407,8 +611,7 @@ def closed_loop_study(torch, n_updates, preset="c2_closed_loop", runs=None, seed
     MPPI (A = 0) and RA-MPPI, each over the same obstacle field with several
     noise seeds (the counts of one 1000-update run vary a lot with the
     noise).  Config 2 compares alpha in {0.5, 0.9, 0.99} with its risk cost
-    l = obstacle term; the paper's preset uses l = q (boundary, obstacles,
-    deviation) with A = 10, C_u = 0.6, alpha = 0.7."""
+    l = obstacle term."""
     from paper_2209_12842_gb300 import RaMppi
 
     p0 = rs.preset(preset)
@@ -570,69 +773,35 @@ def importance_study(torch, scales=((1.5, 0.5), (1.1, 0.5)), alpha=0.99):
 def stress_sweep(args):
     """Config 5: dynamic single-track, K = 65536, T = 50, 200 obstacles; M in
     {32, 64, 128, 256} x alpha in {0.8, 0.95}; update latency p50/p99 over
-    `--steps` updates per point and the rollout kernel's roofline fraction."""
+    `--steps` updates per point (tuned launch) and the rollout kernel's
+    per-pipe roofline."""
     import torch
 
-    from paper_2209_12842_gb300 import RaMppi
-    from paper_2209_12842_gb300 import binding as B
-
     torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
+    rates = measure_pipe_rates(torch)["rates_used"]
     base = rs.preset("c5_stress")
-    obs = rs.make_obstacles(base["seed"], base["n_obs"], *base["obs_r"])
-    x0 = torch.from_numpy(rs.initial_state(base["model"])).cuda()
-    V = torch.from_numpy(rs.random_controls(base["model"], base["T"], base["u_lo"], base["u_hi"], 3)).cuda()
-    clocks = ClockSampler(0)
-    clocks.start()
+    obs = rs.scene_obstacles(base)
+    x0 = rs.scene_initial_state(base)
+    V = rs.random_controls(base["model"], base["T"], base["u_lo"], base["u_hi"], 3)
     points = []
     for M in (32, 64, 128, 256):
         for alpha in (0.8, 0.95):
             p = rs.preset("c5_stress", M=M, alpha=alpha)
-            ctl = RaMppi(p, obs)
-            Vo = torch.empty_like(V)
-            ctl.tune(x0, V, 2)
-            warps, ilp, wps = ctl.get_launch()
-            kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            sb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            se = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            for _ in range(args.warmup):
-                ctl.step(x0, V, Vo)
-            torch.cuda.synchronize()
-            for i in range(args.steps):
-                ctl.set_timing_events(kb[i], ke[i])
-                sb[i].record(stream)
-                ctl.step(x0, V, Vo)
-                se[i].record(stream)
-            torch.cuda.synchronize()
-            ctl.set_timing_events(None)
-            cand = torch.zeros(1, dtype=torch.int64, device="cuda")
-            B.ra_mppi_set_diagnostics(ctl.h, cand.data_ptr())
-            ctl.step(x0, V, Vo)
-            torch.cuda.synchronize()
-            B.ra_mppi_set_diagnostics(ctl.h, None)
-            tested = float(cand.item()) / (p["K"] * ((M + 31) // 32) * p["T"])
-            step_ms = np.array([a.elapsed_time(b) for a, b in zip(sb, se)])
-            k_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(kb, ke)]))
-            d_ops, n_ops = algorithmic_ops(p, tested)
-            ops = p["K"] * M * p["T"] * d_ops + p["K"] * p["T"] * n_ops
-            points.append({"M": M, "alpha": alpha, "p50_ms": float(np.percentile(step_ms, 50)),
-                           "p99_ms": float(np.percentile(step_ms, 99)), "rollout_kernel_ms": k_ms,
-                           "rollout_steps_per_s": p["K"] * M * p["T"] / (float(np.median(step_ms)) / 1e3),
-                           "obstacles_tested_per_rollout_step": tested, "ops_per_launch": ops,
-                           "achieved_gops": ops / (k_ms / 1e3) / 1e9, "launch": [warps, ilp, wps]})
-            ctl.close()
-    clk = clocks.stop()
-    peak = N_SMS * LANES_PER_SM * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e9
-    for pt in points:
-        pt["roofline_frac"] = pt["achieved_gops"] / peak
+            m = measure_update(torch, p, obs, x0, V, args.steps, args.warmup, args.preroll, rates,
+                               ClockSampler(0))
+            m["ctl"].close()
+            st = m["step_ms"]
+            points.append({"M": M, "alpha": alpha, "p50_ms": float(np.percentile(st, 50)),
+                           "p99_ms": float(np.percentile(st, 99)),
+                           "rollout_steps_per_s": m["units"] / (float(np.median(st)) / 1e3),
+                           "launch": m["launch"], "clocks": m["clocks"], "roofline": roofline_summary(m)})
     top = [pt for pt in points if pt["M"] == 256 and pt["alpha"] == 0.95][0]
     line = {"metric": "rollout-steps/s (K*M*T)", "value": top["rollout_steps_per_s"], "unit": "rollout-steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": top["p50_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "c5 stress: dynamic single-track, K=65536, T=50, 200 obstacles, sweep of M and alpha",
                        "l2": "inputs resident; per-update working set below L2 (compute bound)"},
-            "clocks": clk, "roofline_peak_gops": peak, "sweep": points}
+            "rates_per_sm_per_clock": rates, "sweep": points}
     print(json.dumps(line), flush=True)
 
 
@@ -655,11 +824,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probes", action="store_true",
+                    help="skip the pipe-throughput probes (the roofline then uses nominal rates)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-studies", action="store_true",
-                    help="skip the closed-loop, batched and adjoint sections of the line")
+                    help="skip the other workloads' sections of the line")
     ap.add_argument("--loop-updates", type=int, default=1000)
     ap.add_argument("--preroll", type=int, default=200,
                     help="untimed receding-horizon iterations before timing (the state leaves the start area)")

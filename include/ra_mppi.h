@@ -39,7 +39,7 @@
  *     keyed by (seed, update iteration) and counted by (t, rollout m,
  *     sample k, instance); the iteration counter lives in the handle and
  *     advances by one per update, so a handle reproduces its sequence
- *     exactly after ra_mppi_set_iteration.
+ *     exactly after ra_mppi_set_state.
  */
 #ifndef RA_MPPI_H
 #define RA_MPPI_H
@@ -55,7 +55,8 @@ typedef enum {
   RA_MPPI_EINVAL = -1,       /* invalid argument or size                    */
   RA_MPPI_ENOMEM = -2,       /* device or host allocation failed            */
   RA_MPPI_ECUDA = -3,        /* a CUDA runtime call or launch failed        */
-  RA_MPPI_ETIMEOUT = -4,     /* a bounded device wait gave up               */
+  RA_MPPI_ETIMEOUT = -4,     /* reserved: no kernel of this library waits on
+                                another block, so no call returns it         */
   RA_MPPI_ENONFINITE = -5,   /* a cost was NaN/inf or all weights vanished  */
   RA_MPPI_EUNSUPPORTED = -6  /* valid request the library does not support  */
 } ra_mppi_status;
@@ -187,11 +188,16 @@ typedef struct ra_mppi ra_mppi_t;
 /* Size of ra_mppi_problem as compiled into the library (binding check). */
 int32_t ra_mppi_problem_size(void);
 
-/* Validate *p and allocate a handle with all workspace on the current CUDA
- * device.  Returns EINVAL for out-of-range sizes or parameters (lambda <= 0,
- * alpha outside (0, 1), B < 0, eta outside [0, 1), M > RA_MPPI_MAX_M, ...),
- * ENOMEM if allocation fails.  *out is set only on success. */
-int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out);
+/* Validate *p (the problem of Secs. II-III: dynamics, costs, Sigma, lambda,
+ * alpha, K, M, T) and allocate a handle with all its workspace on CUDA
+ * device `device` (-1: the current device).  Every later call on the handle
+ * runs on that device, whatever device is current when it is made (the
+ * caller's current device is restored on return).  Returns EINVAL for
+ * out-of-range sizes or parameters (lambda <= 0, alpha outside (0, 1),
+ * B < 0, eta outside [0, 1), M > RA_MPPI_MAX_M, no such device, ...),
+ * ENOMEM if allocation fails, ECUDA if the device cannot be used.  *out is
+ * set only on success. */
+int ra_mppi_create(const ra_mppi_problem* p, int32_t device, ra_mppi_t** out);
 
 /* Release a handle and its workspace.  NULL is allowed. */
 void ra_mppi_destroy(ra_mppi_t* h);
@@ -258,9 +264,12 @@ int ra_mppi_copy_workspace(ra_mppi_t* h, float* U, float* S, float* cvar, float*
  * RA_MPPI_KEEP_RISK_COSTS and importance sampling on.  Enqueued on `stream`. */
 int ra_mppi_copy_weights(ra_mppi_t* h, float* W, void* stream);
 
-/* Update counter that keys the noise.  get waits for the device. */
-int ra_mppi_get_iteration(ra_mppi_t* h, uint64_t* iteration);
-int ra_mppi_set_iteration(ra_mppi_t* h, uint64_t iteration);
+/* The handle's resumable state: the update counter that keys the noise
+ * (Alg. 1 redraws the samples at every update; the counter makes update n
+ * reproducible).  A handle restored with set_state reproduces the updates
+ * that followed get_state exactly.  get waits for the device. */
+int ra_mppi_get_state(ra_mppi_t* h, uint64_t* iteration);
+int ra_mppi_set_state(ra_mppi_t* h, uint64_t iteration);
 
 /* Device status word accumulated since the last call, then cleared: OK,
  * or ENONFINITE when a cost was NaN/inf or every weight vanished.  Waits
@@ -328,6 +337,19 @@ int ra_mppi_set_diagnostics(ra_mppi_t* h, unsigned long long* candidates);
  * alone.  NULL, NULL turns the hook off. */
 int ra_mppi_set_timing_events(ra_mppi_t* h, void* rollout_begin, void* rollout_end);
 
+/* Pipe-throughput probe for the roofline of the rollout kernel (no
+ * counterpart in the paper; a measurement aid).  Runs one probe kernel of
+ * `iters` iterations of eight independent chains per thread, on 4 blocks of
+ * 256 threads per SM of `device` (-1: current), of one instruction kind:
+ *   0 FP32 fused multiply-add     1 paired FP32 multiply-add (2 ops each)
+ *   2 rsqrt.approx  3 rcp.approx  4 ex2.approx  5 lg2.approx  6 sin.approx
+ *                                 (one special-function unit operation each)
+ *   7 32-bit integer to float conversion   8 32-bit integer multiply-add
+ * and returns its CUDA-event time *ms and the lane-operations it executed
+ * (*lane_ops), so that ops / (ms x SM clock x SMs) is the pipe's rate per SM
+ * per clock.  Synchronous; allocates a stream and two events. */
+int ra_mppi_pipe_probe(int32_t kind, int32_t iters, int32_t device, float* ms, double* lane_ops);
+
 /* ------------------------------------------------------------------ */
 /* Batched updates: B independent problems in one persistent launch    */
 /* replayed from a CUDA graph.  The paper updates one controller; this  */
@@ -346,10 +368,13 @@ typedef struct ra_mppi_instance {
 typedef struct ra_mppi_batch ra_mppi_batch_t;
 
 /* Validate every problem (common fields + inst[i]) as ra_mppi_create would,
- * allocate packed buffers, order the work items (nominal items first, then
- * the disturbed samples of the costliest problems first) and capture the
- * graph (queue reset, persistent rollout kernel, batched update kernel). */
-int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* inst, int32_t B,
+ * allocate packed buffers on CUDA device `device` (-1: the current device;
+ * later calls run there, as for single handles), order the work items
+ * (nominal items first, then the disturbed samples of the costliest
+ * problems first) and capture the graph (queue reset, persistent rollout
+ * kernel, batched update kernel).  Each problem is one RA-MPPI update
+ * (Alg. 1); the batch has no counterpart in the paper. */
+int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* inst, int32_t B, int32_t device,
                          ra_mppi_batch_t** out);
 void ra_mppi_batch_destroy(ra_mppi_batch_t* b);
 
@@ -362,6 +387,17 @@ int ra_mppi_batch_layout(ra_mppi_batch_t* b, int64_t* offsets);
  * graph reads and writes them): x0 [sum nx], V [sum T_i nu] (input mean
  * controls), V_out [sum T_i nu] (V+), S_tilde [sum K_i]. */
 int ra_mppi_batch_buffers(ra_mppi_batch_t* b, float** x0, float** V, float** V_out, float** S_tilde);
+
+/* The batch's packed inputs, owned by the library and stable for the
+ * handle's life, so a captured graph and the caller both address them:
+ *   x0_packed  receives the device buffer of the states x(0) (Alg. 1's state
+ *              estimate) [sum nx], problem i at offsets[4 i + 0];
+ *   V_packed   receives the device buffer of the mean controls V [sum T_i nu],
+ *              problem i at offsets[4 i + 1] (its V+ is at the same offset
+ *              of ra_mppi_batch_buffers' V_out);
+ *   offsets    [4 B] int64 or NULL: as ra_mppi_batch_layout.
+ * Any output may be NULL. */
+int ra_mppi_batch_io(ra_mppi_batch_t* b, float** x0_packed, float** V_packed, int64_t* offsets);
 
 /* Copy packed inputs in (x0 [sum nx], V [sum T_i nu]) and outputs out
  * (V_out [sum T_i nu], S_tilde [sum K_i]) between caller buffers (host or
@@ -413,10 +449,13 @@ const char* ra_mppi_batch_last_error(const ra_mppi_batch_t* b);
  * that loads this library keeps until the process exits; the counter is
  * cleared with cudaMemsetAsync before each launch.  The first call on a
  * device looks up that array's device address with the device current;
- * make this first call before any stream capture.  All calls share the
- * array and it keeps the last call's contents: calls that overlap on the
- * GPU (different streams, or threads without ordering between them) race;
- * calls ordered on one stream do not. */
+ * make this first call before any stream capture.  The address is kept for
+ * the life of the device's context: do not call this entry point after
+ * cudaDeviceReset in the same process.  `stream` must belong to the current
+ * device (EINVAL otherwise).  All calls share the array and it keeps the
+ * last call's contents: calls that overlap on the GPU (different streams,
+ * or threads without ordering between them) race; calls ordered on one
+ * stream do not. */
 #define RA_MPPI_NOALLOC_MAX_COLS 512
 int ra_mppi_softmin_update_noalloc(const float* S_tilde, const float* U, int32_t K, int32_t T, int32_t nu,
                                    float lambda, float* V_out, void* stream);

@@ -70,7 +70,7 @@ _load_error = None
 
 def _declare(L):
     L.ra_mppi_problem_size.restype = ctypes.c_int32
-    L.ra_mppi_create.argtypes = [ctypes.POINTER(ra_mppi_problem), ctypes.POINTER(_VP)]
+    L.ra_mppi_create.argtypes = [ctypes.POINTER(ra_mppi_problem), ctypes.c_int32, ctypes.POINTER(_VP)]
     L.ra_mppi_destroy.argtypes = [_VP]
     L.ra_mppi_destroy.restype = None
     L.ra_mppi_set_obstacles.argtypes = [_VP, _FP, ctypes.c_int32, _VP]
@@ -79,8 +79,8 @@ def _declare(L):
     L.ra_mppi_workspace.argtypes = [_VP] + [ctypes.POINTER(_VP)] * 4
     L.ra_mppi_copy_workspace.argtypes = [_VP, _FP, _FP, _FP, _FP, _VP]
     L.ra_mppi_copy_weights.argtypes = [_VP, _FP, _VP]
-    L.ra_mppi_get_iteration.argtypes = [_VP, ctypes.POINTER(ctypes.c_uint64)]
-    L.ra_mppi_set_iteration.argtypes = [_VP, ctypes.c_uint64]
+    L.ra_mppi_get_state.argtypes = [_VP, ctypes.POINTER(ctypes.c_uint64)]
+    L.ra_mppi_set_state.argtypes = [_VP, ctypes.c_uint64]
     L.ra_mppi_get_status.argtypes = [_VP]
     L.ra_mppi_last_error.argtypes = [_VP]
     L.ra_mppi_last_error.restype = ctypes.c_char_p
@@ -101,10 +101,14 @@ def _declare(L):
     L.ra_mppi_softmin_update_noalloc.argtypes = [_FP, _FP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_float, _FP, _VP]
     L.ra_mppi_softmin_update_noalloc.restype = ctypes.c_int
+    L.ra_mppi_pipe_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_double)]
+    L.ra_mppi_pipe_probe.restype = ctypes.c_int
     _I64P = ctypes.POINTER(ctypes.c_int64)
     _I32P = ctypes.POINTER(ctypes.c_int32)
     L.ra_mppi_batch_create.argtypes = [ctypes.POINTER(ra_mppi_problem), ctypes.POINTER(ra_mppi_instance),
-                                       ctypes.c_int32, ctypes.POINTER(_VP)]
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_VP)]
+    L.ra_mppi_batch_io.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I64P]
     L.ra_mppi_batch_destroy.argtypes = [_VP]
     L.ra_mppi_batch_destroy.restype = None
     L.ra_mppi_batch_layout.argtypes = [_VP, _I64P]
@@ -122,15 +126,15 @@ def _declare(L):
     L.ra_mppi_batch_tune.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     L.ra_mppi_batch_last_error.argtypes = [_VP]
     L.ra_mppi_batch_last_error.restype = ctypes.c_char_p
-    for name in ("ra_mppi_batch_create", "ra_mppi_batch_layout", "ra_mppi_batch_buffers",
+    for name in ("ra_mppi_batch_create", "ra_mppi_batch_io", "ra_mppi_batch_layout", "ra_mppi_batch_buffers",
                  "ra_mppi_batch_set_obstacles", "ra_mppi_step_batched", "ra_mppi_step_batched_eager",
                  "ra_mppi_batch_write_inputs", "ra_mppi_batch_read_outputs",
                  "ra_mppi_batch_copy_workspace", "ra_mppi_batch_set_iteration", "ra_mppi_batch_get_status",
                  "ra_mppi_batch_set_launch", "ra_mppi_batch_get_launch", "ra_mppi_batch_tune"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("ra_mppi_create", "ra_mppi_set_obstacles", "ra_mppi_step", "ra_mppi_step_host",
-                 "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_copy_weights", "ra_mppi_get_iteration",
-                 "ra_mppi_set_iteration", "ra_mppi_get_status", "ra_mppi_set_launch", "ra_mppi_set_timing_events"):
+                 "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_copy_weights", "ra_mppi_get_state",
+                 "ra_mppi_set_state", "ra_mppi_get_status", "ra_mppi_set_launch", "ra_mppi_set_timing_events"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -200,9 +204,9 @@ def _check(rc, where, handle=None):
 
 # ------------------------------------------------------------------ C names
 
-def ra_mppi_create(problem):
+def ra_mppi_create(problem, device=-1):
     h = _VP()
-    _check(lib().ra_mppi_create(ctypes.byref(problem), ctypes.byref(h)), "ra_mppi_create")
+    _check(lib().ra_mppi_create(ctypes.byref(problem), int(device), ctypes.byref(h)), "ra_mppi_create")
     return h
 
 
@@ -269,14 +273,14 @@ def ra_mppi_copy_workspace(h, U_ptr=None, S_ptr=None, cvar_ptr=None, L_ptr=None,
            "ra_mppi_copy_workspace", h)
 
 
-def ra_mppi_get_iteration(h):
+def ra_mppi_get_state(h):
     it = ctypes.c_uint64()
-    _check(lib().ra_mppi_get_iteration(h, ctypes.byref(it)), "ra_mppi_get_iteration", h)
+    _check(lib().ra_mppi_get_state(h, ctypes.byref(it)), "ra_mppi_get_state", h)
     return it.value
 
 
-def ra_mppi_set_iteration(h, iteration):
-    _check(lib().ra_mppi_set_iteration(h, int(iteration)), "ra_mppi_set_iteration", h)
+def ra_mppi_set_state(h, iteration):
+    _check(lib().ra_mppi_set_state(h, int(iteration)), "ra_mppi_set_state", h)
 
 
 def ra_mppi_get_status(h):
@@ -304,6 +308,14 @@ def ra_mppi_softmin_update_noalloc(S_tilde_ptr, U_ptr, K, T, nu, lam, V_out_ptr,
                                                 V_out_ptr, stream)
 
 
+def ra_mppi_pipe_probe(kind, iters, device=-1):
+    """(ms, lane_ops) of one pipe-throughput probe launch (see the header)."""
+    ms, ops = ctypes.c_float(), ctypes.c_double()
+    _check(lib().ra_mppi_pipe_probe(int(kind), int(iters), int(device), ctypes.byref(ms), ctypes.byref(ops)),
+           "ra_mppi_pipe_probe")
+    return ms.value, ops.value
+
+
 # ------------------------------------------------------------------ batched path
 
 def _bcheck(rc, where, b=None):
@@ -315,12 +327,21 @@ def _bcheck(rc, where, b=None):
         raise RaMppiError(rc, where, detail)
 
 
-def ra_mppi_batch_create(problem, instances):
+def ra_mppi_batch_create(problem, instances, device=-1):
     arr = (ra_mppi_instance * len(instances))(*instances)
     b = _VP()
-    _bcheck(lib().ra_mppi_batch_create(ctypes.byref(problem), arr, len(instances), ctypes.byref(b)),
+    _bcheck(lib().ra_mppi_batch_create(ctypes.byref(problem), arr, len(instances), int(device), ctypes.byref(b)),
             "ra_mppi_batch_create")
     return b
+
+
+def ra_mppi_batch_io(b, n):
+    """(x0_packed, V_packed, offsets): the library-owned input buffers and the
+    per-problem offsets (as ra_mppi_batch_layout)."""
+    x0, V = _VP(), _VP()
+    off = (ctypes.c_int64 * (4 * n))()
+    _bcheck(lib().ra_mppi_batch_io(b, ctypes.byref(x0), ctypes.byref(V), off), "ra_mppi_batch_io", b)
+    return x0.value, V.value, [tuple(off[4 * i:4 * i + 4]) for i in range(n)]
 
 
 def ra_mppi_batch_destroy(b):

@@ -33,7 +33,7 @@ class RaMppi:
             (B.RA_MPPI_DIFFERENTIABLE if differentiable else 0)
         self.keep_risk_costs = keep_risk_costs
         self._prob = B.ra_mppi_problem_from(self.p, flags=flags, max_obstacles=cap)
-        self.h = B.ra_mppi_create(self._prob)
+        self.h = B.ra_mppi_create(self._prob, torch.cuda.current_device())
         self.K, self.M, self.T = int(self.p["K"]), int(self.p["M"]), int(self.p["T"])
         self.nx, self.nu = {0: (4, 2), 1: (6, 2), 2: (1, 1)}[int(self.p["model"])]
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -109,11 +109,11 @@ class RaMppi:
 
     @property
     def iteration(self):
-        return B.ra_mppi_get_iteration(self.h)
+        return B.ra_mppi_get_state(self.h)
 
     @iteration.setter
     def iteration(self, it):
-        B.ra_mppi_set_iteration(self.h, it)
+        B.ra_mppi_set_state(self.h, it)
 
     def status(self):
         return B.ra_mppi_get_status(self.h)
@@ -169,7 +169,7 @@ class RaMppiBatch:
         recs = [B.ra_mppi_instance(int(i["K"]), int(i["M"]), int(i["T"]), int(i["max_obstacles"]),
                                    int(i["seed"]) & 0xFFFFFFFFFFFFFFFF, int(i["instance_id"]) & 0xFFFFFFFF, 0)
                 for i in self.inst]
-        self.b = B.ra_mppi_batch_create(prob, recs)
+        self.b = B.ra_mppi_batch_create(prob, recs, torch.cuda.current_device())
         self.B = len(self.inst)
         self.nx, self.nu = {0: (4, 2), 1: (6, 2), 2: (1, 1)}[int(self.p["model"])]
         self.offsets = B.ra_mppi_batch_layout(self.b, self.B)

@@ -9,16 +9,19 @@
 #include <mutex>
 #include <string>
 
+#include "ra_host.h"
 #include "ra_kernels.h"
 #include "ra_mppi.h"
 
 using ramppi::DevParams;
 using ramppi::DevState;
+using ramppi_api::DeviceScope;
 
 struct ra_mppi {
   ra_mppi_problem prob;
   DevParams dp;
   int device = 0;
+  int n_sms = 152;
   int nx = 0, nu = 0;
   int warps = 4, ilp = 1, wps = 1;  // warps per block, rollouts interleaved, warps per sample
   int n_obs_host = 0;                // obstacle count of the last set_obstacles
@@ -74,6 +77,10 @@ bool fault(const char* what) {
   const char* f = std::getenv("RAMPPI_FAULT");
   return f != nullptr && std::strcmp(f, what) == 0;
 }
+
+#define RA_DEVICE_SCOPE(h)                                                   \
+  DeviceScope device_scope_((h)->device);                                    \
+  if (!device_scope_.ok()) return fail((h), RA_MPPI_ECUDA, "cannot make the handle's device current")
 
 int model_nx(int model) { return model == RA_MPPI_KIN_BICYCLE ? 4 : model == RA_MPPI_DYN_SINGLE_TRACK ? 6 : 1; }
 int model_nu(int model) { return model == RA_MPPI_LINEAR_TEST ? 1 : 2; }
@@ -338,15 +345,28 @@ extern "C" {
 
 int32_t ra_mppi_problem_size(void) { return (int32_t)sizeof(ra_mppi_problem); }
 
-int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
+int ra_mppi_create(const ra_mppi_problem* p, int32_t device, ra_mppi_t** out) {
   if (p == nullptr || out == nullptr) return RA_MPPI_EINVAL;
   const std::string why = validate(*p);
   if (!why.empty()) {
     std::fprintf(stderr, "ra_mppi_create: %s\n", why.c_str());
     return RA_MPPI_EINVAL;
   }
+  if (fault("alloc")) return RA_MPPI_ENOMEM;
+  int dev = 0;
+  {
+    cudaError_t e0 = cudaSuccess;
+    if (!ramppi_api::resolve_device(device, &dev, &e0)) {
+      if (e0 == cudaSuccess) return RA_MPPI_EINVAL;
+      std::fprintf(stderr, "ra_mppi_create: %s\n", cudaGetErrorString(e0));
+      return RA_MPPI_ECUDA;
+    }
+  }
+  DeviceScope scope(dev);
+  if (!scope.ok()) return RA_MPPI_ECUDA;
   ra_mppi* h = new (std::nothrow) ra_mppi();
   if (h == nullptr) return RA_MPPI_ENOMEM;
+  h->device = dev;
   h->prob = *p;
   h->dp = make_params(*p);
   h->nx = model_nx(p->model);
@@ -356,17 +376,18 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
   h->warps = 4;
   // few samples with many rollouts: spread a sample over several warps until
   // the sample warps fill the GPU (24 resident warps per SM at 80 registers,
-  // 152 SMs).  The dynamic model's long rollouts gain from two waves, so the
-  // last partial wave is short (config 2, K = 4096, M = 128: 2 warps per
-  // sample 0.845 ms, 1 warp 0.893); the cheaper kinematic rollouts from one.
+  // times the device's SM count).  The dynamic model's long rollouts gain from
+  // two waves, so the last partial wave is short (config 2, K = 4096,
+  // M = 128: 2 warps per sample 0.845 ms, 1 warp 0.893); the cheaper
+  // kinematic rollouts from one.
+  cudaError_t e = cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, dev);
   {
     const int R = (p->M + 31) / 32;
     const long long waves = p->model == RA_MPPI_DYN_SINGLE_TRACK ? 2 : 1;
     int g = 1;
-    while (g < 4 && (long long)p->K * g < waves * 152 * 24 && R >= 2 * g) g *= 2;
+    while (g < 4 && (long long)p->K * g < waves * h->n_sms * 24 && R >= 2 * g) g *= 2;
     h->wps = g;
   }
-  cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaGetDevice(&h->device);
   const size_t K = (size_t)p->K, TN = (size_t)p->T * h->nu;
   h->nb_upd = ramppi::update_blocks((long long)K);
   if (e == cudaSuccess) e = dalloc(&h->U, K * TN);
@@ -419,12 +440,14 @@ int ra_mppi_create(const ra_mppi_problem* p, ra_mppi_t** out) {
 
 void ra_mppi_destroy(ra_mppi_t* h) {
   if (h == nullptr) return;
+  DeviceScope scope(h->device);
   release(h);
   delete h;
 }
 
 int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* stream) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (n_obs < 0 || n_obs > h->obs_cap) return fail(h, RA_MPPI_EINVAL, "n_obs exceeds max_obstacles");
   if (n_obs > 0 && xyr == nullptr) return fail(h, RA_MPPI_EINVAL, "xyr is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -480,6 +503,7 @@ int ra_mppi_set_obstacles(ra_mppi_t* h, const float* xyr, int32_t n_obs, void* s
 int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out, float* S_tilde, float* cvar,
                  void* stream) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (x0 == nullptr || V_in == nullptr || V_out == nullptr) return fail(h, RA_MPPI_EINVAL, "x0, V_in and V_out are required");
   if (fault("launch")) return fail(h, RA_MPPI_ECUDA, "injected launch failure");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -540,6 +564,7 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
 int ra_mppi_step_host(ra_mppi_t* h, const float* x0_host, const float* V_in_host, float* V_out_host,
                       float* S_tilde_host, void* stream) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (x0_host == nullptr || V_in_host == nullptr || V_out_host == nullptr)
     return fail(h, RA_MPPI_EINVAL, "x0, V_in and V_out are required");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -560,6 +585,7 @@ int ra_mppi_step_host(ra_mppi_t* h, const float* x0_host, const float* V_in_host
 int ra_mppi_closed_loop_step(ra_mppi_t* h, float* x, float* V, float* S_tilde, int32_t* collisions,
                              int32_t shift, void* stream) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (x == nullptr || V == nullptr) return fail(h, RA_MPPI_EINVAL, "x and V are required");
   const int rc = ra_mppi_step(h, x, V, h->V_plus, S_tilde, nullptr, stream);
   if (rc != RA_MPPI_OK) return rc;
@@ -580,6 +606,7 @@ int ra_mppi_workspace(ra_mppi_t* h, const float** U, const float** S, const floa
 
 int ra_mppi_copy_workspace(ra_mppi_t* h, float* U, float* S, float* cvar, float* L, void* stream) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (L != nullptr && h->L == nullptr) return fail(h, RA_MPPI_EINVAL, "risk costs were not kept");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t K = (size_t)h->prob.K;
@@ -594,6 +621,7 @@ int ra_mppi_copy_workspace(ra_mppi_t* h, float* U, float* S, float* cvar, float*
 
 int ra_mppi_copy_weights(ra_mppi_t* h, float* W, void* stream) {
   if (h == nullptr || W == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (h->L == nullptr || !importance(h))
     return fail(h, RA_MPPI_EINVAL, "weights are kept only with RA_MPPI_KEEP_RISK_COSTS and importance sampling");
   const size_t KM = (size_t)h->prob.K * h->prob.M;
@@ -603,27 +631,30 @@ int ra_mppi_copy_weights(ra_mppi_t* h, float* W, void* stream) {
   return RA_MPPI_OK;
 }
 
-int ra_mppi_get_iteration(ra_mppi_t* h, uint64_t* iteration) {
+int ra_mppi_get_state(ra_mppi_t* h, uint64_t* iteration) {
   if (h == nullptr || iteration == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   unsigned long long it = 0;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&it, &h->st->iteration, sizeof(it), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(h, e, "get_iteration");
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
   *iteration = it;
   return RA_MPPI_OK;
 }
 
-int ra_mppi_set_iteration(ra_mppi_t* h, uint64_t iteration) {
+int ra_mppi_set_state(ra_mppi_t* h, uint64_t iteration) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   const unsigned long long it = iteration;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&h->st->iteration, &it, sizeof(it), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(h, e, "set_iteration");
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
   return RA_MPPI_OK;
 }
 
 int ra_mppi_get_status(ra_mppi_t* h) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   int status = 0;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&status, &h->st->status, sizeof(int), cudaMemcpyDeviceToHost);
@@ -636,6 +667,7 @@ const char* ra_mppi_last_error(const ra_mppi_t* h) { return h == nullptr ? "null
 
 int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32_t warps_per_sample) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   const int w = warps_per_block == 0 ? h->warps : warps_per_block;
   const int i = ilp == 0 ? h->ilp : ilp;
   const int g = warps_per_sample == 0 ? h->wps : warps_per_sample;
@@ -661,6 +693,7 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32
 
 int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays, float* best_ms) {
   if (h == nullptr || x0 == nullptr || V == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (replays < 1) replays = 3;
   unsigned long long saved_it = 0;
   cudaError_t e = cudaDeviceSynchronize();
@@ -744,6 +777,7 @@ int ra_mppi_set_cost_weights(ra_mppi_t* h, const float* theta) {
 int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, float* gV, float* gtheta,
                      void* stream) {
   if (h == nullptr) return RA_MPPI_EINVAL;
+  RA_DEVICE_SCOPE(h);
   if (gV_plus == nullptr || gV == nullptr || gtheta == nullptr)
     return fail(h, RA_MPPI_EINVAL, "gV_plus, gV and gtheta are required");
   if (h->keep_x0 == nullptr) return fail(h, RA_MPPI_EINVAL, "the problem was created without RA_MPPI_DIFFERENTIABLE");

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "ra_host.h"
 #include "ra_kernels.h"
 #include "ra_mppi.h"
 
@@ -30,6 +31,7 @@ bool obstacle_in_extent(float x, float y, float r);
 struct ra_mppi_batch {
   ra_mppi_problem common;
   DevParams dp;
+  int device = 0;
   int B = 0, nx = 0, nu = 0;
   std::vector<InstDesc> desc_h;
   InstDesc* desc = nullptr;
@@ -66,6 +68,10 @@ int bfail(ra_mppi_batch* b, int code, const std::string& msg) {
 int bcuda(ra_mppi_batch* b, cudaError_t e, const char* where) {
   return bfail(b, RA_MPPI_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+#define RA_BATCH_DEVICE_SCOPE(b)                            \
+  ramppi_api::DeviceScope device_scope_((b)->device);       \
+  if (!device_scope_.ok()) return bfail((b), RA_MPPI_ECUDA, "cannot make the handle's device current")
 
 template <typename T>
 cudaError_t balloc(T** p, long long n) {
@@ -207,7 +213,7 @@ cudaError_t capture(ra_mppi_batch* b) {
 
 extern "C" {
 
-int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* inst, int32_t B,
+int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* inst, int32_t B, int32_t device,
                          ra_mppi_batch_t** out) {
   if (common == nullptr || inst == nullptr || out == nullptr || B < 1 || B > 65536) return RA_MPPI_EINVAL;
   // every problem must be valid as a single problem
@@ -223,8 +229,20 @@ int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* 
       return RA_MPPI_EINVAL;
     }
   }
+  int dev = 0;
+  {
+    cudaError_t e0 = cudaSuccess;
+    if (!ramppi_api::resolve_device(device, &dev, &e0)) {
+      if (e0 == cudaSuccess) return RA_MPPI_EINVAL;
+      std::fprintf(stderr, "ra_mppi_batch_create: %s\n", cudaGetErrorString(e0));
+      return RA_MPPI_ECUDA;
+    }
+  }
+  ramppi_api::DeviceScope scope(dev);
+  if (!scope.ok()) return RA_MPPI_ECUDA;
   ra_mppi_batch* b = new (std::nothrow) ra_mppi_batch();
   if (b == nullptr) return RA_MPPI_ENOMEM;
+  b->device = dev;
   b->common = *common;
   b->dp = ramppi_api::make_params(*common);
   b->is = common->is_scale != 1.0f && common->is_frac > 0.0f;
@@ -305,9 +323,7 @@ int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* 
   seg_base[2 * B] = items;
   b->n_items = items;
 
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = balloc(&b->desc, B);
   if (e == cudaSuccess) e = balloc(&b->st, B);
   if (e == cudaSuccess) e = balloc(&b->x0, b->n_x0);
@@ -350,6 +366,7 @@ int ra_mppi_batch_create(const ra_mppi_problem* common, const ra_mppi_instance* 
 
 void ra_mppi_batch_destroy(ra_mppi_batch_t* b) {
   if (b == nullptr) return;
+  ramppi_api::DeviceScope scope(b->device);
   release(b);
   delete b;
 }
@@ -375,8 +392,16 @@ int ra_mppi_batch_buffers(ra_mppi_batch_t* b, float** x0, float** V, float** V_o
   return RA_MPPI_OK;
 }
 
+int ra_mppi_batch_io(ra_mppi_batch_t* b, float** x0_packed, float** V_packed, int64_t* offsets) {
+  if (b == nullptr) return RA_MPPI_EINVAL;
+  if (x0_packed) *x0_packed = b->x0;
+  if (V_packed) *V_packed = b->V;
+  return offsets != nullptr ? ra_mppi_batch_layout(b, offsets) : RA_MPPI_OK;
+}
+
 int ra_mppi_batch_set_obstacles(ra_mppi_batch_t* b, int32_t i, const float* xyr, int32_t n_obs, void* stream) {
   if (b == nullptr || i < 0 || i >= b->B) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   const InstDesc& q = b->desc_h[i];
   if (n_obs < 0 || n_obs > q.obs_cap) return bfail(b, RA_MPPI_EINVAL, "n_obs exceeds the problem's max_obstacles");
   if (n_obs > 0 && xyr == nullptr) return bfail(b, RA_MPPI_EINVAL, "xyr is NULL");
@@ -406,6 +431,7 @@ int ra_mppi_batch_set_obstacles(ra_mppi_batch_t* b, int32_t i, const float* xyr,
 
 int ra_mppi_batch_write_inputs(ra_mppi_batch_t* b, const float* x0, const float* V, void* stream) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (x0) e = cudaMemcpyAsync(b->x0, x0, sizeof(float) * b->n_x0, cudaMemcpyDefault, s);
@@ -416,6 +442,7 @@ int ra_mppi_batch_write_inputs(ra_mppi_batch_t* b, const float* x0, const float*
 
 int ra_mppi_batch_read_outputs(ra_mppi_batch_t* b, float* V_out, float* S_tilde, void* stream) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (V_out) e = cudaMemcpyAsync(V_out, b->V_out, sizeof(float) * b->n_V, cudaMemcpyDefault, s);
@@ -427,6 +454,7 @@ int ra_mppi_batch_read_outputs(ra_mppi_batch_t* b, float* V_out, float* S_tilde,
 
 int ra_mppi_step_batched(ra_mppi_batch_t* b, void* stream) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   const cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return bcuda(b, e, "graph launch");
   return RA_MPPI_OK;
@@ -434,6 +462,7 @@ int ra_mppi_step_batched(ra_mppi_batch_t* b, void* stream) {
 
 int ra_mppi_step_batched_eager(ra_mppi_batch_t* b, void* stream) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   const cudaError_t e = enqueue(b, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return bcuda(b, e, "batched launch");
   return RA_MPPI_OK;
@@ -441,6 +470,7 @@ int ra_mppi_step_batched_eager(ra_mppi_batch_t* b, void* stream) {
 
 int ra_mppi_batch_copy_workspace(ra_mppi_batch_t* b, float* U, float* S, float* cvar, void* stream) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (U) e = cudaMemcpyAsync(U, b->U, sizeof(float) * b->n_U, cudaMemcpyDefault, s);
@@ -452,6 +482,7 @@ int ra_mppi_batch_copy_workspace(ra_mppi_batch_t* b, float* U, float* S, float* 
 
 int ra_mppi_batch_set_iteration(ra_mppi_batch_t* b, uint64_t iteration) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   cudaError_t e = cudaDeviceSynchronize();
   const unsigned long long it = iteration;
   for (int i = 0; e == cudaSuccess && i < b->B; ++i)
@@ -462,6 +493,7 @@ int ra_mppi_batch_set_iteration(ra_mppi_batch_t* b, uint64_t iteration) {
 
 int ra_mppi_batch_get_status(ra_mppi_batch_t* b) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   std::vector<DevState> st(b->B);
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(st.data(), b->st, sizeof(DevState) * b->B, cudaMemcpyDeviceToHost);
@@ -477,6 +509,7 @@ int ra_mppi_batch_get_status(ra_mppi_batch_t* b) {
 
 int ra_mppi_batch_set_launch(ra_mppi_batch_t* b, int32_t warps_per_block, int32_t ilp) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   if (warps_per_block < 1 || warps_per_block > 8) return bfail(b, RA_MPPI_EINVAL, "warps_per_block in [1, 8]");
   if (ilp != 1 && ilp != 2) return bfail(b, RA_MPPI_EINVAL, "ilp must be 1 or 2");
   const int ow = b->warps, oi = b->ilp;
@@ -504,6 +537,7 @@ int ra_mppi_batch_get_launch(ra_mppi_batch_t* b, int32_t* warps_per_block, int32
 
 int ra_mppi_batch_tune(ra_mppi_batch_t* b, int32_t replays, float* best_ms) {
   if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
   if (replays < 1) replays = 3;
   // the tuner advances the update counters; put them back afterwards
   std::vector<DevState> saved(b->B);

@@ -10,6 +10,15 @@ Tolerances (stage-wise protocol):
                         obstacle indicator may flip under float32 position drift
   CVaR on identical L   rel 1e-5 (float32 tail sums of at most 256 terms)
   V+ from the GPU's S~, U   abs 1e-5
+  end-to-end V+ (the GPU's V+ against the oracle's own V+, when the oracle
+                        ran every sample): reported with the softmin's
+                        amplification bound and checked against it.  With
+                        D = max_k |S~_gpu - S~_oracle| every weight ratio
+                        w'_k / w_k lies in [exp(-2D/lambda), exp(2D/lambda)]
+                        (Eqs. 5, 17), so |dV+| <= (exp(2D/lambda) - 1)
+                        max_k ||U_k - V+||_inf + max |dU| + 1e-5 (rounding of
+                        the update); to first order 2 D / lambda max_k ||U_k -
+                        V+||_inf, the form the scope gives.
 """
 
 import numpy as np
@@ -46,6 +55,37 @@ def check_banded(name, gpu, ref, lo, hi, rtol=RTOL, floor=None):
     return int(np.sum(banded & ~close))
 
 
+def vplus_bound(p, g, ref):
+    """(deviation, bound, first-order bound, D) of the GPU's end-to-end V+
+    against the oracle's own V+, from the oracle's per-sample results over
+    every sample (ref["ks"] must be 0..K-1)."""
+    K = int(p["K"])
+    assert len(ref["ks"]) == K and np.array_equal(ref["ks"], np.arange(K))
+    lam = float(np.float32(p["lam"]))
+    Vo, _ = oracle.update(ref["S_tilde"], ref["U"], lam)
+    dev = float(np.max(np.abs(g["V_plus"].astype(np.float64) - Vo)))
+    sg = g["S_tilde"].astype(np.float64)
+    so = np.asarray(ref["S_tilde"], np.float64)
+    both = np.isfinite(sg) & np.isfinite(so)
+    assert np.array_equal(np.isfinite(sg), np.isfinite(so)), "finite S~ differ between GPU and oracle"
+    D = float(np.max(np.abs(sg[both] - so[both]))) if both.any() else 0.0
+    spread = float(np.max(np.abs(np.asarray(ref["U"], np.float64) - Vo[None]))) if K else 0.0
+    dU = float(np.max(np.abs(g["U"].astype(np.float64) - ref["U"])))
+    with np.errstate(over="ignore"):
+        bound = float(np.expm1(2.0 * D / lam)) * spread + dU + 1e-5
+    first = 2.0 * D / lam * spread
+    return dev, bound, first, D
+
+
+def check_vplus_bound(name, p, g, ref):
+    dev, bound, first, D = vplus_bound(p, g, ref)
+    print(f"{name}: end-to-end |V+_gpu - V+_oracle| = {dev:.3e}, bound {bound:.3e} "
+          f"(first order 2 D/lambda max||U - V+|| = {first:.3e}, D = max|dS~| = {D:.3e}, "
+          f"ratio {dev / bound if bound > 0 else 0.0:.3f})")
+    assert dev <= bound, (name, dev, bound)
+    return dev, bound
+
+
 def compare(p, g, ref, check_update=True):
     ks = ref["ks"]
     # 1. sampled controls
@@ -79,4 +119,7 @@ def compare(p, g, ref, check_update=True):
         Vo, _ = oracle.update(g["S_tilde"].astype(np.float64), g["U"].astype(np.float64),
                               float(np.float32(p["lam"])))
         np.testing.assert_allclose(g["V_plus"], Vo, atol=1e-5, rtol=0)
+        # 5. end to end, when the oracle ran every sample
+        if len(ks) == int(p["K"]) and np.array_equal(ks, np.arange(int(p["K"]))):
+            check_vplus_bound(f"K={p['K']} M={p['M']} T={p['T']}", p, g, ref)
     return nS, nC, nT

@@ -44,6 +44,27 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+# The boundary's calls as the hot-path scope names them: create with a
+# device, set obstacles, the single and batched steps, the batch's
+# library-owned inputs, the adjoint, the status word, resumable state and
+# the error text.  Extra entry points (host-buffer step, closed loop,
+# workspace views, tuning, the allocation-free update) sit beside them.
+BOUNDARY = ("ra_mppi_create", "ra_mppi_set_obstacles", "ra_mppi_step", "ra_mppi_batch_create",
+            "ra_mppi_batch_io", "ra_mppi_step_batched", "ra_mppi_backward", "ra_mppi_get_status",
+            "ra_mppi_get_state", "ra_mppi_set_state", "ra_mppi_last_error", "ra_mppi_destroy",
+            "ra_mppi_batch_destroy")
+
+
+def test_header_declares_the_scoped_boundary():
+    names = _declared_functions()
+    missing = [n for n in BOUNDARY if n not in names]
+    assert not missing, missing
+    text = open(os.path.join(ROOT, "include", "ra_mppi.h")).read()
+    # create and batch_create take the device they bind the handle to
+    assert re.search(r"int ra_mppi_create\(const ra_mppi_problem\* p, int32_t device, ra_mppi_t\*\* out\)", text)
+    assert re.search(r"int ra_mppi_batch_create\([^)]*int32_t B, int32_t device,", text)
+
+
 def test_library_exports_every_declared_symbol(pkg):
     lib = ctypes.CDLL(pkg.binding.LIB_PATH)
     missing = [n for n in _declared_functions() if not hasattr(lib, n)]
@@ -96,7 +117,7 @@ def test_batched_path_validates_importance_sampling(pkg):
 
 def test_null_arguments(pkg):
     L = pkg.lib()
-    assert L.ra_mppi_create(None, None) == pkg.binding.RA_MPPI_EINVAL
+    assert L.ra_mppi_create(None, -1, None) == pkg.binding.RA_MPPI_EINVAL
     assert L.ra_mppi_step(None, None, None, None, None, None, None) == pkg.binding.RA_MPPI_EINVAL
     L.ra_mppi_destroy(None)
     assert L.ra_mppi_last_error(None) == b"null handle"

@@ -68,6 +68,36 @@ def test_adjoint_matches_oracle_small(case):
     _close("gtheta", gth, rth)
 
 
+@pytest.mark.parametrize("M,alpha", [(64, 0.8), (128, 0.9), (32, 0.5)])
+def test_adjoint_tail_lane_groups(M, alpha):
+    """The disturbed reverse sweep gives each rollout of a short CVaR tail a
+    group of lanes: four lanes for at most 8 rollouts with a nonzero
+    cotangent, two for 9 to 16, one above.  Without ties at VaR, M = 64 at
+    alpha = 0.8 and M = 128 at alpha = 0.9 leave 13 tail rollouts (two lanes
+    each) and M = 32 at alpha = 0.5 leaves 16 or 17; each against the
+    oracle's adjoint, and two passes of the backward give the same bits."""
+    from paper_2209_12842_gb300 import RaMppi
+
+    p = rs.preset("c4_gradient", K=96, M=M, T=12, alpha=alpha)
+    obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4)
+    x0 = np.array([0.0, -4.0, 0.0, 1.0], np.float32)
+    V = rs.random_controls(0, p["T"], p["u_lo"], p["u_hi"], 3)
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    ctl = RaMppi(p, obs, differentiable=True)
+    ctl.iteration = 0
+    ctl.step(torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda())
+    gVp_t, gS_t = torch.from_numpy(gVp).cuda(), torch.from_numpy(gS).cuda()
+    gV1, gth1 = ctl.backward(gVp_t, gS_t)
+    gV2, gth2 = ctl.backward(gVp_t, gS_t)
+    torch.cuda.synchronize()
+    assert ctl.status() == 0
+    ctl.close()
+    assert torch.equal(gV1, gV2) and torch.equal(gth1, gth2)
+    rV, rth = oracle.backward(p, x0, V, obs, gVp, gS)
+    _close("gV", gV1.cpu().numpy(), rV)
+    _close("gtheta", gth1.cpu().numpy(), rth)
+
+
 @pytest.mark.parametrize("n_obs", [0, 1, 3, 4, 5, 7, 13])
 def test_adjoint_obstacle_counts(n_obs):
     # the softplus gradient's obstacle loop is unrolled four times: counts

@@ -144,8 +144,12 @@ def test_replays_advance_the_counters():
 
 def test_uneven_batch_workload_sampled():
     """The batched workload's size mix (B = 256, K 512..8192, M 16..256,
-    T 20..60, 5..60 obstacles), checked on four problems against separate
-    handles (bitwise) and one against the oracle."""
+    T 20..60, 5..60 obstacles): four problems bitwise against separate
+    handles, and eight against the oracle stage by stage, among them the
+    largest-K problem with M = 256 (every sample of the smallest one, which
+    also gives the end-to-end V+ against the oracle's own update)."""
+    import os
+
     from paper_2209_12842_gb300.controller import RaMppiBatch
 
     insts = rs.batched_instances(256)
@@ -169,10 +173,22 @@ def test_uneven_batch_workload_sampled():
         q, g = _single(p, insts[i], obs[i], x0s[i], Vs[i], 0)
         for key in ("U", "S", "cvar", "S_tilde", "V_plus"):
             np.testing.assert_array_equal(res[i][key], g[key], err_msg=f"problem {i} {key}")
-    i = 17
-    d = insts[i]
-    q = dict(p, K=d["K"], M=d["M"], T=d["T"], seed=d["seed"], instance_id=d["instance_id"])
-    ks = np.array([0, d["K"] // 2, d["K"] - 1], np.int32)
-    ref = oracle.samples(q, x0s[i], Vs[i], obs[i], ks=ks, n_threads=8)
-    compare(q, dict(res[i], L=None), ref, check_update=True)
+    big = max((i for i, d in enumerate(insts) if d["M"] == 256), key=lambda i: insts[i]["K"])
+    assert insts[big]["K"] >= 6000
+    small = min(range(len(insts)), key=lambda i: insts[i]["K"] * insts[i]["M"] * insts[i]["T"])
+    rng = np.random.default_rng(3)
+    others = [int(i) for i in rng.choice([i for i in range(len(insts)) if i not in (big, small)], 6,
+                                         replace=False)]
+    threads = os.cpu_count() or 8
+    for i in [big, small] + others:
+        d = insts[i]
+        q = dict(p, K=d["K"], M=d["M"], T=d["T"], seed=d["seed"], instance_id=d["instance_id"])
+        if i == small:
+            ks = None
+        else:
+            ks = np.unique(np.concatenate([[0, d["K"] // 2, d["K"] - 1], rng.integers(0, d["K"], 5)])).astype(np.int32)
+        ref = oracle.samples(q, x0s[i], Vs[i], obs[i], ks=ks, n_threads=threads)
+        compare(q, dict(res[i], L=None), ref, check_update=True)
+        print(f"batched problem {i}: K={d['K']} M={d['M']} T={d['T']} obstacles {d['n_obs']}, "
+              f"{len(ref['ks'])} samples against the oracle")
     batch.close()

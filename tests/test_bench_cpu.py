@@ -20,19 +20,41 @@ def test_formula_count_is_consistent():
 
     for name in ("c1_plain", "c2_closed_loop", "c5_stress", "c4_gradient", "paper_sim", "linear_test"):
         p = rs.preset(name)
-        d_bf, n_bf = bench.algorithmic_ops(p)
-        d0, n0 = bench.algorithmic_ops(p, tested_obstacles=0.0)
-        assert d_bf > 0 and n_bf > 0
-        # culling only removes indicator obstacle tests (6 per tested obstacle)
-        if int(p["obs_mode"]) == 0:
-            assert d_bf - d0 == pytest.approx(6 * int(p["n_obs"]))
+        d_bf, n_bf = bench.pipe_counts(p)
+        d0, n0 = bench.pipe_counts(p, tested=0.0)
+        for pipe in ("fp32", "xu", "int", "issue"):
+            assert d_bf[pipe] >= 0 and n_bf[pipe] > 0
+        # culling only removes indicator obstacle tests (6 fp32 per tested obstacle)
+        if int(p["obs_mode"]) == 0 and int(p["risk_mask"]) & 4 and int(p["model"]) != 2:
+            assert d_bf["fp32"] - d0["fp32"] == pytest.approx(6 * int(p["n_obs"]))
         else:
             assert d_bf == d0
         assert n0 == n_bf
-    # the dynamic model's six Heun sub-steps dominate its count
-    dyn, _ = bench.algorithmic_ops(rs.preset("c2_closed_loop"), tested_obstacles=0.0)
-    kin, _ = bench.algorithmic_ops(rs.preset("c1_plain"), tested_obstacles=0.0)
-    assert dyn > 4 * kin
+    # the dynamic model's six Heun sub-steps dominate its count: 6 x (2 derivatives
+    # of 56 fp32 + 7 special-function ops, + 18 for the trapezoid)
+    dyn, _ = bench.pipe_counts(rs.preset("c2_closed_loop"), tested=0.0)
+    kin, _ = bench.pipe_counts(rs.preset("c1_plain"), tested=0.0)
+    assert dyn["fp32"] > 4 * kin["fp32"]
+    assert bench._dyn_substep() == {"fp32": 130, "xu": 14, "int": 0}
+    # paired FP32 halves the dynamics' share of the issue count only
+    d1, _ = bench.pipe_counts(rs.preset("c5_stress"), tested=3.0, ilp=2, paired=False)
+    d2, _ = bench.pipe_counts(rs.preset("c5_stress"), tested=3.0, ilp=2, paired=True)
+    assert d1["fp32"] == d2["fp32"] and d1["issue"] - d2["issue"] == pytest.approx(6 * 130 / 2)
+
+
+def test_pipe_roofline_picks_the_binding_pipe():
+    import bench
+
+    p = rs.preset("c5_stress")
+    units = p["K"] * p["M"] * p["T"]
+    rates = {"fp32": 128.0, "xu": 32.0, "issue": 128.0}
+    bound, pipes = bench.pipe_roofline(p, units, 0.030, 3.0, 2, True, rates, 152, 2070.0)
+    assert bound == max(("fp32", "xu", "issue"), key=lambda k: pipes[k]["frac"])
+    for k in ("fp32", "xu", "issue"):
+        assert pipes[k]["frac"] == pytest.approx(pipes[k]["achieved"] / pipes[k]["peak"])
+    # twice the time, half of every fraction
+    _, slow = bench.pipe_roofline(p, units, 0.060, 3.0, 2, True, rates, 152, 2070.0)
+    assert slow["fp32"]["frac"] == pytest.approx(pipes["fp32"]["frac"] / 2)
 
 
 def test_traffic_record_needs_matching_sources(monkeypatch):

@@ -10,6 +10,8 @@ Sizes: small cases spanning several blocks with ragged tails, config 1 in
 full, and configs 2 and 5 at full size on sampled samples k.
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -89,34 +91,72 @@ def test_config1_full():
         print(f"config 1 ({obs_kind}): banded S {nS}, CVaR {nC}, S~ {nT} of {p['K']}")
 
 
-def test_config2_full_size_sampled():
+def test_config2_full_size():
+    """Config 2 at full size: per-sample parity on 32 sampled k, and the
+    end-to-end V+ against the oracle's own update over all 4096 samples."""
     p = rs.preset("c2_closed_loop")
     obs, x0, V = _inputs(p, "ahead")
     g = run_gpu(p, obs, x0, V)
     K = p["K"]
     ks = np.unique(np.concatenate([[0, 1, K // 2, K - 2, K - 1],
                                    np.random.default_rng(0).integers(0, K, 27)])).astype(np.int32)
-    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=8)
+    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=os.cpu_count() or 8)
     compare(p, g, ref)
-    # the default scene (obstacles spread over the track) as well
+    # the default scene (obstacles spread over the track), every sample
     obs2, _, _ = _inputs(p, "track")
     g2 = run_gpu(p, obs2, x0, V, keep_L=False)
-    ref2 = oracle.samples(p, x0, V, obs2, ks=ks[:12], n_threads=8)
-    compare(p, g2, ref2)
+    ref2 = oracle.samples(p, x0, V, obs2, n_threads=os.cpu_count() or 8)
+    nS, nC, nT = compare(p, g2, ref2)
+    print(f"config 2 (track scene, all {K} samples): banded S {nS}, CVaR {nC}, S~ {nT}")
+
+
+def _tuned_ctl(p, obs, x0, V):
+    from paper_2209_12842_gb300 import RaMppi
+
+    ctl = RaMppi(p, obs)
+    x0t = torch.from_numpy(np.asarray(x0, np.float32)).cuda()
+    Vt = torch.from_numpy(np.asarray(V, np.float32)).cuda()
+    ctl.tune(x0t, Vt, 1)
+    return ctl, x0t, Vt
 
 
 @pytest.mark.parametrize("M,alpha", [(32, 0.8), (256, 0.95)])
 def test_config5_full_size_sampled(M, alpha):
+    """Config 5 at full size in the launch shape the tuner picks (the one the
+    benchmark times): 64 sampled k spread over every wave of that launch,
+    with 16 of them in the last (partial) wave."""
     p = rs.preset("c5_stress", M=M, alpha=alpha)
     obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
     obs = np.concatenate([obs, rs.obstacles_ahead(5, 6, 0.2, 0.5, x_from=0.1, x_to=1.5)])[: p["n_obs"]]
     x0 = rs.initial_state(p["model"])
     V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 9)
-    g = run_gpu(p, obs, x0, V, keep_L=False)
+    ctl, x0t, Vt = _tuned_ctl(p, obs, x0, V)
+    warps, ilp, wps = ctl.get_launch()
+    ctl.iteration = 0
+    Vp = ctl.step(x0t, Vt)
+    ws = ctl.workspace()
+    torch.cuda.synchronize()
+    g = dict(V_plus=Vp.cpu().numpy(), S_tilde=ctl.S_tilde.cpu().numpy(), cvar=ctl.cvar.cpu().numpy(),
+             U=ws["U"].cpu().numpy(), S=ws["S"].cpu().numpy(), L=None)
+    assert ctl.status() == 0
+    ctl.close()
     K = p["K"]
-    ks = np.array([0, 777, 40000, K - 1], dtype=np.int32)
-    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=8)
-    compare(p, g, ref)
+    # samples per wave: resident warps of the GPU (24 per SM at the kernel's
+    # 80 registers) over warps per sample, two samples per warp when paired
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_wave = n_sms * 24 // wps * (2 if (M <= 32 and ilp == 2 and wps == 1) else 1)
+    waves = -(-K // per_wave)
+    rng = np.random.default_rng(M)
+    ks = [int(rng.integers(w * per_wave, min(K, (w + 1) * per_wave))) for w in range(waves)]
+    ks += list(np.linspace(0, K - 1, max(0, 48 - len(ks))).astype(int))
+    last = (waves - 1) * per_wave
+    ks += list(rng.integers(last, K, 15)) + [K - 1]
+    ks = np.unique(np.asarray(ks, np.int32))
+    assert len(ks) >= 60
+    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=os.cpu_count() or 8)
+    nS, nC, nT = compare(p, g, ref)
+    print(f"config 5 M={M}: launch {warps, ilp, wps}, {waves} waves of {per_wave} samples, "
+          f"{len(ks)} sampled k ({int(np.sum(ks >= last))} in the last wave); banded S {nS}, CVaR {nC}, S~ {nT}")
 
 
 @pytest.mark.parametrize("K,M,T", [(1, 1, 1), (1, 32, 5), (3, 16, 4), (70, 33, 6), (129, 64, 3),
