@@ -49,8 +49,10 @@ LANES_PER_SM = 128
 #   fp32  FP32 add, multiply, FMA, min/max, compare-select, rounding;
 #   xu    special-function unit: every rsqrt, rcp, sin, cos, log, exp, sqrt,
 #         tan the kernel calls (a math-library call counts as one operation,
-#         whatever it expands to), and every int <-> float conversion;
-#   int   32-bit integer and logic operations, warp votes and reductions;
+#         whatever it expands to);
+#   int   32-bit integer and logic operations, int <-> float conversions
+#         (64 per SM per clock on GB300, not the special-function rate), warp
+#         votes and reductions;
 #   issue warp instructions x 32 of the three, where the dynamic model's
 #         FP32 arithmetic counts half when the launch steps rollouts in
 #         paired FP32 instructions (loads, moves and branches are not
@@ -80,13 +82,13 @@ def _noise(p):
     """Process noise of one rollout-step (add_process_noise)."""
     model, nt = int(p["model"]), int(p["noise_type"])
     slots = {0: 4, 1: 3, 2: 1}[model]
-    if nt == 1:  # mixture: two Philox calls; per slot mix_value
-        return dict(fp32=14 * slots, xu=5 * slots, int=2 * PHILOX_INT + 4 * slots)
-    if nt == 0:  # Gaussian: one Philox call, ceil(slots / 2) Box-Muller pairs
+    if nt == 1:  # mixture: two Philox calls; per slot mix_value (log, rsqrt, cos, 2 conversions)
+        return dict(fp32=14 * slots, xu=3 * slots, int=2 * PHILOX_INT + 6 * slots)
+    if nt == 0:  # Gaussian: one Philox call, ceil(slots / 2) Box-Muller pairs (log, rsqrt, sin, cos)
         bm = (slots + 1) // 2
-        return dict(fp32=9 * bm + slots, xu=6 * bm, int=PHILOX_INT)
-    if nt == 2:  # uniform
-        return dict(fp32=2 * slots, xu=slots, int=PHILOX_INT)
+        return dict(fp32=9 * bm + slots, xu=4 * bm, int=PHILOX_INT + 2 * bm)
+    if nt == 2:  # uniform: one conversion per slot
+        return dict(fp32=2 * slots, xu=0, int=PHILOX_INT + slots)
     return dict(fp32=slots + 2, xu=0, int=PHILOX_INT + 2)  # impulse (mostly no jump)
 
 
@@ -130,12 +132,12 @@ def pipe_counts(p, tested=None, ilp=1, paired=False):
     fp32_instr = d["fp32"] - (dyn_fp32 / 2 if paired and model == 1 else 0)
     d["issue"] = fp32_instr + d["xu"] + d["int"]
     # nominal step: control draw (Philox, accurate Box-Muller, clip: 11 fp32,
-    # log + sqrt + sin + cos + 2 conversions), the per-step control
+    # log + sqrt + sin + cos, 2 conversions), the per-step control
     # quantities, the dynamics, the full running cost (track 6 fp32 + sqrt,
     # deviation, speed, every obstacle) and the control cost
     n = dict(fp32=11 + step["fp32"] + 6 + 2 + 3 + (6 * n_obs if ind else 10 * n_obs) + 3 + 2,
-             xu=6 + (2 if model == 1 else 2) + step["xu"] + 1 + (0 if ind else 3 * n_obs),
-             int=PHILOX_INT + step["int"] + 4)
+             xu=4 + 2 + step["xu"] + 1 + (0 if ind else 3 * n_obs),
+             int=PHILOX_INT + step["int"] + 6)
     n["issue"] = n["fp32"] + n["xu"] + n["int"]
     return d, n
 
@@ -302,8 +304,8 @@ def config_dict(p, args, reference=False):
 # Default per-SM-per-clock lane-operation rates, used when the probes cannot
 # run: 128 FP32 lanes, 4 schedulers x 32 lanes of issue, and the special-
 # function rate the probe measured on GB300 (see measure_pipe_rates).
-DEFAULT_RATES = {"fp32": 128.0, "issue": 128.0, "xu": 32.0}
-PROBE_KINDS = {"ffma": (0, 400000), "ffma2": (1, 200000), "rsqrt": (2, 60000), "rcp": (3, 60000),
+DEFAULT_RATES = {"fp32": 128.0, "issue": 128.0, "xu": 16.0}
+PROBE_KINDS = {"ffma": (0, 400000), "ffma2": (1, 200000), "rsqrt": (2, 60000), "cos": (3, 60000),
                "ex2": (4, 60000), "lg2": (5, 60000), "sin": (6, 60000), "i2f": (7, 60000),
                "imad": (8, 200000)}
 
@@ -330,7 +332,7 @@ def measure_pipe_rates(torch, reps=3):
     clk = clocks.stop()
     mhz = clk.get("sm_mhz") or 2070.0
     per = {k: v / (n_sms * mhz * 1e6) for k, v in raw.items()}
-    xu = float(np.median([per[k] for k in ("rsqrt", "rcp", "ex2", "lg2", "sin")]))
+    xu = float(np.median([per[k] for k in ("rsqrt", "cos", "ex2", "lg2", "sin")]))
     rates = {"fp32": per["ffma"], "issue": DEFAULT_RATES["issue"], "xu": xu}
     return {"per_sm_per_clock": per, "rates_used": rates, "n_sms": n_sms, "clocks": clk,
             "basis": "probe kernels, 8 independent chains per thread, 4 x 256 threads per SM; "

@@ -342,7 +342,7 @@ int ra_mppi_set_timing_events(ra_mppi_t* h, void* rollout_begin, void* rollout_e
  * `iters` iterations of eight independent chains per thread, on 4 blocks of
  * 256 threads per SM of `device` (-1: current), of one instruction kind:
  *   0 FP32 fused multiply-add     1 paired FP32 multiply-add (2 ops each)
- *   2 rsqrt.approx  3 rcp.approx  4 ex2.approx  5 lg2.approx  6 sin.approx
+ *   2 rsqrt.approx  3 cos.approx  4 ex2.approx  5 lg2.approx  6 sin.approx
  *                                 (one special-function unit operation each)
  *   7 32-bit integer to float conversion   8 32-bit integer multiply-add
  * and returns its CUDA-event time *ms and the lane-operations it executed

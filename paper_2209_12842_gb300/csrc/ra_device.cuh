@@ -86,9 +86,14 @@ __device__ __forceinline__ float u01(uint32_t x) {
   return __fmaf_rn(__uint2float_rn(x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
 }
 
-// Box-Muller pair from two words: sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2)
+// Box-Muller pair from two words: sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+// ln u1 is taken from the word itself: for u1 >= 1/2 as log1p(-(1 - u1)),
+// where 1 - u1 = (~a + 1/2) 2^-32 = u01(~a) keeps its full precision (the
+// float32 u1 itself would be rounded to a multiple of 2^-24 next to 1, and
+// the square root would amplify that near rad = 0).
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
-  const float rad = sqrtf(-2.0f * logf(u01(a)));
+  const float lu = (a >> 31) != 0u ? log1pf(-u01(~a)) : logf(u01(a));
+  const float rad = sqrtf(-2.0f * lu);
   float s, c;
   sincospif(2.0f * u01(b), &s, &c);
   return make_float2(__fmul_rn(rad, c), __fmul_rn(rad, s));

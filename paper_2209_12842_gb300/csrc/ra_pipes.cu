@@ -5,7 +5,7 @@
 // operation, an integer-to-float conversion, an integer multiply-add), on
 // enough warps to cover every latency, so its time is set by the throughput
 // of that instruction's pipe.  The special-function operations are written
-// as single PTX instructions (rsqrt, rcp, ex2, lg2, sin, cos approximations),
+// as single PTX instructions (rsqrt, cos, ex2, lg2, sin approximations),
 // so each counts exactly one operation.  Nothing here is part of the
 // RA-MPPI update.
 #include <cuda_runtime.h>
@@ -30,7 +30,7 @@ __device__ __forceinline__ float probe_op(float x) {
   } else if constexpr (KIND == 2) {
     asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   } else if constexpr (KIND == 3) {
-    asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm volatile("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   } else if constexpr (KIND == 4) {
     asm volatile("{ .reg .f32 t; neg.f32 t, %1; ex2.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x));
   } else if constexpr (KIND == 5) {
