@@ -160,6 +160,67 @@ def pipe_roofline(p, units, kernel_s, tested, ilp, paired, rates, n_sms, sm_mhz)
     return bound, out
 
 
+def adjoint_counts(p):
+    """Per-pipe formula counts of the adjoint's main kernel (bwd_main_kernel):
+    per reversed disturbed rollout-step and per reversed nominal step.  A
+    reversed step replays 7 of 8 forward steps from the checkpoints (dynamics
+    and, disturbed, the process noise), then takes the step's transposed
+    Jacobian and the gradient of the cost terms; the softplus barrier's
+    gradient takes per obstacle 12 fp32 and a reciprocal square root, an
+    exponential, a logarithm and a reciprocal."""
+    model, n_obs, sub = int(p["model"]), int(p["n_obs"]), int(p["substeps"])
+    if model == 1:
+        fwd = {k: v * sub for k, v in _dyn_substep().items()}
+        # the sub-steps recomputed from the step's start (sub (sub - 1) / 2),
+        # then per sub-step one derivative and two transposed derivatives
+        # (each about 80 fp32, 10 special-function operations)
+        vjp = dict(fp32=(sub * (sub - 1) // 2) * 130 + sub * (56 + 2 * 80 + 18),
+                   xu=(sub * (sub - 1) // 2) * 14 + sub * (7 + 2 * 10), int=0)
+    elif model == 0:
+        fwd = {k: v * sub for k, v in _kin_substep().items()}
+        vjp = dict(fp32=sub * 17, xu=sub * 2, int=0)
+    else:
+        fwd, vjp = dict(fp32=sub, xu=0, int=0), dict(fp32=sub, xu=0, int=0)
+    soft = int(p["obs_mode"]) == 1
+    obs_g = dict(fp32=(12 if soft else 6) * n_obs, xu=(4 if soft else 0) * n_obs, int=0)
+    nz = _noise(p)
+    rep = 7.0 / 8.0
+    d = {k: rep * (fwd[k] + nz[k]) + vjp[k] + (obs_g[k] if int(p["risk_mask"]) & 4 else 0)
+         for k in ("fp32", "xu", "int")}
+    d["int"] += 10  # the control cotangents' warp sums
+    n = {k: rep * fwd[k] + vjp[k] + obs_g[k] for k in ("fp32", "xu", "int")}
+    n["fp32"] += 8 + 5 + 4 + 12  # track gradient, deviation, speed, control cost and clip
+    n["xu"] += 2 + (2 if model == 0 else 0)  # track sqrt and division; tan(steer) and its /L
+    for c in (d, n):
+        c["issue"] = c["fp32"] + c["xu"] + c["int"]
+    return d, n
+
+
+def tail_rollouts(p):
+    """Rollouts with a nonzero cotangent of a fractional-tail CVaR: ranks
+    ceil(alpha M) .. M (without ties at VaR)."""
+    M = int(p["M"])
+    j = int(np.ceil(float(np.float32(p["alpha"])) * M))
+    return M - max(1, min(M, j)) + 1
+
+
+def adjoint_roofline(p, kernel_s, rates, n_sms, sm_mhz):
+    d, n = adjoint_counts(p)
+    K, T = int(p["K"]), int(p["T"])
+    n_tail = tail_rollouts(p)
+    clk = sm_mhz * 1e6
+    out = {}
+    for pipe in ("fp32", "xu", "issue"):
+        ops = K * n_tail * T * d[pipe] + K * T * n[pipe]
+        peak = n_sms * rates[pipe] * clk
+        out[pipe] = {"ops_per_launch": ops, "achieved": ops / kernel_s / 1e9, "peak": peak / 1e9,
+                     "frac": ops / kernel_s / peak}
+    bound = max(("fp32", "xu", "issue"), key=lambda k: out[k]["frac"])
+    return {"kernel": "bwd_main_kernel", "bound": "alu", "pipe": bound, "frac": out[bound]["frac"],
+            "kernel_ms_mean": 1e3 * kernel_s, "tail_rollouts_per_sample": n_tail, "pipes": out,
+            "note": "latency bound: one warp per sample on sequential reverse sweeps"}
+
+
 def algorithmic_ops(p, tested_obstacles=None):
     """All counted lane-operations (fp32 + xu + int) per disturbed and per
     nominal step, one number each (the blended count)."""
@@ -557,8 +618,8 @@ def sections(torch, args, rates, flush):
                      "update_hz": 1e3 / float(np.median(m["step_ms"])), "launch": m["launch"],
                      "roofline": roofline_summary(m)}
     out["c2_closed_loop"] = closed_loop_study(torch, args.loop_updates)
-    out["batched"] = batched_study(torch, 10)
-    out["adjoint"] = adjoint_study(torch, 10)
+    out["batched"] = batched_study(torch, 10, rates)
+    out["adjoint"] = adjoint_study(torch, 10, rates)
     out["importance"] = importance_study(torch)
     return out
 
@@ -650,12 +711,15 @@ def closed_loop_study(torch, n_updates, preset="c2_closed_loop", runs=None, seed
     return out
 
 
-def batched_study(torch, steps):
+def batched_study(torch, steps, rates=None):
     """Config 3: B = 256 uneven kinematic problems, one graph replay per round
-    against a loop of 256 plain per-problem updates on the same stream."""
+    against a loop of 256 plain per-problem updates on the same stream; and
+    the persistent rollout kernel's per-pipe roofline (its eager launch timed
+    by the library's event hook, the obstacles tested counted once)."""
     from paper_2209_12842_gb300 import RaMppi
     from paper_2209_12842_gb300.controller import RaMppiBatch
 
+    rates = rates or dict(DEFAULT_RATES)
     insts = rs.batched_instances(256)
     for d in insts:
         d["max_obstacles"] = d["n_obs"]
@@ -673,6 +737,35 @@ def batched_study(torch, steps):
     stream = torch.cuda.current_stream()
     tuned_ms = batch.tune(3)
     g50, g99 = ev_time(torch, lambda: batch.step(graph=True), steps, stream)
+    # the rollout kernel alone (eager launches with the event hook)
+    kb, ke = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batch.set_timing_events(kb, ke)
+    kms = []
+    for _ in range(max(3, steps // 2)):
+        batch.step(graph=False)
+        torch.cuda.synchronize()
+        kms.append(kb.elapsed_time(ke))
+    batch.set_timing_events(None)
+    cand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    batch.set_diagnostics(cand)
+    batch.step(graph=False)
+    torch.cuda.synchronize()
+    batch.set_diagnostics(None)
+    rows = sum(d["K"] * ((d["M"] + 31) // 32) * d["T"] for d in insts)
+    tested = float(cand.item()) / rows
+    launch = batch.get_launch()
+    k_s = float(np.median(kms)) / 1e3
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = 2070.0
+    ops = {"fp32": 0.0, "xu": 0.0, "issue": 0.0}
+    for d in insts:
+        q = dict(p, K=d["K"], M=d["M"], T=d["T"], n_obs=d["n_obs"])
+        dd, nn = pipe_counts(q, tested, launch[1], False)
+        for pipe in ops:
+            ops[pipe] += d["K"] * d["M"] * d["T"] * dd[pipe] + d["K"] * d["T"] * nn[pipe]
+    pipes = {k: {"ops_per_launch": v, "achieved": v / k_s / 1e9, "peak": n_sms * rates[k] * sm_mhz * 1e6 / 1e9,
+                 "frac": v / k_s / (n_sms * rates[k] * sm_mhz * 1e6)} for k, v in ops.items()}
+    bound = max(pipes, key=lambda k: pipes[k]["frac"])
     ctls = []
     for i, d in enumerate(insts):
         q = dict(p, K=d["K"], M=d["M"], T=d["T"], seed=d["seed"], instance_id=d["instance_id"], n_obs=d["n_obs"])
@@ -685,7 +778,6 @@ def batched_study(torch, steps):
             c.step(x, v, o, want_cvar=False)
 
     l50, l99 = ev_time(torch, loop, max(3, steps // 2), stream)
-    launch = batch.get_launch()
     for c, *_ in ctls:
         c.close()
     batch.close()
@@ -693,14 +785,20 @@ def batched_study(torch, steps):
             "batched_graph": {"p50_ms": g50, "p99_ms": g99, "rollout_steps_per_s": units / g50 * 1e3},
             "loop_of_plain_launches": {"p50_ms": l50, "p99_ms": l99, "rollout_steps_per_s": units / l50 * 1e3},
             "speedup_p50": l50 / g50, "tuned_launch": {"warps_per_block": launch[0], "ilp": launch[1],
-                                                       "grid": launch[2], "tune_ms": tuned_ms}}
+                                                       "grid": launch[2], "tune_ms": tuned_ms},
+            "roofline": {"kernel": "batch_rollout_kernel", "bound": "alu", "pipe": bound,
+                         "frac": pipes[bound]["frac"], "kernel_ms_median": 1e3 * k_s,
+                         "obstacles_tested_per_rollout_step": tested, "pipes": pipes,
+                         "peak_basis": f"{n_sms} SMs x measured lane-ops per SM per clock x {sm_mhz:.0f} MHz"}}
 
 
-def adjoint_study(torch, steps):
+def adjoint_study(torch, steps, rates=None):
     """Config 4: forward update and hand-written adjoint latency (kinematic,
-    K = 1024, M = 64, T = 30, softplus barrier)."""
+    K = 1024, M = 64, T = 30, softplus barrier), and the main adjoint
+    kernel's per-pipe roofline (timed alone by the library's event hook)."""
     from paper_2209_12842_gb300 import RaMppi
 
+    rates = rates or dict(DEFAULT_RATES)
     p = rs.preset("c4_gradient")
     obs = rs.make_obstacles(p["seed"], p["n_obs"], *p["obs_r"])
     ctl = RaMppi(p, obs, differentiable=True)
@@ -712,10 +810,20 @@ def adjoint_study(torch, steps):
     f50, f99 = ev_time(torch, lambda: ctl.step(x0, V), steps, stream)
     ctl.step(x0, V)
     b50, b99 = ev_time(torch, lambda: ctl.backward(gVp, gS), steps, stream)
+    kb, ke = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctl.set_timing_events(kb, ke)
+    kms = []
+    for _ in range(steps):
+        ctl.backward(gVp, gS)
+        torch.cuda.synchronize()
+        kms.append(kb.elapsed_time(ke))
+    ctl.set_timing_events(None)
     ctl.close()
     units = p["K"] * p["M"] * p["T"]
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    roof = adjoint_roofline(p, float(np.median(kms)) / 1e3, rates, n_sms, 2070.0)
     return {"forward_p50_ms": f50, "forward_p99_ms": f99, "backward_p50_ms": b50, "backward_p99_ms": b99,
-            "backward_rollout_steps_per_s": units / b50 * 1e3}
+            "backward_rollout_steps_per_s": units / b50 * 1e3, "roofline": roof}
 
 
 def importance_study(torch, scales=((1.5, 0.5), (1.1, 0.5)), alpha=0.99):

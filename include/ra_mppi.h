@@ -333,8 +333,9 @@ int ra_mppi_set_diagnostics(ra_mppi_t* h, unsigned long long* candidates);
 
 /* Timing hook: when set, ra_mppi_step records the caller's CUDA events
  * (cudaEvent_t passed as void*) immediately before and after the fused
- * rollout kernel on the step's stream, so the caller can time that kernel
- * alone.  NULL, NULL turns the hook off. */
+ * rollout kernel on the step's stream, and ra_mppi_backward before and after
+ * its main (reverse-sweep) kernel, so the caller can time that kernel alone.
+ * NULL, NULL turns the hook off. */
 int ra_mppi_set_timing_events(ra_mppi_t* h, void* rollout_begin, void* rollout_end);
 
 /* Pipe-throughput probe for the roofline of the rollout kernel (no
@@ -407,6 +408,15 @@ int ra_mppi_batch_read_outputs(ra_mppi_batch_t* b, float* V_out, float* S_tilde,
 
 /* Obstacles of problem i, as ra_mppi_set_obstacles (synchronous). */
 int ra_mppi_batch_set_obstacles(ra_mppi_batch_t* b, int32_t i, const float* xyr, int32_t n_obs, void* stream);
+
+/* Timing hook and diagnostics of the batched path, as ra_mppi_set_timing_events
+ * and ra_mppi_set_diagnostics: the events are recorded around the persistent
+ * rollout kernel by ra_mppi_step_batched_eager (the captured graph holds no
+ * events); the counter takes the obstacles tested exactly after the cull, by
+ * the eager launches and by the graph captured after the call (the call
+ * recaptures it).  NULL turns either off. */
+int ra_mppi_batch_set_timing_events(ra_mppi_batch_t* b, void* rollout_begin, void* rollout_end);
+int ra_mppi_batch_set_diagnostics(ra_mppi_batch_t* b, unsigned long long* candidates);
 
 /* One update of every problem: replay of the captured graph on `stream`. */
 int ra_mppi_step_batched(ra_mppi_batch_t* b, void* stream);

@@ -122,6 +122,8 @@ def _declare(L):
     L.ra_mppi_batch_set_iteration.argtypes = [_VP, ctypes.c_uint64]
     L.ra_mppi_batch_get_status.argtypes = [_VP]
     L.ra_mppi_batch_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
+    L.ra_mppi_batch_set_timing_events.argtypes = [_VP, _VP, _VP]
+    L.ra_mppi_batch_set_diagnostics.argtypes = [_VP, _VP]
     L.ra_mppi_batch_get_launch.argtypes = [_VP, _I32P, _I32P, _I32P]
     L.ra_mppi_batch_tune.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     L.ra_mppi_batch_last_error.argtypes = [_VP]
@@ -130,7 +132,8 @@ def _declare(L):
                  "ra_mppi_batch_set_obstacles", "ra_mppi_step_batched", "ra_mppi_step_batched_eager",
                  "ra_mppi_batch_write_inputs", "ra_mppi_batch_read_outputs",
                  "ra_mppi_batch_copy_workspace", "ra_mppi_batch_set_iteration", "ra_mppi_batch_get_status",
-                 "ra_mppi_batch_set_launch", "ra_mppi_batch_get_launch", "ra_mppi_batch_tune"):
+                 "ra_mppi_batch_set_launch", "ra_mppi_batch_get_launch", "ra_mppi_batch_tune",
+                 "ra_mppi_batch_set_timing_events", "ra_mppi_batch_set_diagnostics"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("ra_mppi_create", "ra_mppi_set_obstacles", "ra_mppi_step", "ra_mppi_step_host",
                  "ra_mppi_workspace", "ra_mppi_copy_workspace", "ra_mppi_copy_weights", "ra_mppi_get_state",
@@ -403,6 +406,15 @@ def ra_mppi_batch_get_launch(b):
     _bcheck(lib().ra_mppi_batch_get_launch(b, ctypes.byref(w), ctypes.byref(i), ctypes.byref(g)),
             "ra_mppi_batch_get_launch", b)
     return w.value, i.value, g.value
+
+
+def ra_mppi_batch_set_timing_events(b, begin_event_handle=None, end_event_handle=None):
+    _bcheck(lib().ra_mppi_batch_set_timing_events(b, begin_event_handle, end_event_handle),
+            "ra_mppi_batch_set_timing_events", b)
+
+
+def ra_mppi_batch_set_diagnostics(b, counter_ptr=None):
+    _bcheck(lib().ra_mppi_batch_set_diagnostics(b, counter_ptr), "ra_mppi_batch_set_diagnostics", b)
 
 
 def ra_mppi_batch_tune(b, replays=3):

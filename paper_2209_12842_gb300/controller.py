@@ -248,6 +248,22 @@ class RaMppiBatch:
     def get_launch(self):
         return B.ra_mppi_batch_get_launch(self.b)
 
+    def set_timing_events(self, begin=None, end=None):
+        """Record torch.cuda.Event objects around the persistent rollout
+        kernel of the eager launch (step(graph=False))."""
+        if begin is None:
+            B.ra_mppi_batch_set_timing_events(self.b, None, None)
+            return
+        for ev in (begin, end):
+            if ev.cuda_event == 0:  # torch creates the CUDA event lazily
+                ev.record()
+        self._timing = (begin, end)
+        B.ra_mppi_batch_set_timing_events(self.b, begin.cuda_event, end.cuda_event)
+
+    def set_diagnostics(self, counter=None):
+        """Count the obstacles tested exactly into an int64 device tensor."""
+        B.ra_mppi_batch_set_diagnostics(self.b, counter.data_ptr() if counter is not None else None)
+
 
 class RaMppiUpdate(torch.autograd.Function):
     """(V+, S~) = update(V, theta) of one RA-MPPI step with the hand-written

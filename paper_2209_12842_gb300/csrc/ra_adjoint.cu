@@ -13,7 +13,8 @@
 //                shared by the costs equal to VaR, 0 below; the scaling gives
 //                B w + (1 - B)/M
 //   Eqs. 3, 9:   reverse sweeps through each rollout, the states recomputed
-//                from checkpoints every 8 steps:
+//                from the checkpoints (every 8 steps) that the
+//                differentiable forward stored:
 //                u-bar_t = (dF/du)' lam_{t+1}, lam_t = c dq/dx + (dF/dx)' lam_{t+1}
 //   Alg. 1:      U = clip(V + eps) passes u-bar to V inside the box for the
 //                samples drawn around V; the control cost gamma v' S^-1 u
@@ -29,8 +30,7 @@ namespace ramppi {
 
 namespace {
 
-constexpr int kSeg = 8;  // checkpoint spacing (steps)
-constexpr int kMaxCk = RA_MPPI_MAX_T_DEV / kSeg + 1;
+constexpr int kSeg = kCkSeg;  // checkpoint spacing (steps), as the forward stores them
 
 __device__ __forceinline__ float sgnf(float v) { return v > 0.0f ? 1.0f : (v < 0.0f ? -1.0f : 0.0f); }
 
@@ -346,75 +346,88 @@ constexpr int kNomLanes = 4;
 template <int MODEL>
 constexpr int nom_lanes() { return MODEL == 1 ? 1 : kNomLanes; }
 
+// Per warp, the states of the segments being reversed: 32 lanes x 8 steps x
+// NX floats, whatever the lanes per rollout (32 / lpr rollouts of lpr
+// segments each).
+template <int MODEL>
+constexpr int xbuf_floats() { return 32 * kSeg * Model<MODEL>::NX; }
+
 // nominal sample k, reversed by nom_lanes lanes (sub = 0 .. nom_lanes - 1;
 // all 32 lanes of the warp take part, a lane past K on a copy of sample
 // K - 1 that writes nothing): cotangents of U_k from V+, the nominal cost and
-// the control cost, masked by the clip; theta partials of S_k
+// the control cost, masked by the clip; theta partials of S_k.  The states
+// come from the forward's checkpoints: the lanes of a group replay up to
+// nom_lanes segments at once (lane sub the segment slo + sub) into the warp's
+// state buffer xbuf, then reverse them step by step.  The clip of
+// U = clip(V + eps) passes the cotangent iff V + eps lies strictly inside the
+// box, which is the case iff U does, so the mask is read off U.
 template <int MODEL>
 __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a, int k, int sub, bool writes,
-                            const float4* obs_s, int n_obs) {
+                            const float4* obs_s, int n_obs, float* xbuf) {
   using Md = Model<MODEL>;
-  constexpr int NX = Md::NX, NU = Md::NU;
+  constexpr int NX = Md::NX, NU = Md::NU, NL = nom_lanes<MODEL>();
   const int T = in.T, TN = T * NU;
+  const int nseg = (T + kSeg - 1) / kSeg;
+  float* gbuf = xbuf + ((threadIdx.x & 31) / NL) * (NL * kSeg * NX);
   const float sbar = sbar_of<MODEL>(p, a, k);
   const float wk = a.wk[k];
   const float* Uk = a.U + (size_t)k * TN;
-  float ck[kMaxCk][NX];
-  float x[NX];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) x[i] = a.x0[i];
-  for (int t = 0; t < T; ++t) {
-    if (t % kSeg == 0) {
-#pragma unroll
-      for (int i = 0; i < NX; ++i) ck[t / kSeg][i] = x[i];
-    }
-    Md::step(p, x, Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f));
-  }
+  const float* ck = a.ck_nom + (size_t)k * (nseg + 1) * NX;
+  const bool warm = k < in.n_warm;
   float lam[NX];
 #pragma unroll
   for (int i = 0; i < NX; ++i) lam[i] = 0.0f;
   float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (MODEL != 2 && p.c5 != 0.0f) {
     float ds[2];
-    track_s_grad(p, x[0], x[1], ds);
+    track_s_grad(p, ck[nseg * NX], ck[nseg * NX + 1], ds);  // at x_T
     lam[0] = -sbar * p.c5 * ds[0];
     lam[1] = -sbar * p.c5 * ds[1];
   }
-  const int nseg = (T + kSeg - 1) / kSeg;
-  for (int sg = nseg - 1; sg >= 0; --sg) {
-    const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
-    float xs[kSeg][NX];
+  for (int shi = nseg - 1; shi >= 0; shi -= NL) {
+    const int slo = max(0, shi - NL + 1);
+    const int sr = slo + sub;
+    if (sr <= shi) {
+      float x[NX];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) xs[0][i] = ck[sg][i];
-    for (int t = t0; t + 1 < t1; ++t) {
+      for (int i = 0; i < NX; ++i) x[i] = ck[sr * NX + i];
+      const int t0 = sr * kSeg, t1 = min(T, t0 + kSeg);
+      float* dst = gbuf + (sr - slo) * kSeg * NX;
+      for (int t = t0; t < t1; ++t) {
 #pragma unroll
-      for (int i = 0; i < NX; ++i) xs[t + 1 - t0][i] = xs[t - t0][i];
-      Md::step(p, xs[t + 1 - t0], Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f));
+        for (int i = 0; i < NX; ++i) dst[(t - t0) * NX + i] = x[i];
+        if (t + 1 < t1) Md::step(p, x, Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f));
+      }
     }
-    for (int t = t1 - 1; t >= t0; --t) {
-      const float u0 = Uk[t * NU], u1 = NU > 1 ? Uk[t * NU + 1] : 0.0f;
-      float gu[2] = {0.0f, 0.0f};
-      step_vjp<MODEL>(p, xs[t - t0], Md::ctl(p, u0, u1), lam, gu);
-      cost_grad_split<MODEL>(p, xs[t - t0], 0xFFFFFFFFu, sbar, obs_s, n_obs, sub, nom_lanes<MODEL>(), lam, gth);
-      // control cost gamma v_t' S^-1 u_t and the clip of U = clip(V + eps)
-      const float v0 = a.V[t * NU], v1 = NU > 1 ? a.V[t * NU + 1] : 0.0f;
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0xFFFFFFFFu, (uint32_t)k, in.instance), in.k0, in.k1);
-      const float2 z = box_muller(w.x, w.y);
-      const bool warm = k < in.n_warm;
-      const float vv[2] = {v0, v1}, uu[2] = {u0, u1}, zz[2] = {z.x, z.y};
-      gth[2] = fmaf(sbar, v0 * p.inv_sig2[0] * u0 + (NU > 1 ? v1 * p.inv_sig2[1] * u1 : 0.0f), gth[2]);
+    __syncwarp();
+    for (int sg = shi; sg >= slo; --sg) {
+      const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
+      const float* src = gbuf + (sg - slo) * kSeg * NX;
+      for (int t = t1 - 1; t >= t0; --t) {
+        float xs[NX];
 #pragma unroll
-      for (int j = 0; j < NU; ++j) {
-        const float raw = __fmaf_rn(p.sigma_u[j], zz[j], warm ? vv[j] : 0.0f);
-        const float msk = (warm && raw > p.u_lo[j] && raw < p.u_hi[j]) ? 1.0f : 0.0f;
-        const float gc = p.gamma * p.inv_sig2[j];
-        const size_t idx = (size_t)k * TN + t * NU + j;
-        if (writes && sub == 0) {
-          a.mask[idx] = msk;
-          a.Gnom[idx] = msk * (wk * a.gVp[t * NU + j] + gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
+        for (int i = 0; i < NX; ++i) xs[i] = src[(t - t0) * NX + i];
+        const float u0 = Uk[t * NU], u1 = NU > 1 ? Uk[t * NU + 1] : 0.0f;
+        float gu[2] = {0.0f, 0.0f};
+        step_vjp<MODEL>(p, xs, Md::ctl(p, u0, u1), lam, gu);
+        cost_grad_split<MODEL>(p, xs, 0xFFFFFFFFu, sbar, obs_s, n_obs, sub, NL, lam, gth);
+        // control cost gamma v_t' S^-1 u_t and the clip of U = clip(V + eps)
+        const float v0 = a.V[t * NU], v1 = NU > 1 ? a.V[t * NU + 1] : 0.0f;
+        const float vv[2] = {v0, v1}, uu[2] = {u0, u1};
+        gth[2] = fmaf(sbar, v0 * p.inv_sig2[0] * u0 + (NU > 1 ? v1 * p.inv_sig2[1] * u1 : 0.0f), gth[2]);
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          const float msk = (warm && uu[j] > p.u_lo[j] && uu[j] < p.u_hi[j]) ? 1.0f : 0.0f;
+          const float gc = p.gamma * p.inv_sig2[j];
+          const size_t idx = (size_t)k * TN + t * NU + j;
+          if (writes && sub == 0) {
+            a.mask[idx] = msk;
+            a.Gnom[idx] = msk * (wk * a.gVp[t * NU + j] + gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
+          }
         }
       }
     }
+    __syncwarp();
   }
   // the obstacle values are split over the group; the other partials are whole on sub = 0
 #pragma unroll
@@ -438,42 +451,19 @@ __device__ __forceinline__ void replay_noise(const DevParams& p, const Inst& in,
   }
 }
 
-// disturbed rollouts of sample k (one warp): cotangents of U_k through the
-// CVaR term; theta partials of the risk costs.  With importance sampling the
-// importance weights Ws (beside Ls) enter every weight of the risk measure
-// (a separate instantiation, so the plain adjoint keeps its registers).
-template <int MODEL, bool IS>
-__device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs& a, int k, int lane, float4* ctl,
-                              float* Ls, float* Ws, int* act, float* gus, const float4* obs_s, int n_obs) {
-  using Md = Model<MODEL>;
-  constexpr int NX = Md::NX, NU = Md::NU;
-  const int T = in.T, TN = T * NU, M = in.M;
-  const float sbar = sbar_of<MODEL>(p, a, k);
-  const float cv = a.cvar[k];
-  const float cvbar = (cv > p.C_u && isfinite(cv)) ? sbar * p.A : 0.0f;
-  if (cvbar == 0.0f) {
-    for (int c = lane; c < TN; c += 32) a.gUd[(size_t)k * TN + c] = 0.0f;
-    if (lane < 4) a.thd[(size_t)k * 4 + lane] = 0.0f;
-    return;
-  }
-  const float* Uk = a.U + (size_t)k * TN;
-  for (int t = lane; t < T; t += 32) {
-    ctl[t] = Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f);
-  }
-  for (int c = lane; c < TN; c += 32) gus[c] = 0.0f;
-  __syncwarp();
-  float x0[NX];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) x0[i] = a.x0[i];
+// The weights of the risk measure in sample k's M scaled risk costs, times
+// the CVaR cotangent cvbar (one warp): VaR by a radix select over
+// order-preserving keys (ties at VaR share its weight), then each rollout's
+// cotangent.  The rollouts with a nonzero cotangent are packed, (index,
+// cotangent) into (act[], Ls[]); returns their count.  With importance
+// sampling the weights Ws (beside Ls) enter every weight of the measure.
+// RMAX >= ceil(M / 32) rows of costs per lane: sized to M, so the 32 select
+// passes loop over rows that hold costs only.
+template <bool IS, int RMAX>
+__device__ __forceinline__ int bwd_tail(const DevParams& p, const Inst& in, int lane, float cvbar, float* Ls,
+                                        const float* Ws, int* act) {
+  const int M = in.M;
   const int R = (M + 31) >> 5;
-  // the risk costs (and importance weights) the update kept
-  for (int m = lane; m < M; m += 32) {
-    Ls[m] = a.L[(size_t)k * M + m];
-    if constexpr (IS) Ws[m] = a.L[(size_t)in.K * M + (size_t)k * M + m];
-  }
-  __syncwarp();
-  // CVaR weights: VaR by radix select, then the tail
-  constexpr int RMAX = (RA_MPPI_MAX_M_DEV + 31) / 32;
   uint32_t key[RMAX];
   float val[RMAX];
   float sum = 0.0f;
@@ -576,10 +566,10 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     w_dev = p.cvar_mode == 5 ? 2.0f * p.risk_param * p.B / W : 0.0f;
     base = p.cvar_mode == 3 ? 0.0f : (1.0f - p.B) / W;
   }
-  // the rollouts with a nonzero cotangent, packed: (index, cotangent) pairs
-  // in act[] and Ls[] (the costs are in registers now).  A CVaR tail holds
-  // about (1 - alpha) M of them, so the reverse sweeps below take
-  // ceil(n / 32) rows instead of all ceil(M / 32).
+  // pack the rollouts with a nonzero cotangent (the costs are in registers
+  // now, so Ls can take the cotangents).  A CVaR tail holds about
+  // (1 - alpha) M of them, so the reverse sweeps take ceil(n / 32) rows
+  // instead of all ceil(M / 32).
   int n_act = 0;
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) {
@@ -598,53 +588,99 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     n_act += __popc(nz);
   }
   __syncwarp();
-  // pass 2: reverse sweep of every rollout with a nonzero weight.  A short
-  // list (a CVaR tail) would leave lanes idle, so each rollout gets lpr
-  // lanes that split its obstacle terms: 32 / lpr rollouts per pass
+  return n_act;
+}
+
+// disturbed rollouts of sample k (one warp): cotangents of U_k through the
+// CVaR term; theta partials of the risk costs.  With importance sampling the
+// importance weights Ws (beside Ls) enter every weight of the risk measure
+// (a separate instantiation, so the plain adjoint keeps its registers).
+template <int MODEL, bool IS>
+__device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs& a, int k, int lane, float4* ctl,
+                              float* Ls, float* Ws, int* act, float* gus, float* xbuf, const float4* obs_s,
+                              int n_obs) {
+  using Md = Model<MODEL>;
+  constexpr int NX = Md::NX, NU = Md::NU;
+  const int T = in.T, TN = T * NU, M = in.M;
+  const float sbar = sbar_of<MODEL>(p, a, k);
+  const float cv = a.cvar[k];
+  const float cvbar = (cv > p.C_u && isfinite(cv)) ? sbar * p.A : 0.0f;
+  if (cvbar == 0.0f) {
+    for (int c = lane; c < TN; c += 32) a.gUd[(size_t)k * TN + c] = 0.0f;
+    if (lane < 4) a.thd[(size_t)k * 4 + lane] = 0.0f;
+    return;
+  }
+  const float* Uk = a.U + (size_t)k * TN;
+  for (int t = lane; t < T; t += 32) {
+    ctl[t] = Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f);
+  }
+  for (int c = lane; c < TN; c += 32) gus[c] = 0.0f;
+  // the risk costs (and importance weights) the update kept
+  for (int m = lane; m < M; m += 32) {
+    Ls[m] = a.L[(size_t)k * M + m];
+    if constexpr (IS) Ws[m] = a.L[(size_t)in.K * M + (size_t)k * M + m];
+  }
+  __syncwarp();
+  int n_act;
+  if (M <= 32) n_act = bwd_tail<IS, 1>(p, in, lane, cvbar, Ls, Ws, act);
+  else if (M <= 64) n_act = bwd_tail<IS, 2>(p, in, lane, cvbar, Ls, Ws, act);
+  else if (M <= 128) n_act = bwd_tail<IS, 4>(p, in, lane, cvbar, Ls, Ws, act);
+  else if (M <= 256) n_act = bwd_tail<IS, 8>(p, in, lane, cvbar, Ls, Ws, act);
+  else n_act = bwd_tail<IS, (RA_MPPI_MAX_M_DEV + 31) / 32>(p, in, lane, cvbar, Ls, Ws, act);
+  // reverse sweep of every rollout with a nonzero weight.  A short list (a
+  // CVaR tail) would leave lanes idle, so each rollout gets lpr lanes that
+  // split its obstacle terms (32 / lpr rollouts per pass) and replay up to
+  // lpr of its segments at once from the forward's checkpoints
   const int lpr = MODEL == 1 ? 1 : (n_act <= 8 ? 4 : (n_act <= 16 ? 2 : 1));  // as nom_lanes
   const int slots = 32 / lpr, slot = lane / lpr, sub = lane % lpr;
+  const int nseg = (T + kSeg - 1) / kSeg;
+  const float* ckk = a.ck_dist + (size_t)k * nseg * NX * M;
+  float* gbuf = xbuf + slot * (lpr * kSeg * NX);
   float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int c0 = 0; c0 < n_act; c0 += slots) {
     const bool has = c0 + slot < n_act;
     const int m = has ? act[c0 + slot] : 0;  // an idle group replays rollout 0 with no cotangent
     const float lbar = has ? Ls[c0 + slot] : 0.0f;
-    float ck[kMaxCk][NX];
-    float x[NX];
-#pragma unroll
-    for (int i = 0; i < NX; ++i) x[i] = x0[i];
-    for (int t = 0; t < T; ++t) {
-      if (t % kSeg == 0) {
-#pragma unroll
-        for (int i = 0; i < NX; ++i) ck[t / kSeg][i] = x[i];
-      }
-      Md::step(p, x, ctl[t]);
-      replay_noise<MODEL, IS>(p, in, t, m, k, x);
-    }
     float lam[NX];
 #pragma unroll
     for (int i = 0; i < NX; ++i) lam[i] = 0.0f;
-    const int nseg = (T + kSeg - 1) / kSeg;
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
-      float xs[kSeg][NX];
+    for (int shi = nseg - 1; shi >= 0; shi -= lpr) {
+      const int slo = max(0, shi - lpr + 1);
+      const int sr = slo + sub;
+      if (sr <= shi) {
+        float x[NX];
 #pragma unroll
-      for (int i = 0; i < NX; ++i) xs[0][i] = ck[sg][i];
-      for (int t = t0; t + 1 < t1; ++t) {
+        for (int i = 0; i < NX; ++i) x[i] = ckk[((size_t)sr * NX + i) * M + m];
+        const int t0 = sr * kSeg, t1 = min(T, t0 + kSeg);
+        float* dst = gbuf + (sr - slo) * kSeg * NX;
+        for (int t = t0; t < t1; ++t) {
 #pragma unroll
-        for (int i = 0; i < NX; ++i) xs[t + 1 - t0][i] = xs[t - t0][i];
-        Md::step(p, xs[t + 1 - t0], ctl[t]);
-        replay_noise<MODEL, IS>(p, in, t, m, k, xs[t + 1 - t0]);
-      }
-      for (int t = t1 - 1; t >= t0; --t) {
-        float gu[2] = {0.0f, 0.0f};
-        step_vjp<MODEL>(p, xs[t - t0], ctl[t], lam, gu);
-        cost_grad_split<MODEL>(p, xs[t - t0], p.risk_mask, lbar, obs_s, n_obs, sub, lpr, lam, gth);
-#pragma unroll
-        for (int j = 0; j < NU; ++j) {
-          const float s = warp_sum(sub == 0 ? gu[j] : 0.0f);  // one copy per rollout
-          if (lane == 0) gus[t * NU + j] += s;
+          for (int i = 0; i < NX; ++i) dst[(t - t0) * NX + i] = x[i];
+          if (t + 1 < t1) {
+            Md::step(p, x, ctl[t]);
+            replay_noise<MODEL, IS>(p, in, t, m, k, x);
+          }
         }
       }
+      __syncwarp();
+      for (int sg = shi; sg >= slo; --sg) {
+        const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
+        const float* src = gbuf + (sg - slo) * kSeg * NX;
+        for (int t = t1 - 1; t >= t0; --t) {
+          float xs[NX];
+#pragma unroll
+          for (int i = 0; i < NX; ++i) xs[i] = src[(t - t0) * NX + i];
+          float gu[2] = {0.0f, 0.0f};
+          step_vjp<MODEL>(p, xs, ctl[t], lam, gu);
+          cost_grad_split<MODEL>(p, xs, p.risk_mask, lbar, obs_s, n_obs, sub, lpr, lam, gth);
+#pragma unroll
+          for (int j = 0; j < NU; ++j) {
+            const float s = warp_sum(sub == 0 ? gu[j] : 0.0f);  // one copy per rollout
+            if (lane == 0) gus[t * NU + j] += s;
+          }
+        }
+      }
+      __syncwarp();
     }
   }
   __syncwarp();
@@ -659,8 +695,12 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
 template <int MODEL, bool IS>
 __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const BwdArgs a) {
   extern __shared__ float4 smem[];
+  // the obstacles, the warps' state buffers, then the disturbed warps' scratch
   float4* obs_s = smem;
-  float4* const scratch = obs_s + a.obs_cap;  // the warps' scratch after the obstacles
+  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* xbuf = reinterpret_cast<float*>(obs_s + a.obs_cap) + w * xbuf_floats<MODEL>();
+  float4* const scratch = reinterpret_cast<float4*>(reinterpret_cast<float*>(obs_s + a.obs_cap) +
+                                                    warps * xbuf_floats<MODEL>());
   const int n_obs = a.st->n_obs;
   // the differentiated update already advanced the counter
   const Inst in = inst_of(p, (uint32_t)(a.st->iteration - 1ull));
@@ -674,10 +714,9 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt / NL, sub = gt % NL;
     const int k_warp0 = (gt & ~31) / NL;
-    if (k_warp0 < in.K) bwd_nominal<MODEL>(p, in, a, min(k, in.K - 1), sub, k < in.K, obs_s, n_obs);
+    if (k_warp0 < in.K) bwd_nominal<MODEL>(p, in, a, min(k, in.K - 1), sub, k < in.K, obs_s, n_obs, xbuf);
     return;
   }
-  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
   if (k >= in.K) return;
   float4* ctl = scratch + w * in.T;
@@ -688,7 +727,7 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
   float* Ws = Ls + in.M;
   int* act = reinterpret_cast<int*>(Ws + wcap);
   float* gus = reinterpret_cast<float*>(act + in.M);
-  bwd_disturbed<MODEL, IS>(p, in, a, k, lane, ctl, Ls, Ws, act, gus, obs_s, n_obs);
+  bwd_disturbed<MODEL, IS>(p, in, a, k, lane, ctl, Ls, Ws, act, gus, xbuf, obs_s, n_obs);
 }
 
 // gV and gtheta: column sums over the K samples of the U cotangents (the
@@ -763,7 +802,7 @@ cudaError_t launch_bwd_main(const DevParams& p, const BwdArgs& a, bool is, int g
 }
 
 cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
-                            size_t smem, int nb_red, cudaStream_t s) {
+                            size_t smem, int nb_red, cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   bwd_prep_kernel<<<nb_prep, 256, 0, s>>>(p, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -774,12 +813,20 @@ cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int
   else b.nb_nom = a.nb_nom * nom_lanes<2>();
   const int grid = b.nb_nom + nb_dist;
   const bool is = p.is_b > 0.0f;
+  if (ev_begin != nullptr) {
+    e = cudaEventRecord(ev_begin, s);
+    if (e != cudaSuccess) return e;
+  }
   if (model == 0) e = launch_bwd_main<0>(p, b, is, grid, smem, s);
   else if (model == 1) e = launch_bwd_main<1>(p, b, is, grid, smem, s);
   else e = launch_bwd_main<2>(p, b, is, grid, smem, s);
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (ev_end != nullptr) {
+    e = cudaEventRecord(ev_end, s);
+    if (e != cudaSuccess) return e;
+  }
   bwd_reduce_kernel<<<nb_red, 256, 0, s>>>(p, a);
   return cudaGetLastError();
 }

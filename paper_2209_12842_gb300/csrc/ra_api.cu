@@ -53,6 +53,8 @@ struct ra_mppi {
   float* b_thn = nullptr;
   float* b_thd = nullptr;
   float* b_red = nullptr;
+  float* b_ck_nom = nullptr;   // state checkpoints of the last update (every 8 steps)
+  float* b_ck_dist = nullptr;
   int nb_prep = 0, nb_red = 0;
   cudaEvent_t ev_begin = nullptr;  // optional timing hook around the rollout kernel
   cudaEvent_t ev_end = nullptr;
@@ -262,6 +264,8 @@ void release(ra_mppi* h) {
   cudaFree(h->b_thn);
   cudaFree(h->b_thd);
   cudaFree(h->b_red);
+  cudaFree(h->b_ck_nom);
+  cudaFree(h->b_ck_dist);
 }
 
 // The limit is a property of the kernel, shared by every handle: raise it
@@ -276,11 +280,17 @@ bool importance(const ra_mppi* h) { return is_count(h->prob) > 0; }
 
 // the obstacle cull's x window: dynamic model with more than 64 obstacles
 // (below that the box test takes two rounds at most)
-bool windowed(const ra_mppi* h) { return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->n_obs_host > 64; }
+// (differentiable handles run the checkpointing kernel instances, which have
+// neither the x window nor sample pairs: those change speed only)
+bool differentiable(const ra_mppi* h) { return (h->prob.flags & RA_MPPI_DIFFERENTIABLE) != 0; }
+
+bool windowed(const ra_mppi* h) {
+  return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->n_obs_host > 64 && !differentiable(h);
+}
 
 bool pairs_samples(const ra_mppi* h) {
   return h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && h->ilp == 2 && h->wps == 1 && h->prob.M <= 32 &&
-         !importance(h);
+         !importance(h) && !differentiable(h);
 }
 
 // samples per disturbed block
@@ -422,6 +432,11 @@ int ra_mppi_create(const ra_mppi_problem* p, int32_t device, ra_mppi_t** out) {
     if (e == cudaSuccess) e = dalloc(&h->b_thn, K * 4);
     if (e == cudaSuccess) e = dalloc(&h->b_thd, K * 4);
     if (e == cudaSuccess) e = dalloc(&h->b_red, (size_t)h->nb_red * (TN + 4));
+    // the forward's state checkpoints every 8 steps: nominal x_0, x_8, ...
+    // and x_T; every disturbed rollout's x_0, x_8, ...
+    const size_t nseg = ((size_t)p->T + 7) / 8;
+    if (e == cudaSuccess) e = dalloc(&h->b_ck_nom, K * (nseg + 1) * h->nx);
+    if (e == cudaSuccess) e = dalloc(&h->b_ck_dist, K * nseg * h->nx * (size_t)p->M);
     if (e == cudaSuccess) e = cudaMemset(h->b_arrive, 0, 2 * sizeof(unsigned int));
   }
   if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(DevState));
@@ -517,6 +532,8 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
   a.S = h->S;
   a.cvar = h->cvar;
   a.L = h->L;
+  a.ck_nom = h->b_ck_nom;
+  a.ck_dist = h->b_ck_dist;
   a.nb_nom = (p.K + 32 * h->warps - 1) / (32 * h->warps);
   a.obs_cap = h->obs_cap;
   a.wps = h->wps;
@@ -674,6 +691,7 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32
   if (w < 1 || w > 8) return fail(h, RA_MPPI_EINVAL, "warps_per_block must be in [1, 8]");
   if (i != 1 && i != 2 && i != 4) return fail(h, RA_MPPI_EINVAL, "ilp must be 1, 2 or 4");
   if (i == 4 && importance(h)) return fail(h, RA_MPPI_EINVAL, "importance-sampled rollouts interleave 1 or 2");
+  if (i == 4 && differentiable(h)) return fail(h, RA_MPPI_EINVAL, "differentiable handles interleave 1 or 2");
   if (g < 1 || g > w || w % g != 0) return fail(h, RA_MPPI_EINVAL, "warps_per_sample must divide warps_per_block");
   const int old_w = h->warps, old_i = h->ilp, old_g = h->wps;
   h->warps = w;
@@ -717,7 +735,7 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   for (int w : warps_c) {
     for (int il : ilp_c)
     for (int g : wps_c) {
-      if (il == 4 && importance(h)) continue;
+      if (il == 4 && (importance(h) || differentiable(h))) continue;
       // shapes that leave a warp without a full set of interleaved rows add
       // nothing, except one row per sample, which two samples share (dynamic model)
       const bool sample_pairs = h->prob.model == RA_MPPI_DYN_SINGLE_TRACK && R == 1 && il == 2 && g == 1;
@@ -789,6 +807,8 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.S = h->S;
   a.cvar = h->cvar;
   a.L = h->L;
+  a.ck_nom = h->b_ck_nom;
+  a.ck_dist = h->b_ck_dist;
   a.obs = h->obs;
   a.st = h->st;
   a.gVp = gV_plus;
@@ -810,12 +830,14 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.nb_nom = (p.K + 32 * kBwdWarps - 1) / (32 * kBwdWarps);
   a.obs_cap = h->obs_cap;
   const int nb_dist = (p.K + kBwdWarps - 1) / kBwdWarps;
-  // per warp: controls, risk costs, importance weights (when on), packed
-  // rollout indices, U cotangents
-  const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * p.T * sizeof(float4) +
+  // per warp: the states of the segments being reversed (32 x 8 steps x nx),
+  // then controls, risk costs, importance weights (when on), packed rollout
+  // indices, U cotangents
+  const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * 32 * 8 * h->nx * sizeof(float) +
+                      (size_t)kBwdWarps * p.T * sizeof(float4) +
                       (size_t)kBwdWarps * (p.M * (importance(h) ? 3 : 2) + (size_t)p.T * h->nu) * sizeof(float);
   const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, h->nb_prep, nb_dist, smem, h->nb_red,
-                                                static_cast<cudaStream_t>(stream));
+                                                static_cast<cudaStream_t>(stream), h->ev_begin, h->ev_end);
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
   return RA_MPPI_OK;
 }

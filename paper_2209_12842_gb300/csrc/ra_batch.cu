@@ -32,6 +32,7 @@ struct ra_mppi_batch {
   ra_mppi_problem common;
   DevParams dp;
   int device = 0;
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // optional timing hook (eager launches)
   int B = 0, nx = 0, nu = 0;
   std::vector<InstDesc> desc_h;
   InstDesc* desc = nullptr;
@@ -166,18 +167,27 @@ BatchArgs rollout_args(const ra_mppi_batch* b) {
 }
 
 // queue reset, persistent rollout launch and batched update on stream s
-cudaError_t enqueue(ra_mppi_batch* b, cudaStream_t s) {
+// (timed: the timing hook's events around the rollout launch)
+cudaError_t enqueue(ra_mppi_batch* b, cudaStream_t s, bool timed = false) {
   cudaError_t e = cudaMemsetAsync(b->queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const BatchArgs a = rollout_args(b);
   const size_t smem = batch_smem(b);
   const int grid = b->blocks_per_sm * b->n_sms;
+  if (timed && b->ev_begin != nullptr) {
+    e = cudaEventRecord(b->ev_begin, s);
+    if (e != cudaSuccess) return e;
+  }
   switch (b->common.model) {
     case 0: e = ramppi::launch_batch_rollout<0>(b->dp, a, b->warps, b->ilp, b->is, smem, grid, s); break;
     case 1: e = ramppi::launch_batch_rollout<1>(b->dp, a, b->warps, b->ilp, b->is, smem, grid, s); break;
     default: e = ramppi::launch_batch_rollout<2>(b->dp, a, b->warps, b->ilp, b->is, smem, grid, s); break;
   }
   if (e != cudaSuccess) return e;
+  if (timed && b->ev_end != nullptr) {
+    e = cudaEventRecord(b->ev_end, s);
+    if (e != cudaSuccess) return e;
+  }
   BatchUpdateArgs u{};
   u.desc = b->desc;
   u.B = b->B;
@@ -463,8 +473,26 @@ int ra_mppi_step_batched(ra_mppi_batch_t* b, void* stream) {
 int ra_mppi_step_batched_eager(ra_mppi_batch_t* b, void* stream) {
   if (b == nullptr) return RA_MPPI_EINVAL;
   RA_BATCH_DEVICE_SCOPE(b);
-  const cudaError_t e = enqueue(b, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = enqueue(b, static_cast<cudaStream_t>(stream), true);
   if (e != cudaSuccess) return bcuda(b, e, "batched launch");
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_batch_set_timing_events(ra_mppi_batch_t* b, void* rollout_begin, void* rollout_end) {
+  if (b == nullptr) return RA_MPPI_EINVAL;
+  if ((rollout_begin == nullptr) != (rollout_end == nullptr))
+    return bfail(b, RA_MPPI_EINVAL, "set both timing events or neither");
+  b->ev_begin = static_cast<cudaEvent_t>(rollout_begin);
+  b->ev_end = static_cast<cudaEvent_t>(rollout_end);
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_batch_set_diagnostics(ra_mppi_batch_t* b, unsigned long long* candidates) {
+  if (b == nullptr) return RA_MPPI_EINVAL;
+  RA_BATCH_DEVICE_SCOPE(b);
+  b->dp.diag = candidates;
+  const cudaError_t e = capture(b);
+  if (e != cudaSuccess) return bcuda(b, e, "batch_set_diagnostics");
   return RA_MPPI_OK;
 }
 

@@ -41,6 +41,8 @@ struct BwdArgs {
   const float* S;       // [K]
   const float* cvar;    // [K]
   const float* L;       // [K][M] risk costs of the update (then [K][M] importance weights)
+  const float* ck_nom;  // [K][nseg + 1][NX] nominal state checkpoints of the update (x_0, x_8, ..., x_T)
+  const float* ck_dist; // [K][nseg][NX][M] disturbed state checkpoints of the update
   const float4* obs;
   DevState* st;
   const float* gVp;     // [T][nu]
@@ -60,8 +62,10 @@ struct BwdArgs {
   float* gtheta;        // [4] out
   int nb_nom, obs_cap;  // nb_nom: 128-thread blocks at one lane per nominal rollout
 };
+// (ev_begin / ev_end: optional events recorded around the main kernel)
 cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
-                            size_t smem, int nb_red, cudaStream_t s);
+                            size_t smem, int nb_red, cudaStream_t s, cudaEvent_t ev_begin = nullptr,
+                            cudaEvent_t ev_end = nullptr);
 
 // Batched path (ra_batch.cuh, ra_batch.cu): persistent rollout kernel of one
 // model, its shared-memory limit and occupancy, and the batched update

@@ -63,6 +63,11 @@ struct RolloutArgs {
   float* S;            // [K]
   float* cvar;         // [K]
   float* L;            // [K][M] or nullptr
+  // state checkpoints for the adjoint (nullptr unless differentiable):
+  // nominal x_t at t = 0, 8, ... and x_T, [K][nseg + 1][NX]; disturbed x_t at
+  // t = 0, 8, ..., [K][nseg][NX][M] (nseg = ceil(T / 8))
+  float* ck_nom;
+  float* ck_dist;
   int nb_nom;          // number of nominal blocks
   int obs_cap;
   int wps;             // warps per sample in the disturbed blocks (divides the block's warps)
@@ -89,18 +94,27 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-// Nominal rollout of sample k: writes U^k [T][nu] and S_k.
+constexpr int kCkSeg = 8;  // checkpoint spacing (steps) of the adjoint's state checkpoints
+
+// Nominal rollout of sample k: writes U^k [T][nu] and S_k (and, for the
+// adjoint, the checkpoints x_0, x_8, ... and x_T of sample k into ck).
 template <int MODEL>
 __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& in, const float* __restrict__ x0,
                                                 const float* __restrict__ V, float* __restrict__ U,
                                                 float* __restrict__ S_out, int k, const float4* obs_s,
-                                                int n_obs) {
+                                                int n_obs, float* __restrict__ ck = nullptr) {
   using Md = Model<MODEL>;
   float x[Md::NX];
 #pragma unroll
   for (int i = 0; i < Md::NX; ++i) x[i] = x0[i];
   float S = 0.0f;
+  const int nseg = (in.T + kCkSeg - 1) / kCkSeg;
+  float* ckk = ck != nullptr ? ck + (size_t)k * (nseg + 1) * Md::NX : nullptr;
   for (int t = 0; t < in.T; ++t) {
+    if (ckk != nullptr && t % kCkSeg == 0) {
+#pragma unroll
+      for (int i = 0; i < Md::NX; ++i) ckk[(t / kCkSeg) * Md::NX + i] = x[i];
+    }
     const float v0 = V[t * Md::NU];
     const float v1 = Md::NU > 1 ? V[t * Md::NU + 1] : 0.0f;
     const float2 u = control_sample(p, in.k0, in.k1, k, t, v0, v1, in.n_warm, in.instance);
@@ -114,6 +128,10 @@ __device__ __forceinline__ void nominal_rollout(const DevParams& p, const Inst& 
   }
   S += terminal_cost<MODEL>(p, x);
   S_out[k] = S;
+  if (ckk != nullptr) {
+#pragma unroll
+    for (int i = 0; i < Md::NX; ++i) ckk[nseg * Md::NX + i] = x[i];
+  }
 }
 
 // Number of obstacles (sorted by x, at most 1024) with x < v (or x <= v when
@@ -248,10 +266,12 @@ __device__ __forceinline__ float is_weight(const DevParams& p, const Inst& in, f
 // ILP disturbed rollouts of one lane: rollouts lane + 32 (r0 + i rstride),
 // i < ILP (rows r0, r0 + rstride, ... of the M rollouts); risk costs to Ls
 // (IS: and importance weights to Ws)
+// (ck: this sample's checkpoint block [nseg][NX][M] of the adjoint, or nullptr)
 template <int MODEL, int ILP, bool IS = false, bool WIN = false>
 __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in, const float* x0, int k, int lane,
                                              int r0, int rstride, const float4* ctl, float* Ls,
-                                             const float4* obs_s, int n_obs, float* Ws = nullptr) {
+                                             const float4* obs_s, int n_obs, float* Ws = nullptr,
+                                             float* __restrict__ ck = nullptr) {
   using Md = Model<MODEL>;
   float x[ILP][Md::NX];
   float L[ILP];
@@ -267,6 +287,14 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
     for (int j = 0; j < Md::NX; ++j) x[i][j] = x0[j];
   }
   for (int t = 0; t < in.T; ++t) {
+    if (ck != nullptr && t % kCkSeg == 0) {
+#pragma unroll
+      for (int i = 0; i < ILP; ++i)
+        if ((int)m[i] < in.M) {
+#pragma unroll
+          for (int j = 0; j < Md::NX; ++j) ck[((size_t)(t / kCkSeg) * Md::NX + j) * in.M + m[i]] = x[i][j];
+        }
+    }
     const float4 c = ctl[t];
     risk_cost_ilp<MODEL, ILP, WIN>(p, x, L, obs_s, n_obs);
     if constexpr (MODEL == 1 && ILP % 2 == 0) {
@@ -319,7 +347,8 @@ __device__ __forceinline__ void fill_controls(const DevParams& p, const Inst& in
 template <int MODEL, int ILP, bool IS = false, bool WIN = false>
 __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in, const float* __restrict__ x0g, int k,
                                              int lane, int r_first, int r_stride, const float4* ctl, float* Ls,
-                                             const float4* obs_s, int n_obs, float* Ws = nullptr) {
+                                             const float4* obs_s, int n_obs, float* Ws = nullptr,
+                                             float* __restrict__ ck = nullptr) {
   using Md = Model<MODEL>;
   float x0[Md::NX];
 #pragma unroll
@@ -327,10 +356,10 @@ __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in,
   const int R = (in.M + 31) >> 5;
   int r = r_first;
   for (; r + (ILP - 1) * r_stride < R; r += ILP * r_stride)
-    rollouts_ilp<MODEL, ILP, IS, WIN>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
+    rollouts_ilp<MODEL, ILP, IS, WIN>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws, ck);
   if (ILP > 1)
     for (; r < R; r += r_stride)
-      rollouts_ilp<MODEL, 1, IS, WIN>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws);
+      rollouts_ilp<MODEL, 1, IS, WIN>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws, ck);
 }
 
 // CVaR_k (or the selected risk measure) of the M risk costs in Ls (one warp),
@@ -594,11 +623,12 @@ template <int MODEL, int ILP, bool IS = false, bool WIN = false>
 __device__ __forceinline__ void disturbed_sample(const DevParams& p, const Inst& in, const float* __restrict__ x0g,
                                                  const float* __restrict__ V, int k, int lane, float4* ctl, float* Ls,
                                                  const float4* obs_s, int n_obs, float* __restrict__ cvar,
-                                                 float* __restrict__ Lout, int* status, float* Ws = nullptr) {
+                                                 float* __restrict__ Lout, int* status, float* Ws = nullptr,
+                                                 float* __restrict__ ck = nullptr) {
   fill_controls<MODEL>(p, in, V, k, lane, 32, ctl);
   __syncwarp();
   // disturbed rollouts and their risk costs (Eq. 9)
-  run_rollouts<MODEL, ILP, IS, WIN>(p, in, x0g, k, lane, 0, 1, ctl, Ls, obs_s, n_obs, Ws);
+  run_rollouts<MODEL, ILP, IS, WIN>(p, in, x0g, k, lane, 0, 1, ctl, Ls, obs_s, n_obs, Ws, ck);
   __syncwarp();
   if constexpr (IS) risk_from_shared_w(p, in, Ls, Ws, k, lane, cvar, Lout, status);
   else risk_from_shared(p, in, Ls, k, lane, cvar, Lout, status);
@@ -614,7 +644,9 @@ __device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const 
                                                       const float* __restrict__ V, int ka, int kb, int lane,
                                                       float4* ctl_a, float4* ctl_b, float* Ls_a, float* Ls_b,
                                                       const float4* obs_s, int n_obs, float* __restrict__ cvar,
-                                                      float* __restrict__ Lout, int* status) {
+                                                      float* __restrict__ Lout, int* status,
+                                                      float* __restrict__ ck_a = nullptr,
+                                                      float* __restrict__ ck_b = nullptr) {
   using Md = Model<MODEL>;
   fill_controls<MODEL>(p, in, V, ka, lane, 32, ctl_a);
   fill_controls<MODEL>(p, in, V, kb, lane, 32, ctl_b);
@@ -625,6 +657,13 @@ __device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const 
   for (int j = 0; j < Md::NX; ++j) x[0][j] = x[1][j] = x0g[j];
   const uint32_t m = (uint32_t)lane;
   for (int t = 0; t < in.T; ++t) {
+    if (ck_a != nullptr && t % kCkSeg == 0 && (int)m < in.M) {
+#pragma unroll
+      for (int j = 0; j < Md::NX; ++j) {
+        ck_a[((size_t)(t / kCkSeg) * Md::NX + j) * in.M + m] = x[0][j];
+        if (kb < in.K) ck_b[((size_t)(t / kCkSeg) * Md::NX + j) * in.M + m] = x[1][j];
+      }
+    }
     risk_cost_ilp<MODEL, 2>(p, x, L, obs_s, n_obs);
     float2 xx[Md::NX];
 #pragma unroll
@@ -654,7 +693,9 @@ __device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const 
 // costs (a separate instantiation; never with PAIRS)
 // WIN: the obstacle cull's x window (dynamic model, more than kWindowMin
 // obstacles; a separate instantiation so the others keep their code)
-template <int MODEL, int ILP, bool PAIRS = false, bool IS = false, bool WIN = false>
+// CK: store the state checkpoints the adjoint reads (differentiable handles;
+// a separate instantiation, so the others compile without the stores)
+template <int MODEL, int ILP, bool PAIRS = false, bool IS = false, bool WIN = false, bool CK = false>
 __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
   extern __shared__ float4 smem[];
   // WIN: smem[0].x holds the largest obstacle radius and the obstacles start
@@ -678,7 +719,7 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
 
   if ((int)blockIdx.x < a.nb_nom) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < in.K) nominal_rollout<MODEL>(p, in, a.x0, a.V, a.U, a.S, k, obs_s, n_obs);
+    if (k < in.K) nominal_rollout<MODEL>(p, in, a.x0, a.V, a.U, a.S, k, obs_s, n_obs, CK ? a.ck_nom : nullptr);
     return;
   }
   // disturbed blocks: G = a.wps warps per sample, warps / G samples per block
@@ -690,20 +731,23 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   float4* ctl = scratch + gi * in.T;
   float* Ls = reinterpret_cast<float*>(scratch + spb * in.T) + gi * in.M;
   float* Ws = IS ? Ls + spb * in.M : nullptr;
+  // this sample's block of disturbed checkpoints (adjoint only)
+  const size_t ck_per_sample = (size_t)((in.T + kCkSeg - 1) / kCkSeg) * Model<MODEL>::NX * in.M;
   if constexpr (PAIRS) {
     // two samples per warp: slots 2w and 2w + 1 of the block's controls and costs
     const int ka = ((int)blockIdx.x - a.nb_nom) * 2 * warps + 2 * w, kb = ka + 1;
     if (ka >= in.K) return;
     float4* ctl_a = scratch + (2 * w) * in.T;
     float* Ls_a = reinterpret_cast<float*>(scratch + 2 * warps * in.T) + (2 * w) * in.M;
+    float* ck_a = CK ? a.ck_dist + (size_t)ka * ck_per_sample : nullptr;
     disturbed_sample_pair<MODEL>(p, in, a.x0, a.V, ka, kb, lane, ctl_a, ctl_a + in.T, Ls_a, Ls_a + in.M, obs_s,
-                                 n_obs, a.cvar, a.L, &a.st->status);
+                                 n_obs, a.cvar, a.L, &a.st->status, ck_a, ck_a != nullptr ? ck_a + ck_per_sample : nullptr);
     return;
   } else {
   if (G == 1) {
     if (k >= in.K) return;
     disturbed_sample<MODEL, ILP, IS, WIN>(p, in, a.x0, a.V, k, lane, ctl, Ls, obs_s, n_obs, a.cvar, a.L,
-                                     &a.st->status, Ws);
+                                     &a.st->status, Ws, CK ? a.ck_dist + (size_t)k * ck_per_sample : nullptr);
     return;
   }
   // a sample's rollout rows split over its G warps; every warp of the block
@@ -711,7 +755,9 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
   const bool valid = k < in.K;
   if (valid) fill_controls<MODEL>(p, in, a.V, k, g * 32 + lane, 32 * G, ctl);
   __syncthreads();
-  if (valid) run_rollouts<MODEL, ILP, IS, WIN>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs, Ws);
+  if (valid)
+    run_rollouts<MODEL, ILP, IS, WIN>(p, in, a.x0, k, lane, g, G, ctl, Ls, obs_s, n_obs, Ws,
+                                      CK ? a.ck_dist + (size_t)k * ck_per_sample : nullptr);
   __syncthreads();
   if (valid && g == 0) {
     if constexpr (IS) risk_from_shared_w(p, in, Ls, Ws, k, lane, a.cvar, a.L, &a.st->status);

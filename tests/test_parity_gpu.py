@@ -148,11 +148,14 @@ def test_config5_full_size_sampled(M, alpha):
     waves = -(-K // per_wave)
     rng = np.random.default_rng(M)
     ks = [int(rng.integers(w * per_wave, min(K, (w + 1) * per_wave))) for w in range(waves)]
-    ks += list(np.linspace(0, K - 1, max(0, 48 - len(ks))).astype(int))
     last = (waves - 1) * per_wave
     ks += list(rng.integers(last, K, 15)) + [K - 1]
+    n_spread = 48
+    while len(np.unique(ks)) < 64:
+        ks += list(np.linspace(0, K - 1, n_spread).astype(int))
+        n_spread += 7
     ks = np.unique(np.asarray(ks, np.int32))
-    assert len(ks) >= 60
+    assert len(ks) >= 64
     ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=os.cpu_count() or 8)
     nS, nC, nT = compare(p, g, ref)
     print(f"config 5 M={M}: launch {warps, ilp, wps}, {waves} waves of {per_wave} samples, "
