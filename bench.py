@@ -599,14 +599,20 @@ def roofline_summary(m):
                 "obstacles_tested_per_rollout_step"]}
 
 
+SECTIONS = ("c2_update", "paper_preset_update", "c1_update", "c2_closed_loop", "batched", "adjoint", "importance")
+
+
 def sections(torch, args, rates, flush):
     """The other workloads of the same line: config 2 (update rate and
     roofline, and its 1000-update closed loop), the paper's simulation preset
-    (update rate only), config 3 (batched), config 4 (adjoint), and the
-    importance-sampling study."""
+    (update rate only), config 1, config 3 (batched), config 4 (adjoint), and
+    the importance-sampling study (`--sections` picks a subset)."""
     out = {}
+    want = set(args.sections.split(",")) if args.sections else set(SECTIONS)
     for name, preset in (("c2_update", "c2_closed_loop"), ("paper_preset_update", "paper_sim"),
                          ("c1_update", "c1_plain")):
+        if name not in want:
+            continue
         q = rs.preset(preset)
         m = measure_update(torch, q, rs.scene_obstacles(q), rs.scene_initial_state(q),
                            rs.random_controls(q["model"], q["T"], q["u_lo"], q["u_hi"], 3), 20, 5,
@@ -617,10 +623,14 @@ def sections(torch, args, rates, flush):
                      "rollout_steps_per_s": m["units"] / (float(np.median(m["step_ms"])) / 1e3),
                      "update_hz": 1e3 / float(np.median(m["step_ms"])), "launch": m["launch"],
                      "roofline": roofline_summary(m)}
-    out["c2_closed_loop"] = closed_loop_study(torch, args.loop_updates)
-    out["batched"] = batched_study(torch, 10, rates)
-    out["adjoint"] = adjoint_study(torch, 10, rates)
-    out["importance"] = importance_study(torch)
+    if "c2_closed_loop" in want:
+        out["c2_closed_loop"] = closed_loop_study(torch, args.loop_updates)
+    if "batched" in want:
+        out["batched"] = batched_study(torch, 10, rates)
+    if "adjoint" in want:
+        out["adjoint"] = adjoint_study(torch, 10, rates)
+    if "importance" in want:
+        out["importance"] = importance_study(torch)
     return out
 
 
@@ -941,6 +951,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-studies", action="store_true",
                     help="skip the other workloads' sections of the line")
+    ap.add_argument("--sections", default="",
+                    help=f"comma-separated subset of the line's sections ({', '.join(SECTIONS)}); default all")
     ap.add_argument("--loop-updates", type=int, default=1000)
     ap.add_argument("--preroll", type=int, default=200,
                     help="untimed receding-horizon iterations before timing (the state leaves the start area)")

@@ -19,8 +19,13 @@
 //   Alg. 1:      U = clip(V + eps) passes u-bar to V inside the box for the
 //                samples drawn around V; the control cost gamma v' S^-1 u
 //                depends on V directly as well.
-// Three launches: prep (d_k, w^_k, c), main (nominal blocks + one warp per
-// sample for the disturbed rollouts), reduce (sum over samples, clip mask).
+// Every reverse sweep is linear in its sample's cotangent S~-bar_k, so the
+// sweeps run at a unit cotangent and the reduction scales them:
+//   gU_k = mask_k w^_k gV+ + S~-bar_k (G_nom,k + mask_k G_dist,k)
+// with G the unit-cotangent sweeps.  Two launches: main (nominal blocks +
+// one warp per sample for the disturbed rollouts, which also form d_k, w^_k
+// and, in the last block to arrive, c) and reduce (S~-bar_k, then the sums
+// over samples with the clip mask).
 // All three models are differentiated (the dynamic one through its Heun
 // sub-steps); the indicator obstacle term has zero derivative almost
 // everywhere.
@@ -277,64 +282,13 @@ __device__ __forceinline__ float s_tilde_of(const DevParams& p, float S, float c
 
 }  // namespace
 
-// d_k = <gV+, U_k>, w^_k, and c = sum_k w^_k d_k.  One warp per sample (the
-// lanes read U_k's row together and sum in a fixed shuffle tree), eight
-// samples per block; the FP64 block partials are summed by the last block to
-// arrive, all its threads at once, in an order fixed by K: deterministic
-constexpr int kPrepSamples = 8;  // warps of a 256-thread block
-__global__ void __launch_bounds__(256) bwd_prep_kernel(const DevParams p, const BwdArgs a) {
-  __shared__ double red[kPrepSamples];
-  __shared__ unsigned int is_last;
-  const int TN = p.T * p.nu;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int k = blockIdx.x * kPrepSamples + w;
-  double part = 0.0;
-  if (k < p.K) {
-    const float* Uk = a.U + (size_t)k * TN;
-    float d = 0.0f;
-    for (int c = lane; c < TN; c += 32) d = fmaf(a.gVp[c], Uk[c], d);
-    d = warp_sum(d);
-    const float m = a.st->last_min;
-    const double s_tot = a.st->last_sum;
-    const float st = s_tilde_of(p, a.S[k], a.cvar[k]);
-    const float wt = (isfinite(st) && s_tot > 0.0) ? (float)((double)expf((m - st) * p.inv_lambda) / s_tot) : 0.0f;
-    if (lane == 0) {
-      a.dk[k] = d;
-      a.wk[k] = wt;
-    }
-    part = (double)wt * (double)d;
-  }
-  if (lane == 0) red[w] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kPrepSamples; ++i) t += red[i];
-    a.prep_part[blockIdx.x] = t;
-    __threadfence();
-    is_last = atomicAdd(&a.arrive[0], 1u) == gridDim.x - 1 ? 1u : 0u;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  double c = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) c += __ldcg(&a.prep_part[b]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-  if (lane == 0) red[w] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kPrepSamples; ++i) t += red[i];
-    *a.c_out = t;
-    a.arrive[0] = 0u;
-  }
-}
-
-template <int MODEL>
-__device__ __forceinline__ float sbar_of(const DevParams& p, const BwdArgs& a, int k) {
-  const float c = (float)*a.c_out;
-  const float g = a.gS != nullptr ? a.gS[k] : 0.0f;
-  return g - a.wk[k] * p.inv_lambda * (a.dk[k] - c);
+// w^_k = exp(-(S~_k - min S~) / lambda) / sum, from the shift and sum the
+// update kept (0 for a non-finite S~_k)
+__device__ __forceinline__ float weight_of(const DevParams& p, const BwdArgs& a, int k) {
+  const float m = a.st->last_min;
+  const double s_tot = a.st->last_sum;
+  const float st = s_tilde_of(p, a.S[k], a.cvar[k]);
+  return (isfinite(st) && s_tot > 0.0) ? (float)((double)expf((m - st) * p.inv_lambda) / s_tot) : 0.0f;
 }
 
 // lanes per nominal rollout in the adjoint: they carry the same state and
@@ -354,8 +308,9 @@ constexpr int xbuf_floats() { return 32 * kSeg * Model<MODEL>::NX; }
 
 // nominal sample k, reversed by nom_lanes lanes (sub = 0 .. nom_lanes - 1;
 // all 32 lanes of the warp take part, a lane past K on a copy of sample
-// K - 1 that writes nothing): cotangents of U_k from V+, the nominal cost and
-// the control cost, masked by the clip; theta partials of S_k.  The states
+// K - 1 that writes nothing), at a unit cotangent of S~_k: cotangents of U_k
+// from the nominal cost and the control cost, and the clip mask; theta
+// partials of S_k.  The states
 // come from the forward's checkpoints: the lanes of a group replay up to
 // nom_lanes segments at once (lane sub the segment slo + sub) into the warp's
 // state buffer xbuf, then reverse them step by step.  The clip of
@@ -369,8 +324,7 @@ __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a
   const int T = in.T, TN = T * NU;
   const int nseg = (T + kSeg - 1) / kSeg;
   float* gbuf = xbuf + ((threadIdx.x & 31) / NL) * (NL * kSeg * NX);
-  const float sbar = sbar_of<MODEL>(p, a, k);
-  const float wk = a.wk[k];
+  const float sbar = 1.0f;  // unit cotangent: the reduction scales by S~-bar_k
   const float* Uk = a.U + (size_t)k * TN;
   const float* ck = a.ck_nom + (size_t)k * (nseg + 1) * NX;
   const bool warm = k < in.n_warm;
@@ -422,7 +376,7 @@ __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a
           const size_t idx = (size_t)k * TN + t * NU + j;
           if (writes && sub == 0) {
             a.mask[idx] = msk;
-            a.Gnom[idx] = msk * (wk * a.gVp[t * NU + j] + gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
+            a.Gnom[idx] = msk * (gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
           }
         }
       }
@@ -591,8 +545,8 @@ __device__ __forceinline__ int bwd_tail(const DevParams& p, const Inst& in, int 
   return n_act;
 }
 
-// disturbed rollouts of sample k (one warp): cotangents of U_k through the
-// CVaR term; theta partials of the risk costs.  With importance sampling the
+// disturbed rollouts of sample k (one warp), at a unit cotangent of S~_k:
+// cotangents of U_k through the CVaR term; theta partials of the risk costs.  With importance sampling the
 // importance weights Ws (beside Ls) enter every weight of the risk measure
 // (a separate instantiation, so the plain adjoint keeps its registers).
 template <int MODEL, bool IS>
@@ -602,9 +556,8 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   using Md = Model<MODEL>;
   constexpr int NX = Md::NX, NU = Md::NU;
   const int T = in.T, TN = T * NU, M = in.M;
-  const float sbar = sbar_of<MODEL>(p, a, k);
   const float cv = a.cvar[k];
-  const float cvbar = (cv > p.C_u && isfinite(cv)) ? sbar * p.A : 0.0f;
+  const float cvbar = (cv > p.C_u && isfinite(cv)) ? p.A : 0.0f;  // at a unit cotangent of S~_k
   if (cvbar == 0.0f) {
     for (int c = lane; c < TN; c += 32) a.gUd[(size_t)k * TN + c] = 0.0f;
     if (lane < 4) a.thd[(size_t)k * 4 + lane] = 0.0f;
@@ -717,7 +670,51 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
     if (k_warp0 < in.K) bwd_nominal<MODEL>(p, in, a, min(k, in.K - 1), sub, k < in.K, obs_s, n_obs, xbuf);
     return;
   }
+  // d_k = <gV+, U_k> and w^_k of this block's samples, a warp each; the
+  // block's sum of w^_k d_k (FP64, fixed order), and in the last block to
+  // arrive c = sum_k w^_k d_k over all K, in an order fixed by K
+  __shared__ double wd[4];
+  __shared__ unsigned int is_last;
   const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
+  {
+    double part = 0.0;
+    if (k < in.K) {
+      const int TN = in.T * p.nu;
+      const float* Uk = a.U + (size_t)k * TN;
+      float d = 0.0f;
+      for (int c = lane; c < TN; c += 32) d = fmaf(a.gVp[c], Uk[c], d);
+      d = warp_sum(d);
+      const float wt = weight_of(p, a, k);
+      if (lane == 0) {
+        a.dk[k] = d;
+        a.wk[k] = wt;
+      }
+      part = (double)wt * (double)d;
+    }
+    if (lane == 0) wd[w] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < warps; ++i) t += wd[i];
+      const int nb_dist = (int)gridDim.x - a.nb_nom;
+      a.prep_part[blockIdx.x - a.nb_nom] = t;
+      __threadfence();
+      is_last = atomicAdd(&a.arrive[0], 1u) == (unsigned)nb_dist - 1u ? 1u : 0u;
+    }
+    __syncthreads();
+    if (is_last && w == 0) {
+      __threadfence();
+      const int nb_dist = (int)gridDim.x - a.nb_nom;
+      double c = 0.0;
+      for (int b = lane; b < nb_dist; b += 32) c += __ldcg(&a.prep_part[b]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+      if (lane == 0) {
+        *a.c_out = c;
+        a.arrive[0] = 0u;
+      }
+    }
+  }
   if (k >= in.K) return;
   float4* ctl = scratch + w * in.T;
   // per warp: risk costs [M], importance weights [M] (when on), packed
@@ -731,8 +728,9 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
 }
 
 // gV and gtheta: column sums over the K samples of the U cotangents (the
+// softmin part mask w^_k gV+ plus S~-bar_k times the unit sweeps, the
 // nominal part plus the clip-masked disturbed part) and of the theta
-// partials.  A block sums a slice of the samples, kRedRows row lanes per
+// partials (S~-bar_k times the unit ones).  A block sums a slice of the samples, kRedRows row lanes per
 // column in FP64, combined in a fixed order; the last block to arrive merges
 // the slices the same way.  The order depends on K and the grid only.
 constexpr int kRedCols = 64, kRedRows = 4;  // 256 threads
@@ -743,18 +741,23 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const D
   const int per = (p.K + gridDim.x - 1) / gridDim.x;
   const int kb = blockIdx.x * per, ke = min(p.K, kb + per);
   const int cl = threadIdx.x % kRedCols, rl = threadIdx.x / kRedCols;
+  const float cf = (float)*a.c_out;
   float* part = a.red_part + (size_t)blockIdx.x * NC;
   for (int c0 = 0; c0 < NC; c0 += kRedCols) {
     const int c = c0 + cl;
     double s = 0.0;
     if (c < NC) {
       for (int k = kb + rl; k < ke; k += kRedRows) {
+        // S~-bar_k = gS~_k - (w^_k / lambda)(d_k - c) (Eqs. 4, 5, 17)
+        const float wk = a.wk[k];
+        const float sbar = (a.gS != nullptr ? a.gS[k] : 0.0f) - wk * p.inv_lambda * (a.dk[k] - cf);
         float v;
         if (c < TN) {
           const size_t idx = (size_t)k * TN + c;
-          v = a.Gnom[idx] + a.mask[idx] * a.gUd[idx];
+          const float msk = a.mask[idx];
+          v = msk * (wk * a.gVp[c]) + sbar * (a.Gnom[idx] + msk * a.gUd[idx]);
         } else {
-          v = a.thn[(size_t)k * 4 + (c - TN)] + a.thd[(size_t)k * 4 + (c - TN)];
+          v = sbar * (a.thn[(size_t)k * 4 + (c - TN)] + a.thd[(size_t)k * 4 + (c - TN)]);
         }
         s += (double)v;
       }
@@ -801,11 +804,9 @@ cudaError_t launch_bwd_main(const DevParams& p, const BwdArgs& a, bool is, int g
   return e;
 }
 
-cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
-                            size_t smem, int nb_red, cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
-  bwd_prep_kernel<<<nb_prep, 256, 0, s>>>(p, a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_dist, size_t smem, int nb_red,
+                            cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+  cudaError_t e = cudaSuccess;
   // a.nb_nom counts blocks at one lane per nominal rollout
   BwdArgs b = a;
   if (model == 0) b.nb_nom = a.nb_nom * nom_lanes<0>();

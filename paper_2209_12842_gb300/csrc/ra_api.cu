@@ -415,9 +415,10 @@ int ra_mppi_create(const ra_mppi_problem* p, int32_t device, ra_mppi_t** out) {
   if (e == cudaSuccess) e = dalloc(&h->V_dev, TN);
   if (e == cudaSuccess) e = dalloc(&h->V_plus, TN);
   if (e == cudaSuccess && (p->flags & RA_MPPI_DIFFERENTIABLE)) {
-    // adjoint grids: one warp per sample in the prep (8 per block); the
-    // column reduction takes slices of 32 samples, at most 256 slices
-    h->nb_prep = (int)((K + 7) / 8);
+    // adjoint grids: one warp per disturbed sample in the main kernel (4 per
+    // block, one partial of c each); the column reduction takes slices of 32
+    // samples, at most 256 slices
+    h->nb_prep = (int)((K + 3) / 4);
     h->nb_red = (int)std::min<size_t>((K + 31) / 32, 256);
     e = dalloc(&h->keep_x0, 8);
     if (e == cudaSuccess) e = dalloc(&h->keep_V, TN);
@@ -836,7 +837,7 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * 32 * 8 * h->nx * sizeof(float) +
                       (size_t)kBwdWarps * p.T * sizeof(float4) +
                       (size_t)kBwdWarps * (p.M * (importance(h) ? 3 : 2) + (size_t)p.T * h->nu) * sizeof(float);
-  const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, h->nb_prep, nb_dist, smem, h->nb_red,
+  const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, nb_dist, smem, h->nb_red,
                                                 static_cast<cudaStream_t>(stream), h->ev_begin, h->ev_end);
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
   return RA_MPPI_OK;

@@ -49,7 +49,7 @@ struct BwdArgs {
   const float* gS;      // [K] or nullptr
   float* dk;            // [K]
   float* wk;            // [K]
-  double* prep_part;    // [nb_prep]
+  double* prep_part;    // [disturbed blocks of the main kernel] partials of c = sum_k w^_k d_k
   double* c_out;        // [1]
   unsigned int* arrive; // [2] counters of the prep and reduce merges
   float* Gnom;          // [K][T][nu]
@@ -63,9 +63,8 @@ struct BwdArgs {
   int nb_nom, obs_cap;  // nb_nom: 128-thread blocks at one lane per nominal rollout
 };
 // (ev_begin / ev_end: optional events recorded around the main kernel)
-cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_prep, int nb_dist,
-                            size_t smem, int nb_red, cudaStream_t s, cudaEvent_t ev_begin = nullptr,
-                            cudaEvent_t ev_end = nullptr);
+cudaError_t launch_backward(int model, const DevParams& p, const BwdArgs& a, int nb_dist, size_t smem, int nb_red,
+                            cudaStream_t s, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 
 // Batched path (ra_batch.cuh, ra_batch.cu): persistent rollout kernel of one
 // model, its shared-memory limit and occupancy, and the batched update
