@@ -420,6 +420,7 @@ def measure_update(torch, p, obs, x0, V, steps, warmup, preroll, rates, clocks=N
     torch.cuda.synchronize()
     tune_ms = ctl.tune(x_d, V_d, 3) if tune else None
     warps, ilp, wps = ctl.get_launch()
+    plan = ctl.launch_plan()
     V_out = torch.empty_like(V_d)
     for _ in range(warmup):
         ctl.step(x_d, V_d, V_out, want_cvar=False)
@@ -461,6 +462,8 @@ def measure_update(torch, p, obs, x0, V, steps, warmup, preroll, rates, clocks=N
     _, pipes_bf = pipe_roofline(p, units, k_s, None, ilp, paired, rates, n_sms, sm_mhz)
     out = {"ctl": ctl, "x": x_d, "V": V_d, "step_ms": step_ms, "kern_ms": kern_ms, "clocks": clk,
            "status": status, "tested": tested, "units": units, "launch": (warps, ilp, wps), "tune_ms": tune_ms,
+           "plan": {"grid": plan[0], "tail_first_block": plan[1], "tail_warps_per_sample": plan[2],
+                    "blocks_per_sm": plan[3]},
            "roofline": {
                "bound": "alu", "kernel": "rollout_cvar_kernel", "pipe": bound,
                "achieved": pipes[bound]["achieved"], "peak": pipes[bound]["peak"],
@@ -543,7 +546,7 @@ def run_ours(args, p, x0, V, obs):
             "wall_s_timed_section": wall,
             "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
             "launch": {"warps_per_block": warps, "rollouts_interleaved": ilp, "warps_per_sample": wps,
-                       "tune_ms": m["tune_ms"]},
+                       "tune_ms": m["tune_ms"], **m["plan"]},
             "status": B.STATUS_NAMES.get(m["status"], m["status"]),
             "clocks": m["clocks"],
             "e2e": {"value": world * m["units"] / e2e_t, "unit": "rollout-steps/s",
@@ -621,7 +624,7 @@ def sections(torch, args, rates, flush):
         out[name] = {"K": q["K"], "M": q["M"], "T": q["T"], "p50_ms": float(np.percentile(m["step_ms"], 50)),
                      "p99_ms": float(np.percentile(m["step_ms"], 99)),
                      "rollout_steps_per_s": m["units"] / (float(np.median(m["step_ms"])) / 1e3),
-                     "update_hz": 1e3 / float(np.median(m["step_ms"])), "launch": m["launch"],
+                     "update_hz": 1e3 / float(np.median(m["step_ms"])), "launch": m["launch"], "plan": m["plan"],
                      "roofline": roofline_summary(m)}
     if "c2_closed_loop" in want:
         out["c2_closed_loop"] = closed_loop_study(torch, args.loop_updates)

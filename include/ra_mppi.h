@@ -324,6 +324,17 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
  * takes two samples (the default there).  Results never depend on the shape. */
 int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32_t warps_per_sample);
 
+/* Tail split of the rollout launch (on by default; the tuner keeps it only
+ * where it is faster): when the grid's last round of disturbed blocks would
+ * fill at most half of the GPU's resident-block slots, the samples of that
+ * round take twice the warps per sample (half the rows each), so the last
+ * round is made of more, shorter blocks.  Results never depend on it. */
+int ra_mppi_set_tail_split(ra_mppi_t* h, int32_t enable);
+/* The rollout launch ra_mppi_step makes at the current shape: its grid,
+ * the first disturbed block of the tail split (-1 without one), the tail's
+ * warps per sample and the resident blocks per SM.  Any output may be NULL. */
+int ra_mppi_get_launch_plan(ra_mppi_t* h, int32_t* grid, int32_t* nb_head, int32_t* wps_tail, int32_t* blocks_per_sm);
+
 /* Diagnostics: when `candidates` (device uint64) is set, the disturbed
  * rollouts add to it, per step and per row of 32 rollouts, the number of
  * obstacles tested exactly after the warp's bounding-box cull (the work the

@@ -86,6 +86,10 @@ def _declare(L):
     L.ra_mppi_last_error.restype = ctypes.c_char_p
     L.ra_mppi_set_launch.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.ra_mppi_set_timing_events.argtypes = [_VP, _VP, _VP]
+    L.ra_mppi_set_tail_split.argtypes = [_VP, ctypes.c_int32]
+    L.ra_mppi_set_tail_split.restype = ctypes.c_int
+    L.ra_mppi_get_launch_plan.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 4
+    L.ra_mppi_get_launch_plan.restype = ctypes.c_int
     L.ra_mppi_set_diagnostics.argtypes = [_VP, _VP]
     L.ra_mppi_set_diagnostics.restype = ctypes.c_int
     L.ra_mppi_tune.argtypes = [_VP, _FP, _FP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
@@ -298,6 +302,17 @@ def ra_mppi_last_error(h):
 def ra_mppi_set_launch(h, warps_per_block=0, ilp=0, warps_per_sample=0):
     _check(lib().ra_mppi_set_launch(h, int(warps_per_block), int(ilp), int(warps_per_sample)),
            "ra_mppi_set_launch", h)
+
+
+def ra_mppi_set_tail_split(h, enable):
+    _check(lib().ra_mppi_set_tail_split(h, 1 if enable else 0), "ra_mppi_set_tail_split", h)
+
+
+def ra_mppi_get_launch_plan(h):
+    """(grid, first tail block or -1, tail warps per sample, blocks per SM)."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().ra_mppi_get_launch_plan(h, *[ctypes.byref(x) for x in v]), "ra_mppi_get_launch_plan", h)
+    return tuple(x.value for x in v)
 
 
 def ra_mppi_set_timing_events(h, begin_event_handle=None, end_event_handle=None):

@@ -121,6 +121,13 @@ class RaMppi:
     def set_launch(self, warps_per_block=0, ilp=0, warps_per_sample=0):
         B.ra_mppi_set_launch(self.h, warps_per_block, ilp, warps_per_sample)
 
+    def set_tail_split(self, enable):
+        B.ra_mppi_set_tail_split(self.h, enable)
+
+    def launch_plan(self):
+        """(grid, first tail block or -1, tail warps per sample, blocks per SM)."""
+        return B.ra_mppi_get_launch_plan(self.h)
+
     def tune(self, x0, V, replays=3):
         """Pick the fastest launch shape on these inputs (results unchanged)."""
         return B.ra_mppi_tune(self.h, x0.contiguous().data_ptr(), V.contiguous().data_ptr(), replays)

@@ -23,9 +23,10 @@
 // sweeps run at a unit cotangent and the reduction scales them:
 //   gU_k = mask_k w^_k gV+ + S~-bar_k (G_nom,k + mask_k G_dist,k)
 // with G the unit-cotangent sweeps.  Two launches: main (nominal blocks +
-// one warp per sample for the disturbed rollouts, which also form d_k, w^_k
-// and, in the last block to arrive, c) and reduce (S~-bar_k, then the sums
-// over samples with the clip mask).
+// one warp per sample for the disturbed rollouts) and reduce (d_k, w^_k and
+// the sums over samples, with S~-bar_k = a_k + b_k c split as
+// a_k = gS~_k - w^_k d_k / lambda, b_k = w^_k / lambda, so that c is only
+// needed in the final merge).
 // All three models are differentiated (the dynamic one through its Heun
 // sub-steps); the indicator obstacle term has zero derivative almost
 // everywhere.
@@ -36,6 +37,7 @@ namespace ramppi {
 namespace {
 
 constexpr int kSeg = kCkSeg;  // checkpoint spacing (steps), as the forward stores them
+constexpr int kGusSlotCols = 128;  // T nu up to which each slot keeps its own row of control cotangents
 
 __device__ __forceinline__ float sgnf(float v) { return v > 0.0f ? 1.0f : (v < 0.0f ? -1.0f : 0.0f); }
 
@@ -567,7 +569,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   for (int t = lane; t < T; t += 32) {
     ctl[t] = Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f);
   }
-  for (int c = lane; c < TN; c += 32) gus[c] = 0.0f;
+  for (int c = lane; c < (TN <= kGusSlotCols ? 32 * TN : TN); c += 32) gus[c] = 0.0f;
   // the risk costs (and importance weights) the update kept
   for (int m = lane; m < M; m += 32) {
     Ls[m] = a.L[(size_t)k * M + m];
@@ -589,6 +591,11 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   const int nseg = (T + kSeg - 1) / kSeg;
   const float* ckk = a.ck_dist + (size_t)k * nseg * NX * M;
   float* gbuf = xbuf + slot * (lpr * kSeg * NX);
+  // the control cotangents: with room for a row per slot (32 T nu floats,
+  // T nu <= kGusSlotCols), each group's first lane adds into its own row and
+  // the rows are summed once at the end in a fixed order; otherwise a warp
+  // sum per step
+  const bool slot_rows = TN <= kGusSlotCols;
   float gth[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int c0 = 0; c0 < n_act; c0 += slots) {
     const bool has = c0 + slot < n_act;
@@ -626,10 +633,17 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
           float gu[2] = {0.0f, 0.0f};
           step_vjp<MODEL>(p, xs, ctl[t], lam, gu);
           cost_grad_split<MODEL>(p, xs, p.risk_mask, lbar, obs_s, n_obs, sub, lpr, lam, gth);
+          if (slot_rows) {
+            if (sub == 0 && has) {
 #pragma unroll
-          for (int j = 0; j < NU; ++j) {
-            const float s = warp_sum(sub == 0 ? gu[j] : 0.0f);  // one copy per rollout
-            if (lane == 0) gus[t * NU + j] += s;
+              for (int j = 0; j < NU; ++j) gus[slot * TN + t * NU + j] += gu[j];
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < NU; ++j) {
+              const float s = warp_sum(sub == 0 ? gu[j] : 0.0f);  // one copy per rollout
+              if (lane == 0) gus[t * NU + j] += s;
+            }
           }
         }
       }
@@ -637,7 +651,12 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     }
   }
   __syncwarp();
-  for (int c = lane; c < TN; c += 32) a.gUd[(size_t)k * TN + c] = gus[c];
+  for (int c = lane; c < TN; c += 32) {
+    float v = gus[c];
+    if (slot_rows)
+      for (int r = 1; r < slots; ++r) v += gus[r * TN + c];
+    a.gUd[(size_t)k * TN + c] = v;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const float s = warp_sum(gth[i]);
@@ -670,121 +689,145 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
     if (k_warp0 < in.K) bwd_nominal<MODEL>(p, in, a, min(k, in.K - 1), sub, k < in.K, obs_s, n_obs, xbuf);
     return;
   }
-  // d_k = <gV+, U_k> and w^_k of this block's samples, a warp each; the
-  // block's sum of w^_k d_k (FP64, fixed order), and in the last block to
-  // arrive c = sum_k w^_k d_k over all K, in an order fixed by K
-  __shared__ double wd[4];
-  __shared__ unsigned int is_last;
   const int k = ((int)blockIdx.x - a.nb_nom) * warps + w;
-  {
-    double part = 0.0;
-    if (k < in.K) {
-      const int TN = in.T * p.nu;
-      const float* Uk = a.U + (size_t)k * TN;
-      float d = 0.0f;
-      for (int c = lane; c < TN; c += 32) d = fmaf(a.gVp[c], Uk[c], d);
-      d = warp_sum(d);
-      const float wt = weight_of(p, a, k);
-      if (lane == 0) {
-        a.dk[k] = d;
-        a.wk[k] = wt;
-      }
-      part = (double)wt * (double)d;
-    }
-    if (lane == 0) wd[w] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < warps; ++i) t += wd[i];
-      const int nb_dist = (int)gridDim.x - a.nb_nom;
-      a.prep_part[blockIdx.x - a.nb_nom] = t;
-      __threadfence();
-      is_last = atomicAdd(&a.arrive[0], 1u) == (unsigned)nb_dist - 1u ? 1u : 0u;
-    }
-    __syncthreads();
-    if (is_last && w == 0) {
-      __threadfence();
-      const int nb_dist = (int)gridDim.x - a.nb_nom;
-      double c = 0.0;
-      for (int b = lane; b < nb_dist; b += 32) c += __ldcg(&a.prep_part[b]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-      if (lane == 0) {
-        *a.c_out = c;
-        a.arrive[0] = 0u;
-      }
-    }
-  }
   if (k >= in.K) return;
   float4* ctl = scratch + w * in.T;
   // per warp: risk costs [M], importance weights [M] (when on), packed
-  // rollout indices [M], U cotangents [T nu]
+  // rollout indices [M], U cotangents [T nu] (a row per slot, [32][T nu],
+  // when T nu <= kGusSlotCols)
   const int wcap = IS ? in.M : 0;
-  float* Ls = reinterpret_cast<float*>(scratch + warps * in.T) + w * (2 * in.M + wcap + in.T * p.nu);
+  const int TNw = in.T * p.nu;
+  const int gcap = TNw <= kGusSlotCols ? 32 * TNw : TNw;
+  float* Ls = reinterpret_cast<float*>(scratch + warps * in.T) + w * (2 * in.M + wcap + gcap);
   float* Ws = Ls + in.M;
   int* act = reinterpret_cast<int*>(Ws + wcap);
   float* gus = reinterpret_cast<float*>(act + in.M);
   bwd_disturbed<MODEL, IS>(p, in, a, k, lane, ctl, Ls, Ws, act, gus, xbuf, obs_s, n_obs);
 }
 
-// gV and gtheta: column sums over the K samples of the U cotangents (the
-// softmin part mask w^_k gV+ plus S~-bar_k times the unit sweeps, the
-// nominal part plus the clip-masked disturbed part) and of the theta
-// partials (S~-bar_k times the unit ones).  A block sums a slice of the samples, kRedRows row lanes per
-// column in FP64, combined in a fixed order; the last block to arrive merges
-// the slices the same way.  The order depends on K and the grid only.
+// gV and gtheta: sums over the K samples of
+//   v_k = mask_k w^_k gV+ + S~-bar_k B_k,  B_k = G_nom,k + mask_k G_dist,k
+// (U columns; the theta columns have B_k = the unit theta partials and no
+// softmin part).  With S~-bar_k = a_k + b_k c (a_k = gS~_k - w^_k d_k /
+// lambda, b_k = w^_k / lambda, c = sum_k w^_k d_k) every column is
+// gV+ sum_k mask_k w^_k + sum_k a_k B_k + c sum_k b_k B_k, so one pass over
+// the samples forms the three sums and c, and the last block combines them.
+// A block takes a slice of the samples in chunks of 32: first d_k and w^_k
+// (a warp per sample), then the column sums with kRedRows row lanes per
+// column, in FP64; the last block to arrive merges the slices.  The order
+// depends on K and the grid only.
 constexpr int kRedCols = 64, kRedRows = 4;  // 256 threads
+constexpr int kRedChunk = 32;
+constexpr int kRedColIters = (2 * RA_MPPI_MAX_T_DEV + 4 + kRedCols - 1) / kRedCols;
 __global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const DevParams p, const BwdArgs a) {
-  __shared__ double acc[kRedRows][kRedCols];
+  __shared__ double acc[3][kRedRows][kRedCols];
+  __shared__ float ch_w[kRedChunk];
+  __shared__ double ch_a[kRedChunk], ch_b[kRedChunk], ch_wd[kRedChunk];
   __shared__ unsigned int is_last;
-  const int TN = p.T * p.nu, NC = TN + 4;
+  const int TN = p.T * p.nu, NC = TN + 4, stride = 3 * NC + 1;
   const int per = (p.K + gridDim.x - 1) / gridDim.x;
   const int kb = blockIdx.x * per, ke = min(p.K, kb + per);
   const int cl = threadIdx.x % kRedCols, rl = threadIdx.x / kRedCols;
-  const float cf = (float)*a.c_out;
-  float* part = a.red_part + (size_t)blockIdx.x * NC;
-  for (int c0 = 0; c0 < NC; c0 += kRedCols) {
-    const int c = c0 + cl;
-    double s = 0.0;
-    if (c < NC) {
-      for (int k = kb + rl; k < ke; k += kRedRows) {
-        // S~-bar_k = gS~_k - (w^_k / lambda)(d_k - c) (Eqs. 4, 5, 17)
-        const float wk = a.wk[k];
-        const float sbar = (a.gS != nullptr ? a.gS[k] : 0.0f) - wk * p.inv_lambda * (a.dk[k] - cf);
-        float v;
-        if (c < TN) {
-          const size_t idx = (size_t)k * TN + c;
-          const float msk = a.mask[idx];
-          v = msk * (wk * a.gVp[c]) + sbar * (a.Gnom[idx] + msk * a.gUd[idx]);
-        } else {
-          v = sbar * (a.thn[(size_t)k * 4 + (c - TN)] + a.thd[(size_t)k * 4 + (c - TN)]);
-        }
-        s += (double)v;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double inv_lam = (double)p.inv_lambda;
+  double R[kRedColIters], P[kRedColIters], Q[kRedColIters];
+#pragma unroll
+  for (int j = 0; j < kRedColIters; ++j) R[j] = P[j] = Q[j] = 0.0;
+  double wd = 0.0;  // thread 0: the slice's sum of w^_k d_k
+  for (int k0 = kb; k0 < ke; k0 += kRedChunk) {
+    const int n = min(kRedChunk, ke - k0);
+    // d_k = <gV+, U_k> and w^_k, one warp per sample
+    for (int i = warp; i < n; i += kRedCols * kRedRows / 32) {
+      const int k = k0 + i;
+      const float* Uk = a.U + (size_t)k * TN;
+      float d = 0.0f;
+      for (int c = lane; c < TN; c += 32) d = fmaf(a.gVp[c], Uk[c], d);
+      d = warp_sum(d);
+      if (lane == 0) {
+        const float wk = weight_of(p, a, k);
+        const double gs = a.gS != nullptr ? (double)a.gS[k] : 0.0;
+        ch_w[i] = wk;
+        ch_a[i] = gs - (double)wk * (double)d * inv_lam;
+        ch_b[i] = (double)wk * inv_lam;
+        ch_wd[i] = (double)wk * (double)d;
       }
     }
-    acc[rl][cl] = s;
     __syncthreads();
-    if (rl == 0 && c < NC) part[c] = (float)(((acc[0][cl] + acc[1][cl]) + acc[2][cl]) + acc[3][cl]);
+    if (threadIdx.x == 0)
+      for (int i = 0; i < n; ++i) wd += ch_wd[i];
+#pragma unroll
+    for (int j = 0; j < kRedColIters; ++j) {
+      const int c = j * kRedCols + cl;
+      if (c < NC) {
+        for (int i = rl; i < n; i += kRedRows) {
+          const int k = k0 + i;
+          float B;
+          if (c < TN) {
+            const size_t idx = (size_t)k * TN + c;
+            const float msk = a.mask[idx];
+            B = a.Gnom[idx] + msk * a.gUd[idx];
+            R[j] += (double)(msk * ch_w[i]);
+          } else {
+            B = a.thn[(size_t)k * 4 + (c - TN)] + a.thd[(size_t)k * 4 + (c - TN)];
+          }
+          P[j] = fma(ch_a[i], (double)B, P[j]);
+          Q[j] = fma(ch_b[i], (double)B, Q[j]);
+        }
+      }
+    }
     __syncthreads();
   }
+  // the slice's partials: (R, P, Q) per column, then sum w^_k d_k
+  double* part = a.red_part + (size_t)blockIdx.x * stride;
+#pragma unroll
+  for (int j = 0; j < kRedColIters; ++j) {
+    const int c = j * kRedCols + cl;
+    acc[0][rl][cl] = R[j];
+    acc[1][rl][cl] = P[j];
+    acc[2][rl][cl] = Q[j];
+    __syncthreads();
+    if (rl < 3 && c < NC)
+      part[rl * NC + c] = ((acc[rl][0][cl] + acc[rl][1][cl]) + acc[rl][2][cl]) + acc[rl][3][cl];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[3 * NC] = wd;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = atomicAdd(&a.arrive[1], 1u) == gridDim.x - 1 ? 1u : 0u;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
+  const int nb = (int)gridDim.x;
+  __shared__ double c_all;
+  if (threadIdx.x == 0) {
+    double c = 0.0;
+    for (int b = 0; b < nb; ++b) c += __ldcg(&a.red_part[(size_t)b * stride + 3 * NC]);
+    c_all = c;
+  }
+  __syncthreads();
+  const double c = c_all;
   for (int c0 = 0; c0 < NC; c0 += kRedCols) {
-    const int c = c0 + cl;
-    double s = 0.0;
-    if (c < NC) {
-      for (int b = rl; b < (int)gridDim.x; b += kRedRows) s += (double)__ldcg(&a.red_part[(size_t)b * NC + c]);
+    const int col = c0 + cl;
+    double r = 0.0, pp = 0.0, q = 0.0;
+    if (col < NC) {
+      for (int b = rl; b < nb; b += kRedRows) {
+        const double* pb = a.red_part + (size_t)b * stride;
+        r += __ldcg(pb + col);
+        pp += __ldcg(pb + NC + col);
+        q += __ldcg(pb + 2 * NC + col);
+      }
     }
-    acc[rl][cl] = s;
+    acc[0][rl][cl] = r;
+    acc[1][rl][cl] = pp;
+    acc[2][rl][cl] = q;
     __syncthreads();
-    if (rl == 0 && c < NC) {
-      const double t = ((acc[0][cl] + acc[1][cl]) + acc[2][cl]) + acc[3][cl];
-      if (c < TN) a.gV[c] = (float)t;
-      else a.gtheta[c - TN] = (float)t;
+    if (rl == 0 && col < NC) {
+      const double R4 = ((acc[0][0][cl] + acc[0][1][cl]) + acc[0][2][cl]) + acc[0][3][cl];
+      const double P4 = ((acc[1][0][cl] + acc[1][1][cl]) + acc[1][2][cl]) + acc[1][3][cl];
+      const double Q4 = ((acc[2][0][cl] + acc[2][1][cl]) + acc[2][2][cl]) + acc[2][3][cl];
+      const double t = (col < TN ? R4 * (double)a.gVp[col] : 0.0) + P4 + c * Q4;
+      if (col < TN) a.gV[col] = (float)t;
+      else a.gtheta[col - TN] = (float)t;
     }
     __syncthreads();
   }

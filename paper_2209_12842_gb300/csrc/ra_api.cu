@@ -24,6 +24,8 @@ struct ra_mppi {
   int n_sms = 152;
   int nx = 0, nu = 0;
   int warps = 4, ilp = 1, wps = 1;  // warps per block, rollouts interleaved, warps per sample
+  bool tail_split = true;            // the last partial wave in smaller units (see tail_plan)
+  int occ_blocks = 0;                // resident rollout blocks per SM at the current shape
   int n_obs_host = 0;                // obstacle count of the last set_obstacles
   int nb_upd = 1;
   int obs_cap = 0;
@@ -42,20 +44,16 @@ struct ra_mppi {
   // adjoint (RA_MPPI_DIFFERENTIABLE): inputs of the last update and scratch
   float* keep_x0 = nullptr;
   float* keep_V = nullptr;
-  float* b_dk = nullptr;
-  float* b_wk = nullptr;
-  double* b_prep = nullptr;
-  double* b_c = nullptr;
   unsigned int* b_arrive = nullptr;
   float* b_Gnom = nullptr;
   float* b_mask = nullptr;
   float* b_gUd = nullptr;
   float* b_thn = nullptr;
   float* b_thd = nullptr;
-  float* b_red = nullptr;
+  double* b_red = nullptr;
   float* b_ck_nom = nullptr;   // state checkpoints of the last update (every 8 steps)
   float* b_ck_dist = nullptr;
-  int nb_prep = 0, nb_red = 0;
+  int nb_red = 0;
   cudaEvent_t ev_begin = nullptr;  // optional timing hook around the rollout kernel
   cudaEvent_t ev_end = nullptr;
   std::string err;
@@ -253,10 +251,6 @@ void release(ra_mppi* h) {
   cudaFree(h->V_plus);
   cudaFree(h->keep_x0);
   cudaFree(h->keep_V);
-  cudaFree(h->b_dk);
-  cudaFree(h->b_wk);
-  cudaFree(h->b_prep);
-  cudaFree(h->b_c);
   cudaFree(h->b_arrive);
   cudaFree(h->b_Gnom);
   cudaFree(h->b_mask);
@@ -304,6 +298,44 @@ size_t rollout_smem(const ra_mppi* h) {
          spb * h->prob.M * sizeof(float) * (importance(h) ? 2 : 1);
 }
 
+cudaError_t occupancy(ra_mppi* h) {
+  const int m = h->prob.model;
+  const bool ck = differentiable(h);
+  int blocks = 0;
+  cudaError_t e;
+  switch (m) {
+    case 0: e = ramppi::rollout_occupancy<0>(h->warps, h->ilp, pairs_samples(h), importance(h), windowed(h), ck, h->smem, &blocks); break;
+    case 1: e = ramppi::rollout_occupancy<1>(h->warps, h->ilp, pairs_samples(h), importance(h), windowed(h), ck, h->smem, &blocks); break;
+    default: e = ramppi::rollout_occupancy<2>(h->warps, h->ilp, pairs_samples(h), importance(h), windowed(h), ck, h->smem, &blocks); break;
+  }
+  h->occ_blocks = e == cudaSuccess ? blocks : 0;
+  return e;
+}
+
+// The tail split of the disturbed blocks.  With Ba blocks of warps / wps
+// samples each and S = SMs x resident blocks per SM slots, the grid runs
+// floor(Ba / S) full rounds and a last round of Ba mod S blocks; when that
+// last round is at most half full, its samples take 2 wps warps each instead
+// (half the rows per warp), so the last round is made of twice as many
+// shorter blocks and the SMs stay busier to the end.  Needs 2 wps to divide
+// the block and leave each warp a row; results do not depend on it.
+void tail_plan(const ra_mppi* h, int nb_dist, int* nb_head, int* wps_tail, int* nb_total) {
+  *nb_head = 0x7FFFFFFF;
+  *wps_tail = h->wps;
+  *nb_total = nb_dist;
+  const int R = (h->prob.M + 31) / 32, G2 = 2 * h->wps;
+  if (!h->tail_split || pairs_samples(h) || h->occ_blocks < 1 || G2 > R || h->warps % G2 != 0) return;
+  const long long slots = (long long)h->n_sms * h->occ_blocks;
+  const long long rounds = nb_dist / slots, rem = nb_dist - rounds * slots;
+  if (rounds < 1 || rem == 0 || 2 * rem > slots) return;
+  const int spb_h = h->warps / h->wps, spb_t = h->warps / G2;
+  const long long head = rounds * slots, tail_samples = (long long)h->prob.K - head * spb_h;
+  if (tail_samples <= 0) return;
+  *nb_head = (int)head;
+  *wps_tail = G2;
+  *nb_total = (int)(head + (tail_samples + spb_t - 1) / spb_t);
+}
+
 cudaError_t prepare(ra_mppi* h) {
   h->smem = rollout_smem(h);
   const int m = h->prob.model < 0 || h->prob.model > 2 ? 2 : h->prob.model;
@@ -322,7 +354,7 @@ cudaError_t prepare(ra_mppi* h) {
       g_smem_limit[dev][m] = h->smem;
     }
   }
-  return cudaSuccess;
+  return occupancy(h);
 }
 
 // largest interleave in {2, 1} that divides the rollouts per lane
@@ -415,24 +447,17 @@ int ra_mppi_create(const ra_mppi_problem* p, int32_t device, ra_mppi_t** out) {
   if (e == cudaSuccess) e = dalloc(&h->V_dev, TN);
   if (e == cudaSuccess) e = dalloc(&h->V_plus, TN);
   if (e == cudaSuccess && (p->flags & RA_MPPI_DIFFERENTIABLE)) {
-    // adjoint grids: one warp per disturbed sample in the main kernel (4 per
-    // block, one partial of c each); the column reduction takes slices of 32
-    // samples, at most 256 slices
-    h->nb_prep = (int)((K + 3) / 4);
+    // the column reduction takes slices of 32 samples, at most 256 slices
     h->nb_red = (int)std::min<size_t>((K + 31) / 32, 256);
     e = dalloc(&h->keep_x0, 8);
     if (e == cudaSuccess) e = dalloc(&h->keep_V, TN);
-    if (e == cudaSuccess) e = dalloc(&h->b_dk, K);
-    if (e == cudaSuccess) e = dalloc(&h->b_wk, K);
-    if (e == cudaSuccess) e = dalloc(&h->b_prep, (size_t)h->nb_prep);
-    if (e == cudaSuccess) e = dalloc(&h->b_c, 1);
     if (e == cudaSuccess) e = dalloc(&h->b_arrive, 2);
     if (e == cudaSuccess) e = dalloc(&h->b_Gnom, K * TN);
     if (e == cudaSuccess) e = dalloc(&h->b_mask, K * TN);
     if (e == cudaSuccess) e = dalloc(&h->b_gUd, K * TN);
     if (e == cudaSuccess) e = dalloc(&h->b_thn, K * 4);
     if (e == cudaSuccess) e = dalloc(&h->b_thd, K * 4);
-    if (e == cudaSuccess) e = dalloc(&h->b_red, (size_t)h->nb_red * (TN + 4));
+    if (e == cudaSuccess) e = dalloc(&h->b_red, (size_t)h->nb_red * (3 * (TN + 4) + 1));
     // the forward's state checkpoints every 8 steps: nominal x_0, x_8, ...
     // and x_T; every disturbed rollout's x_0, x_8, ...
     const size_t nseg = ((size_t)p->T + 7) / 8;
@@ -539,7 +564,8 @@ int ra_mppi_step(ra_mppi_t* h, const float* x0, const float* V_in, float* V_out,
   a.obs_cap = h->obs_cap;
   a.wps = h->wps;
   const int spb = samples_per_block(h);
-  const int nb_dist = (p.K + spb - 1) / spb;
+  int nb_dist = (p.K + spb - 1) / spb;
+  tail_plan(h, nb_dist, &a.nb_head, &a.wps_tail, &nb_dist);
   const int grid = a.nb_nom + nb_dist;
   cudaError_t e;
   if (h->keep_x0 != nullptr) {
@@ -710,6 +736,25 @@ int ra_mppi_set_launch(ra_mppi_t* h, int32_t warps_per_block, int32_t ilp, int32
 }
 
 
+int ra_mppi_get_launch_plan(ra_mppi_t* h, int32_t* grid, int32_t* nb_head, int32_t* wps_tail, int32_t* blocks_per_sm) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  const int nb_nom = (h->prob.K + 32 * h->warps - 1) / (32 * h->warps);
+  const int spb = samples_per_block(h);
+  int nh = 0, wt = 0, nd = (h->prob.K + spb - 1) / spb;
+  tail_plan(h, nd, &nh, &wt, &nd);
+  if (grid) *grid = nb_nom + nd;
+  if (nb_head) *nb_head = nh == 0x7FFFFFFF ? -1 : nh;
+  if (wps_tail) *wps_tail = wt;
+  if (blocks_per_sm) *blocks_per_sm = h->occ_blocks;
+  return RA_MPPI_OK;
+}
+
+int ra_mppi_set_tail_split(ra_mppi_t* h, int32_t enable) {
+  if (h == nullptr) return RA_MPPI_EINVAL;
+  h->tail_split = enable != 0;
+  return RA_MPPI_OK;
+}
+
 int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays, float* best_ms) {
   if (h == nullptr || x0 == nullptr || V == nullptr) return RA_MPPI_EINVAL;
   RA_DEVICE_SCOPE(h);
@@ -726,6 +771,7 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
   if (e != cudaSuccess) return cuda_fail(h, e, "tune");
   const int R = (h->prob.M + 31) / 32;
   const int old_w = h->warps, old_i = h->ilp, old_g = h->wps;
+  h->tail_split = true;
   int bw = old_w, bi = old_i, bg = old_g;
   float best = 1e30f;
   // warps per sample need not be a power of two: M = 300 has 10 rows of 32
@@ -761,13 +807,33 @@ int ra_mppi_tune(ra_mppi_t* h, const float* x0, const float* V, int32_t replays,
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(s);
   h->warps = bw;
   h->ilp = bi;
   h->wps = bg;
   e = prepare(h);
+  // the tail split at the chosen shape: keep it only if it is faster
+  if (e == cudaSuccess) {
+    int nh = 0, wt = 0, nt = 0;
+    tail_plan(h, (h->prob.K + samples_per_block(h) - 1) / samples_per_block(h), &nh, &wt, &nt);
+    if (nh != 0x7FFFFFFF) {
+      float t_on = best, t_off = 1e30f;
+      h->tail_split = false;
+      if (ra_mppi_step(h, x0, V, h->V_plus, nullptr, nullptr, s) == RA_MPPI_OK) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < replays; ++r) ra_mppi_step(h, x0, V, h->V_plus, nullptr, nullptr, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) == cudaSuccess) {
+          cudaEventElapsedTime(&t_off, e0, e1);
+          t_off /= (float)replays;
+        }
+      }
+      h->tail_split = t_on <= t_off;
+      if (!h->tail_split) best = t_off;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
   if (e == cudaSuccess) e = cudaMemcpy(&h->st->iteration, &saved_it, sizeof(saved_it), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(h, e, "tune");
   if (best_ms) *best_ms = best;
@@ -814,10 +880,6 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.st = h->st;
   a.gVp = gV_plus;
   a.gS = gS_tilde;
-  a.dk = h->b_dk;
-  a.wk = h->b_wk;
-  a.prep_part = h->b_prep;
-  a.c_out = h->b_c;
   a.arrive = h->b_arrive;
   a.Gnom = h->b_Gnom;
   a.mask = h->b_mask;
@@ -834,9 +896,11 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   // per warp: the states of the segments being reversed (32 x 8 steps x nx),
   // then controls, risk costs, importance weights (when on), packed rollout
   // indices, U cotangents
+  // (the U cotangents: a row per slot, 32 T nu floats, when T nu <= 128)
+  const size_t TNb = (size_t)p.T * h->nu, gcap = TNb <= 128 ? 32 * TNb : TNb;
   const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * 32 * 8 * h->nx * sizeof(float) +
                       (size_t)kBwdWarps * p.T * sizeof(float4) +
-                      (size_t)kBwdWarps * (p.M * (importance(h) ? 3 : 2) + (size_t)p.T * h->nu) * sizeof(float);
+                      (size_t)kBwdWarps * (p.M * (importance(h) ? 3 : 2) + gcap) * sizeof(float);
   const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, nb_dist, smem, h->nb_red,
                                                 static_cast<cudaStream_t>(stream), h->ev_begin, h->ev_end);
   if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");

@@ -30,6 +30,10 @@ cudaError_t launch_rollout(const DevParams& p, const RolloutArgs& a, int warps, 
 // Raise the dynamic shared memory limit of every instance of a model.
 template <int MODEL>
 cudaError_t prepare_rollout(size_t smem);
+// Resident blocks per SM of the instance launch_rollout runs for these
+// arguments (ck: the checkpointing instances of differentiable handles).
+template <int MODEL>
+cudaError_t rollout_occupancy(int warps, int ilp, bool pairs, bool is, bool win, bool ck, size_t smem, int* blocks);
 
 cudaError_t launch_update(const DevParams& p, const UpdateArgs& a, int nblocks, cudaStream_t s);
 
@@ -47,17 +51,13 @@ struct BwdArgs {
   DevState* st;
   const float* gVp;     // [T][nu]
   const float* gS;      // [K] or nullptr
-  float* dk;            // [K]
-  float* wk;            // [K]
-  double* prep_part;    // [disturbed blocks of the main kernel] partials of c = sum_k w^_k d_k
-  double* c_out;        // [1]
-  unsigned int* arrive; // [2] counters of the prep and reduce merges
+  unsigned int* arrive; // [2] arrival counter of the reduction (the other is spare)
   float* Gnom;          // [K][T][nu]
   float* mask;          // [K][T][nu]
   float* gUd;           // [K][T][nu]
   float* thn;           // [K][4]
   float* thd;           // [K][4]
-  float* red_part;      // [nb_red][T nu + 4]
+  double* red_part;     // [nb_red][3 (T nu + 4) + 1] the reduction's slice partials
   float* gV;            // [T][nu] out
   float* gtheta;        // [4] out
   int nb_nom, obs_cap;  // nb_nom: 128-thread blocks at one lane per nominal rollout

@@ -71,6 +71,11 @@ struct RolloutArgs {
   int nb_nom;          // number of nominal blocks
   int obs_cap;
   int wps;             // warps per sample in the disturbed blocks (divides the block's warps)
+  // tail split: disturbed blocks from nb_head on take wps_tail (> wps) warps
+  // per sample, so the last partial wave of the grid is made of smaller units
+  // (nb_head = INT_MAX: no split)
+  int nb_head;
+  int wps_tail;
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -722,15 +727,20 @@ __global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, co
     if (k < in.K) nominal_rollout<MODEL>(p, in, a.x0, a.V, a.U, a.S, k, obs_s, n_obs, CK ? a.ck_nom : nullptr);
     return;
   }
-  // disturbed blocks: G = a.wps warps per sample, warps / G samples per block
-  // (the hardware hands out blocks as SM slots free up; a persistent grid
-  // taking samples from a counter was slower: its per-unit barriers cost more)
+  // disturbed blocks: G = a.wps warps per sample, warps / G samples per block;
+  // the blocks of the tail split (from a.nb_head on) take a.wps_tail warps
+  // per sample.  (The hardware hands out blocks as SM slots free up; a
+  // persistent grid taking samples from a counter was slower: its per-unit
+  // barriers cost more.)  The shared-memory slots keep the head's layout.
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int G = a.wps, spb = warps / G, gi = w / G, g = w - gi * G;
-  const int k = ((int)blockIdx.x - a.nb_nom) * spb + gi;
+  const int db = (int)blockIdx.x - a.nb_nom;
+  const bool tail = db >= a.nb_head;
+  const int spb_h = warps / a.wps;
+  const int G = tail ? a.wps_tail : a.wps, spb = warps / G, gi = w / G, g = w - gi * G;
+  const int k = tail ? a.nb_head * spb_h + (db - a.nb_head) * spb + gi : db * spb_h + gi;
   float4* ctl = scratch + gi * in.T;
-  float* Ls = reinterpret_cast<float*>(scratch + spb * in.T) + gi * in.M;
-  float* Ws = IS ? Ls + spb * in.M : nullptr;
+  float* Ls = reinterpret_cast<float*>(scratch + spb_h * in.T) + gi * in.M;
+  float* Ws = IS ? Ls + spb_h * in.M : nullptr;
   // this sample's block of disturbed checkpoints (adjoint only)
   const size_t ck_per_sample = (size_t)((in.T + kCkSeg - 1) / kCkSeg) * Model<MODEL>::NX * in.M;
   if constexpr (PAIRS) {

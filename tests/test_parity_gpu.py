@@ -225,6 +225,40 @@ def test_launch_shapes_are_bitwise_identical(launch):
     np.testing.assert_allclose(g["V_plus"], base["V_plus"], atol=1e-6)
 
 
+@pytest.mark.parametrize("name,K", [("small_dyn", 2124), ("small_kin", 2300)])
+def test_tail_split_is_bitwise_identical(name, K):
+    """The launch that gives the samples of the grid's last partial round
+    twice the warps per sample (half the rows each) gives the same bits as
+    the plain launch, and its tail samples match the oracle."""
+    from paper_2209_12842_gb300 import RaMppi
+
+    p = rs.preset(name, K=K, M=128, T=6)
+    obs, x0, V = _inputs(p)
+    out, plans = [], []
+    for split in (False, True):
+        ctl = RaMppi(p, obs, keep_risk_costs=True)
+        ctl.set_launch(8, 2, 2)
+        ctl.set_tail_split(split)
+        plans.append(ctl.launch_plan())
+        ctl.iteration = 0
+        Vp = ctl.step(torch.from_numpy(x0).cuda(), torch.from_numpy(V).cuda())
+        ws = ctl.workspace()
+        torch.cuda.synchronize()
+        out.append(dict(V_plus=Vp.cpu().numpy(), S_tilde=ctl.S_tilde.cpu().numpy(), cvar=ctl.cvar.cpu().numpy(),
+                        U=ws["U"].cpu().numpy(), S=ws["S"].cpu().numpy(), L=ws["L"].cpu().numpy()))
+        assert ctl.status() == 0
+        ctl.close()
+    grid, head, wps_tail, bps = plans[1]
+    assert plans[0][1] == -1 and head > 0 and wps_tail == 4, plans
+    for key in ("U", "S", "cvar", "S_tilde", "L", "V_plus"):
+        np.testing.assert_array_equal(out[1][key], out[0][key], err_msg=key)
+    first_tail = head * 4  # samples of the head blocks (8 warps / 2 warps per sample)
+    ks = np.unique(np.concatenate([[first_tail - 1, first_tail, K - 1],
+                                   np.random.default_rng(1).integers(first_tail, K, 9)])).astype(np.int32)
+    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=os.cpu_count() or 8)
+    compare(p, out[1], ref)
+
+
 def test_iteration_keys_the_noise():
     p = rs.preset("small_kin")
     obs, x0, V = _inputs(p)
