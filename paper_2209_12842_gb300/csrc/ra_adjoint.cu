@@ -23,8 +23,8 @@
 // sweeps run at a unit cotangent and the reduction scales them:
 //   gU_k = mask_k w^_k gV+ + S~-bar_k (G_nom,k + mask_k G_dist,k)
 // with G the unit-cotangent sweeps.  Two launches: main (nominal blocks +
-// one warp per sample for the disturbed rollouts) and reduce (d_k, w^_k and
-// the sums over samples, with S~-bar_k = a_k + b_k c split as
+// one warp per sample for the disturbed rollouts, which also form d_k and
+// w^_k) and reduce (the sums over samples, with S~-bar_k = a_k + b_k c split as
 // a_k = gS~_k - w^_k d_k / lambda, b_k = w^_k / lambda, so that c is only
 // needed in the final merge).
 // All three models are differentiated (the dynamic one through its Heun
@@ -291,6 +291,19 @@ __device__ __forceinline__ float weight_of(const DevParams& p, const BwdArgs& a,
   const double s_tot = a.st->last_sum;
   const float st = s_tilde_of(p, a.S[k], a.cvar[k]);
   return (isfinite(st) && s_tot > 0.0) ? (float)((double)expf((m - st) * p.inv_lambda) / s_tot) : 0.0f;
+}
+
+// d_k = <gV+, U_k> and w^_k of sample k into a.dk, a.wk (one warp; the
+// lanes read U_k's row together and sum it in a fixed shuffle tree)
+__device__ __forceinline__ void softmin_terms(const DevParams& p, const BwdArgs& a, int k, int TN, int lane) {
+  const float* Uk = a.U + (size_t)k * TN;
+  float d = 0.0f;
+  for (int c = lane; c < TN; c += 32) d = fmaf(a.gVp[c], Uk[c], d);
+  d = warp_sum(d);
+  if (lane == 0) {
+    a.dk[k] = d;
+    a.wk[k] = weight_of(p, a, k);
+  }
 }
 
 // lanes per nominal rollout in the adjoint: they carry the same state and
@@ -563,6 +576,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   if (cvbar == 0.0f) {
     for (int c = lane; c < TN; c += 32) a.gUd[(size_t)k * TN + c] = 0.0f;
     if (lane < 4) a.thd[(size_t)k * 4 + lane] = 0.0f;
+    softmin_terms(p, a, k, TN, lane);
     return;
   }
   const float* Uk = a.U + (size_t)k * TN;
@@ -662,6 +676,7 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     const float s = warp_sum(gth[i]);
     if (lane == 0) a.thd[(size_t)k * 4 + i] = s;
   }
+  softmin_terms(p, a, k, TN, lane);
 }
 
 template <int MODEL, bool IS>
@@ -712,8 +727,8 @@ __global__ void __launch_bounds__(128) bwd_main_kernel(const DevParams p, const 
 // lambda, b_k = w^_k / lambda, c = sum_k w^_k d_k) every column is
 // gV+ sum_k mask_k w^_k + sum_k a_k B_k + c sum_k b_k B_k, so one pass over
 // the samples forms the three sums and c, and the last block combines them.
-// A block takes a slice of the samples in chunks of 32: first d_k and w^_k
-// (a warp per sample), then the column sums with kRedRows row lanes per
+// A block takes a slice of the samples in chunks of 32 (d_k and w^_k come
+// from the main kernel): the column sums with kRedRows row lanes per
 // column, in FP64; the last block to arrive merges the slices.  The order
 // depends on K and the grid only.
 constexpr int kRedCols = 64, kRedRows = 4;  // 256 threads
@@ -736,21 +751,15 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const D
   double wd = 0.0;  // thread 0: the slice's sum of w^_k d_k
   for (int k0 = kb; k0 < ke; k0 += kRedChunk) {
     const int n = min(kRedChunk, ke - k0);
-    // d_k = <gV+, U_k> and w^_k, one warp per sample
-    for (int i = warp; i < n; i += kRedCols * kRedRows / 32) {
-      const int k = k0 + i;
-      const float* Uk = a.U + (size_t)k * TN;
-      float d = 0.0f;
-      for (int c = lane; c < TN; c += 32) d = fmaf(a.gVp[c], Uk[c], d);
-      d = warp_sum(d);
-      if (lane == 0) {
-        const float wk = weight_of(p, a, k);
-        const double gs = a.gS != nullptr ? (double)a.gS[k] : 0.0;
-        ch_w[i] = wk;
-        ch_a[i] = gs - (double)wk * (double)d * inv_lam;
-        ch_b[i] = (double)wk * inv_lam;
-        ch_wd[i] = (double)wk * (double)d;
-      }
+    // the chunk's a_k, b_k from d_k and w^_k (formed by the main kernel)
+    if (threadIdx.x < n) {
+      const int k = k0 + threadIdx.x;
+      const float wk = a.wk[k], d = a.dk[k];
+      const double gs = a.gS != nullptr ? (double)a.gS[k] : 0.0;
+      ch_w[threadIdx.x] = wk;
+      ch_a[threadIdx.x] = gs - (double)wk * (double)d * inv_lam;
+      ch_b[threadIdx.x] = (double)wk * inv_lam;
+      ch_wd[threadIdx.x] = (double)wk * (double)d;
     }
     __syncthreads();
     if (threadIdx.x == 0)
@@ -781,6 +790,7 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const D
   double* part = a.red_part + (size_t)blockIdx.x * stride;
 #pragma unroll
   for (int j = 0; j < kRedColIters; ++j) {
+    if (j * kRedCols >= NC) break;  // uniform across the block
     const int c = j * kRedCols + cl;
     acc[0][rl][cl] = R[j];
     acc[1][rl][cl] = P[j];
@@ -799,10 +809,14 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const D
   __threadfence();
   const int nb = (int)gridDim.x;
   __shared__ double c_all;
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
+    // c = sum_k w^_k d_k: the slices' sums, lanes strided over the blocks
+    // (their loads in flight together), then a fixed shuffle tree
     double c = 0.0;
-    for (int b = 0; b < nb; ++b) c += __ldcg(&a.red_part[(size_t)b * stride + 3 * NC]);
-    c_all = c;
+    for (int b = lane; b < nb; b += 32) c += __ldcg(&a.red_part[(size_t)b * stride + 3 * NC]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane == 0) c_all = c;
   }
   __syncthreads();
   const double c = c_all;
@@ -810,6 +824,7 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const D
     const int col = c0 + cl;
     double r = 0.0, pp = 0.0, q = 0.0;
     if (col < NC) {
+#pragma unroll 4
       for (int b = rl; b < nb; b += kRedRows) {
         const double* pb = a.red_part + (size_t)b * stride;
         r += __ldcg(pb + col);

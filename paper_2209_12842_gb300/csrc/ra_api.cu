@@ -45,6 +45,8 @@ struct ra_mppi {
   float* keep_x0 = nullptr;
   float* keep_V = nullptr;
   unsigned int* b_arrive = nullptr;
+  float* b_dk = nullptr;
+  float* b_wk = nullptr;
   float* b_Gnom = nullptr;
   float* b_mask = nullptr;
   float* b_gUd = nullptr;
@@ -252,6 +254,8 @@ void release(ra_mppi* h) {
   cudaFree(h->keep_x0);
   cudaFree(h->keep_V);
   cudaFree(h->b_arrive);
+  cudaFree(h->b_dk);
+  cudaFree(h->b_wk);
   cudaFree(h->b_Gnom);
   cudaFree(h->b_mask);
   cudaFree(h->b_gUd);
@@ -452,6 +456,8 @@ int ra_mppi_create(const ra_mppi_problem* p, int32_t device, ra_mppi_t** out) {
     e = dalloc(&h->keep_x0, 8);
     if (e == cudaSuccess) e = dalloc(&h->keep_V, TN);
     if (e == cudaSuccess) e = dalloc(&h->b_arrive, 2);
+    if (e == cudaSuccess) e = dalloc(&h->b_dk, K);
+    if (e == cudaSuccess) e = dalloc(&h->b_wk, K);
     if (e == cudaSuccess) e = dalloc(&h->b_Gnom, K * TN);
     if (e == cudaSuccess) e = dalloc(&h->b_mask, K * TN);
     if (e == cudaSuccess) e = dalloc(&h->b_gUd, K * TN);
@@ -881,6 +887,8 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.gVp = gV_plus;
   a.gS = gS_tilde;
   a.arrive = h->b_arrive;
+  a.dk = h->b_dk;
+  a.wk = h->b_wk;
   a.Gnom = h->b_Gnom;
   a.mask = h->b_mask;
   a.gUd = h->b_gUd;

@@ -51,6 +51,8 @@ struct BwdArgs {
   DevState* st;
   const float* gVp;     // [T][nu]
   const float* gS;      // [K] or nullptr
+  float* dk;            // [K] d_k = <gV+, U_k>
+  float* wk;            // [K] the softmin weights w^_k
   unsigned int* arrive; // [2] arrival counter of the reduction (the other is spare)
   float* Gnom;          // [K][T][nu]
   float* mask;          // [K][T][nu]
