@@ -768,6 +768,8 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) bwd_reduce_kernel(const D
     for (int j = 0; j < kRedColIters; ++j) {
       const int c = j * kRedCols + cl;
       if (c < NC) {
+        // (unrolled: the loads of several samples are in flight together)
+#pragma unroll 8
         for (int i = rl; i < n; i += kRedRows) {
           const int k = k0 + i;
           float B;

@@ -99,14 +99,28 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
   return make_float2(__fmul_rn(rad, c), __fmul_rn(rad, s));
 }
 
+// ln v of a uniform v in (0, 1] given with w = 1 - v (both exact to one
+// rounding): the hardware logarithm, whose absolute error is about 2^-21,
+// except next to v = 1 (w < 2^-10), where that error would be large against
+// ln v itself and the series log1p(-w) = -w (1 + w/2 + w^2/3 + ...) to the
+// cubic term is exact to the float32 rounding (the next term is below
+// w^4/4 < 2^-40).  Both are formed and one is selected, so a warp never
+// diverges on it.
+__device__ __forceinline__ float log_unit(float v, float w) {
+  const float series = -w * __fmaf_rn(w, __fmaf_rn(w, 0.333333343f, 0.5f), 1.0f);
+  const float hw = __logf(v);
+  return w < 9.765625e-4f ? series : hw;
+}
+
 // The same pair for process noise, where an absolute error of a few 1e-7 in
 // the unit normal is far below the disturbance scale: the angle 2 pi u2 - pi
 // lies in (-pi, pi], where the hardware sine and cosine are accurate to about
 // 2^-21 absolute, and cos(2 pi u2) = -cos(2 pi u2 - pi) (likewise sin).  The
-// radius keeps the accurate logarithm (its error would be amplified by the
-// square root near u1 = 1) and takes the square root as x rsqrt(x).
+// radius takes ln u1 from log_unit with 1 - u1 = (~a + 1/2) 2^-32 from the
+// word (so its error is not amplified by the square root next to u1 = 1) and
+// the square root as x rsqrt(x).
 __device__ __forceinline__ float2 box_muller_process(uint32_t a, uint32_t b) {
-  const float e = -2.0f * logf(u01(a));
+  const float e = -2.0f * log_unit(u01(a), u01(~a));
   const float rad = e > 0.0f ? e * rsqrtf(e) : 0.0f;
   float s, c;
   __sincosf(fmaf(2.0f * kPi, u01(b), -kPi), &s, &c);
@@ -116,7 +130,8 @@ __device__ __forceinline__ float2 box_muller_process(uint32_t a, uint32_t b) {
 // Heavy-tailed slot value from a selector word and a value word.  The value
 // word gives the tail mass v = 2 min(a, 1 - a) of the uniform
 // a = (word + 1/2) 2^-32, computed from the integer so no precision is lost
-// near a = 1, and the sign of a - 1/2.  With the selector at or above
+// near a = 1 (and 1 - v = (r' + 1/2) 2^-31 with r' the 31 low bits of ~r, for
+// log_unit), and the sign of a - 1/2.  With the selector at or above
 // floor(p 2^32): Laplace(0, b) by its inverse CDF, -b ln v.  Below it:
 // N(0, g^2) by Box-Muller from v and the selector itself, which is uniform
 // on [0, floor(p 2^32)) given the branch, as the angle
@@ -127,7 +142,8 @@ __device__ __forceinline__ float mix_value(uint32_t sel, uint32_t word, float b,
   const bool hi = (word >> 31) != 0u;
   const uint32_t r = hi ? ~word : word;
   const float v = __fmaf_rn(__uint2float_rn(r), 4.656612873077393e-10f, 2.3283064365386963e-10f);
-  const float lv = logf(v);
+  const float w = __fmaf_rn(__uint2float_rn(~r & 0x7FFFFFFFu), 4.656612873077393e-10f, 2.3283064365386963e-10f);
+  const float lv = log_unit(v, w);
   const float e = -2.0f * lv;
   const float rad = e > 0.0f ? e * rsqrtf(e) : 0.0f;
   const float u2 = (__uint2float_rn(sel) + 0.5f) * inv_thresh;
@@ -145,7 +161,8 @@ __device__ __forceinline__ float mix_value_is(uint32_t sel, uint32_t word, float
   const bool hi = (word >> 31) != 0u;
   const uint32_t r = hi ? ~word : word;
   const float v = __fmaf_rn(__uint2float_rn(r), 4.656612873077393e-10f, 2.3283064365386963e-10f);
-  const float lv = logf(v);
+  const float w = __fmaf_rn(__uint2float_rn(~r & 0x7FFFFFFFu), 4.656612873077393e-10f, 2.3283064365386963e-10f);
+  const float lv = log_unit(v, w);
   const float e = -2.0f * lv;
   const float rad = e > 0.0f ? e * rsqrtf(e) : 0.0f;
   const float u2 = (__uint2float_rn(sel) + 0.5f) * inv_thresh;
