@@ -335,15 +335,18 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     sincosf(u0, &s, &c);
     return make_float4(p.mp[4] * u0, u1, s, c);
   }
-  // lateral acceleration k sin(C atan z) of one axle (k = D Fz / m).  For
+  // lateral acceleration k sin(C atan z) of one axle (k = D Fz / m).  C15:
+  // 1 for C = 3/2, 0 for any other C, -1 to read it off the parameters (the
+  // sub-step loop below decides once per control step, so the derivatives
+  // carry no branch on it).  For
   // C = 3/2 the shape has the closed form z (q + 2) / (q sqrt(2 q (q + 1))),
   // q = sqrt(1 + z^2) (half-angle identities with cos(atan z) = 1/q; no
   // cancellation near 0).  With s = 1 + z^2, 2 q (q + 1) = 2 (s + q), so it
   // is z (q + 2) (1/q) rsqrt(s + q) / sqrt(2), the 1/sqrt(2) being folded
   // into k on the host.
-  template <class T>
+  template <class T, int C15 = -1>
   __device__ static __forceinline__ T pacejka(const DevParams& p, T z, float k) {
-    if (p.pacejka_c15) {
+    if (C15 == 1 || (C15 < 0 && p.pacejka_c15)) {
       const T s = vfma(z, z, bc<T>(1.0f));
       const T u = vmap(s, rsqrt_hw);  // 1 / q, and q = s u
       const T w = vmap(vfma(s, u, s), rsqrt_hw);  // rsqrt(s + q)
@@ -352,7 +355,7 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     const float C = p.mp[5];
     return vmul(bc<T>(k), vmap(z, [C](float v) { return sinf(C * atanf(v)); }));
   }
-  template <class T>
+  template <class T, int C15 = -1>
   __device__ static __forceinline__ void deriv(const DevParams& p, const T* x, const CtlT<T>& c, T* f) {
     const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], vfloor = p.mp[7];
     const T vx = x[3], vy = x[4], r = x[5];
@@ -361,8 +364,8 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     T tf, tr;
     atan_pair<T>(vmul(vfma(bc<T>(lf), r, vy), inv_vx), vmul(vfma(bc<T>(-lr), r, vy), inv_vx), &tf, &tr);
     // Pacejka arguments B alpha_f = B (steer - atan_f), B alpha_r = -B atan_r
-    const T ay_f = pacejka<T>(p, vfma(bc<T>(-Bt), tf, c.bd), p.acc_f);
-    const T ay_r = pacejka<T>(p, vmul(bc<T>(-Bt), tr), p.acc_r);
+    const T ay_f = pacejka<T, C15>(p, vfma(bc<T>(-Bt), tf, c.bd), p.acc_f);
+    const T ay_r = pacejka<T, C15>(p, vmul(bc<T>(-Bt), tr), p.acc_r);
     T sp, cp;
     vsincos(x[2], &sp, &cp);
     // (negated factors make the products exact negations: a (-b) = -(a b))
@@ -375,20 +378,24 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(-p.yaw_r), ay_r));
   }
   // one Heun sub-step of size h
-  template <class T>
+  template <class T, int C15 = -1>
   __device__ static __forceinline__ void substep_t(const DevParams& p, T* x, const CtlT<T>& c) {
     T k1[6], k2[6], xp[6];
-    deriv<T>(p, x, c, k1);
+    deriv<T, C15>(p, x, c, k1);
 #pragma unroll
     for (int i = 0; i < 6; ++i) xp[i] = vfma(bc<T>(p.h), k1[i], x[i]);
-    deriv<T>(p, xp, c, k2);
+    deriv<T, C15>(p, xp, c, k2);
     const float hh = 0.5f * p.h;
 #pragma unroll
     for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), vadd(k1[i], k2[i]), x[i]);
   }
   template <class T>
   __device__ static __forceinline__ void step_t(const DevParams& p, T* x, const CtlT<T>& c) {
-    for (int s = 0; s < p.substeps; ++s) substep_t<T>(p, x, c);
+    if (p.pacejka_c15) {
+      for (int s = 0; s < p.substeps; ++s) substep_t<T, 1>(p, x, c);
+    } else {
+      for (int s = 0; s < p.substeps; ++s) substep_t<T, 0>(p, x, c);
+    }
   }
   // the derivative with one sample's control quantities
   template <class T>
@@ -429,12 +436,13 @@ struct Model<2> {  // linear test system x+ = x + h u
 };
 
 // ---------------------------------------------------------------- noise
-// Process noise of rollout m of sample k at step t, added to the state:
+// Process noise of rollout m of sample k at step t, added to the state
+// (NT: the noise type fixed at compile time, -1 to read it off p):
 // counter (t | draw << 16, m, k, instance).  IS: every value is multiplied by
 // f (the rollout's proposal factor, 1 or s; f = 1 keeps the bits) and the
 // unit-scale draws are summed into *aL (Laplace magnitudes) and *aG (squared
 // normals) for the importance weight (Gaussian and mixture noise only).
-template <int MODEL, bool IS = false>
+template <int MODEL, bool IS = false, int NT = -1>
 __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k0, uint32_t k1,
                                                   uint32_t t, uint32_t m, uint32_t k, uint32_t instance,
                                                   float* x, float f = 1.0f, float* aL = nullptr,
@@ -465,7 +473,8 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
     }
     return;
   }
-  if (p.noise_type == 0) {
+  const int nt = NT >= 0 ? NT : p.noise_type;
+  if (nt == 0) {
     const uint4 w = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
     const float2 z01 = box_muller_process(w.x, w.y);
     x[Md::slot_dim(0)] = fmaf(p.w_scale[0], z01.x, x[Md::slot_dim(0)]);
@@ -475,7 +484,7 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
       x[Md::slot_dim(2)] = fmaf(p.w_scale[2], z23.x, x[Md::slot_dim(2)]);
       if (Md::NS > 3) x[Md::slot_dim(3)] = fmaf(p.w_scale[3], z23.y, x[Md::slot_dim(3)]);
     }
-  } else if (p.noise_type == 1) {
+  } else if (nt == 1) {
     const uint4 sel = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
     const uint4 val = philox4x32_10(make_uint4(t | (1u << 16), m, k, instance), k0, k1);
     const uint32_t sw[4] = {sel.x, sel.y, sel.z, sel.w};
@@ -485,7 +494,7 @@ __device__ __forceinline__ void add_process_noise(const DevParams& p, uint32_t k
       if (p.w_scale[s] != 0.0f)
         x[Md::slot_dim(s)] += mix_value(sw[s], vw[s], p.w_scale[s], p.mix_gauss[s], p.mix_thresh, p.mix_inv_thresh);
     }
-  } else if (p.noise_type == 2) {
+  } else if (nt == 2) {
     // uniform on [-a_s, a_s]: (2u - 1) a_s
     const uint4 w = philox4x32_10(make_uint4(t, m, k, instance), k0, k1);
     const uint32_t ww[4] = {w.x, w.y, w.z, w.w};

@@ -272,7 +272,7 @@ __device__ __forceinline__ float is_weight(const DevParams& p, const Inst& in, f
 // i < ILP (rows r0, r0 + rstride, ... of the M rollouts); risk costs to Ls
 // (IS: and importance weights to Ws)
 // (ck: this sample's checkpoint block [nseg][NX][M] of the adjoint, or nullptr)
-template <int MODEL, int ILP, bool IS = false, bool WIN = false>
+template <int MODEL, int ILP, bool IS = false, bool WIN = false, int NT = -1>
 __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in, const float* x0, int k, int lane,
                                              int r0, int rstride, const float4* ctl, float* Ls,
                                              const float4* obs_s, int n_obs, float* Ws = nullptr,
@@ -322,8 +322,8 @@ __device__ __forceinline__ void rollouts_ilp(const DevParams& p, const Inst& in,
     }
 #pragma unroll
     for (int i = 0; i < ILP; ++i)
-      add_process_noise<MODEL, IS>(p, in.k0, in.k1, (uint32_t)t, m[i], (uint32_t)k, in.instance, x[i], fis[i],
-                                   &aL[i], &aG[i]);
+      add_process_noise<MODEL, IS, NT>(p, in.k0, in.k1, (uint32_t)t, m[i], (uint32_t)k, in.instance, x[i], fis[i],
+                                       &aL[i], &aG[i]);
   }
 #pragma unroll
   for (int i = 0; i < ILP; ++i)
@@ -360,6 +360,15 @@ __device__ __forceinline__ void run_rollouts(const DevParams& p, const Inst& in,
   for (int i = 0; i < Md::NX; ++i) x0[i] = x0g[i];
   const int R = (in.M + 31) >> 5;
   int r = r_first;
+  // the interleaved rows with the noise type fixed at compile time for the
+  // mixture (the dynamic workloads) and Gaussian noise
+  if (!IS && p.noise_type == 1) {
+    for (; r + (ILP - 1) * r_stride < R; r += ILP * r_stride)
+      rollouts_ilp<MODEL, ILP, IS, WIN, 1>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws, ck);
+  } else if (!IS && p.noise_type == 0) {
+    for (; r + (ILP - 1) * r_stride < R; r += ILP * r_stride)
+      rollouts_ilp<MODEL, ILP, IS, WIN, 0>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws, ck);
+  }
   for (; r + (ILP - 1) * r_stride < R; r += ILP * r_stride)
     rollouts_ilp<MODEL, ILP, IS, WIN>(p, in, x0, k, lane, r, r_stride, ctl, Ls, obs_s, n_obs, Ws, ck);
   if (ILP > 1)
@@ -700,8 +709,12 @@ __device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const 
 // obstacles; a separate instantiation so the others keep their code)
 // CK: store the state checkpoints the adjoint reads (differentiable handles;
 // a separate instantiation, so the others compile without the stores)
+// (at least 3 blocks of 256 threads per SM: 80 registers, 24 resident warps
+// per SM; without the bound the register count of some instances drifts
+// between 64 and 128 with each code change, and the measured kernels are
+// fastest at 80)
 template <int MODEL, int ILP, bool PAIRS = false, bool IS = false, bool WIN = false, bool CK = false>
-__global__ void __launch_bounds__(256) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
+__global__ void __launch_bounds__(256, 3) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
   extern __shared__ float4 smem[];
   // WIN: smem[0].x holds the largest obstacle radius and the obstacles start
   // at smem[1]; otherwise at smem[0].  The samples' controls, costs (and
