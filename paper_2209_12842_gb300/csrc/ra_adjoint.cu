@@ -51,10 +51,11 @@ __device__ __forceinline__ float track_e_grad(const DevParams& p, float px, floa
     return fabsf(py) - p.track_R;
   }
   const float dx = ax - half;
-  const float rho = sqrtf(fmaf(dx, dx, py * py));
-  de[0] = rho > 0.0f ? sgnf(px) * dx / rho : 0.0f;
-  de[1] = rho > 0.0f ? py / rho : 0.0f;
-  return rho - p.track_R;
+  const float r2 = fmaf(dx, dx, py * py);
+  const float ir = r2 > 0.0f ? rsqrtf(r2) : 0.0f;  // hardware 1/rho: a gradient needs no more
+  de[0] = sgnf(px) * dx * ir;
+  de[1] = py * ir;
+  return r2 * ir - p.track_R;
 }
 
 // gradient of the arc length s(x) w.r.t. (px, py)
@@ -67,8 +68,9 @@ __device__ __forceinline__ void track_s_grad(const DevParams& p, float px, float
   }
   const float dx = px > half ? px - half : px + half;
   const float r2 = fmaf(dx, dx, py * py);
-  ds[0] = r2 > 0.0f ? p.track_R * (-py) / r2 : 0.0f;
-  ds[1] = r2 > 0.0f ? p.track_R * dx / r2 : 0.0f;
+  const float ir2 = r2 > 0.0f ? __fdividef(p.track_R, r2) : 0.0f;
+  ds[0] = -py * ir2;
+  ds[1] = dx * ir2;
 }
 
 // The obstacle term at x over the obstacles first, first + stride, ...:
@@ -125,7 +127,7 @@ __device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, un
     }
     if (mask & 8u) {
       const float d = p.track_hw - fabsf(e);
-      const float db = (-100.0f / kPi) / fmaf(1e4f * d, d, 1.0f);
+      const float db = __fdividef(-100.0f / kPi, fmaf(1e4f * d, d, 1.0f));
       const float k = c * p.w_bdry * db * (-sgnf(e));
       g[0] = fmaf(k, de[0], g[0]);
       g[1] = fmaf(k, de[1], g[1]);
@@ -184,7 +186,9 @@ __device__ __forceinline__ void cost_grad_split(const DevParams& p, const float*
 // applied to fb: xb += (df/dx)' fb, gu += (df/du)' fb with u = (steer, accel).
 // The same formulas as the forward: slip angles atan(y / max(vx, floor)),
 // lateral accelerations k sin(C atan(B alpha)) (k = D Fz / m), yaw arms
-// l m / Iz; the derivative values use the library atan, sin and cos.
+// l m / Iz; the derivative values use the library arctangent and the
+// hardware sine, cosine and quotients (errors of a few 1e-7, far inside the
+// adjoint's tolerance).
 __device__ __forceinline__ void dyn_deriv_vjp(const DevParams& p, const float* x, const float4 c, const float* fb,
                                               float* xb, float* gu) {
   const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], C = p.mp[5], vfloor = p.mp[7];
@@ -194,13 +198,15 @@ __device__ __forceinline__ void dyn_deriv_vjp(const DevParams& p, const float* x
   const float sd = c.z, cd = c.w;
   const float vxs = fmaxf(vx, vfloor);
   const float yf = fmaf(lf, r, vy), yr = fmaf(-lr, r, vy);
-  const float tf = atanf(yf / vxs), tr = atanf(yr / vxs);
+  const float ivx = __fdividef(1.0f, vxs);
+  const float tf = atanf(yf * ivx), tr = atanf(yr * ivx);
   const float zf = fmaf(-Bt, tf, c.x), zr = -Bt * tr;
   const float qf = C * atanf(zf), qr = C * atanf(zr);
-  const float ayf = kf * sinf(qf), ayr = kr * sinf(qr);
-  const float dsf = C * cosf(qf) / fmaf(zf, zf, 1.0f), dsr = C * cosf(qr) / fmaf(zr, zr, 1.0f);
+  // (hardware sine, cosine and quotients: a gradient needs no more)
+  const float ayf = kf * __sinf(qf), ayr = kr * __sinf(qr);
+  const float dsf = __fdividef(C * __cosf(qf), fmaf(zf, zf, 1.0f)), dsr = __fdividef(C * __cosf(qr), fmaf(zr, zr, 1.0f));
   float sp, cp;
-  sincosf(psi, &sp, &cp);
+  heading_sincos(psi, &sp, &cp);
   // f0 = vx cos psi - vy sin psi, f1 = vx sin psi + vy cos psi, f2 = r
   xb[2] += fb[0] * (-vx * sp - vy * cp) + fb[1] * (vx * cp - vy * sp);
   xb[3] += fb[0] * cp + fb[1] * sp - fb[4] * r;
@@ -216,8 +222,9 @@ __device__ __forceinline__ void dyn_deriv_vjp(const DevParams& p, const float* x
   gu[0] += Bt * zfb;
   const float tfb = -Bt * zfb, trb = -Bt * zrb;
   const float nf = fmaf(vxs, vxs, yf * yf), nr = fmaf(vxs, vxs, yr * yr);
-  const float yfb = tfb * vxs / nf, yrb = trb * vxs / nr;
-  const float vxsb = -tfb * yf / nf - trb * yr / nr;
+  const float inf_ = __fdividef(1.0f, nf), inr = __fdividef(1.0f, nr);
+  const float yfb = tfb * vxs * inf_, yrb = trb * vxs * inr;
+  const float vxsb = -tfb * yf * inf_ - trb * yr * inr;
   xb[4] += yfb + yrb;
   xb[5] += lf * yfb - lr * yrb;
   if (vx > vfloor) xb[3] += vxsb;
@@ -232,7 +239,7 @@ __device__ __forceinline__ void substep_vjp(const DevParams& p, const float* s, 
     heading_sincos(s[2], &sp, &cp);
     const float h = p.h, v = s[3], L = p.mp[0];
     const float tl = c.z * L;                 // tan(steer)
-    const float sec2_over_L = fmaf(tl, tl, 1.0f) / L;
+    const float sec2_over_L = __fdividef(fmaf(tl, tl, 1.0f), L);
     const float l0 = lam[0], l1 = lam[1], l2 = lam[2], l3 = lam[3];
     lam[2] = l2 + h * v * (cp * l1 - sp * l0);
     lam[3] = l3 + h * (cp * l0 + sp * l1 + c.z * l2);
