@@ -125,7 +125,7 @@ __device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, un
       g[1] = fmaf(k, de[1], g[1]);
       gth[0] = fmaf(c, e * e, gth[0]);
     }
-    if (mask & 8u) {
+    if ((mask & 8u) && p.w_bdry != 0.0f) {  // (the boundary weight is not among theta)
       const float d = p.track_hw - fabsf(e);
       const float db = __fdividef(-100.0f / kPi, fmaf(1e4f * d, d, 1.0f));
       const float k = c * p.w_bdry * db * (-sgnf(e));
@@ -147,39 +147,6 @@ __device__ __forceinline__ void cost_grad(const DevParams& p, const float* x, un
     gth[3] = fmaf(c, val, gth[3]);
   }
   if (mask & 16u) g[0] = fmaf(c, p.c_lin, g[0]);
-}
-
-// cost_grad for one state held by `lpr` lanes (an aligned group of the warp,
-// sub = 0 .. lpr - 1; every lane of the warp calls it with the same lpr):
-// the obstacles split over the group and their slopes summed by shuffles, so
-// g stays the same on every lane of the group; the other terms on every lane,
-// their theta partials kept on sub = 0 only, and each lane keeps its share of
-// the obstacle values (a sum over the group adds them up)
-template <int MODEL>
-__device__ __forceinline__ void cost_grad_split(const DevParams& p, const float* x, unsigned mask, float c,
-                                                const float4* __restrict__ obs, int n_obs, int sub, int lpr,
-                                                float* g, float* gth) {
-  if (lpr == 1) {
-    cost_grad<MODEL>(p, x, mask, c, obs, n_obs, g, gth);
-    return;
-  }
-  float gt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  cost_grad<MODEL>(p, x, mask & ~4u, c, obs, n_obs, g, gt);
-  const float keep = sub == 0 ? 1.0f : 0.0f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) gth[i] = fmaf(keep, gt[i], gth[i]);
-  if (MODEL != 2 && (mask & 4u)) {
-    float val = 0.0f, g0 = 0.0f, g1 = 0.0f;
-    obstacle_grad_part(p, x, obs, n_obs, sub, lpr, val, g0, g1);
-    for (int o = 1; o < lpr; o <<= 1) {
-      g0 += __shfl_xor_sync(0xFFFFFFFFu, g0, o);
-      g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, o);
-    }
-    if (p.obs_mode != 0) val *= p.inv_kappa;
-    g[0] = fmaf(c * p.w_obs, g0, g[0]);
-    g[1] = fmaf(c * p.w_obs, g1, g[1]);
-    gth[3] = fmaf(c, val, gth[3]);
-  }
 }
 
 // Transposed Jacobians of the dynamic model's derivative f(x, u) at x
@@ -322,11 +289,38 @@ constexpr int kNomLanes = 4;
 template <int MODEL>
 constexpr int nom_lanes() { return MODEL == 1 ? 1 : kNomLanes; }
 
-// Per warp, the states of the segments being reversed: 32 lanes x 8 steps x
-// NX floats, whatever the lanes per rollout (32 / lpr rollouts of lpr
-// segments each).
+// Per warp, the steps of the segments being reversed: 32 lanes x 8 steps x
+// (2 NX + 2 NU) floats, whatever the lanes per rollout (32 / lpr rollouts of
+// lpr segments each).  Per step: the state x_t, the control u_t and mean
+// control v_t (nominal chains), and the cost gradient g_t.
 template <int MODEL>
-constexpr int xbuf_floats() { return 32 * kSeg * Model<MODEL>::NX; }
+constexpr int step_floats() { return 2 * Model<MODEL>::NX + 2 * Model<MODEL>::NU; }
+template <int MODEL>
+constexpr int xbuf_floats() { return 32 * kSeg * step_floats<MODEL>(); }
+
+// The cost gradients of steps [tb0, tb1) held in buf (stride step_floats):
+// c d(cost terms in mask)/dx at x_t into the step's g_t, the theta partials
+// into gth.  They do not depend on the adjoint state, so the L lanes of a
+// group split the steps (lane sub takes t = tb0 + sub, tb0 + sub + L, ...)
+// and the serial reverse sweep only adds them.
+template <int MODEL>
+__device__ __forceinline__ void step_cost_grads(const DevParams& p, float* buf, int tb0, int tb1, int sub, int L,
+                                                unsigned mask, float c, const float4* __restrict__ obs, int n_obs,
+                                                float* gth) {
+  constexpr int NX = Model<MODEL>::NX, SW = step_floats<MODEL>(), GO = NX + 2 * Model<MODEL>::NU;
+  for (int t = tb0 + sub; t < tb1; t += L) {
+    float* st = buf + (t - tb0) * SW;
+    float x[NX], g[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      x[i] = st[i];
+      g[i] = 0.0f;
+    }
+    cost_grad<MODEL>(p, x, mask, c, obs, n_obs, g, gth);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) st[GO + i] = g[i];
+  }
+}
 
 // nominal sample k, reversed by nom_lanes lanes (sub = 0 .. nom_lanes - 1;
 // all 32 lanes of the warp take part, a lane past K on a copy of sample
@@ -345,7 +339,8 @@ __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a
   constexpr int NX = Md::NX, NU = Md::NU, NL = nom_lanes<MODEL>();
   const int T = in.T, TN = T * NU;
   const int nseg = (T + kSeg - 1) / kSeg;
-  float* gbuf = xbuf + ((threadIdx.x & 31) / NL) * (NL * kSeg * NX);
+  constexpr int SW = step_floats<MODEL>(), GO = NX + 2 * NU;  // per step: x_t, u_t, v_t, g_t
+  float* gbuf = xbuf + ((threadIdx.x & 31) / NL) * (NL * kSeg * SW);
   const float sbar = 1.0f;  // unit cotangent: the reduction scales by S~-bar_k
   const float* Uk = a.U + (size_t)k * TN;
   const float* ck = a.ck_nom + (size_t)k * (nseg + 1) * NX;
@@ -362,52 +357,72 @@ __device__ void bwd_nominal(const DevParams& p, const Inst& in, const BwdArgs& a
   }
   for (int shi = nseg - 1; shi >= 0; shi -= NL) {
     const int slo = max(0, shi - NL + 1);
+    const int tb0 = slo * kSeg, tb1 = min(T, (shi + 1) * kSeg);
     const int sr = slo + sub;
     if (sr <= shi) {
+      const int t0 = sr * kSeg, t1 = min(T, t0 + kSeg);
+      float* dst = gbuf + (t0 - tb0) * SW;
+      // the segment's controls and mean controls first: independent loads,
+      // in flight together, and the reverse reads them from shared memory
+      for (int t = t0; t < t1; ++t) {
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          dst[(t - t0) * SW + NX + j] = Uk[t * NU + j];
+          dst[(t - t0) * SW + NX + NU + j] = a.V[t * NU + j];
+        }
+      }
       float x[NX];
 #pragma unroll
       for (int i = 0; i < NX; ++i) x[i] = ck[sr * NX + i];
-      const int t0 = sr * kSeg, t1 = min(T, t0 + kSeg);
-      float* dst = gbuf + (sr - slo) * kSeg * NX;
       for (int t = t0; t < t1; ++t) {
 #pragma unroll
-        for (int i = 0; i < NX; ++i) dst[(t - t0) * NX + i] = x[i];
-        if (t + 1 < t1) Md::step(p, x, Md::ctl(p, Uk[t * NU], NU > 1 ? Uk[t * NU + 1] : 0.0f));
+        for (int i = 0; i < NX; ++i) dst[(t - t0) * SW + i] = x[i];
+        if (t + 1 < t1)
+          Md::step(p, x, Md::ctl(p, dst[(t - t0) * SW + NX], NU > 1 ? dst[(t - t0) * SW + NX + 1] : 0.0f));
       }
     }
     __syncwarp();
-    for (int sg = shi; sg >= slo; --sg) {
-      const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
-      const float* src = gbuf + (sg - slo) * kSeg * NX;
-      for (int t = t1 - 1; t >= t0; --t) {
-        float xs[NX];
+    // the cost gradients of the batch's steps, split over the group's lanes,
+    // with the control cost's theta partial gamma v_t' S^-1 u_t
+    step_cost_grads<MODEL>(p, gbuf, tb0, tb1, sub, NL, 0xFFFFFFFFu, sbar, obs_s, n_obs, gth);
+    for (int t = tb0 + sub; t < tb1; t += NL) {
+      const float* st = gbuf + (t - tb0) * SW;
+      gth[2] = fmaf(sbar, st[NX + NU] * p.inv_sig2[0] * st[NX] +
+                              (NU > 1 ? st[NX + NU + 1] * p.inv_sig2[1] * st[NX + 1] : 0.0f), gth[2]);
+    }
+    __syncwarp();
+    // the serial reverse sweep: lam_t = (dF/dx)' lam_{t+1} + g_t
+    for (int t = tb1 - 1; t >= tb0; --t) {
+      const float* st = gbuf + (t - tb0) * SW;
+      float xs[NX];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) xs[i] = src[(t - t0) * NX + i];
-        const float u0 = Uk[t * NU], u1 = NU > 1 ? Uk[t * NU + 1] : 0.0f;
-        float gu[2] = {0.0f, 0.0f};
-        step_vjp<MODEL>(p, xs, Md::ctl(p, u0, u1), lam, gu);
-        cost_grad_split<MODEL>(p, xs, 0xFFFFFFFFu, sbar, obs_s, n_obs, sub, NL, lam, gth);
-        // control cost gamma v_t' S^-1 u_t and the clip of U = clip(V + eps)
-        const float v0 = a.V[t * NU], v1 = NU > 1 ? a.V[t * NU + 1] : 0.0f;
-        const float vv[2] = {v0, v1}, uu[2] = {u0, u1};
-        gth[2] = fmaf(sbar, v0 * p.inv_sig2[0] * u0 + (NU > 1 ? v1 * p.inv_sig2[1] * u1 : 0.0f), gth[2]);
+      for (int i = 0; i < NX; ++i) xs[i] = st[i];
+      const float u0 = st[NX], u1 = NU > 1 ? st[NX + 1] : 0.0f;
+      float gu[2] = {0.0f, 0.0f};
+      step_vjp<MODEL>(p, xs, Md::ctl(p, u0, u1), lam, gu);
 #pragma unroll
-        for (int j = 0; j < NU; ++j) {
-          const float msk = (warm && uu[j] > p.u_lo[j] && uu[j] < p.u_hi[j]) ? 1.0f : 0.0f;
-          const float gc = p.gamma * p.inv_sig2[j];
-          const size_t idx = (size_t)k * TN + t * NU + j;
-          if (writes && sub == 0) {
-            a.mask[idx] = msk;
-            a.Gnom[idx] = msk * (gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
-          }
+      for (int i = 0; i < NX; ++i) lam[i] += st[GO + i];
+      // the clip of U = clip(V + eps) and the control cost
+      const float vv[2] = {st[NX + NU], NU > 1 ? st[NX + NU + 1] : 0.0f}, uu[2] = {u0, u1};
+#pragma unroll
+      for (int j = 0; j < NU; ++j) {
+        const float msk = (warm && uu[j] > p.u_lo[j] && uu[j] < p.u_hi[j]) ? 1.0f : 0.0f;
+        const float gc = p.gamma * p.inv_sig2[j];
+        const size_t idx = (size_t)k * TN + t * NU + j;
+        if (writes && sub == 0) {
+          a.mask[idx] = msk;
+          a.Gnom[idx] = msk * (gu[j] + sbar * gc * vv[j]) + sbar * gc * uu[j];
         }
       }
     }
     __syncwarp();
   }
-  // the obstacle values are split over the group; the other partials are whole on sub = 0
+  // the theta partials are split over the group's lanes (by step)
 #pragma unroll
-  for (int o = 1; o < nom_lanes<MODEL>(); o <<= 1) gth[3] += __shfl_xor_sync(0xFFFFFFFFu, gth[3], o);
+  for (int o = 1; o < nom_lanes<MODEL>(); o <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) gth[i] += __shfl_xor_sync(0xFFFFFFFFu, gth[i], o);
+  }
   if (writes && sub == 0) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) a.thn[(size_t)k * 4 + i] = gth[i];
@@ -605,13 +620,14 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
   else n_act = bwd_tail<IS, (RA_MPPI_MAX_M_DEV + 31) / 32>(p, in, lane, cvbar, Ls, Ws, act);
   // reverse sweep of every rollout with a nonzero weight.  A short list (a
   // CVaR tail) would leave lanes idle, so each rollout gets lpr lanes that
-  // split its obstacle terms (32 / lpr rollouts per pass) and replay up to
-  // lpr of its segments at once from the forward's checkpoints
+  // replay up to lpr of its segments at once from the forward's checkpoints
+  // and split the steps' cost gradients (32 / lpr rollouts per pass)
   const int lpr = MODEL == 1 ? 1 : (n_act <= 8 ? 4 : (n_act <= 16 ? 2 : 1));  // as nom_lanes
   const int slots = 32 / lpr, slot = lane / lpr, sub = lane % lpr;
   const int nseg = (T + kSeg - 1) / kSeg;
   const float* ckk = a.ck_dist + (size_t)k * nseg * NX * M;
-  float* gbuf = xbuf + slot * (lpr * kSeg * NX);
+  constexpr int SW = step_floats<MODEL>(), GO = NX + 2 * NU;  // per step: x_t, (unused u, v), g_t
+  float* gbuf = xbuf + slot * (lpr * kSeg * SW);
   // the control cotangents: with room for a row per slot (32 T nu floats,
   // T nu <= kGusSlotCols), each group's first lane adds into its own row and
   // the rows are summed once at the end in a fixed order; otherwise a warp
@@ -627,16 +643,17 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
     for (int i = 0; i < NX; ++i) lam[i] = 0.0f;
     for (int shi = nseg - 1; shi >= 0; shi -= lpr) {
       const int slo = max(0, shi - lpr + 1);
+      const int tb0 = slo * kSeg, tb1 = min(T, (shi + 1) * kSeg);
       const int sr = slo + sub;
       if (sr <= shi) {
         float x[NX];
 #pragma unroll
         for (int i = 0; i < NX; ++i) x[i] = ckk[((size_t)sr * NX + i) * M + m];
         const int t0 = sr * kSeg, t1 = min(T, t0 + kSeg);
-        float* dst = gbuf + (sr - slo) * kSeg * NX;
+        float* dst = gbuf + (t0 - tb0) * SW;
         for (int t = t0; t < t1; ++t) {
 #pragma unroll
-          for (int i = 0; i < NX; ++i) dst[(t - t0) * NX + i] = x[i];
+          for (int i = 0; i < NX; ++i) dst[(t - t0) * SW + i] = x[i];
           if (t + 1 < t1) {
             Md::step(p, x, ctl[t]);
             replay_noise<MODEL, IS>(p, in, t, m, k, x);
@@ -644,27 +661,29 @@ __device__ void bwd_disturbed(const DevParams& p, const Inst& in, const BwdArgs&
         }
       }
       __syncwarp();
-      for (int sg = shi; sg >= slo; --sg) {
-        const int t0 = sg * kSeg, t1 = min(T, t0 + kSeg);
-        const float* src = gbuf + (sg - slo) * kSeg * NX;
-        for (int t = t1 - 1; t >= t0; --t) {
-          float xs[NX];
+      // the risk-cost gradients of the batch's steps, split over the group's lanes
+      step_cost_grads<MODEL>(p, gbuf, tb0, tb1, sub, lpr, p.risk_mask, lbar, obs_s, n_obs, gth);
+      __syncwarp();
+      // the serial reverse sweep: lam_t = (dF/dx)' lam_{t+1} + g_t
+      for (int t = tb1 - 1; t >= tb0; --t) {
+        const float* st = gbuf + (t - tb0) * SW;
+        float xs[NX];
 #pragma unroll
-          for (int i = 0; i < NX; ++i) xs[i] = src[(t - t0) * NX + i];
-          float gu[2] = {0.0f, 0.0f};
-          step_vjp<MODEL>(p, xs, ctl[t], lam, gu);
-          cost_grad_split<MODEL>(p, xs, p.risk_mask, lbar, obs_s, n_obs, sub, lpr, lam, gth);
-          if (slot_rows) {
-            if (sub == 0 && has) {
+        for (int i = 0; i < NX; ++i) xs[i] = st[i];
+        float gu[2] = {0.0f, 0.0f};
+        step_vjp<MODEL>(p, xs, ctl[t], lam, gu);
 #pragma unroll
-              for (int j = 0; j < NU; ++j) gus[slot * TN + t * NU + j] += gu[j];
-            }
-          } else {
+        for (int i = 0; i < NX; ++i) lam[i] += st[GO + i];
+        if (slot_rows) {
+          if (sub == 0 && has) {
 #pragma unroll
-            for (int j = 0; j < NU; ++j) {
-              const float s = warp_sum(sub == 0 ? gu[j] : 0.0f);  // one copy per rollout
-              if (lane == 0) gus[t * NU + j] += s;
-            }
+            for (int j = 0; j < NU; ++j) gus[slot * TN + t * NU + j] += gu[j];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NU; ++j) {
+            const float s = warp_sum(sub == 0 ? gu[j] : 0.0f);  // one copy per rollout
+            if (lane == 0) gus[t * NU + j] += s;
           }
         }
       }

@@ -901,12 +901,13 @@ int ra_mppi_backward(ra_mppi_t* h, const float* gV_plus, const float* gS_tilde, 
   a.nb_nom = (p.K + 32 * kBwdWarps - 1) / (32 * kBwdWarps);
   a.obs_cap = h->obs_cap;
   const int nb_dist = (p.K + kBwdWarps - 1) / kBwdWarps;
-  // per warp: the states of the segments being reversed (32 x 8 steps x nx),
+  // per warp: the steps of the segments being reversed (32 x 8 steps x
+  // (2 nx + 2 nu): state, control, mean control, cost gradient),
   // then controls, risk costs, importance weights (when on), packed rollout
   // indices, U cotangents
   // (the U cotangents: a row per slot, 32 T nu floats, when T nu <= 128)
   const size_t TNb = (size_t)p.T * h->nu, gcap = TNb <= 128 ? 32 * TNb : TNb;
-  const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * 32 * 8 * h->nx * sizeof(float) +
+  const size_t smem = (size_t)h->obs_cap * sizeof(float4) + (size_t)kBwdWarps * 32 * 8 * (2 * h->nx + 2 * h->nu) * sizeof(float) +
                       (size_t)kBwdWarps * p.T * sizeof(float4) +
                       (size_t)kBwdWarps * (p.M * (importance(h) ? 3 : 2) + gcap) * sizeof(float);
   const cudaError_t e = ramppi::launch_backward(p.model, h->dp, a, nb_dist, smem, h->nb_red,

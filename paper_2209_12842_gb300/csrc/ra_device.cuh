@@ -597,7 +597,7 @@ __device__ __forceinline__ float state_cost(const DevParams& p, const float* x, 
   if (mask & 9u) {  // deviation or boundary needs e(x)
     const float e = track_e(p, x[0], x[1]);
     if (mask & 1u) c = fmaf(p.w_dev, e * e, c);
-    if (mask & 8u) {
+    if ((mask & 8u) && p.w_bdry != 0.0f) {
       const float d = p.track_hw - fabsf(e);
       const float b = atanf(-100.0f * d) * (1.0f / kPi) + 0.5f;
       c = fmaf(p.w_bdry, fmaxf(b, 0.0f), c);
