@@ -60,16 +60,26 @@ LANES_PER_SM = 128
 PHILOX_INT = 60  # 10 rounds x (2 wide multiplies, 2 three-input xors, 2 key adds)
 
 
+DYN_DERIV_FP32 = 1 + 4 + 1 + 18 + 2 + 10 + 1 + 11
+DYN_SUBSTEP_FP32 = 2 * DYN_DERIV_FP32 + 18
+
+
 def _dyn_substep():
     """One Heun sub-step of the dynamic single-track model (Model<1>):
     two derivative evaluations and the trapezoid update.  Per derivative:
     the floored 1/vx (1 fp32 + rcp), slip arguments (4), the warp's range
     vote (1), two arctangent polynomials (2 x 9), Pacejka arguments (2), two
-    closed-form C = 3/2 shapes (2 x (7 fp32 + 2 rsqrt)), the heading sincos
-    (5 fp32 + sin + cos) and the six derivatives (11)."""
-    deriv_fp32 = 1 + 4 + 1 + 18 + 2 + 14 + 5 + 11
-    deriv_xu = 1 + 4 + 2
-    return dict(fp32=2 * deriv_fp32 + 18, xu=2 * deriv_xu, int=0)
+    closed-form C = 3/2 shapes (2 x (5 fp32 + 2 rsqrt)), the heading sincos
+    of a heading near [-pi, pi] (its argument scaling, 1 fp32, + sin + cos)
+    and the six derivatives (11)."""
+    return dict(fp32=DYN_SUBSTEP_FP32, xu=2 * (1 + 4 + 2), int=0)
+
+
+def _dyn_step_extra(ilp):
+    """Once per control step of the dynamic model: the heading wrapped to
+    [-pi, pi] (4 fp32) and the front axle's two control terms (2 fp32, shared
+    by the ILP rollouts of a lane)."""
+    return 4 + 2 / ilp
 
 
 def _kin_substep():
@@ -105,6 +115,7 @@ def pipe_counts(p, tested=None, ilp=1, paired=False):
     ind = int(p["obs_mode"]) == 0
     if model == 1:
         step = {k: v * sub for k, v in _dyn_substep().items()}
+        step["fp32"] += _dyn_step_extra(ilp)
     elif model == 0:
         step = {k: v * sub for k, v in _kin_substep().items()}
     else:
@@ -174,7 +185,7 @@ def adjoint_counts(p):
         # the sub-steps recomputed from the step's start (sub (sub - 1) / 2),
         # then per sub-step one derivative and two transposed derivatives
         # (each about 80 fp32, 10 special-function operations)
-        vjp = dict(fp32=(sub * (sub - 1) // 2) * 130 + sub * (56 + 2 * 80 + 18),
+        vjp = dict(fp32=(sub * (sub - 1) // 2) * DYN_SUBSTEP_FP32 + sub * (DYN_DERIV_FP32 + 2 * 80 + 18),
                    xu=(sub * (sub - 1) // 2) * 14 + sub * (7 + 2 * 10), int=0)
     elif model == 0:
         fwd = {k: v * sub for k, v in _kin_substep().items()}

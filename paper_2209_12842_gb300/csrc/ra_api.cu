@@ -178,6 +178,7 @@ DevParams make_params(const ra_mppi_problem& p) {
     d.acc_r = (float)(D * g * lf / (lf + lr) * fold);
     d.yaw_f = (float)(lf * m / Iz);
     d.yaw_r = (float)(lr * m / Iz);
+    d.nyaw_acc_r = (float)(-(double)d.yaw_r * (double)d.acc_r);
   }
   for (int j2 = 0; j2 < 2; ++j2) {
     d.sigma_u[j2] = p.sigma_u[j2];

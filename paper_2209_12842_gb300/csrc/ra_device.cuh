@@ -27,6 +27,7 @@ struct DevParams {
   int pacejka_c15;    // Pacejka shape factor C is exactly 3/2 (closed form below)
   float acc_f, acc_r;  // D Fz / m per axle (times 1/sqrt(2) when pacejka_c15)
   float yaw_f, yaw_r;  // l_f m / Iz, l_r m / Iz
+  float nyaw_acc_r;    // -yaw_r acc_r: rear shape to yaw acceleration
   float sigma_u[2], inv_sig2[2], u_lo[2], u_hi[2];
   float w_scale[4];
   uint32_t mix_thresh;    // floor(mix_p 2^32): Gaussian branch iff selector word < it
@@ -234,47 +235,81 @@ __device__ __forceinline__ void vsincos(float2 a, float2* s, float2* c) {
   __sincosf(r.y, &s->y, &c->y);
 }
 
+// The heading reduced to [-pi, pi] by the same two-constant split (once per
+// control step of the dynamic model, so that its sub-steps can take the
+// hardware sine and cosine directly: their argument is scaled by 1/(2 pi) in
+// float32, and a heading within a few tenths of a radian of [-pi, pi] keeps
+// the absolute error near 2^-21).  A heading already in [-pi, pi] is
+// returned unchanged (n = 0).
+__device__ __forceinline__ float vwrap(float a) {
+  const float n = rintf(__fmul_rn(a, 0.15915494309189535f));
+  return __fmaf_rn(n, 1.7484556e-7f, __fmaf_rn(n, -6.28318548202514648f, a));
+}
+__device__ __forceinline__ float2 vwrap(float2 a) {
+  const float2 y = vmul(a, bc<float2>(0.15915494309189535f));
+  const float2 n = make_float2(rintf(y.x), rintf(y.y));
+  return vfma(n, bc<float2>(1.7484556e-7f), vfma(n, bc<float2>(-6.28318548202514648f), a));
+}
+// sin and cos of a heading near [-pi, pi] (see vwrap)
+__device__ __forceinline__ void vsincos_near(float a, float* s, float* c) { __sincosf(a, s, c); }
+__device__ __forceinline__ void vsincos_near(float2 a, float2* s, float2* c) {
+  __sincosf(a.x, &s->x, &c->x);
+  __sincosf(a.y, &s->y, &c->y);
+}
+
 // The per-step control quantities of the dynamic model in the lane type T:
-// B steer, accel, sin steer, -sin steer, cos steer.  For T = float2 they are
-// either the same for both halves (two rollouts of one sample) or the two
-// samples' own (one rollout each of two samples).
+// B steer, accel, and the front axle's -acc_f sin steer and acc_f cos steer
+// (its lateral acceleration per unit tyre shape along the body x and y
+// axes).  For T = float2 they are either the same for both halves (two
+// rollouts of one sample) or the two samples' own (one rollout each of two
+// samples).
 template <class T>
 struct CtlT {
-  T bd, a, sd, nsd, cd;
+  T bd, a, kns, kc;
 };
-__device__ __forceinline__ CtlT<float> ctl_of(const float4 c, float) { return {c.x, c.y, c.z, -c.z, c.w}; }
-__device__ __forceinline__ CtlT<float2> ctl_of(const float4 c, float2) {
-  return {bc<float2>(c.x), bc<float2>(c.y), bc<float2>(c.z), bc<float2>(-c.z), bc<float2>(c.w)};
+__device__ __forceinline__ CtlT<float> ctl_of(const DevParams& p, const float4 c, float) {
+  return {c.x, c.y, __fmul_rn(-p.acc_f, c.z), __fmul_rn(p.acc_f, c.w)};
 }
-__device__ __forceinline__ CtlT<float2> ctl_pair(const float4 ca, const float4 cb) {
-  return {make_float2(ca.x, cb.x), make_float2(ca.y, cb.y), make_float2(ca.z, cb.z), make_float2(-ca.z, -cb.z),
-          make_float2(ca.w, cb.w)};
+__device__ __forceinline__ CtlT<float2> ctl_of(const DevParams& p, const float4 c, float2) {
+  const CtlT<float> q = ctl_of(p, c, 0.0f);
+  return {bc<float2>(q.bd), bc<float2>(q.a), bc<float2>(q.kns), bc<float2>(q.kc)};
+}
+__device__ __forceinline__ CtlT<float2> ctl_pair(const DevParams& p, const float4 ca, const float4 cb) {
+  const CtlT<float> a = ctl_of(p, ca, 0.0f), b = ctl_of(p, cb, 0.0f);
+  return {make_float2(a.bd, b.bd), make_float2(a.a, b.a), make_float2(a.kns, b.kns), make_float2(a.kc, b.kc)};
 }
 
 // arctangent for the slip angles: z P(z^2) on [0, 1] with P of degree 7 in
 // z^2 (coefficients fitted here by iterated weighted least squares on
 // Chebyshev nodes for the relative error; max 2.5e-7 in float32), reflected
-// as pi/2 - atan(1/|z|) above 1, odd in z.
+// as pi/2 - atan(1/|z|) above 1, odd in z.  atan_coef(i) multiplies z^(2i).
+__device__ __forceinline__ constexpr float atan_coef(int i) {
+  return i == 0 ? 9.999998808e-01f
+       : i == 1 ? -3.333199322e-01f
+       : i == 2 ? 1.996973604e-01f
+       : i == 3 ? -1.401953697e-01f
+       : i == 4 ? 9.914427996e-02f
+       : i == 5 ? -5.948816240e-02f
+       : i == 6 ? 2.425358072e-02f
+                : -4.693589173e-03f;
+}
+// P(s) by Horner (the coefficients as immediates)
 template <class T>
-__device__ __forceinline__ T atan_core(T t) {  // |t| <= 1
-  const T s = vmul(t, t);
-  T q = bc<T>(-4.693589173e-03f);
-  q = vfma(q, s, bc<T>(2.425358072e-02f));
-  q = vfma(q, s, bc<T>(-5.948816240e-02f));
-  q = vfma(q, s, bc<T>(9.914427996e-02f));
-  q = vfma(q, s, bc<T>(-1.401953697e-01f));
-  q = vfma(q, s, bc<T>(1.996973604e-01f));
-  q = vfma(q, s, bc<T>(-3.333199322e-01f));
-  q = vfma(q, s, bc<T>(9.999998808e-01f));
-  return vmul(t, q);
+__device__ __forceinline__ T atan_q(T s) {
+  T q = bc<T>(atan_coef(7));
+#pragma unroll
+  for (int i = 6; i >= 0; --i) q = vfma(q, s, bc<T>(atan_coef(i)));
+  return q;
 }
 __device__ __forceinline__ float atan_poly(float z) {
   const float a = fabsf(z);
   const bool big = a > 1.0f;
-  float r = atan_core<float>(big ? __fdividef(1.0f, a) : a);
+  const float t = big ? __fdividef(1.0f, a) : a;
+  float r = vmul(t, atan_q<float>(vmul(t, t)));
   r = big ? __fadd_rn(1.57079632679489662f, -r) : r;
   return copysignf(r, z);
 }
+
 // Two arctangents at once (of T, so up to four rollouts' worth).  When no
 // active lane has an argument above 1 in magnitude (the common case), the
 // warp skips the reflection; z P(z^2) with the odd z equals
@@ -286,12 +321,24 @@ __device__ __forceinline__ float atan_poly(float z) {
 template <class T>
 __device__ __forceinline__ void atan_pair(T za, T zb, T* ta, T* tb) {
   if (__all_sync(__activemask(), fmaxf(vmaxabs(za), vmaxabs(zb)) <= 1.0f)) {
-    *ta = atan_core<T>(za);
-    *tb = atan_core<T>(zb);
+    *ta = vmul(za, atan_q<T>(vmul(za, za)));
+    *tb = vmul(zb, atan_q<T>(vmul(zb, zb)));
   } else {
     *ta = vmap(za, atan_poly);
     *tb = vmap(zb, atan_poly);
   }
+}
+// Both axles' Pacejka arguments from the slip ratios yf, yr:
+// zf = B steer - B atan(yf), zr = -B atan(yr).  (Folding -B into the
+// polynomial's coefficients saves two operations but takes them from the
+// parameter bank instead of immediates; on GB300 that was slower.)
+template <class T>
+__device__ __forceinline__ void pacejka_args(const DevParams& p, T yf, T yr, T bd, T* zf, T* zr) {
+  T tf, tr;
+  atan_pair<T>(yf, yr, &tf, &tr);
+  const float Bt = p.mp[4];
+  *zf = vfma(bc<T>(-Bt), tf, bd);
+  *zr = vmul(bc<T>(-Bt), tr);
 }
 
 // ---------------------------------------------------------------- models
@@ -322,6 +369,8 @@ struct Model<0> {  // kinematic bicycle, explicit Euler
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
     for (int s = 0; s < p.substeps; ++s) substep(p, x, c);
   }
+  // the plant's step (the same: every sub-step reduces the heading itself)
+  __device__ static __forceinline__ void step_exact(const DevParams& p, float* x, const float4 c) { step(p, x, c); }
   __device__ static __forceinline__ float speed(const float* x) { return x[3]; }
 };
 
@@ -335,86 +384,98 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     sincosf(u0, &s, &c);
     return make_float4(p.mp[4] * u0, u1, s, c);
   }
-  // lateral acceleration k sin(C atan z) of one axle (k = D Fz / m).  C15:
-  // 1 for C = 3/2, 0 for any other C, -1 to read it off the parameters (the
-  // sub-step loop below decides once per control step, so the derivatives
-  // carry no branch on it).  For
-  // C = 3/2 the shape has the closed form z (q + 2) / (q sqrt(2 q (q + 1))),
-  // q = sqrt(1 + z^2) (half-angle identities with cos(atan z) = 1/q; no
-  // cancellation near 0).  With s = 1 + z^2, 2 q (q + 1) = 2 (s + q), so it
-  // is z (q + 2) (1/q) rsqrt(s + q) / sqrt(2), the 1/sqrt(2) being folded
-  // into k on the host.
+  // tyre shape sin(C atan z) of one axle; its lateral acceleration is
+  // acc_{f,r} times it.  C15: 1 for C = 3/2, 0 for any other C, -1 to read
+  // it off the parameters (the step below decides once per control step, so
+  // the derivatives carry no branch on it).  For C = 3/2 the shape has the
+  // closed form z (q + 2) / (q sqrt(2 q (q + 1))), q = sqrt(1 + z^2)
+  // (half-angle identities with cos(atan z) = 1/q; no cancellation near 0).
+  // With s = 1 + z^2, 2 q (q + 1) = 2 (s + q) and (q + 2) / q = 1 + 2/q, so
+  // it is z (1 + 2u) rsqrt(s + q) / sqrt(2) with u = rsqrt(s) = 1/q; this
+  // returns it without the 1/sqrt(2), which the host folds into acc_{f,r}.
   template <class T, int C15 = -1>
-  __device__ static __forceinline__ T pacejka(const DevParams& p, T z, float k) {
+  __device__ static __forceinline__ T pacejka(const DevParams& p, T z) {
     if (C15 == 1 || (C15 < 0 && p.pacejka_c15)) {
       const T s = vfma(z, z, bc<T>(1.0f));
-      const T u = vmap(s, rsqrt_hw);  // 1 / q, and q = s u
+      const T u = vmap(s, rsqrt_hw);              // 1 / q, and q = s u
       const T w = vmap(vfma(s, u, s), rsqrt_hw);  // rsqrt(s + q)
-      return vmul(vmul(vmul(vmul(bc<T>(k), z), vfma(s, u, bc<T>(2.0f))), u), w);  // ... (q + 2) ...
+      return vmul(vmul(z, vfma(u, bc<T>(2.0f), bc<T>(1.0f))), w);
     }
     const float C = p.mp[5];
-    return vmul(bc<T>(k), vmap(z, [C](float v) { return sinf(C * atanf(v)); }));
+    return vmap(z, [C](float v) { return sinf(C * atanf(v)); });
   }
-  template <class T, int C15 = -1>
+  // f(x, u).  EXACT: the heading's sine and cosine after the full reduction
+  // (the plant, whose heading is never wrapped); otherwise the heading lies
+  // near [-pi, pi] (step_t wraps it once per control step).
+  template <class T, int C15 = -1, bool EXACT = false>
   __device__ static __forceinline__ void deriv(const DevParams& p, const T* x, const CtlT<T>& c, T* f) {
-    const float lf = p.mp[2], lr = p.mp[3], Bt = p.mp[4], vfloor = p.mp[7];
+    const float lf = p.mp[2], lr = p.mp[3], vfloor = p.mp[7];
     const T vx = x[3], vy = x[4], r = x[5];
-    // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx)
-    const T inv_vx = vmap(vx, [vfloor](float v) { return __fdividef(1.0f, fmaxf(v, vfloor)); });
-    T tf, tr;
-    atan_pair<T>(vmul(vfma(bc<T>(lf), r, vy), inv_vx), vmul(vfma(bc<T>(-lr), r, vy), inv_vx), &tf, &tr);
+    // slip angles; the floored vx is positive, so atan2(y, vx) = atan(y / vx).
     // Pacejka arguments B alpha_f = B (steer - atan_f), B alpha_r = -B atan_r
-    const T ay_f = pacejka<T, C15>(p, vfma(bc<T>(-Bt), tf, c.bd), p.acc_f);
-    const T ay_r = pacejka<T, C15>(p, vmul(bc<T>(-Bt), tr), p.acc_r);
+    const T inv_vx = vmap(vx, [vfloor](float v) { return __fdividef(1.0f, fmaxf(v, vfloor)); });
+    T zf, zr;
+    pacejka_args<T>(p, vmul(vfma(bc<T>(lf), r, vy), inv_vx), vmul(vfma(bc<T>(-lr), r, vy), inv_vx), c.bd, &zf, &zr);
+    const T sh_f = pacejka<T, C15>(p, zf), sh_r = pacejka<T, C15>(p, zr);
     T sp, cp;
-    vsincos(x[2], &sp, &cp);
+    if (EXACT) vsincos(x[2], &sp, &cp);
+    else vsincos_near(x[2], &sp, &cp);
     // (negated factors make the products exact negations: a (-b) = -(a b))
     f[0] = vfma(vx, cp, vmul(vneg(vy), sp));
     f[1] = vfma(vx, sp, vmul(vy, cp));
     f[2] = r;
-    const T g = vmul(ay_f, c.cd);  // front force along the body y axis, per unit mass
-    f[3] = vfma(ay_f, c.nsd, vfma(r, vy, c.a));
-    f[4] = vfma(r, vneg(vx), vfma(ay_f, c.cd, ay_r));
-    f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(-p.yaw_r), ay_r));
+    const T g = vmul(sh_f, c.kc);  // front force along the body y axis, per unit mass
+    f[3] = vfma(sh_f, c.kns, vfma(r, vy, c.a));
+    f[4] = vfma(r, vneg(vx), vfma(bc<T>(p.acc_r), sh_r, g));
+    f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(p.nyaw_acc_r), sh_r));
   }
   // one Heun sub-step of size h
-  template <class T, int C15 = -1>
+  template <class T, int C15 = -1, bool EXACT = false>
   __device__ static __forceinline__ void substep_t(const DevParams& p, T* x, const CtlT<T>& c) {
     T k1[6], k2[6], xp[6];
-    deriv<T, C15>(p, x, c, k1);
+    deriv<T, C15, EXACT>(p, x, c, k1);
 #pragma unroll
     for (int i = 0; i < 6; ++i) xp[i] = vfma(bc<T>(p.h), k1[i], x[i]);
-    deriv<T, C15>(p, xp, c, k2);
+    deriv<T, C15, EXACT>(p, xp, c, k2);
     const float hh = 0.5f * p.h;
 #pragma unroll
     for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), vadd(k1[i], k2[i]), x[i]);
   }
-  template <class T>
+  // one control step: the heading wrapped to [-pi, pi] (the state's other
+  // components and every cost are unaffected), then the sub-steps
+  template <class T, bool EXACT = false>
   __device__ static __forceinline__ void step_t(const DevParams& p, T* x, const CtlT<T>& c) {
+    if (!EXACT) x[2] = vwrap(x[2]);
     if (p.pacejka_c15) {
-      for (int s = 0; s < p.substeps; ++s) substep_t<T, 1>(p, x, c);
+      for (int s = 0; s < p.substeps; ++s) substep_t<T, 1, EXACT>(p, x, c);
     } else {
-      for (int s = 0; s < p.substeps; ++s) substep_t<T, 0>(p, x, c);
+      for (int s = 0; s < p.substeps; ++s) substep_t<T, 0, EXACT>(p, x, c);
     }
   }
-  // the derivative with one sample's control quantities
+  // the derivative with one sample's control quantities (heading near [-pi, pi])
   template <class T>
   __device__ static __forceinline__ void deriv(const DevParams& p, const T* x, const float4 c, T* f) {
-    deriv<T>(p, x, ctl_of(c, T{}), f);
+    deriv<T>(p, x, ctl_of(p, c, T{}), f);
   }
+  // one sub-step from a state whose heading is near [-pi, pi]
   __device__ static __forceinline__ void substep(const DevParams& p, float* x, const float4 c) {
-    substep_t<float>(p, x, ctl_of(c, 0.0f));
+    substep_t<float>(p, x, ctl_of(p, c, 0.0f));
   }
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
-    step_t<float>(p, x, ctl_of(c, 0.0f));
+    step_t<float>(p, x, ctl_of(p, c, 0.0f));
+  }
+  // the plant's step: the heading is kept as it is (no wrap) and reduced
+  // exactly inside every derivative
+  __device__ static __forceinline__ void step_exact(const DevParams& p, float* x, const float4 c) {
+    step_t<float, true>(p, x, ctl_of(p, c, 0.0f));
   }
   // two rollouts at once: x[i] = (state i of rollout a, state i of rollout b)
   __device__ static __forceinline__ void step2(const DevParams& p, float2* x, const float4 c) {
-    step_t<float2>(p, x, ctl_of(c, float2{}));
+    step_t<float2>(p, x, ctl_of(p, c, float2{}));
   }
   // one rollout each of two samples: x[i] = (state i under ca, state i under cb)
   __device__ static __forceinline__ void step2x(const DevParams& p, float2* x, const float4 ca, const float4 cb) {
-    step_t<float2>(p, x, ctl_pair(ca, cb));
+    step_t<float2>(p, x, ctl_pair(p, ca, cb));
   }
   __device__ static __forceinline__ float speed(const float* x) { return x[3]; }
 };
@@ -432,6 +493,8 @@ struct Model<2> {  // linear test system x+ = x + h u
   __device__ static __forceinline__ void step(const DevParams& p, float* x, const float4 c) {
     for (int s = 0; s < p.substeps; ++s) substep(p, x, c);
   }
+  // the plant's step (the same: every sub-step reduces the heading itself)
+  __device__ static __forceinline__ void step_exact(const DevParams& p, float* x, const float4 c) { step(p, x, c); }
   __device__ static __forceinline__ float speed(const float*) { return 0.f; }
 };
 

@@ -24,7 +24,7 @@ __global__ void plant_step_kernel(const DevParams p, const float4* __restrict__ 
   for (int i = 0; i < Md::NX; ++i) s[i] = x[i];
   const float u0 = V_plus[0];
   const float u1 = Md::NU > 1 ? V_plus[1] : 0.0f;
-  Md::step(p, s, Md::ctl(p, u0, u1));
+  Md::step_exact(p, s, Md::ctl(p, u0, u1));
   add_process_noise<MODEL>(p, k0, k1, 0u, 0xFFFFFFFEu, 0xFFFFFFFFu, p.instance, s);
   if (MODEL != 2 && collisions != nullptr) {
     bool hit = false;

@@ -44,9 +44,9 @@ __global__ void pair_probe(const uint32_t* words, int n, ramppi::DevParams p, fl
   // the Pacejka shape and one derivative evaluation, scalar and paired
   {
     const float za = 60.0f * ramppi::u01(w[0]) - 30.0f, zb = 60.0f * ramppi::u01(w[1]) - 30.0f;
-    o[24] = Md::pacejka<float>(p, za, p.acc_f);
-    o[25] = Md::pacejka<float>(p, zb, p.acc_f);
-    const float2 pz = Md::pacejka<float2>(p, make_float2(za, zb), p.acc_f);
+    o[24] = Md::pacejka<float>(p, za);
+    o[25] = Md::pacejka<float>(p, zb);
+    const float2 pz = Md::pacejka<float2>(p, make_float2(za, zb));
     o[26] = pz.x;
     o[27] = pz.y;
     float da[6], db[6];

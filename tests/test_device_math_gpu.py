@@ -2,8 +2,10 @@
 
 atan_poly (the slip-angle arctangent) must stay within 3e-7 relative of the
 true arctangent and within 4 float32 ulp of CUDA's atanf, and the paired
-arctangent must give its bits on both of its paths; the closed form of
-sin(1.5 atan z) used by the Pacejka force must agree with CUDA's
+arctangent must give its bits on both of its paths; the Pacejka arguments
+B steer - B atan(y) must agree with float64; the closed form of
+sin(1.5 atan z) used by the Pacejka force (returned without the 1/sqrt(2)
+that the host folds into the axle constants) must agree with CUDA's
 sinf(1.5f * atanf(z)) and with float64 to 1e-6 relative.
 """
 
@@ -37,7 +39,7 @@ def probe(tmp_path_factory):
 
 def _run(lib, z):
     zt = torch.from_numpy(z.astype(np.float32)).cuda()
-    out = torch.empty((z.size, 8), dtype=torch.float32, device="cuda")
+    out = torch.empty((z.size, 10), dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     assert lib.device_math_probe(zt.data_ptr(), z.size, out.data_ptr()) == 0
     return out.cpu().numpy().astype(np.float64)
@@ -72,6 +74,16 @@ def test_atan_pair_paths_are_bitwise_equal(probe):
     np.testing.assert_array_equal(r[:, 4], r[:, 0])
     np.testing.assert_array_equal(r[:, 5], r[:, 6])
     np.testing.assert_array_equal(r[:, 7], r[:, 6])
+
+
+def test_pacejka_arguments(probe):
+    # B = 10, B steer = 0.25: the front argument 0.25 - 10 atan(y), the rear -10 atan(0.5)
+    z = np.concatenate([np.linspace(-4, 4, 200001), np.logspace(-20, 6, 10001),
+                        -np.logspace(-20, 6, 10001)]).astype(np.float32)
+    r = _run(probe, z)
+    exact = 0.25 - 10.0 * np.arctan(z.astype(np.float64))
+    assert np.max(np.abs(r[:, 8] - exact)) < 1e-5
+    assert np.max(np.abs(r[:, 9] + 10.0 * np.arctan(0.5))) < 1e-5
 
 
 @pytest.fixture(scope="module")
