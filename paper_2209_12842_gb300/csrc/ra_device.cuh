@@ -429,17 +429,22 @@ struct Model<1> {  // dynamic single-track with Pacejka lateral tyre forces, Heu
     f[4] = vfma(r, vneg(vx), vfma(bc<T>(p.acc_r), sh_r, g));
     f[5] = vfma(bc<T>(p.yaw_f), g, vmul(bc<T>(p.nyaw_acc_r), sh_r));
   }
-  // one Heun sub-step of size h
+  // one Heun sub-step of size h: x + h/2 k1 + h/2 k2 with k1 = f(x) and
+  // k2 = f(x + h k1), accumulated as (x + h/2 k1) + h/2 k2, so that x and k1
+  // are dead while k2 is formed (fewer live registers than x + h/2 (k1 + k2))
   template <class T, int C15 = -1, bool EXACT = false>
   __device__ static __forceinline__ void substep_t(const DevParams& p, T* x, const CtlT<T>& c) {
-    T k1[6], k2[6], xp[6];
-    deriv<T, C15, EXACT>(p, x, c, k1);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) xp[i] = vfma(bc<T>(p.h), k1[i], x[i]);
-    deriv<T, C15, EXACT>(p, xp, c, k2);
+    T k[6], xp[6];
+    deriv<T, C15, EXACT>(p, x, c, k);
     const float hh = 0.5f * p.h;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), vadd(k1[i], k2[i]), x[i]);
+    for (int i = 0; i < 6; ++i) {
+      xp[i] = vfma(bc<T>(p.h), k[i], x[i]);
+      x[i] = vfma(bc<T>(hh), k[i], x[i]);
+    }
+    deriv<T, C15, EXACT>(p, xp, c, k);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = vfma(bc<T>(hh), k[i], x[i]);
   }
   // one control step: the heading wrapped to [-pi, pi] (the state's other
   // components and every cost are unaffected), then the sub-steps
