@@ -61,6 +61,10 @@ PHILOX_INT = 60  # 10 rounds x (2 wide multiplies, 2 three-input xors, 2 key add
 
 
 DYN_DERIV_FP32 = 1 + 4 + 1 + 18 + 2 + 10 + 1 + 11
+# one obstacle of the softplus barrier (softplus_fast): offsets 2, squared
+# distance 2, distance 2, argument 2, the exponential's scaling 1, the series
+# 5, the logarithm's sum and scaling 2, select, max, sum and accumulation 4
+SOFTPLUS_FP32 = 20
 DYN_SUBSTEP_FP32 = 2 * DYN_DERIV_FP32 + 18
 
 
@@ -134,8 +138,8 @@ def pipe_counts(p, tested=None, ilp=1, paired=False):
         # candidate loop (3 int, shared); the x window's two searches (10 int)
         d["fp32"] += (2 * (ilp - 1) + 8 + 8 * rounds) / ilp + 6 * n_test + 1
         d["int"] += (4 + 4 * rounds + (10 if windowed else 0)) / ilp + 3 * n_test / ilp
-    elif risk_obs and model != 2:  # softplus barrier: per obstacle 10 fp32, sqrt + exp + log
-        d["fp32"] += 10 * n_obs + 1
+    elif risk_obs and model != 2:  # softplus barrier: per obstacle 20 fp32, rsqrt + ex2 + lg2
+        d["fp32"] += SOFTPLUS_FP32 * n_obs + 1
         d["xu"] += 3 * n_obs
     if int(p["risk_mask"]) & ~4:
         d["fp32"] += 8
@@ -146,7 +150,7 @@ def pipe_counts(p, tested=None, ilp=1, paired=False):
     # log + sqrt + sin + cos, 2 conversions), the per-step control
     # quantities, the dynamics, the full running cost (track 6 fp32 + sqrt,
     # deviation, speed, every obstacle) and the control cost
-    n = dict(fp32=11 + step["fp32"] + 6 + 2 + 3 + (6 * n_obs if ind else 10 * n_obs) + 3 + 2,
+    n = dict(fp32=11 + step["fp32"] + 6 + 2 + 3 + (6 * n_obs if ind else SOFTPLUS_FP32 * n_obs) + 3 + 2,
              xu=4 + 2 + step["xu"] + 1 + (0 if ind else 3 * n_obs),
              int=PHILOX_INT + step["int"] + 6)
     n["issue"] = n["fp32"] + n["xu"] + n["int"]

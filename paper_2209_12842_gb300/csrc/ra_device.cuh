@@ -630,6 +630,20 @@ __device__ __forceinline__ float track_s(const DevParams& p, float px, float py)
   return half + kPi * R + S + R * phi;
 }
 
+// softplus(z) = log(1 + exp(z)) = max(z, 0) + log(1 + e), e = exp(-|z|) in
+// (0, 1], from the hardware exponential (relative error about 2^-22) and,
+// for e >= 2^-6, the hardware logarithm of 1 + e (absolute error about 1e-7
+// against a value above 0.0155).  Below 2^-6, where that error would be large
+// against log(1 + e) itself, the series e (1 - e/2 + e^2/3 - e^3/4 + e^4/5),
+// whose first omitted term is below 2^-32 e.  Both are formed and one is
+// selected, so a warp never diverges on it.
+__device__ __forceinline__ float softplus_fast(float z) {
+  const float e = __expf(-fabsf(z));
+  const float ser = e * fmaf(e, fmaf(e, fmaf(e, fmaf(e, 0.2f, -0.25f), 0.333333343f), -0.5f), 1.0f);
+  const float hw = __logf(1.0f + e);
+  return fmaxf(z, 0.0f) + (e < 0.015625f ? ser : hw);
+}
+
 // obstacle term: obstacles are (x, y, r, r^2)
 __device__ __forceinline__ float obstacle_term(const DevParams& p, float px, float py,
                                                const float4* __restrict__ obs, int n_obs) {
@@ -644,9 +658,9 @@ __device__ __forceinline__ float obstacle_term(const DevParams& p, float px, flo
     for (int i = 0; i < n_obs; ++i) {
       const float4 o = obs[i];
       const float dx = px - o.x, dy = py - o.y;
-      const float z = p.kappa * (o.z - sqrtf(fmaf(dx, dx, dy * dy)));
-      const float sp = z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
-      acc += sp;
+      const float d2 = fmaf(dx, dx, dy * dy);
+      const float d = d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f;
+      acc += softplus_fast(p.kappa * (o.z - d));
     }
     acc *= p.inv_kappa;
   }
