@@ -604,10 +604,24 @@ def cpu_baseline(p, x0, V, obs, threads, seconds):
         spent += time.perf_counter() - t0
         reps += 1
     rate = reps * len(ks) * M * T / spent
+    # the same oracle on one core, over K/1024 of the samples for about a
+    # fifth of the time
+    ks1 = ks[: max(1, K // 1024)]
+    reps1, spent1 = 0, 0.0
+    while spent1 < seconds / 5 or reps1 == 0:
+        t0 = time.perf_counter()
+        out = oracle.samples(p, x0, V, obs, ks=ks1, iteration=reps1, n_threads=1)
+        oracle.update(out["S_tilde"], out["U"], float(np.float32(p["lam"])))
+        spent1 += time.perf_counter() - t0
+        reps1 += 1
+    rate1 = reps1 * len(ks1) * M * T / spent1
     return {"value": rate, "unit": "rollout-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(ks)} of {K} samples (K/64) x M={M} x T={T}, {reps} updates in {spent:.1f} s "
                       f"(FP64 C oracle, OpenMP over samples); the full update extrapolates to "
-                      f"{K * M * T / rate:.1f} s"}
+                      f"{K * M * T / rate:.1f} s",
+            "single_thread": {"value": rate1, "unit": "rollout-steps/s", "cores": 1,
+                              "sample": f"{len(ks1)} of {K} samples (K/1024) x M={M} x T={T}, {reps1} updates "
+                                        f"in {spent1:.1f} s on one core"}}
 
 
 def roofline_summary(m):

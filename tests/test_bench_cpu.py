@@ -80,3 +80,16 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["K"] == 256 and line["config"]["M"] == 32
+
+
+def test_cpu_baseline_reports_all_cores_and_one():
+    import bench
+
+    p = rs.preset("c1_plain")
+    obs = rs.scene_obstacles(p)
+    x0 = rs.initial_state(int(p["model"]))
+    V = rs.random_controls(int(p["model"]), int(p["T"]), p["u_lo"], p["u_hi"], 3)
+    cb = bench.cpu_baseline(p, x0, V, obs, 2, 0.5)
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] > 0
+    st = cb["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and st["unit"] == cb["unit"]
