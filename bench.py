@@ -851,6 +851,7 @@ def adjoint_study(torch, steps, rates=None):
     gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 11)
     gVp, gS = torch.from_numpy(gVp).cuda(), torch.from_numpy(gS).cuda()
     stream = torch.cuda.current_stream()
+    ctl.tune(x0, V)  # the forward's launch shape (the adjoint reads the same checkpoints for any shape)
     f50, f99 = ev_time(torch, lambda: ctl.step(x0, V), steps, stream)
     ctl.step(x0, V)
     b50, b99 = ev_time(torch, lambda: ctl.backward(gVp, gS), steps, stream)
@@ -864,11 +865,13 @@ def adjoint_study(torch, steps, rates=None):
         kms.append(kb.elapsed_time(ke))
     torch.cuda.nvtx.range_pop()
     ctl.set_timing_events(None)
+    ctl_launch = ctl.get_launch()
     ctl.close()
     units = p["K"] * p["M"] * p["T"]
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
     roof = adjoint_roofline(p, float(np.median(kms)) / 1e3, rates, n_sms, 2070.0)
-    return {"forward_p50_ms": f50, "forward_p99_ms": f99, "backward_p50_ms": b50, "backward_p99_ms": b99,
+    return {"forward_p50_ms": f50, "forward_p99_ms": f99, "forward_launch": list(ctl_launch),
+            "backward_p50_ms": b50, "backward_p99_ms": b99,
             "backward_rollout_steps_per_s": units / b50 * 1e3, "roofline": roof}
 
 

@@ -36,7 +36,7 @@ static_assert(kNaMaxBlocks <= ramppi::kSoftminMaxBlocks, "the merge rescales eve
 // the call.  About 130 KB per device.
 static __device__ __align__(256) float g_noalloc_scratch[kNaFloats];
 
-__global__ void __launch_bounds__(ramppi::kSoftminThreads)
+__global__ void __launch_bounds__(ramppi::kSoftminThreads, 2)
 softmin_update_noalloc_kernel(const float* __restrict__ S_tilde, const float* __restrict__ U, int K, int TN,
                               float inv_lambda, float* __restrict__ V_out, float* scratch) {
   __shared__ SoftminShared sh;

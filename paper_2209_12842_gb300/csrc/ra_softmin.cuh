@@ -23,6 +23,13 @@ constexpr int kSoftminWarps = kSoftminThreads / 32;
 constexpr int kSoftminMaxCols = 512;       // T nu (RA_MPPI_MAX_T x 2)
 constexpr int kSoftminMaxBlocks = 256;     // blocks that one merge can rescale
 constexpr int kSoftminColChunks = kSoftminMaxCols / 32;
+// Loads in flight before their sums: U rows per warp in the block partials
+// (RIF) and partials per column in the merge (MIF).  More in flight shortens
+// a single problem's update, a latency-bound launch of a few blocks; the
+// batched update, many blocks at once, keeps the smaller counts and the
+// registers they need.  The order of every sum is the same for any count.
+constexpr int kRowsInFlight = 8, kMergeInFlight = 16;
+constexpr int kBatchRowsInFlight = 4, kBatchMergeInFlight = 8;
 
 // Shared memory of one block of a softmin update.
 struct SoftminShared {
@@ -80,8 +87,11 @@ __device__ __forceinline__ double softmin_block_sum(double v, double* red) {
 // The partials (m_b, s_b, y_b[TN]) of samples [kb, ke) into part[2 + TN],
 // given the block minimum mb of their finite S~.  Threads take samples
 // k0 + threadIdx.x, k0 = kb, kb + blockDim, ...; warps take rows of each
-// chunk of blockDim samples and lanes the columns l, l + 32, ..., four rows
-// in flight.  Called by all threads of a block of kSoftminThreads.
+// chunk of blockDim samples and lanes the columns l, l + 32, ..., RIF
+// rows in flight (a warp adds its rows w, w + 8, w + 16, ... in that order
+// whatever the number in flight).  Called by all threads of a block of
+// kSoftminThreads.
+template <int RIF = kRowsInFlight>
 __device__ __forceinline__ void softmin_block_partials(const float* __restrict__ S_tilde,
                                                        const float* __restrict__ U, int kb, int ke, int TN,
                                                        float inv_lambda, float mb, float* part,
@@ -103,11 +113,11 @@ __device__ __forceinline__ void softmin_block_partials(const float* __restrict__
     neumaier_add(s_sum, s_comp, e);
     __syncthreads();
     const int n = min((int)blockDim.x, ke - k0);
-    for (int i0 = warp; i0 < n; i0 += 4 * kSoftminWarps) {
-      float ev[4];
-      const float* rows[4];
+    for (int i0 = warp; i0 < n; i0 += RIF * kSoftminWarps) {
+      float ev[RIF];
+      const float* rows[RIF];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < RIF; ++u) {
         const int i = i0 + u * kSoftminWarps;
         ev[u] = i < n ? sh.e[i] : 0.0f;
         rows[u] = U + (size_t)(k0 + (i < n ? i : 0)) * TN;
@@ -116,11 +126,11 @@ __device__ __forceinline__ void softmin_block_partials(const float* __restrict__
       for (int j = 0; j < kSoftminColChunks; ++j) {
         const int col = lane + 32 * j;
         if (j < nj && col < TN) {
-          float v[4];
+          float v[RIF];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = ev[u] != 0.0f ? rows[u][col] : 0.0f;
+          for (int u = 0; u < RIF; ++u) v[u] = ev[u] != 0.0f ? rows[u][col] : 0.0f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < RIF; ++u)
             if (ev[u] != 0.0f) neumaier_add(y_sum[j], y_comp[j], ev[u] * v[u]);
         }
       }
@@ -171,6 +181,7 @@ __device__ __forceinline__ bool softmin_arrive_last(unsigned int* arrive, int nb
 // The other blocks' partials are read through L2 (ld.global.cg): they were
 // stored before those blocks' fence and arrival, and L1 may hold nothing
 // newer; unlike volatile loads these can be in flight together.
+template <int MIF = kMergeInFlight>
 __device__ __forceinline__ bool softmin_merge(const float* parts, int nb, int TN, float inv_lambda,
                                               float* __restrict__ V_out, float* m_out, double* s_out,
                                               SoftminShared& sh) {
@@ -191,7 +202,7 @@ __device__ __forceinline__ bool softmin_merge(const float* parts, int nb, int TN
   const bool ok = isfinite(m) && s_tot > 0.0 && isfinite(s_tot);
   for (int col = threadIdx.x; col < TN; col += blockDim.x) {
     float y = 0.0f, yc = 0.0f;
-#pragma unroll 8
+#pragma unroll MIF
     for (int b = 0; b < nb; ++b) {
       const float sc = sh.scale[b];
       const float v = __ldcg(parts + (size_t)b * stride + 2 + col);

@@ -25,6 +25,8 @@ __device__ __forceinline__ float s_tilde_of(const DevParams& p, float S, float c
 
 // One block of the update of one problem: `block` of `nblocks` blocks that
 // share the problem's samples, partials and arrival counter.
+// RIF, MIF: loads in flight in the partials and the merge (ra_softmin.cuh).
+template <int RIF, int MIF>
 __device__ __forceinline__ void update_block(const DevParams& p, const UpdateArgs& a, int K, int TN, int block,
                                              int nblocks) {
   __shared__ SoftminShared sh;
@@ -43,11 +45,11 @@ __device__ __forceinline__ void update_block(const DevParams& p, const UpdateArg
   }
   const float mb = softmin_block_min(mloc, sh.red);
   // each thread reads back only the S~ it wrote above (same sample mapping)
-  softmin_block_partials(a.S_tilde, a.U, kb, ke, TN, p.inv_lambda, mb, a.partials + (size_t)block * (2 + TN), sh);
+  softmin_block_partials<RIF>(a.S_tilde, a.U, kb, ke, TN, p.inv_lambda, mb, a.partials + (size_t)block * (2 + TN), sh);
   if (!softmin_arrive_last(&a.st->arrive, nblocks, sh)) return;
   float m;
   double s_tot;
-  const bool ok = softmin_merge(a.partials, nblocks, TN, p.inv_lambda, a.V_out, &m, &s_tot, sh);
+  const bool ok = softmin_merge<MIF>(a.partials, nblocks, TN, p.inv_lambda, a.V_out, &m, &s_tot, sh);
   if (threadIdx.x == 0) {
     if (!ok) atomicOr(&a.st->status, kStatusNoWeight);
     a.st->last_min = m;
@@ -57,8 +59,8 @@ __device__ __forceinline__ void update_block(const DevParams& p, const UpdateArg
   }
 }
 
-__global__ void __launch_bounds__(kUpdateThreads) softmin_update_kernel(const DevParams p, const UpdateArgs a) {
-  update_block(p, a, p.K, p.T * p.nu, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kUpdateThreads, 2) softmin_update_kernel(const DevParams p, const UpdateArgs a) {
+  update_block<kRowsInFlight, kMergeInFlight>(p, a, p.K, p.T * p.nu, blockIdx.x, gridDim.x);
 }
 
 // Updates of B problems in one launch: problem i owns blocks
@@ -79,7 +81,8 @@ __global__ void __launch_bounds__(kUpdateThreads) batch_update_kernel(const DevP
   a.V_out = b.V_out + d.V_off;
   a.partials = b.partials + d.part_off;
   a.st = b.st + lo;
-  update_block(p, a, d.K, d.T * p.nu, (int)blockIdx.x - d.upd_block_base, d.nb_upd);
+  update_block<kBatchRowsInFlight, kBatchMergeInFlight>(p, a, d.K, d.T * p.nu, (int)blockIdx.x - d.upd_block_base,
+                                                        d.nb_upd);
 }
 
 cudaError_t launch_batch_update(const DevParams& p, const BatchUpdateArgs& a, int nblocks, cudaStream_t s) {
