@@ -219,6 +219,39 @@ def test_adjoint_is_deterministic(K):
     assert np.all(np.isfinite(runs[0][0])) and np.all(np.isfinite(runs[0][1]))
 
 
+@pytest.mark.parametrize("model", [0, 1])
+def test_adjoint_does_not_depend_on_the_forward_launch(model):
+    """The forward stores the same state checkpoints for any launch shape, so
+    the backward gives the same bits whichever shape the forward ran (the
+    benchmark tunes config 4's forward)."""
+    from paper_2209_12842_gb300 import RaMppi
+
+    if model == 0:
+        p = rs.preset("c4_gradient", K=200, M=64, T=17)
+        obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.05, x_to=0.9, lateral=0.4)
+        x0 = torch.tensor([0.0, -4.0, 0.0, 1.0], device="cuda")
+    else:
+        p = rs.preset("small_dyn", K=70, M=64, T=11)
+        obs = rs.obstacles_ahead(1, 8, 0.15, 0.3, x_from=0.3, x_to=2.5)
+        x0 = torch.from_numpy(rs.initial_state(1)).cuda()
+    V = torch.from_numpy(rs.random_controls(model, p["T"], p["u_lo"], p["u_hi"], 3)).cuda()
+    gVp, gS = rs.random_cotangents(p["T"], 2, p["K"], 7)
+    gVp, gS = torch.from_numpy(gVp).cuda(), torch.from_numpy(gS).cuda()
+    outs = []
+    for launch in [(4, 1, 1), (2, 2, 1), (8, 1, 2), (2, 1, 2)]:
+        ctl = RaMppi(p, obs, differentiable=True)
+        ctl.set_launch(*launch)
+        ctl.iteration = 0
+        Vp = ctl.step(x0, V)
+        gV, gth = ctl.backward(gVp, gS)
+        outs.append((Vp.cpu().numpy(), gV.cpu().numpy(), gth.cpu().numpy()))
+        assert ctl.status() == 0
+        ctl.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            np.testing.assert_array_equal(a, b)
+
+
 def test_adjoint_rejects_missing_flag():
     from paper_2209_12842_gb300 import RaMppi, RaMppiError
 

@@ -120,7 +120,7 @@ def _tuned_ctl(p, obs, x0, V):
     return ctl, x0t, Vt
 
 
-@pytest.mark.parametrize("M,alpha", [(32, 0.8), (256, 0.95)])
+@pytest.mark.parametrize("M,alpha", [(32, 0.8), (64, 0.8), (128, 0.95), (256, 0.95)])
 def test_config5_full_size_sampled(M, alpha):
     """Config 5 at full size in the launch shape the tuner picks (the one the
     benchmark times): 64 sampled k spread over every wave of that launch,
