@@ -49,11 +49,14 @@ __host__ __device__ inline int batch_warp_f4(int obs_cap_max, int T_max, int M_m
 }
 
 // IS: importance-sampled rollouts (a separate instantiation).  At least 3
-// blocks of 256 threads per SM, as the single-problem kernel: 80 registers,
-// 24 resident warps per SM (108 registers and 16 warps without the bound;
-// config 3's round 20.05 -> 19.29 ms).
+// blocks of 256 threads per SM for the dynamic model, as the single-problem
+// kernel: 80 registers, 24 resident warps per SM.  The lighter kinematic and
+// linear models fit 64 registers (the importance-sampled instances with a few
+// bytes of spill), so they take 4 blocks: 32 resident warps per SM.  (The
+// kinematic kernel without a bound took 108 registers and 16 warps; config
+// 3's round went 20.05 -> 19.29 ms at 80 registers.)
 template <int MODEL, int ILP, bool IS = false>
-__global__ void __launch_bounds__(256, 3) batch_rollout_kernel(const DevParams p, const BatchArgs a) {
+__global__ void __launch_bounds__(256, MODEL == 1 ? 3 : 4) batch_rollout_kernel(const DevParams p, const BatchArgs a) {
   extern __shared__ float4 smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4* base = smem + (size_t)w * batch_warp_f4(a.obs_cap_max, a.T_max, a.M_max, IS);

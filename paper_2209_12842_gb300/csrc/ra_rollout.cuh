@@ -712,9 +712,11 @@ __device__ __forceinline__ void disturbed_sample_pair(const DevParams& p, const 
 // (at least 3 blocks of 256 threads per SM: 80 registers, 24 resident warps
 // per SM; without the bound the register count of some instances drifts
 // between 64 and 128 with each code change, and the measured kernels are
-// fastest at 80)
+// fastest at 80.  The two-samples-per-warp instance fits 64 registers
+// without spilling, so it takes 4 blocks: 32 resident warps per SM, config
+// 5 at M = 32 4.07 -> 3.97 ms; the others spill at 64 and slow down.)
 template <int MODEL, int ILP, bool PAIRS = false, bool IS = false, bool WIN = false, bool CK = false>
-__global__ void __launch_bounds__(256, 3) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
+__global__ void __launch_bounds__(256, PAIRS ? 4 : 3) rollout_cvar_kernel(const DevParams p, const RolloutArgs a) {
   extern __shared__ float4 smem[];
   // WIN: smem[0].x holds the largest obstacle radius and the obstacles start
   // at smem[1]; otherwise at smem[0].  The samples' controls, costs (and

@@ -132,6 +132,7 @@ def test_config5_full_size_sampled(M, alpha):
     V = rs.random_controls(p["model"], p["T"], p["u_lo"], p["u_hi"], 9)
     ctl, x0t, Vt = _tuned_ctl(p, obs, x0, V)
     warps, ilp, wps = ctl.get_launch()
+    blocks_per_sm = ctl.launch_plan()[3]
     ctl.iteration = 0
     Vp = ctl.step(x0t, Vt)
     ws = ctl.workspace()
@@ -141,10 +142,11 @@ def test_config5_full_size_sampled(M, alpha):
     assert ctl.status() == 0
     ctl.close()
     K = p["K"]
-    # samples per wave: resident warps of the GPU (24 per SM at the kernel's
-    # 80 registers) over warps per sample, two samples per warp when paired
+    # samples per wave: resident warps of the GPU (the launch's blocks per SM
+    # times its warps per block) over warps per sample, two samples per warp
+    # when paired
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
-    per_wave = n_sms * 24 // wps * (2 if (M <= 32 and ilp == 2 and wps == 1) else 1)
+    per_wave = n_sms * blocks_per_sm * warps // wps * (2 if (M <= 32 and ilp == 2 and wps == 1) else 1)
     waves = -(-K // per_wave)
     rng = np.random.default_rng(M)
     ks = [int(rng.integers(w * per_wave, min(K, (w + 1) * per_wave))) for w in range(waves)]
