@@ -373,7 +373,8 @@ def config_dict(p, args, reference=False):
                      f"one RA-MPPI update (ra_mppi_step: sampling, nominal and disturbed rollouts, CVaR, "
                      f"softmin update) of the state that an untimed {args.preroll}-iteration receding-horizon "
                      f"pre-roll from the track origin reaches"),
-            "l2": "flushed before every timed step (256 MB write, outside the step's events)"}
+            "l2": ("not applicable: the oracle runs on the host cores" if reference else
+                   "flushed before every timed step (256 MB write, outside the step's events)")}
 
 
 # ---------------------------------------------------------------- GPU arm

@@ -297,6 +297,21 @@ def test_linear_gaussian_cvar_statistics():
     np.testing.assert_allclose(g["S"], mu, rtol=1e-6)
 
 
+def test_create_binds_the_requested_device():
+    """ra_mppi_create takes a device index (-1: the current device); an index
+    past the device count, or below -1, is refused with EINVAL."""
+    from paper_2209_12842_gb300 import binding as B
+
+    prob = B.ra_mppi_problem_from(rs.preset("small_kin"), max_obstacles=1)
+    for dev in (-1, torch.cuda.current_device()):
+        h = B.ra_mppi_create(prob, dev)
+        B.ra_mppi_destroy(h)
+    for dev in (torch.cuda.device_count(), -2):
+        with pytest.raises(B.RaMppiError) as e:
+            B.ra_mppi_create(prob, dev)
+        assert e.value.code == B.RA_MPPI_EINVAL
+
+
 def test_step_host_matches_step():
     from paper_2209_12842_gb300 import RaMppi
 
