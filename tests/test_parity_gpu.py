@@ -120,6 +120,34 @@ def _tuned_ctl(p, obs, x0, V):
     return ctl, x0t, Vt
 
 
+def test_paper_preset_full_size_tuned():
+    """The paper's simulation preset at full size (K = 1024, M = 300,
+    T = 30: ten rows of rollouts per sample, the last one partly filled) in
+    the launch shape the tuner picks, as the benchmark times it: 46 sampled
+    k spread over the launch, the first and last included."""
+    p = rs.preset("paper_sim")
+    obs = rs.scene_obstacles(p)
+    obs = np.concatenate([obs, np.array([[0.25, -0.3, 0.1], [0.45, -0.2, 0.1]], np.float32)])
+    p["n_obs"] = len(obs)
+    x0 = rs.scene_initial_state(p)
+    V = rs.random_controls(1, p["T"], p["u_lo"], p["u_hi"], 9)
+    ctl, x0t, Vt = _tuned_ctl(p, obs, x0, V)
+    launch = ctl.get_launch()
+    ctl.iteration = 0
+    Vp = ctl.step(x0t, Vt)
+    ws = ctl.workspace()
+    torch.cuda.synchronize()
+    g = dict(V_plus=Vp.cpu().numpy(), S_tilde=ctl.S_tilde.cpu().numpy(), cvar=ctl.cvar.cpu().numpy(),
+             U=ws["U"].cpu().numpy(), S=ws["S"].cpu().numpy(), L=None)
+    assert ctl.status() == 0
+    ctl.close()
+    K = p["K"]
+    ks = np.unique(np.concatenate([[0, 1, K - 2, K - 1], np.linspace(0, K - 1, 44).astype(int)])).astype(np.int32)
+    ref = oracle.samples(p, x0, V, obs, ks=ks, n_threads=os.cpu_count() or 8)
+    nS, nC, nT = compare(p, g, ref)
+    print(f"paper preset: launch {launch}, {len(ks)} sampled k; banded S {nS}, CVaR {nC}, S~ {nT}")
+
+
 @pytest.mark.parametrize("M,alpha", [(32, 0.8), (64, 0.8), (128, 0.95), (256, 0.95)])
 def test_config5_full_size_sampled(M, alpha):
     """Config 5 at full size in the launch shape the tuner picks (the one the
