@@ -717,14 +717,17 @@ def closed_loop_study(torch, n_updates, preset="c2_closed_loop", runs=None, seed
     MPPI (A = 0) and RA-MPPI, each over the same obstacle field with several
     noise seeds (the counts of one 1000-update run vary a lot with the
     noise).  Config 2 compares alpha in {0.5, 0.9, 0.99} with its risk cost
-    l = obstacle term."""
+    l = obstacle term, and alpha in {0.5, 0.9} with l = obstacle term +
+    squared deviation from the centreline at A = 3 (a risk cost that sees
+    the track edges, which the obstacle term does not)."""
     from paper_2209_12842_gb300 import RaMppi
 
     p0 = rs.preset(preset)
     obs = rs.scene_obstacles(p0)
     out = {"preset": preset, "updates": n_updates, "seeds": list(seeds)}
     if runs is None:
-        runs = [("mppi", dict(A=0.0))] + [(f"ra_alpha{a}", dict(alpha=a)) for a in (0.5, 0.9, 0.99)]
+        runs = [("mppi", dict(A=0.0))] + [(f"ra_alpha{a}", dict(alpha=a)) for a in (0.5, 0.9, 0.99)] + \
+            [(f"ra_alpha{a}_obs_dev_A3", dict(alpha=a, A=3.0, risk_mask=rs.RISK_OBS | rs.RISK_DEV)) for a in (0.5, 0.9)]
     for name, ov in runs:
         hits_per_seed, exits_per_seed, hz, status = [], [], None, 0
         for seed in seeds:
